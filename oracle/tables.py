@@ -1,0 +1,69 @@
+"""Stiffness lookup table mat[K] (eq. 49-52, 56-57) by Gauss quadrature over micro elements.
+
+  T[m, C, i, j] = int_{Omega_T} d/dxi_i (R_A o T^r^-1) * d/dxi_j (R_B o T^r^-1) * N_C dxi,
+
+for every pair m = (A, B) of I_coo (eq. 56).  Each micro element is a box of a
+patch; on it xi = lo + (hi - lo) theta, so d/dxi_i = (1/(hi-lo)_i) d/dtheta_i and
+dxi = prod(hi - lo) dtheta.  The integrand is a polynomial on the element, of
+degree at most 2 p_T + q per direction, so an n_g-point rule with
+2 n_g - 1 >= 2 p_T + q integrates it exactly ("accurate enough numerical
+integration", eq. 52).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import quadrature
+
+
+def default_gauss_points(p_T: int, q: int) -> int:
+    return (2 * p_T + q + 2) // 2
+
+
+def build_table(tile, q: int, n_g: int | None = None) -> np.ndarray:
+    """mat[K] as an array (n_nz, (q+1)^3, 3, 3)."""
+    p_T = max(max(P["degree"]) for P in tile.patches)
+    n_g = n_g or default_gauss_points(p_T, q)
+    n_pi = (q + 1) ** 3
+    T = np.zeros((tile.n_nz, n_pi, 3, 3))
+    g1, w1 = quadrature.gauss_legendre(n_g)
+    for el in tile.elements:
+        P = tile.patches[el["patch"]]
+        lo, hi = P["lo"], P["hi"]
+        # element Gauss points in the patch parameter theta
+        pts = [el["th_lo"][d] + (el["th_hi"][d] - el["th_lo"][d]) * g1 for d in range(3)]
+        wts = [(el["th_hi"][d] - el["th_lo"][d]) * w1 for d in range(3)]
+        theta = np.array([(a, b, c) for c in pts[2] for b in pts[1] for a in pts[0]])
+        wgt = np.array([wa * wb * wc for wc in wts[2] for wb in wts[1] for wa in wts[0]])
+        wgt = wgt * np.prod(hi - lo)                    # |det J_{T^r}| for the affine patch
+        xi = lo + (hi - lo) * theta
+        _, grads = tile.patch_basis(el["patch"], theta)  # (g, nf, 3) in theta
+        nf = P["nfun"]
+        cols = [a1 + nf[0] * (a2 + nf[1] * a3) for (a1, a2, a3) in el["loc"]]
+        dphi = grads[:, cols, :] / (hi - lo)            # (g, 27, 3) d/dxi
+        NC = quadrature.tensor_lagrange(q, xi)          # (g, n_pi)
+        # local contribution Tloc[a, b, C, i, j] = sum_g w dphi[g,a,i] dphi[g,b,j] N_C
+        Tloc = np.einsum("g,gai,gbj,gc->abcij", wgt, dphi, dphi, NC, optimize=True)
+        ids = el["ids"]
+        for a, A in enumerate(ids):
+            for b, B in enumerate(ids):
+                if A <= B:
+                    T[tile.pair_index[(A, B)]] += Tloc[a, b]
+    return T
+
+
+def volume_table(tile, q: int, n_g: int | None = None) -> np.ndarray:
+    """t^h of eq. 18 for the projection basis N_C: t_C = int_{Omega_T} N_C dxi."""
+    p_T = max(max(P["degree"]) for P in tile.patches)
+    n_g = n_g or default_gauss_points(p_T, q)
+    g1, w1 = quadrature.gauss_legendre(n_g)
+    t = np.zeros((q + 1) ** 3)
+    for el in tile.elements:
+        P = tile.patches[el["patch"]]
+        lo, hi = P["lo"], P["hi"]
+        pts = [el["th_lo"][d] + (el["th_hi"][d] - el["th_lo"][d]) * g1 for d in range(3)]
+        wts = [(el["th_hi"][d] - el["th_lo"][d]) * w1 for d in range(3)]
+        theta = np.array([(a, b, c) for c in pts[2] for b in pts[1] for a in pts[0]])
+        wgt = np.array([wa * wb * wc for wc in wts[2] for wb in wts[1] for wa in wts[0]]) * np.prod(hi - lo)
+        t += wgt @ quadrature.tensor_lagrange(q, lo + (hi - lo) * theta)
+    return t
