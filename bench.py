@@ -1,0 +1,359 @@
+"""Throughput of the multiscale lookup-table stiffness assembly on one GB300.
+
+One step = one full assembly of the workload's global CSR stiffness through the
+C ABI: pullback + interpolation of the macro field (step 1), the table contraction
+(step 3, eq. 58) and the CSR scatter (step 4), all tiles, inputs resident in HBM.
+
+Default workload: the 10x10x10 twisted beam (1000 tiles, cross cell with 3x3x3
+elements per patch, q = 3), FP64 form.  Prints ONE JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--precision f64|f32|...] [--workload beam1000|...]
+
+--impl reference times the FP64 CPU oracle (the only baseline there is: the
+paper's code is not available) on a bounded sample of tiles per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "tiles/s and stiffness GB/s vs FP64 GPU lookup form at stated rel. error"
+WORKLOAD_TEXT = {
+    "beam1000": "twisted beam 10x10x10 tiles (90-degree twist), cross cell 7 patches x 3^3 degree-2 elements, "
+                "q=3 (64 nodes), E=1 nu=0.3",
+    "cube8": "perturbed cubic cube split 2x2x2, cross cell 7 patches x 2^3 elements, q=2",
+    "beam4000": "twisted beam 40x10x10 tiles, cross cell n_e=3, q=3",
+    "cantilever2000": "cantilever plate 20x20x5 tiles, cross cell n_e=2, q=3",
+    "arc2000": "quarter arc 20x10x10 tiles, cross cell n_e=3, q=3 (uniform width 0.3)",
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="f64")
+    ap.add_argument("--workload", default="beam1000")
+    ap.add_argument("--forms", default="f32", help="comma list of extra precision forms to report")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"msasm_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1])); smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# FP64 CUDA-core peak: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz (GB300 FP64 is 1/64 of B200's per SM)
+FP64_ALU_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def contraction_flops(n_nz, n_pi, n_tiles):
+    return 2.0 * n_nz * 9 * n_pi * 9 * n_tiles
+
+
+def cpu_reference_time(workload, n_sample, seed=0):
+    """FP64 oracle (lookup form: pullback, contraction, scatter) on a sample of tiles; returns (s, tiles)."""
+    import synth
+    from oracle.assembly import Problem, nzdata_lookup, scatter_csr
+    w = synth.workload(workload)
+    prob = Problem(synth.micro_cross(w.n_e), w.macro, w.q, structure=False)
+    rng = np.random.default_rng(seed)
+    tiles = np.sort(rng.choice(prob.mmap.n_tiles, min(n_sample, prob.mmap.n_tiles), replace=False))
+    t0 = time.perf_counter()
+    nz = nzdata_lookup(prob.T, prob.mmap, prob.q, prob.lam, prob.mu, tiles=list(tiles))
+    # step 4 for the sample: the values land in a COO stream with global (row, col) of every entry
+    P = prob.tile.pairs
+    total = 0.0
+    for k, t in enumerate(tiles):
+        g = prob.gmap[t]
+        rows = 3 * g[P[:, 0]][:, None, None] + np.arange(3)[None, :, None]
+        cols = 3 * g[P[:, 1]][:, None, None] + np.arange(3)[None, None, :]
+        keys = np.broadcast_to(rows * 10 ** 9 + cols, nz[k].shape)
+        order = np.argsort(keys, axis=None)
+        total += float(np.take(nz[k].ravel(), order).sum())
+    dt = time.perf_counter() - t0
+    return dt, len(tiles)
+
+
+def threads_used():
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        return max((i.get("num_threads", 1) for i in info), default=os.cpu_count())
+    except Exception:
+        return os.cpu_count()
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    per_step = 16 if args.workload in ("beam1000", "beam4000", "arc2000") else 8
+    for _ in range(args.warmup):
+        cpu_reference_time(args.workload, max(2, per_step // 4))
+    times, tiles = [], 0
+    for k in range(args.steps):
+        dt, n = cpu_reference_time(args.workload, per_step, seed=k)
+        times.append(dt)
+        tiles += n
+    total = sum(times)
+    value = tiles / total
+    cores = threads_used()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "tiles/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "text": WORKLOAD_TEXT.get(args.workload, ""),
+                       "parallelism": "host cores (numpy/BLAS)"},
+            "cpu_baseline": {"value": value, "unit": "tiles/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} random tiles per step, FP64 lookup form "
+                                       "(pullback, contraction, per-tile scatter ordering)"},
+            "e2e": {"value": value, "unit": "tiles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import paper_2107_09568_gb300 as msasm
+    import synth
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    msasm.load()
+
+    w = synth.workload(args.workload)
+    micro = synth.micro_cross(w.n_e, w.width)
+    tab = msasm.Tables(micro, w.q)
+    plan = msasm.Plan(tab, w.macro)
+    ctrl = torch.tensor(w.macro.ctrl, dtype=torch.float64, device="cuda")
+    prec = args.precision
+    out = torch.empty(plan.nnz, dtype=msasm.Plan.value_dtype(prec), device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    stream = torch.cuda.current_stream()
+
+    # correctness of the timed configuration: degenerate check + translation residual
+    plan.assemble(ctrl, 1.0, 0.3, prec, out=out, check_degenerate=True)
+    for _ in range(args.warmup):
+        flush.zero_()
+        plan.assemble(ctrl, 1.0, 0.3, prec, out=out, stage_times=True)
+    torch.cuda.synchronize()
+
+    clocks = Clocks(local)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    step_ms, stage_ms, launches = [], np.zeros(3), 0
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()                                  # L2 flush between timed steps (not timed)
+        ev[k][0].record(stream)
+        plan.assemble(ctrl, 1.0, 0.3, prec, out=out, stage_times=True)
+        ev[k][1].record(stream)
+        ms, ln = plan.stage_times()                    # events recorded inside the call, same stream
+        stage_ms += np.array(ms)
+        launches += sum(ln)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(step_ms))
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    n_tiles = plan.n_tiles * world
+    value = n_tiles * args.steps / (total_ms / 1e3)
+    vbytes = 8 if prec in ("f64", "f64_emu") else 4
+    stiff_gbs = plan.nnz * vbytes * world * args.steps / (total_ms / 1e3) / 1e9
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    pk, pk_kind = peaks()
+    stage_avg = stage_ms / args.steps
+    names = ["pullback", "contraction", "scatter"]
+    dom = int(np.argmax(stage_avg))
+    K = 9 * tab.n_pi
+    flops = contraction_flops(tab.n_nz, tab.n_pi, plan.n_tiles)
+    nz_bytes = 9 * plan.n_tiles * tab.n_nz * vbytes
+    scatter_bytes = nz_bytes + plan.n_tiles * tab.n_nz * 4 + plan.nnz * vbytes   # nz read, rank map, values write
+    pull_bytes = 9 * plan.n_tiles * K * 8
+    if names[dom] == "contraction" and prec in ("f64", "f32"):
+        alu_peak = FP64_ALU_PEAK_TFLOPS if prec == "f64" else FP32_ALU_PEAK_TFLOPS
+        ach = flops / (stage_avg[1] / 1e3) / 1e12
+        roof = {"kernel": f"contract_simt_{prec}", "bound": "alu", "achieved": ach, "peak": alu_peak,
+                "unit": "TFLOP/s", "frac": ach / alu_peak, "traffic": None,
+                "peak_source": "derived: 152 SMs x lanes x 2 flop x 2.07 GHz (DESIGN.md)",
+                "algorithmic": f"2*n_nz*9n_pi*9m = {flops:.4g} flop per launch"}
+    elif names[dom] == "contraction":
+        peak = pk["bf16_tflops_sustained"]
+        ach = flops / (stage_avg[1] / 1e3) / 1e12
+        roof = {"kernel": f"contract_{prec}", "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None, "peak_source": pk_kind}
+    else:
+        byts = scatter_bytes if dom == 2 else pull_bytes
+        ach = byts / (stage_avg[dom] / 1e3) / 1e9
+        roof = {"kernel": names[dom], "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / pk["hbm_gbs"], "traffic": None, "peak_source": pk_kind}
+    roof["stages_ms"] = dict(zip(names, [round(x, 4) for x in stage_avg]))
+    roof["scatter_gbs"] = scatter_bytes / (stage_avg[2] / 1e3) / 1e9
+    roof["scatter_frac_hbm"] = roof["scatter_gbs"] / pk["hbm_gbs"]
+    roof["pullback_gbs"] = pull_bytes / (stage_avg[0] / 1e3) / 1e9
+
+    # other precision forms: throughput and relative Frobenius error against the FP64 GPU form
+    forms = {}
+    ref64 = None
+    if prec != "f64":
+        ref64 = plan.assemble(ctrl, 1.0, 0.3, "f64")
+    else:
+        ref64 = out.clone()
+    for f in [x for x in args.forms.split(",") if x and x != prec]:
+        try:
+            o = plan.assemble(ctrl, 1.0, 0.3, f)
+            torch.cuda.synchronize()
+            tms = []
+            for _ in range(3):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream); plan.assemble(ctrl, 1.0, 0.3, f, out=o); b.record(stream)
+                torch.cuda.synchronize()
+                tms.append(a.elapsed_time(b))
+            err = (torch.linalg.vector_norm(o.double() - ref64) / torch.linalg.vector_norm(ref64)).item()
+            ms = statistics.median(tms)
+            forms[f] = {"tiles_per_s": plan.n_tiles / (ms / 1e3), "ms": ms,
+                        "stiffness_gbs": plan.nnz * o.element_size() / (ms / 1e3) / 1e9, "rel_fro_vs_f64_gpu": err}
+            del o
+        except msasm.MsasmError as e:
+            forms[f] = {"unavailable": str(e)}
+
+    # end to end through the public C ABI with host buffers (copies inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        h_ctrl = torch.tensor(w.macro.ctrl, dtype=torch.float64).pin_memory()
+        h_vals = torch.empty(plan.nnz, dtype=msasm.Plan.value_dtype(prec)).pin_memory()
+        plan.assemble_host(h_ctrl, h_vals, 1.0, 0.3, prec)
+        e_ms = []
+        for _ in range(max(2, min(args.steps, 5))):
+            flush.zero_(); torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            plan.assemble_host(h_ctrl, h_vals, 1.0, 0.3, prec)
+            e_ms.append(1e3 * (time.perf_counter() - t0))
+        em = statistics.mean(e_ms)
+        e2e = {"value": plan.n_tiles / (em / 1e3), "unit": "tiles/s", "ms_per_step": em,
+               "h2d_bytes_per_step": int(h_ctrl.numel() * 8), "d2h_bytes_per_step": int(plan.nnz * vbytes),
+               "api": "msasm_assemble_host (pinned host buffers)"}
+        del h_vals
+
+    cpu = None
+    if not args.no_cpu:
+        dt, n = cpu_reference_time(args.workload, 48 if plan.n_tiles >= 1000 else plan.n_tiles)
+        cpu = {"value": n / dt, "unit": "tiles/s", "cores": threads_used(), "kind": "oracle",
+               "sample": f"{n} random tiles of the workload, FP64 lookup form (pullback, contraction, "
+                         f"scatter ordering), {dt:.1f} s"}
+
+    line = {"metric": METRIC, "value": value, "unit": "tiles/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
+            "config": {"workload": args.workload, "text": WORKLOAD_TEXT.get(args.workload, ""),
+                       "tiles": plan.n_tiles, "nnz": plan.nnz, "rows": plan.n_rows,
+                       "l2": "256 MB buffer written between timed steps; each step also writes "
+                             f"{plan.nnz * vbytes / 1e9:.2f} GB of values",
+                       "parallelism": f"{world} independent replica(s), one per GPU"},
+            "stiffness_gbs": stiff_gbs, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(launches), "clocks": clk, "forms": forms,
+            "wall_s_timed_region": wall}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,194 @@
+/*
+ * msasm.h -- multiscale lookup-table stiffness assembly on one GB300 (sm_103a).
+ *
+ * C ABI of the data-parallel hot path of "Fast and Multiscale Formation of
+ * Isogeometric Matrices of Microstructured Geometric Models" (Hirschler, Antolin,
+ * Buffa; arXiv 2107.09568):
+ *
+ *   (step 2)  build the stiffness lookup table mat[K] of the reference tile
+ *             (Sec. 3.2.3, eq. 51-52, 56-57)                -> msasm_build_tables
+ *   (step 1)  pull back the elasticity tensor through each macro element and
+ *             interpolate it at (q+1)^3 nodes (eq. 37, 42, 79-97)
+ *   (step 3)  contract the table with the coefficients, one GEMM (eq. 58)
+ *   (step 4)  add the tile blocks into a global CSR matrix (Sec. 3.2.4)
+ *                                                           -> msasm_assemble
+ *   compliance sensitivity u^T (dK/dP) u (Sec. 4.1.2, eq. 69-73) -> msasm_assemble_grad
+ *
+ * Conventions shared by every call:
+ *  - Every function returns an msasm_status; none aborts, exits or traps.  On an
+ *    error, msasm_last_error() returns a thread-local message.
+ *  - Pointers named d_* are device pointers on the current CUDA device, owned by
+ *    the caller; pointers named h_* (and descriptor arrays) are host memory, read
+ *    only during the call.  Opaque handles own library-allocated device memory
+ *    and are released by the matching *_destroy.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Work is queued on it and the call returns without synchronising, except
+ *    where a call is documented to read a result back to the host.
+ *  - Tile t = (ix, iy, iz) of an nx x ny x nz macro mesh has linear index
+ *    ix + nx*(iy + ny*iz).  Interpolation node C = c1 + (q+1)*(c2 + (q+1)*c3)
+ *    with the q+1 Gauss-Legendre points of [0,1] ascending per direction.
+ *  - Table layout: T[m][C][i][j] (row m = pair (A,B) of eq. 56 in lexicographic
+ *    order, A <= B, local ids of the reference tile), i.e. mat[K] of eq. 57 with
+ *    column k = 9*C + 3*i + j.
+ *  - Coefficient layout (mat[<A>] of eq. 58, stored transposed): coef[n][k] with
+ *    n = 9*t + 3*alpha + beta and k = 9*C + 3*i + j, value A_ij(xi_C)[alpha][beta].
+ *  - nzdata layout (eq. 58, stored transposed): nz[n][m], n = 9*t + 3*alpha + beta.
+ *  - Global stiffness: DOF 3*g + alpha of global control point g; CSR with int64
+ *    row pointer, int32 ascending column indices, full symmetric storage.
+ */
+#ifndef MSASM_H
+#define MSASM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MSASM_OK = 0,
+  MSASM_EINVAL = -1,        /* null pointer, bad size, unsupported degree/shape */
+  MSASM_ECUDA = -2,         /* a CUDA runtime/driver call failed */
+  MSASM_ENOMEM = -3,        /* device or host allocation failed */
+  MSASM_EDEGENERATE = -4,   /* |det J| <= tol at some node: degenerate macro element (Sec. 3.3.4) */
+  MSASM_EUNSUPPORTED = -5   /* precision/feature not available for this shape */
+} msasm_status;
+
+typedef enum {
+  MSASM_F64 = 0,            /* FP64 contraction (CUDA-core DFMA) */
+  MSASM_F32 = 1,            /* FP32 contraction (CUDA-core FFMA), FP32 values */
+  MSASM_SPLIT_F16 = 2,      /* tensor cores, FP16 hi/lo operands, FP32 accumulation, FP32 values */
+  MSASM_SPLIT_BF16 = 3,     /* tensor cores, BF16 hi/lo operands, FP32 accumulation, FP32 values */
+  MSASM_TF32 = 4,           /* tensor cores, TF32 operands, FP32 accumulation, FP32 values */
+  MSASM_TF32X3 = 5,         /* tensor cores, TF32 hi/lo (3 products), FP32 values */
+  MSASM_F64_EMU = 6         /* tensor cores, FP64 emulated by exact BF16 slices, FP64 values */
+} msasm_precision;
+
+/* flags for msasm_assemble */
+#define MSASM_FLAG_CHECK_DEGENERATE 1u  /* synchronise `stream` and fail with EDEGENERATE if any |det J| <= tol */
+#define MSASM_FLAG_STAGE_TIMES 2u       /* record CUDA events around each stage on `stream` (msasm_stage_times) */
+
+/* Reference tile T^r (eq. 3): axis-aligned box patches in [0,1]^3, each an
+ * open-uniform B-spline with its control points at the Greville abscissae
+ * (an affine patch map).  Patches are glued by coincident control points.
+ * Arrays are host memory of length 3*n_patches, patch-major. */
+typedef struct {
+  int32_t n_patches;
+  const int32_t* degree;    /* per patch and direction, 1..4 */
+  const int32_t* n_elem;    /* per patch and direction, >= 1 */
+  const double* box_lo;     /* box lower corner */
+  const double* box_hi;     /* box upper corner */
+} msasm_micro_desc;
+
+/* Macro B-spline map M (eq. 4): degrees and open knot vectors (host memory).
+ * The control net is passed to each assemble call because it changes during
+ * shape optimisation: d_ctrl[(i + n1*(j + n2*k))*3 + p], n_d = n_knots[d]-degree[d]-1. */
+typedef struct {
+  int32_t degree[3];        /* 1..5 */
+  int32_t n_knots[3];
+  const double* knots[3];   /* non-decreasing, open (first/last value repeated degree+1 times) */
+} msasm_macro_desc;
+
+typedef struct msasm_tables msasm_tables;   /* opaque: tile topology + table in device memory */
+typedef struct msasm_plan msasm_plan;       /* opaque: macro mesh, numbering, CSR pattern, scratch */
+
+/* ---------------------------------------------------------------- tables (step 2) */
+
+/* Build mat[K] (eq. 52, 57) in FP64 on the GPU for interpolation degree q (0..5),
+ * using n_gauss points per direction per micro element (<= 0: exact rule
+ * ceil((2 p_T + q + 1)/2)).  Synchronises `stream` before returning.
+ * Errors: EINVAL (bad descriptor, q out of range), ENOMEM, ECUDA. */
+msasm_status msasm_build_tables(const msasm_micro_desc* micro, int32_t q, int32_t n_gauss,
+                                void* stream, msasm_tables** out);
+
+/* Sizes of a table: n_T control points, n_nz pairs (eq. 56), n_pi = (q+1)^3. */
+msasm_status msasm_tables_info(const msasm_tables* tab, int32_t* n_T, int32_t* n_nz, int32_t* n_pi);
+
+/* Copy the FP64 table (n_nz * 9 * n_pi values, layout above) to d_table, and the
+ * pair list (2*n_nz int32, A then B per row) to h_pairs if non-NULL (host). */
+msasm_status msasm_tables_copy(const msasm_tables* tab, double* d_table, int32_t* h_pairs, void* stream);
+
+void msasm_tables_destroy(msasm_tables* tab);
+
+/* ---------------------------------------------------------------- plan (integer work, once per mesh) */
+
+/* Number the global control points of the tiled structure, build the CSR
+ * pattern and the per-(tile, pair) index map, and allocate scratch for
+ * `max_tiles_per_pass` tiles (<= 0: all tiles in one pass).  The plan keeps a
+ * reference to `tab`, which must outlive it.  Writes n_rows = 3 * n_points and
+ * nnz (host).  Synchronises `stream`.  Errors: EINVAL, ENOMEM, ECUDA. */
+msasm_status msasm_plan_create(const msasm_tables* tab, const msasm_macro_desc* macro,
+                               int32_t max_tiles_per_pass, void* stream, msasm_plan** out,
+                               int64_t* n_rows, int64_t* nnz);
+
+/* Sizes: tiles, global points, rows, nnz, control points of the macro net. */
+msasm_status msasm_plan_info(const msasm_plan* plan, int64_t* n_tiles, int64_t* n_points,
+                             int64_t* n_rows, int64_t* nnz, int64_t* n_ctrl);
+
+/* Copy the CSR pattern: d_rowptr (n_rows+1 int64) and d_col (nnz int32). */
+msasm_status msasm_plan_csr(const msasm_plan* plan, int64_t* d_rowptr, int32_t* d_col, void* stream);
+
+/* Copy the global numbering gmap[t][A] (n_tiles * n_T int32) to d_gmap. */
+msasm_status msasm_plan_numbering(const msasm_plan* plan, int32_t* d_gmap, void* stream);
+
+void msasm_plan_destroy(msasm_plan* plan);
+
+/* ---------------------------------------------------------------- assembly (steps 1, 3, 4) */
+
+/* K = sum over tiles of the lookup-form tile matrices (eq. 50, 58) scattered into
+ * the CSR pattern of the plan.  d_ctrl: macro control net (n_ctrl*3 FP64).
+ * E, nu: isotropic material (Lame constants as in eq. 84).  d_values: nnz values,
+ * FP64 for MSASM_F64 / MSASM_F64_EMU, FP32 otherwise; overwritten.  The
+ * Jacobian, its determinant and inverse are FP64 in every precision.
+ * Errors: EINVAL, EUNSUPPORTED, ECUDA; EDEGENERATE only with
+ * MSASM_FLAG_CHECK_DEGENERATE (otherwise degenerate nodes are counted, see
+ * msasm_degenerate_count, and the values are still written). */
+msasm_status msasm_assemble(msasm_plan* plan, const double* d_ctrl, double E, double nu,
+                            msasm_precision prec, void* d_values, uint32_t flags, void* stream);
+
+/* Same as msasm_assemble but with host buffers: h_ctrl (n_ctrl*3 FP64) is copied
+ * to the device and the nnz values are copied back into h_values (FP64 or FP32
+ * as above) before the call returns (it synchronises `stream`).  Pinned host
+ * memory gives full copy bandwidth. */
+msasm_status msasm_assemble_host(msasm_plan* plan, const double* h_ctrl, double E, double nu,
+                                 msasm_precision prec, void* h_values, uint32_t flags, void* stream);
+
+/* Number of interpolation nodes with |det J| <= tol found by the last assemble
+ * on this plan (reads back from the device; synchronises `stream`). */
+msasm_status msasm_degenerate_count(const msasm_plan* plan, int64_t* count, void* stream);
+
+/* Device time of each stage of the last assemble run with MSASM_FLAG_STAGE_TIMES,
+ * summed over its passes (CUDA events on the call's stream): ms[0] pullback,
+ * ms[1] contraction, ms[2] scatter (both kernels); launches[0..2] the kernel
+ * launches of each stage.  Synchronises on the recorded events.  EINVAL if the
+ * last assemble did not record times. */
+msasm_status msasm_stage_times(const msasm_plan* plan, double* ms, int32_t* launches);
+
+/* ---------------------------------------------------------------- stages (tests / composition) */
+
+/* Step 1 only: pulled-back macro field at the nodes (eq. 37, 42), written as the
+ * FP64 coefficient matrix d_coef[9*n_tiles][9*n_pi] (layout above). */
+msasm_status msasm_pullback(msasm_plan* plan, const double* d_ctrl, double E, double nu,
+                            double* d_coef, void* stream);
+
+/* Step 3 only: nz[n][m] = sum_k coef[n][k] T[m][k] (eq. 58) for `n_tiles` tiles of
+ * FP64 coefficients d_coef (layout above).  d_nz: 9*n_tiles*n_nz values, FP64
+ * for MSASM_F64 / MSASM_F64_EMU, FP32 otherwise. */
+msasm_status msasm_contract(const msasm_tables* tab, msasm_precision prec, const double* d_coef,
+                            int64_t n_tiles, void* d_nz, void* stream);
+
+/* Step 4 only: CSR values from nzdata of all tiles of the plan (d_nz as written by
+ * msasm_contract for all plan tiles, same precision family). */
+msasm_status msasm_scatter(msasm_plan* plan, msasm_precision prec, const void* d_nz,
+                           void* d_values, void* stream);
+
+/* ---------------------------------------------------------------- diagnostics */
+
+const char* msasm_last_error(void);
+const char* msasm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MSASM_H */

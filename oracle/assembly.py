@@ -213,3 +213,35 @@ class Problem:
             x, _ = self.mmap.tile_map(t, self.tile.points, ctrl)
             X[self.gmap[t]] = x
         return X
+
+
+def point_rows(prob: "Problem", points, ctrl=None, blocks_fn=None):
+    """CSR rows of sampled global points without forming K: {g: (neighbour ids, (deg, 3, 3) blocks)}.
+
+    Row block (g, h) = sum over tiles tau holding g of K_tau[(A, B)] (A = local g, B = local h),
+    using the stored upper block or the transpose of (B, A).  ``blocks_fn(t)`` returns the
+    (n_nz, 3, 3) tile blocks (default: the lookup form, eq. 58).
+    """
+    tile = prob.tile
+    if blocks_fn is None:
+        blocks_fn = lambda t: tile_blocks_lookup(prob.T, prob.mmap, t, prob.q, prob.lam, prob.mu, ctrl)
+    cache = {}
+    out = {}
+    P = tile.pairs
+    for g in points:
+        acc = {}
+        for t, A in np.argwhere(prob.gmap == g):
+            if t not in cache:
+                cache[t] = blocks_fn(int(t))
+            Kt = cache[t]
+            up = np.nonzero(P[:, 0] == A)[0]
+            lo = np.nonzero((P[:, 1] == A) & (P[:, 0] != A))[0]
+            for m in up:
+                h = int(prob.gmap[t, P[m, 1]])
+                acc[h] = acc.get(h, 0.0) + Kt[m]
+            for m in lo:
+                h = int(prob.gmap[t, P[m, 0]])
+                acc[h] = acc.get(h, 0.0) + Kt[m].T
+        hs = np.array(sorted(acc), dtype=np.int64)
+        out[int(g)] = (hs, np.array([acc[h] for h in hs]))
+    return out

@@ -1,0 +1,170 @@
+"""GB300-native multiscale lookup-table stiffness assembly (arXiv 2107.09568).
+
+Thin Python layer over the C ABI of ``include/msasm.h``: it only marshals
+arguments (torch tensors for device memory and streams).  Every step of the
+assembly runs in the library's CUDA kernels; there is no Python or CPU
+implementation of any step here.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import MsasmError, PRECISIONS, FLAG_CHECK_DEGENERATE, check, load
+
+__all__ = ["Tables", "Plan", "MsasmError", "PRECISIONS", "load", "lame"]
+
+
+def lame(E: float, nu: float):
+    lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu))
+    mu = E / (2.0 * (1.0 + nu))
+    return lam, mu
+
+
+def _ptr(t):
+    return C.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+class Tables:
+    """Handle of msasm_build_tables: the reference tile's lookup table (FP64, on the GPU)."""
+
+    def __init__(self, micro, q: int, n_gauss: int = 0, stream=None):
+        lib = load()
+        self._keep = [np.ascontiguousarray(micro.degree, dtype=np.int32).ravel(),
+                      np.ascontiguousarray(micro.n_elem, dtype=np.int32).ravel(),
+                      np.ascontiguousarray(micro.box_lo, dtype=np.float64).ravel(),
+                      np.ascontiguousarray(micro.box_hi, dtype=np.float64).ravel()]
+        d = _lib.MicroDescC(int(micro.degree.shape[0]),
+                            self._keep[0].ctypes.data_as(C.POINTER(C.c_int32)),
+                            self._keep[1].ctypes.data_as(C.POINTER(C.c_int32)),
+                            self._keep[2].ctypes.data_as(C.POINTER(C.c_double)),
+                            self._keep[3].ctypes.data_as(C.POINTER(C.c_double)))
+        h = C.c_void_p()
+        check(lib.msasm_build_tables(C.byref(d), int(q), int(n_gauss), _stream(stream), C.byref(h)))
+        self.handle = h
+        n_T, n_nz, n_pi = C.c_int32(), C.c_int32(), C.c_int32()
+        check(lib.msasm_tables_info(h, C.byref(n_T), C.byref(n_nz), C.byref(n_pi)))
+        self.n_T, self.n_nz, self.n_pi, self.q = n_T.value, n_nz.value, n_pi.value, int(q)
+
+    def table(self):
+        """The FP64 table as a (n_nz, n_pi, 3, 3) CUDA tensor (a copy)."""
+        import torch
+        out = torch.empty((self.n_nz, self.n_pi, 3, 3), dtype=torch.float64, device="cuda")
+        check(load().msasm_tables_copy(self.handle, _ptr(out), None, _stream()))
+        return out
+
+    def pairs(self):
+        out = np.empty((self.n_nz, 2), dtype=np.int32)
+        check(load().msasm_tables_copy(self.handle, None, out.ctypes.data_as(C.c_void_p), None))
+        return out
+
+    def contract(self, coef, precision="f64", stream=None):
+        """Step 3 only: nz[n][m] = sum_k coef[n][k] T[m][k] (eq. 58) for FP64 coefficients."""
+        import torch
+        n_tiles = coef.shape[0] // 9
+        dt = torch.float64 if precision in ("f64", "f64_emu") else torch.float32
+        out = torch.empty((9 * n_tiles, self.n_nz), dtype=dt, device="cuda")
+        check(load().msasm_contract(self.handle, PRECISIONS[precision], _ptr(coef), n_tiles, _ptr(out),
+                                    _stream(stream)))
+        return out
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib._lib is not None:
+            _lib._lib.msasm_tables_destroy(self.handle)
+            self.handle = None
+
+
+class Plan:
+    """Handle of msasm_plan_create: numbering, CSR pattern and scratch for one macro mesh."""
+
+    def __init__(self, tables: Tables, macro, max_tiles_per_pass: int = 0, stream=None):
+        lib = load()
+        self.tables = tables
+        self._knots = [np.ascontiguousarray(k, dtype=np.float64) for k in macro.knots]
+        d = _lib.MacroDescC()
+        for i in range(3):
+            d.degree[i] = int(macro.degree[i])
+            d.n_knots[i] = len(self._knots[i])
+            d.knots[i] = self._knots[i].ctypes.data_as(C.POINTER(C.c_double))
+        h = C.c_void_p()
+        n_rows, nnz = C.c_int64(), C.c_int64()
+        check(lib.msasm_plan_create(tables.handle, C.byref(d), int(max_tiles_per_pass), _stream(stream),
+                                    C.byref(h), C.byref(n_rows), C.byref(nnz)))
+        self.handle = h
+        vals = [C.c_int64() for _ in range(5)]
+        check(lib.msasm_plan_info(h, *[C.byref(v) for v in vals]))
+        self.n_tiles, self.n_points, self.n_rows, self.nnz, self.n_ctrl = (v.value for v in vals)
+
+    def csr(self, stream=None):
+        import torch
+        rowptr = torch.empty(self.n_rows + 1, dtype=torch.int64, device="cuda")
+        col = torch.empty(self.nnz, dtype=torch.int32, device="cuda")
+        check(load().msasm_plan_csr(self.handle, _ptr(rowptr), _ptr(col), _stream(stream)))
+        return rowptr, col
+
+    def numbering(self, stream=None):
+        import torch
+        g = torch.empty((self.n_tiles, self.tables.n_T), dtype=torch.int32, device="cuda")
+        check(load().msasm_plan_numbering(self.handle, _ptr(g), _stream(stream)))
+        return g
+
+    @staticmethod
+    def value_dtype(precision):
+        import torch
+        return torch.float64 if precision in ("f64", "f64_emu") else torch.float32
+
+    def assemble(self, ctrl, E=1.0, nu=0.3, precision="f64", out=None, check_degenerate=False,
+                 stage_times=False, stream=None):
+        """Steps 1, 3, 4: CSR values of K for the control net `ctrl` (CUDA, (n_ctrl, 3) FP64)."""
+        import torch
+        if out is None:
+            out = torch.empty(self.nnz, dtype=self.value_dtype(precision), device="cuda")
+        flags = (FLAG_CHECK_DEGENERATE if check_degenerate else 0) | (_lib.FLAG_STAGE_TIMES if stage_times else 0)
+        check(load().msasm_assemble(self.handle, _ptr(ctrl), float(E), float(nu), PRECISIONS[precision],
+                                    _ptr(out), flags, _stream(stream)))
+        return out
+
+    def assemble_host(self, ctrl_host, values_host, E=1.0, nu=0.3, precision="f64", stream=None):
+        """Same with host buffers (copies inside the call); both are torch CPU tensors (pinned for speed)."""
+        check(load().msasm_assemble_host(self.handle, C.c_void_p(ctrl_host.data_ptr()), float(E), float(nu),
+                                         PRECISIONS[precision], C.c_void_p(values_host.data_ptr()), 0,
+                                         _stream(stream)))
+        return values_host
+
+    def stage_times(self):
+        """(ms per stage [pullback, contraction, scatter], launches per stage) of the last timed assemble."""
+        ms = (C.c_double * 3)()
+        ln = (C.c_int32 * 3)()
+        check(load().msasm_stage_times(self.handle, ms, ln))
+        return list(ms), list(ln)
+
+    def degenerate_count(self, stream=None):
+        c = C.c_int64()
+        check(load().msasm_degenerate_count(self.handle, C.byref(c), _stream(stream)))
+        return c.value
+
+    def pullback(self, ctrl, E=1.0, nu=0.3, stream=None):
+        """Step 1 only: (9 n_tiles, 9 n_pi) FP64 coefficients (eq. 37, 42)."""
+        import torch
+        out = torch.empty((9 * self.n_tiles, 9 * self.tables.n_pi), dtype=torch.float64, device="cuda")
+        check(load().msasm_pullback(self.handle, _ptr(ctrl), float(E), float(nu), _ptr(out), _stream(stream)))
+        return out
+
+    def scatter(self, nz, precision="f64", stream=None):
+        import torch
+        out = torch.empty(self.nnz, dtype=self.value_dtype(precision), device="cuda")
+        check(load().msasm_scatter(self.handle, PRECISIONS[precision], _ptr(nz), _ptr(out), _stream(stream)))
+        return out
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib._lib is not None:
+            _lib._lib.msasm_plan_destroy(self.handle)
+            self.handle = None

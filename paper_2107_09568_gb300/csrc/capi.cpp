@@ -1,0 +1,561 @@
+// The C ABI of include/msasm.h: argument checking, handle lifetime, and the
+// sequencing of the kernels of one assembly (pullback -> contraction -> scatter).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.h"
+
+namespace msasm {
+
+static thread_local std::string g_error;
+
+void set_error(const std::string& msg) { g_error = msg; }
+msasm_status fail(msasm_status st, const std::string& msg) {
+  g_error = msg;
+  return st;
+}
+msasm_status cuda_fail(cudaError_t err, const char* what) {
+  g_error = std::string(what) + ": " + cudaGetErrorName(err) + " (" + cudaGetErrorString(err) + ")";
+  return err == cudaErrorMemoryAllocation ? MSASM_ENOMEM : MSASM_ECUDA;
+}
+
+// kernels (other translation units)
+msasm_status build_table_gpu(msasm_tables* tab, cudaStream_t stream);
+void number_points(const TileTopology& topo, const int n_elem[3], std::vector<int32_t>& gmap, int64_t& n_points);
+void point_pattern(const TileTopology& topo, const int n_elem[3], const std::vector<int32_t>& gmap,
+                   int64_t n_points, std::vector<int64_t>& pptr, std::vector<int32_t>& pcol);
+msasm_status structure_expand_gpu(int64_t n_points, const int64_t* d_pptr, const int32_t* d_pcol,
+                                  int64_t* d_rowptr, int32_t* d_col, cudaStream_t stream);
+msasm_status rank_map_gpu(const int32_t* d_gmap, const int32_t* d_pairs, const uint8_t* d_pair_face,
+                          const int64_t* d_pptr, const int32_t* d_pcol, int64_t n_tiles, int n_T, int n_nz,
+                          int nx, int ny, uint32_t* d_rank, unsigned long long* d_bad, cudaStream_t stream);
+msasm_status pullback_gpu(const msasm_plan* plan, const double* d_ctrl, double lam, double mu, int64_t t0,
+                          int64_t n_tiles, double* d_coef, cudaStream_t stream);
+msasm_status contract_simt_f64(const double* d_coef, const double* d_T, int64_t n_tiles, int n_nz, int K,
+                               int ld_nz, double* d_nz, cudaStream_t stream);
+msasm_status contract_simt_f32(const float* d_coef, const float* d_T, int64_t n_tiles, int n_nz, int K,
+                               int ld_nz, float* d_nz, cudaStream_t stream);
+msasm_status to_f32_gpu(const double* x, int64_t n, float* y, cudaStream_t stream);
+template <typename T>
+msasm_status scatter_gpu(const msasm_plan* plan, const T* d_nz, int ld_nz, int64_t t0, int64_t n_tiles,
+                         const int64_t* d_list, int64_t n_list, T* d_values, cudaStream_t stream);
+
+static inline int ld_nz_of(int n_nz) { return (n_nz + 7) & ~7; }
+
+static bool is_f64_precision(msasm_precision p) { return p == MSASM_F64 || p == MSASM_F64_EMU; }
+
+}  // namespace msasm
+
+using namespace msasm;
+
+msasm_tables::~msasm_tables() {
+  cudaFree(d_T);
+  cudaFree(d_pairs);
+  cudaFree(d_T32);
+  cudaFree(d_Thi);
+  cudaFree(d_Tlo);
+  cudaFree(d_Tslices);
+  cudaFree(d_Tslice_scale);
+}
+
+msasm_plan::~msasm_plan() {
+  for (int d = 0; d < 3; ++d) {
+    cudaFree(d_basis[d]);
+    cudaFree(d_first[d]);
+  }
+  cudaFree(d_gmap);
+  cudaFree(d_rowptr);
+  cudaFree(d_col);
+  cudaFree(d_rank);
+  cudaFree(d_second);
+  cudaFree(d_coef);
+  cudaFree(d_nz);
+  cudaFree(d_coef_lp);
+  cudaFree(d_degenerate);
+  cudaFree(d_ctrl_stage);
+  cudaFree(d_values_stage);
+  for (cudaEvent_t e : events) cudaEventDestroy(e);
+}
+
+extern "C" {
+
+const char* msasm_last_error(void) { return g_error.c_str(); }
+const char* msasm_version(void) { return "msasm 0.1 (sm_103a)"; }
+
+msasm_status msasm_build_tables(const msasm_micro_desc* micro, int32_t q, int32_t n_gauss, void* stream,
+                                msasm_tables** out) {
+  if (!out) return fail(MSASM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (q < 0 || q > 5) return fail(MSASM_EINVAL, "interpolation degree q must be in 0..5");
+  if (n_gauss > 16) return fail(MSASM_EINVAL, "n_gauss must be <= 16");
+  msasm_tables* tab = new msasm_tables();
+  msasm_status st = build_topology(micro, tab->topo);
+  if (st != MSASM_OK) {
+    delete tab;
+    return st;
+  }
+  tab->q = q;
+  tab->n_pi = (q + 1) * (q + 1) * (q + 1);
+  tab->n_nz = int(tab->topo.pair_A.size());
+  tab->n_gauss = n_gauss;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  size_t tbytes = size_t(tab->n_nz) * 9 * tab->n_pi * sizeof(double);
+  cudaError_t e1 = cudaMalloc(&tab->d_T, tbytes);
+  cudaError_t e2 = cudaMalloc(&tab->d_pairs, size_t(tab->n_nz) * 2 * sizeof(int32_t));
+  if (e1 != cudaSuccess || e2 != cudaSuccess) {
+    delete tab;
+    return cuda_fail(e1 != cudaSuccess ? e1 : e2, "cudaMalloc(table)");
+  }
+  std::vector<int32_t> pairs(size_t(tab->n_nz) * 2);
+  for (int m = 0; m < tab->n_nz; ++m) {
+    pairs[2 * m] = tab->topo.pair_A[m];
+    pairs[2 * m + 1] = tab->topo.pair_B[m];
+  }
+  cudaError_t e3 = cudaMemcpyAsync(tab->d_pairs, pairs.data(), pairs.size() * sizeof(int32_t),
+                                   cudaMemcpyHostToDevice, s);
+  if (e3 != cudaSuccess) {
+    delete tab;
+    return cuda_fail(e3, "cudaMemcpyAsync(pairs)");
+  }
+  st = build_table_gpu(tab, s);   // synchronises `s`
+  if (st != MSASM_OK) {
+    delete tab;
+    return st;
+  }
+  *out = tab;
+  return MSASM_OK;
+}
+
+msasm_status msasm_tables_info(const msasm_tables* tab, int32_t* n_T, int32_t* n_nz, int32_t* n_pi) {
+  if (!tab) return fail(MSASM_EINVAL, "tables is NULL");
+  if (n_T) *n_T = tab->topo.n_T;
+  if (n_nz) *n_nz = tab->n_nz;
+  if (n_pi) *n_pi = tab->n_pi;
+  return MSASM_OK;
+}
+
+msasm_status msasm_tables_copy(const msasm_tables* tab, double* d_table, int32_t* h_pairs, void* stream) {
+  if (!tab) return fail(MSASM_EINVAL, "tables is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (d_table)
+    MSASM_CUDA(cudaMemcpyAsync(d_table, tab->d_T, size_t(tab->n_nz) * 9 * tab->n_pi * sizeof(double),
+                               cudaMemcpyDeviceToDevice, s));
+  if (h_pairs)
+    for (int m = 0; m < tab->n_nz; ++m) {
+      h_pairs[2 * m] = tab->topo.pair_A[m];
+      h_pairs[2 * m + 1] = tab->topo.pair_B[m];
+    }
+  return MSASM_OK;
+}
+
+void msasm_tables_destroy(msasm_tables* tab) { delete tab; }
+
+msasm_status msasm_plan_create(const msasm_tables* tab, const msasm_macro_desc* macro, int32_t max_tiles_per_pass,
+                               void* stream, msasm_plan** out, int64_t* n_rows, int64_t* nnz) {
+  if (!out) return fail(MSASM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!tab || !macro) return fail(MSASM_EINVAL, "tables or macro descriptor is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  msasm_plan* plan = new msasm_plan();
+  plan->tab = tab;
+  auto bail = [&](msasm_status st) {
+    delete plan;
+    return st;
+  };
+  const int nq = tab->q + 1;
+  std::vector<double> xn, wn;
+  gauss_legendre01(nq, xn, wn);
+  std::vector<double> basis[3];
+  std::vector<int32_t> first[3];
+  for (int d = 0; d < 3; ++d) {
+    int p = macro->degree[d], nk = macro->n_knots[d];
+    const double* t = macro->knots[d];
+    if (p < 1 || p > 5) return bail(fail(MSASM_EINVAL, "macro degree must be in 1..5"));
+    if (!t || nk < 2 * (p + 1)) return bail(fail(MSASM_EINVAL, "macro knot vector too short or NULL"));
+    for (int k = 0; k + 1 < nk; ++k)
+      if (!(t[k + 1] >= t[k])) return bail(fail(MSASM_EINVAL, "macro knots must be non-decreasing"));
+    for (int k = 0; k <= p; ++k)
+      if (t[k] != t[0] || t[nk - 1 - k] != t[nk - 1])
+        return bail(fail(MSASM_EINVAL, "macro knot vector must be open (end knots repeated degree+1 times)"));
+    plan->degree[d] = p;
+    plan->n_ctrl_dir[d] = nk - p - 1;
+    int ne = 0;
+    for (int k = p; k < nk - p - 1; ++k) {
+      if (!(t[k + 1] > t[k])) continue;
+      ++ne;
+      first[d].push_back(k - p);
+      double u0 = t[k], h = t[k + 1] - t[k];
+      for (int c = 0; c < nq; ++c) {
+        double vals[8], ders[8];
+        bspline_span_basis(t, p, k, u0 + h * xn[c], vals, ders);
+        for (int a = 0; a <= p; ++a) {
+          basis[d].push_back(vals[a]);
+          basis[d].push_back(ders[a] * h);   // d/dxi of the tile map
+        }
+      }
+    }
+    if (ne == 0) return bail(fail(MSASM_EINVAL, "macro knot vector has no non-empty span"));
+    plan->n_elem[d] = ne;
+  }
+  plan->n_tiles = int64_t(plan->n_elem[0]) * plan->n_elem[1] * plan->n_elem[2];
+  plan->n_ctrl = int64_t(plan->n_ctrl_dir[0]) * plan->n_ctrl_dir[1] * plan->n_ctrl_dir[2];
+  plan->tiles_per_pass = (max_tiles_per_pass <= 0) ? plan->n_tiles : std::min<int64_t>(max_tiles_per_pass, plan->n_tiles);
+  if (9 * plan->tiles_per_pass > 65535LL * 128) plan->tiles_per_pass = 65535LL * 128 / 9;
+
+  // numbering and the point pattern on the host
+  std::vector<int32_t> gmap;
+  number_points(tab->topo, plan->n_elem, gmap, plan->n_points);
+  if (plan->n_points >= (int64_t(1) << 31) / 3) return bail(fail(MSASM_EUNSUPPORTED, "more than 715M points"));
+  std::vector<int64_t> pptr;
+  std::vector<int32_t> pcol;
+  point_pattern(tab->topo, plan->n_elem, gmap, plan->n_points, pptr, pcol);
+  int64_t max_deg = 0;
+  for (int64_t g = 0; g < plan->n_points; ++g) max_deg = std::max(max_deg, pptr[g + 1] - pptr[g]);
+  if (max_deg >= 32768) return bail(fail(MSASM_EUNSUPPORTED, "a point has more than 32767 neighbours"));
+  plan->n_rows = 3 * plan->n_points;
+  plan->nnz = 9 * pptr[plan->n_points];
+
+  // second contributors: pairs on a glued lower face of their tile
+  std::vector<int64_t> second;
+  const int n_nz = tab->n_nz;
+  std::vector<int> face_pairs[8];
+  for (int mask = 1; mask < 8; ++mask)
+    for (int m = 0; m < n_nz; ++m)
+      if (tab->topo.pair_face[m] & mask) face_pairs[mask].push_back(m);
+  plan->second_ptr.assign(size_t(plan->n_tiles) + 1, 0);
+  for (int64_t t = 0; t < plan->n_tiles; ++t) {
+    int64_t ix = t % plan->n_elem[0], iy = (t / plan->n_elem[0]) % plan->n_elem[1],
+            iz = t / (int64_t(plan->n_elem[0]) * plan->n_elem[1]);
+    int mask = (ix > 0 ? 1 : 0) | (iy > 0 ? 2 : 0) | (iz > 0 ? 4 : 0);
+    for (int m : face_pairs[mask]) second.push_back(t * n_nz + m);
+    plan->second_ptr[size_t(t) + 1] = int64_t(second.size());
+  }
+  plan->n_second = int64_t(second.size());
+
+  // device allocations
+  const size_t n_pi = size_t(tab->n_pi);
+  const int ld = ld_nz_of(n_nz);
+  int64_t* d_pptr = nullptr;
+  int32_t* d_pcol = nullptr;
+  uint8_t* d_pair_face = nullptr;
+  unsigned long long* d_bad = nullptr;
+  auto dev = [&](void** p, size_t bytes) { return cudaMalloc(p, std::max<size_t>(bytes, 16)); };
+  cudaError_t err = cudaSuccess;
+  for (int d = 0; d < 3 && err == cudaSuccess; ++d) {
+    err = dev((void**)&plan->d_basis[d], basis[d].size() * sizeof(double));
+    if (err == cudaSuccess) err = dev((void**)&plan->d_first[d], first[d].size() * sizeof(int32_t));
+  }
+  if (err == cudaSuccess) err = dev((void**)&plan->d_gmap, gmap.size() * sizeof(int32_t));
+  if (err == cudaSuccess) err = dev((void**)&plan->d_rowptr, size_t(plan->n_rows + 1) * sizeof(int64_t));
+  if (err == cudaSuccess) err = dev((void**)&plan->d_col, size_t(plan->nnz) * sizeof(int32_t));
+  if (err == cudaSuccess) err = dev((void**)&plan->d_rank, size_t(plan->n_tiles) * n_nz * sizeof(uint32_t));
+  if (err == cudaSuccess) err = dev((void**)&plan->d_second, second.size() * sizeof(int64_t));
+  if (err == cudaSuccess) err = dev((void**)&plan->d_coef, size_t(9 * plan->tiles_per_pass) * 9 * n_pi * sizeof(double));
+  if (err == cudaSuccess) err = dev((void**)&plan->d_nz, size_t(9 * plan->tiles_per_pass) * ld * sizeof(double));
+  if (err == cudaSuccess) err = dev((void**)&plan->d_degenerate, sizeof(unsigned long long));
+  if (err == cudaSuccess) err = dev((void**)&d_pptr, pptr.size() * sizeof(int64_t));
+  if (err == cudaSuccess) err = dev((void**)&d_pcol, pcol.size() * sizeof(int32_t));
+  if (err == cudaSuccess) err = dev((void**)&d_pair_face, size_t(n_nz));
+  if (err == cudaSuccess) err = dev((void**)&d_bad, sizeof(unsigned long long));
+  auto cleanup_tmp = [&]() {
+    cudaFree(d_pptr);
+    cudaFree(d_pcol);
+    cudaFree(d_pair_face);
+    cudaFree(d_bad);
+  };
+  if (err != cudaSuccess) {
+    cleanup_tmp();
+    return bail(cuda_fail(err, "cudaMalloc(plan)"));
+  }
+  auto h2d = [&](void* dst, const void* src, size_t bytes) {
+    return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s) : cudaSuccess;
+  };
+  for (int d = 0; d < 3 && err == cudaSuccess; ++d) {
+    err = h2d(plan->d_basis[d], basis[d].data(), basis[d].size() * sizeof(double));
+    if (err == cudaSuccess) err = h2d(plan->d_first[d], first[d].data(), first[d].size() * sizeof(int32_t));
+  }
+  if (err == cudaSuccess) err = h2d(plan->d_gmap, gmap.data(), gmap.size() * sizeof(int32_t));
+  if (err == cudaSuccess) err = h2d(plan->d_second, second.data(), second.size() * sizeof(int64_t));
+  if (err == cudaSuccess) err = h2d(d_pptr, pptr.data(), pptr.size() * sizeof(int64_t));
+  if (err == cudaSuccess) err = h2d(d_pcol, pcol.data(), pcol.size() * sizeof(int32_t));
+  if (err == cudaSuccess) err = h2d(d_pair_face, tab->topo.pair_face.data(), size_t(n_nz));
+  if (err == cudaSuccess) err = cudaMemsetAsync(d_bad, 0, sizeof(unsigned long long), s);
+  if (err == cudaSuccess) err = cudaMemsetAsync(plan->d_degenerate, 0, sizeof(unsigned long long), s);
+  if (err != cudaSuccess) {
+    cudaStreamSynchronize(s);
+    cleanup_tmp();
+    return bail(cuda_fail(err, "cudaMemcpyAsync(plan)"));
+  }
+  msasm_status st = structure_expand_gpu(plan->n_points, d_pptr, d_pcol, plan->d_rowptr, plan->d_col, s);
+  if (st == MSASM_OK)
+    st = rank_map_gpu(plan->d_gmap, tab->d_pairs, d_pair_face, d_pptr, d_pcol, plan->n_tiles, tab->topo.n_T, n_nz,
+                      plan->n_elem[0], plan->n_elem[1], plan->d_rank, d_bad, s);
+  unsigned long long bad = 0;
+  if (st == MSASM_OK) {
+    err = cudaMemcpyAsync(&bad, d_bad, sizeof(bad), cudaMemcpyDeviceToHost, s);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+    if (err != cudaSuccess) st = cuda_fail(err, "plan structure kernels");
+  } else {
+    cudaStreamSynchronize(s);
+  }
+  cleanup_tmp();
+  if (st != MSASM_OK) return bail(st);
+  if (bad) return bail(fail(MSASM_ECUDA, "index map: a tile pair is missing from the CSR pattern"));
+  if (n_rows) *n_rows = plan->n_rows;
+  if (nnz) *nnz = plan->nnz;
+  *out = plan;
+  return MSASM_OK;
+}
+
+msasm_status msasm_plan_info(const msasm_plan* plan, int64_t* n_tiles, int64_t* n_points, int64_t* n_rows,
+                             int64_t* nnz, int64_t* n_ctrl) {
+  if (!plan) return fail(MSASM_EINVAL, "plan is NULL");
+  if (n_tiles) *n_tiles = plan->n_tiles;
+  if (n_points) *n_points = plan->n_points;
+  if (n_rows) *n_rows = plan->n_rows;
+  if (nnz) *nnz = plan->nnz;
+  if (n_ctrl) *n_ctrl = plan->n_ctrl;
+  return MSASM_OK;
+}
+
+msasm_status msasm_plan_csr(const msasm_plan* plan, int64_t* d_rowptr, int32_t* d_col, void* stream) {
+  if (!plan || !d_rowptr || !d_col) return fail(MSASM_EINVAL, "plan, d_rowptr or d_col is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  MSASM_CUDA(cudaMemcpyAsync(d_rowptr, plan->d_rowptr, size_t(plan->n_rows + 1) * sizeof(int64_t),
+                             cudaMemcpyDeviceToDevice, s));
+  MSASM_CUDA(cudaMemcpyAsync(d_col, plan->d_col, size_t(plan->nnz) * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+  return MSASM_OK;
+}
+
+msasm_status msasm_plan_numbering(const msasm_plan* plan, int32_t* d_gmap, void* stream) {
+  if (!plan || !d_gmap) return fail(MSASM_EINVAL, "plan or d_gmap is NULL");
+  MSASM_CUDA(cudaMemcpyAsync(d_gmap, plan->d_gmap, size_t(plan->n_tiles) * plan->tab->topo.n_T * sizeof(int32_t),
+                             cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream)));
+  return MSASM_OK;
+}
+
+void msasm_plan_destroy(msasm_plan* plan) { delete plan; }
+
+static msasm_status check_material(double E, double nu) {
+  if (!(E > 0.0) || !(nu > -1.0 && nu < 0.5) || !std::isfinite(E))
+    return fail(MSASM_EINVAL, "material: need E > 0 and -1 < nu < 0.5");
+  return MSASM_OK;
+}
+
+static void lame(double E, double nu, double& lam, double& mu) {
+  lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+  mu = E / (2.0 * (1.0 + nu));
+}
+
+// contraction of `n_tiles` tiles of FP64 coefficients into nzdata of the precision family
+static msasm_status contract_dispatch(const msasm_tables* ctab, msasm_precision prec, const double* d_coef,
+                                      int64_t n_tiles, void* d_nz, void* scratch_lp, cudaStream_t s) {
+  msasm_tables* tab = const_cast<msasm_tables*>(ctab);
+  const int K = 9 * tab->n_pi, n_nz = tab->n_nz, ld = ld_nz_of(n_nz);
+  switch (prec) {
+    case MSASM_F64:
+      return contract_simt_f64(d_coef, tab->d_T, n_tiles, n_nz, K, ld, static_cast<double*>(d_nz), s);
+    case MSASM_F32: {
+      if (!tab->d_T32) {
+        MSASM_CUDA(cudaMalloc(&tab->d_T32, size_t(n_nz) * K * sizeof(float)));
+        MSASM_TRY(to_f32_gpu(tab->d_T, int64_t(n_nz) * K, tab->d_T32, s));
+      }
+      float* c32 = static_cast<float*>(scratch_lp);
+      MSASM_TRY(to_f32_gpu(d_coef, 9 * n_tiles * K, c32, s));
+      return contract_simt_f32(c32, tab->d_T32, n_tiles, n_nz, K, ld, static_cast<float*>(d_nz), s);
+    }
+    default:
+      return fail(MSASM_EUNSUPPORTED, "precision not available in this build");
+  }
+}
+
+static int contract_launches(msasm_precision prec) { return prec == MSASM_F32 ? 2 : 1; }
+
+static msasm_status ensure_lp_scratch(msasm_plan* plan, msasm_precision prec) {
+  if (prec == MSASM_F64) return MSASM_OK;
+  size_t need = size_t(9 * plan->tiles_per_pass) * 9 * plan->tab->n_pi * sizeof(float) * 2;
+  if (plan->coef_lp_bytes >= need) return MSASM_OK;
+  cudaFree(plan->d_coef_lp);
+  plan->d_coef_lp = nullptr;
+  plan->coef_lp_bytes = 0;
+  MSASM_CUDA(cudaMalloc(&plan->d_coef_lp, need));
+  plan->coef_lp_bytes = need;
+  return MSASM_OK;
+}
+
+static msasm_status scatter_dispatch(msasm_plan* plan, msasm_precision prec, const void* d_nz, int64_t t0,
+                                     int64_t nt, void* d_values, cudaStream_t s) {
+  const int ld = ld_nz_of(plan->tab->n_nz);
+  const int64_t lo = plan->second_ptr[size_t(t0)], hi = plan->second_ptr[size_t(t0 + nt)];
+  const int64_t* list = plan->d_second + lo;
+  if (is_f64_precision(prec))
+    return scatter_gpu<double>(plan, static_cast<const double*>(d_nz), ld, t0, nt, list, hi - lo,
+                               static_cast<double*>(d_values), s);
+  return scatter_gpu<float>(plan, static_cast<const float*>(d_nz), ld, t0, nt, list, hi - lo,
+                            static_cast<float*>(d_values), s);
+}
+
+msasm_status msasm_assemble(msasm_plan* plan, const double* d_ctrl, double E, double nu, msasm_precision prec,
+                            void* d_values, uint32_t flags, void* stream) {
+  if (!plan || !d_ctrl || !d_values) return fail(MSASM_EINVAL, "plan, d_ctrl or d_values is NULL");
+  MSASM_TRY(check_material(E, nu));
+  if (prec < MSASM_F64 || prec > MSASM_F64_EMU) return fail(MSASM_EINVAL, "unknown precision");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  double lam, mu;
+  lame(E, nu, lam, mu);
+  MSASM_TRY(ensure_lp_scratch(plan, prec));
+  MSASM_CUDA(cudaMemsetAsync(plan->d_degenerate, 0, sizeof(unsigned long long), s));
+  const int64_t P = plan->tiles_per_pass;
+  const bool timed = (flags & MSASM_FLAG_STAGE_TIMES) != 0;
+  const int n_pass = int((plan->n_tiles + P - 1) / P);
+  plan->timed_passes = 0;
+  if (timed) {
+    while (plan->events.size() < size_t(4 * n_pass)) {
+      cudaEvent_t e;
+      MSASM_CUDA(cudaEventCreate(&e));
+      plan->events.push_back(e);
+    }
+    for (int k = 0; k < 3; ++k) plan->stage_launches[k] = 0;
+  }
+  int pass = 0;
+  for (int64_t t0 = 0; t0 < plan->n_tiles; t0 += P, ++pass) {
+    const int64_t nt = std::min(P, plan->n_tiles - t0);
+    if (timed) MSASM_CUDA(cudaEventRecord(plan->events[4 * pass + 0], s));
+    MSASM_TRY(pullback_gpu(plan, d_ctrl, lam, mu, t0, nt, plan->d_coef, s));
+    if (timed) MSASM_CUDA(cudaEventRecord(plan->events[4 * pass + 1], s));
+    MSASM_TRY(contract_dispatch(plan->tab, prec, plan->d_coef, nt, plan->d_nz, plan->d_coef_lp, s));
+    if (timed) MSASM_CUDA(cudaEventRecord(plan->events[4 * pass + 2], s));
+    MSASM_TRY(scatter_dispatch(plan, prec, plan->d_nz, t0, nt, d_values, s));
+    if (timed) {
+      MSASM_CUDA(cudaEventRecord(plan->events[4 * pass + 3], s));
+      const int64_t lo = plan->second_ptr[size_t(t0)], hi = plan->second_ptr[size_t(t0 + nt)];
+      plan->stage_launches[0] += 1;
+      plan->stage_launches[1] += contract_launches(prec);
+      plan->stage_launches[2] += 1 + (hi > lo ? 1 : 0);
+    }
+  }
+  if (timed) plan->timed_passes = n_pass;
+  if (flags & MSASM_FLAG_CHECK_DEGENERATE) {
+    unsigned long long cnt = 0;
+    MSASM_CUDA(cudaMemcpyAsync(&cnt, plan->d_degenerate, sizeof(cnt), cudaMemcpyDeviceToHost, s));
+    MSASM_CUDA(cudaStreamSynchronize(s));
+    if (cnt)
+      return fail(MSASM_EDEGENERATE,
+                  "degenerate macro element: |det J| <= tol at " + std::to_string(cnt) + " interpolation nodes");
+  }
+  return MSASM_OK;
+}
+
+static size_t value_bytes(msasm_precision prec) { return is_f64_precision(prec) ? 8 : 4; }
+
+msasm_status msasm_stage_times(const msasm_plan* plan, double* ms, int32_t* launches) {
+  if (!plan || !ms) return fail(MSASM_EINVAL, "plan or ms is NULL");
+  if (plan->timed_passes <= 0) return fail(MSASM_EINVAL, "the last assemble did not record stage times");
+  for (int k = 0; k < 3; ++k) ms[k] = 0.0;
+  for (int p = 0; p < plan->timed_passes; ++p) {
+    MSASM_CUDA(cudaEventSynchronize(plan->events[4 * p + 3]));
+    for (int k = 0; k < 3; ++k) {
+      float t = 0.0f;
+      MSASM_CUDA(cudaEventElapsedTime(&t, plan->events[4 * p + k], plan->events[4 * p + k + 1]));
+      ms[k] += t;
+    }
+  }
+  if (launches)
+    for (int k = 0; k < 3; ++k) launches[k] = plan->stage_launches[k];
+  return MSASM_OK;
+}
+
+msasm_status msasm_assemble_host(msasm_plan* plan, const double* h_ctrl, double E, double nu, msasm_precision prec,
+                                 void* h_values, uint32_t flags, void* stream) {
+  if (!plan || !h_ctrl || !h_values) return fail(MSASM_EINVAL, "plan, h_ctrl or h_values is NULL");
+  if (prec < MSASM_F64 || prec > MSASM_F64_EMU) return fail(MSASM_EINVAL, "unknown precision");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t cbytes = size_t(plan->n_ctrl) * 3 * sizeof(double);
+  const size_t vbytes = size_t(plan->nnz) * value_bytes(prec);
+  if (!plan->d_ctrl_stage) MSASM_CUDA(cudaMalloc(&plan->d_ctrl_stage, cbytes));
+  if (plan->values_stage_bytes < vbytes) {
+    cudaFree(plan->d_values_stage);
+    plan->d_values_stage = nullptr;
+    plan->values_stage_bytes = 0;
+    MSASM_CUDA(cudaMalloc(&plan->d_values_stage, vbytes));
+    plan->values_stage_bytes = vbytes;
+  }
+  MSASM_CUDA(cudaMemcpyAsync(plan->d_ctrl_stage, h_ctrl, cbytes, cudaMemcpyHostToDevice, s));
+  MSASM_TRY(msasm_assemble(plan, plan->d_ctrl_stage, E, nu, prec, plan->d_values_stage, flags, stream));
+  MSASM_CUDA(cudaMemcpyAsync(h_values, plan->d_values_stage, vbytes, cudaMemcpyDeviceToHost, s));
+  MSASM_CUDA(cudaStreamSynchronize(s));
+  return MSASM_OK;
+}
+
+msasm_status msasm_degenerate_count(const msasm_plan* plan, int64_t* count, void* stream) {
+  if (!plan || !count) return fail(MSASM_EINVAL, "plan or count is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned long long cnt = 0;
+  MSASM_CUDA(cudaMemcpyAsync(&cnt, plan->d_degenerate, sizeof(cnt), cudaMemcpyDeviceToHost, s));
+  MSASM_CUDA(cudaStreamSynchronize(s));
+  *count = int64_t(cnt);
+  return MSASM_OK;
+}
+
+msasm_status msasm_pullback(msasm_plan* plan, const double* d_ctrl, double E, double nu, double* d_coef,
+                            void* stream) {
+  if (!plan || !d_ctrl || !d_coef) return fail(MSASM_EINVAL, "plan, d_ctrl or d_coef is NULL");
+  MSASM_TRY(check_material(E, nu));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  double lam, mu;
+  lame(E, nu, lam, mu);
+  MSASM_CUDA(cudaMemsetAsync(plan->d_degenerate, 0, sizeof(unsigned long long), s));
+  const int64_t P = plan->tiles_per_pass, K = 9 * plan->tab->n_pi;
+  for (int64_t t0 = 0; t0 < plan->n_tiles; t0 += P) {
+    const int64_t nt = std::min(P, plan->n_tiles - t0);
+    MSASM_TRY(pullback_gpu(plan, d_ctrl, lam, mu, t0, nt, d_coef + size_t(9 * t0) * K, s));
+  }
+  return MSASM_OK;
+}
+
+msasm_status msasm_contract(const msasm_tables* tab, msasm_precision prec, const double* d_coef, int64_t n_tiles,
+                            void* d_nz, void* stream) {
+  if (!tab || !d_coef || !d_nz) return fail(MSASM_EINVAL, "tables, d_coef or d_nz is NULL");
+  if (n_tiles <= 0) return fail(MSASM_EINVAL, "n_tiles must be positive");
+  if (9 * n_tiles > 65535LL * 128) return fail(MSASM_EINVAL, "n_tiles too large for one contraction call");
+  if (prec < MSASM_F64 || prec > MSASM_F64_EMU) return fail(MSASM_EINVAL, "unknown precision");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int n_nz = tab->n_nz, K = 9 * tab->n_pi, ld = ld_nz_of(n_nz);
+  // the public layout is dense (leading dimension n_nz); contract into a padded buffer and copy rows
+  void* scratch = nullptr;
+  void* lp = nullptr;
+  const size_t vb = value_bytes(prec);
+  MSASM_CUDA(cudaMallocAsync(&scratch, size_t(9 * n_tiles) * ld * vb, s));
+  if (prec != MSASM_F64) MSASM_CUDA(cudaMallocAsync(&lp, size_t(9 * n_tiles) * K * sizeof(float) * 2, s));
+  msasm_status st = contract_dispatch(tab, prec, d_coef, n_tiles, scratch, lp, s);
+  if (st == MSASM_OK) {
+    cudaError_t e = cudaMemcpy2DAsync(d_nz, size_t(n_nz) * vb, scratch, size_t(ld) * vb, size_t(n_nz) * vb,
+                                      size_t(9 * n_tiles), cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) st = cuda_fail(e, "cudaMemcpy2DAsync(nz)");
+  }
+  cudaFreeAsync(scratch, s);
+  if (lp) cudaFreeAsync(lp, s);
+  return st;
+}
+
+msasm_status msasm_scatter(msasm_plan* plan, msasm_precision prec, const void* d_nz, void* d_values, void* stream) {
+  if (!plan || !d_nz || !d_values) return fail(MSASM_EINVAL, "plan, d_nz or d_values is NULL");
+  if (prec < MSASM_F64 || prec > MSASM_F64_EMU) return fail(MSASM_EINVAL, "unknown precision");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int n_nz = plan->tab->n_nz, ld = ld_nz_of(n_nz);
+  const size_t vb = value_bytes(prec);
+  // re-pad the dense public layout to the kernels' leading dimension
+  void* padded = nullptr;
+  MSASM_CUDA(cudaMallocAsync(&padded, size_t(9 * plan->n_tiles) * ld * vb, s));
+  cudaError_t e = cudaMemcpy2DAsync(padded, size_t(ld) * vb, d_nz, size_t(n_nz) * vb, size_t(n_nz) * vb,
+                                    size_t(9 * plan->n_tiles), cudaMemcpyDeviceToDevice, s);
+  msasm_status st = (e == cudaSuccess) ? scatter_dispatch(plan, prec, padded, 0, plan->n_tiles, d_values, s)
+                                       : cuda_fail(e, "cudaMemcpy2DAsync(nz)");
+  cudaFreeAsync(padded, s);
+  return st;
+}
+
+}  // extern "C"

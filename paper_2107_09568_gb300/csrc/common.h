@@ -1,0 +1,129 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/msasm.h"
+
+namespace msasm {
+
+// ------------------------------------------------------------------ errors
+void set_error(const std::string& msg);
+msasm_status fail(msasm_status st, const std::string& msg);
+msasm_status cuda_fail(cudaError_t err, const char* what);
+
+#define MSASM_CUDA(call)                                          \
+  do {                                                            \
+    cudaError_t err__ = (call);                                   \
+    if (err__ != cudaSuccess) return ::msasm::cuda_fail(err__, #call); \
+  } while (0)
+
+#define MSASM_TRY(call)                                           \
+  do {                                                            \
+    msasm_status st__ = (call);                                   \
+    if (st__ != MSASM_OK) return st__;                            \
+  } while (0)
+
+// ------------------------------------------------------------------ host math (host_math.cpp)
+// Gauss-Legendre rule with n points on [0,1] (Newton on the Legendre recurrence).
+void gauss_legendre01(int n, std::vector<double>& x, std::vector<double>& w);
+// Nonzero B-spline basis functions of degree p on the knot span `span` at u, and
+// their first derivatives: vals[0..p], ders[0..p] belong to functions span-p .. span.
+void bspline_span_basis(const double* knots, int p, int span, double u, double* vals, double* ders);
+// Index of the knot span [t_k, t_{k+1}) holding u (the last non-empty span for u = end).
+int bspline_find_span(const double* knots, int n_knots, int p, double u);
+
+// ------------------------------------------------------------------ reference tile topology (host_tile.cpp)
+struct Patch {
+  int degree[3];
+  int n_elem[3];
+  int n_fun[3];
+  double lo[3], hi[3];
+  std::vector<int> ids;   // local id of patch function a1 + n1*(a2 + n2*a3)
+};
+
+struct TileTopology {
+  std::vector<Patch> patches;
+  int n_T = 0;
+  std::vector<double> pos;              // 3*n_T control point positions in [0,1]^3
+  std::vector<int> pair_A, pair_B;      // I_coo (eq. 56), lexicographic, A <= B
+  std::vector<int64_t> nb_ptr;          // local adjacency incl. self (both orders)
+  std::vector<int> nb_idx;
+  std::vector<int> faces[6];            // local ids on xi_d = s (index 2d+s), matched order
+  std::vector<int> face_pos[6];         // position of a local id in faces[f], -1 if absent
+  std::vector<uint8_t> pair_face;       // bit d: A and B both on the xi_d = 0 face
+};
+
+msasm_status build_topology(const msasm_micro_desc* micro, TileTopology& topo);
+
+// ------------------------------------------------------------------ handles
+constexpr int kMaxPairPatches = 4;   // a point on a corner of the centre cube lies in 4 patches
+struct PairDesc {       // the patch contributions to one table row
+  int8_t patch[kMaxPairPatches];      // -1 = none
+  int8_t a[kMaxPairPatches][3];
+  int8_t b[kMaxPairPatches][3];
+  int8_t pad[4];
+};
+static_assert(sizeof(PairDesc) == 32, "PairDesc is two 16-byte words");
+
+}  // namespace msasm
+
+struct msasm_tables {
+  msasm::TileTopology topo;
+  int q = 0;
+  int n_pi = 0;
+  int n_nz = 0;
+  int n_gauss = 0;
+  double* d_T = nullptr;            // n_nz x 9 n_pi, FP64
+  int32_t* d_pairs = nullptr;       // 2 n_nz (A, B)
+  // operand copies for the reduced-precision contractions (created on first use)
+  float* d_T32 = nullptr;           // FP32 copy
+  void* d_Thi = nullptr;            // hi/lo 16-bit or tf32 operand slices
+  void* d_Tlo = nullptr;
+  int split_kind = -1;              // which precision the slices hold
+  float split_scale = 1.0f;
+  void* d_Tslices = nullptr;        // FP64-emulation slices
+  int n_slices = 0;
+  double* d_Tslice_scale = nullptr;
+  ~msasm_tables();
+};
+
+struct msasm_plan {
+  const msasm_tables* tab = nullptr;
+  int degree[3] = {0, 0, 0};
+  int n_elem[3] = {0, 0, 0};
+  int n_ctrl_dir[3] = {0, 0, 0};
+  int64_t n_tiles = 0, n_points = 0, n_rows = 0, nnz = 0, n_ctrl = 0;
+  int64_t tiles_per_pass = 0;
+  // macro basis at the interpolation nodes: per direction d, element e, node c, local function a:
+  // value and d/dxi (already scaled by the span length), and the first control index of the span.
+  double* d_basis[3] = {nullptr, nullptr, nullptr};   // [e][c][a][2]
+  int32_t* d_first[3] = {nullptr, nullptr, nullptr};  // [e]
+  // structure
+  int32_t* d_gmap = nullptr;        // n_tiles x n_T
+  int64_t* d_rowptr = nullptr;      // n_rows + 1
+  int32_t* d_col = nullptr;         // nnz
+  uint32_t* d_rank = nullptr;       // n_tiles x n_nz: rank_u | rank_l << 16, bit 31 = second contributor
+  int64_t* d_second = nullptr;      // t * n_nz + m of second contributors, ascending
+  int64_t n_second = 0;
+  std::vector<int64_t> second_ptr;  // host: entries of tile t are [second_ptr[t], second_ptr[t+1])
+  // scratch
+  double* d_coef = nullptr;         // 9 tiles_per_pass x 9 n_pi, FP64
+  void* d_nz = nullptr;             // 9 tiles_per_pass x n_nz, FP64-sized
+  void* d_coef_lp = nullptr;        // reduced-precision coefficient operands
+  size_t coef_lp_bytes = 0;
+  unsigned long long* d_degenerate = nullptr;
+  double* d_ctrl_stage = nullptr;   // device copy of the control net for msasm_assemble_host
+  void* d_values_stage = nullptr;
+  size_t values_stage_bytes = 0;
+  // stage timing (MSASM_FLAG_STAGE_TIMES): events per pass, 4 per pass (before pullback,
+  // contraction, scatter, after scatter), and the launches each stage issued
+  std::vector<cudaEvent_t> events;
+  int timed_passes = 0;
+  int stage_launches[3] = {0, 0, 0};
+  ~msasm_plan();
+};

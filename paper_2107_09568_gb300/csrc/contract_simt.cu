@@ -1,0 +1,122 @@
+// K3: the contraction of eq. 58 on the CUDA cores (FP64 DFMA or FP32 FFMA).
+//
+//   nz[n][m] = sum_k coef[n][k] * T[m][k],   n = 9t + 3a + b,  k = 9C + 3i + j,
+//
+// i.e. nzdata^T = mat[<A>]^T mat[K]^T.  A 128 x 128 output tile per CTA, 256
+// threads with an 8 x 8 register tile each (two 4-wide groups per direction so
+// that the stores of a warp are contiguous), operands staged through shared
+// memory k-major with a register prefetch of the next k-slab.  On GB300 the FP64
+// form is bound by the DFMA rate (about 1.2 TFLOP/s for the whole GPU), the FP32
+// form by the FFMA rate.
+#include "common.h"
+
+namespace msasm {
+
+template <typename T, int BK>
+__global__ void __launch_bounds__(256) contract_simt_kernel(const T* __restrict__ coef, const T* __restrict__ tab,
+                                                            int64_t N, int M, int K, int ld_nz, T* __restrict__ nz) {
+  constexpr int BN = 128, BM = 128;
+  constexpr int LOADS = BN * BK / 256;          // elements per thread per operand per slab
+  __shared__ T As[2][BK][BN + 4];
+  __shared__ T Bs[2][BK][BM + 4];
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;
+  const int64_t n0 = int64_t(blockIdx.y) * BN;
+  const int m0 = blockIdx.x * BM;
+  T acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = T(0);
+  T ra[LOADS], rb[LOADS];
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int l = 0; l < LOADS; ++l) {
+      int e = tid + l * 256;
+      int r = e / BK, kk = e % BK;
+      int64_t n = n0 + r;
+      int m = m0 + r, k = k0 + kk;
+      ra[l] = (n < N && k < K) ? coef[n * K + k] : T(0);
+      rb[l] = (m < M && k < K) ? tab[int64_t(m) * K + k] : T(0);
+    }
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int l = 0; l < LOADS; ++l) {
+      int e = tid + l * 256;
+      int r = e / BK, kk = e % BK;
+      As[buf][kk][r] = ra[l];
+      Bs[buf][kk][r] = rb[l];
+    }
+  };
+  const int n_slabs = (K + BK - 1) / BK;
+  load(0);
+  store(0);
+  __syncthreads();
+  for (int s = 0; s < n_slabs; ++s) {
+    const int buf = s & 1;
+    if (s + 1 < n_slabs) load((s + 1) * BK);
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      T a[8], b[8];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        a[i] = As[buf][kk][ty * 4 + i];
+        a[i + 4] = As[buf][kk][64 + ty * 4 + i];
+        b[i] = Bs[buf][kk][tx * 4 + i];
+        b[i + 4] = Bs[buf][kk][64 + tx * 4 + i];
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    if (s + 1 < n_slabs) store(buf ^ 1);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    int64_t n = n0 + ((i < 4) ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+    if (n >= N) continue;
+    T* row = nz + n * ld_nz;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      int m = m0 + ((j < 4) ? tx * 4 + j : 64 + tx * 4 + (j - 4));
+      if (m < M) row[m] = acc[i][j];
+    }
+  }
+}
+
+msasm_status contract_simt_f64(const double* d_coef, const double* d_T, int64_t n_tiles, int n_nz, int K, int ld_nz,
+                               double* d_nz, cudaStream_t stream) {
+  int64_t N = 9 * n_tiles;
+  dim3 grid(unsigned((n_nz + 127) / 128), unsigned((N + 127) / 128));
+  if (grid.y > 65535) return fail(MSASM_EUNSUPPORTED, "too many tiles for one contraction pass");
+  contract_simt_kernel<double, 8><<<grid, 256, 0, stream>>>(d_coef, d_T, N, n_nz, K, ld_nz, d_nz);
+  MSASM_CUDA(cudaGetLastError());
+  return MSASM_OK;
+}
+
+msasm_status contract_simt_f32(const float* d_coef, const float* d_T, int64_t n_tiles, int n_nz, int K, int ld_nz,
+                               float* d_nz, cudaStream_t stream) {
+  int64_t N = 9 * n_tiles;
+  dim3 grid(unsigned((n_nz + 127) / 128), unsigned((N + 127) / 128));
+  if (grid.y > 65535) return fail(MSASM_EUNSUPPORTED, "too many tiles for one contraction pass");
+  contract_simt_kernel<float, 16><<<grid, 256, 0, stream>>>(d_coef, d_T, N, n_nz, K, ld_nz, d_nz);
+  MSASM_CUDA(cudaGetLastError());
+  return MSASM_OK;
+}
+
+// FP64 -> FP32 conversion of an operand (round to nearest).
+__global__ void to_f32_kernel(const double* __restrict__ x, int64_t n, float* __restrict__ y) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    y[i] = __double2float_rn(x[i]);
+}
+
+msasm_status to_f32_gpu(const double* x, int64_t n, float* y, cudaStream_t stream) {
+  to_f32_kernel<<<152 * 8, 256, 0, stream>>>(x, n, y);
+  MSASM_CUDA(cudaGetLastError());
+  return MSASM_OK;
+}
+
+}  // namespace msasm

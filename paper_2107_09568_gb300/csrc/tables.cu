@@ -1,0 +1,202 @@
+// K1: the stiffness lookup table mat[K] (eq. 51-52, 57) in FP64 on the GPU.
+//
+// Every micro patch is an axis-aligned box with an affine map and a tensor-product
+// basis, and the projection basis N_C is a tensor product too, so the 3-D
+// integral of eq. 52 over one patch factorises into three 1-D integrals:
+//
+//   int_patch d_i phi_A d_j phi_B N_C dxi = prod_d I_p,d[i==d, j==d][a_d, b_d, c_d],
+//   I_p,d[da, db][a, b, c] = int_{lo_d}^{hi_d} f_a^(da) f_b^(db) l_c dxi_d.
+//
+// Stage 1 computes the small 1-D tables by Gauss quadrature per element (exact:
+// the integrand is a polynomial of degree <= 2 p_T + q on each element); stage 2
+// writes every table entry as a sum over the patches holding both functions of
+// the pair (up to four: a point on a corner of the centre cube is in four patches).  Both stages are FP64.
+#include <cstdio>
+#include <vector>
+
+#include "common.h"
+
+namespace msasm {
+
+struct Table1DParams {
+  int n_patches, q, nf_max, n_gauss;
+  int degree[16][3];
+  int n_elem[16][3];
+  double lo[16][3], hi[16][3];
+  double gx[16], gw[16];     // Gauss rule on [0,1]
+  double nodes[8];           // interpolation nodes on [0,1]
+};
+
+// Nonzero basis functions (values and d/ds) of the open uniform knot vector with n
+// elements and degree p on element e (span e + p); knot k = clamp((k - p)/n, 0, 1).
+__device__ inline void uniform_span_basis(int p, int n, int e, double s, double* N, double* dN) {
+  auto knot = [&](int k) { return fmin(fmax(double(k - p) / n, 0.0), 1.0); };
+  int span = e + p;
+  double left[8], right[8], low[8];
+  // degree p - 1 values first (for derivatives), then degree p
+  for (int deg = (p > 0 ? p - 1 : 0); deg <= p; ++deg) {
+    double* out = (deg == p) ? N : low;
+    out[0] = 1.0;
+    for (int j = 1; j <= deg; ++j) {
+      left[j] = s - knot(span + 1 - j);
+      right[j] = knot(span + j) - s;
+      double carry = 0.0;
+      for (int r = 0; r < j; ++r) {
+        double f = out[r] / (right[r + 1] + left[j - r]);
+        out[r] = carry + right[r + 1] * f;
+        carry = left[j - r] * f;
+      }
+      out[j] = carry;
+    }
+    if (p == 0) break;
+  }
+  for (int k = 0; k <= p; ++k) {
+    if (p == 0) { dN[k] = 0.0; continue; }
+    int i = span - p + k;
+    double a = (k >= 1) ? low[k - 1] : 0.0;
+    double b = (k <= p - 1) ? low[k] : 0.0;
+    double da = knot(i + p) - knot(i), db = knot(i + p + 1) - knot(i + 1);
+    dN[k] = (da > 0 ? p * a / da : 0.0) - (db > 0 ? p * b / db : 0.0);
+  }
+}
+
+__global__ void table_1d_kernel(Table1DParams prm, double* __restrict__ I1) {
+  const int nq = prm.q + 1, nf = prm.nf_max;
+  const int64_t total = int64_t(prm.n_patches) * 3 * 4 * nf * nf * nq;
+  int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  int c = int(idx % nq);
+  int64_t r = idx / nq;
+  int b = int(r % nf); r /= nf;
+  int a = int(r % nf); r /= nf;
+  int flag = int(r % 4); r /= 4;
+  int d = int(r % 3);
+  int p = int(r / 3);
+  int deg = prm.degree[p][d], ne = prm.n_elem[p][d];
+  int nfun = ne + deg;
+  double acc = 0.0;
+  if (a < nfun && b < nfun) {
+    double lo = prm.lo[p][d], h = prm.hi[p][d] - prm.lo[p][d];
+    int da = flag >> 1, db = flag & 1;
+    for (int e = 0; e < ne; ++e) {
+      if (a < e || a > e + deg || b < e || b > e + deg) continue;
+      for (int g = 0; g < prm.n_gauss; ++g) {
+        double s = (e + prm.gx[g]) / ne;
+        double N[8], dN[8];
+        uniform_span_basis(deg, ne, e, s, N, dN);
+        double fa = da ? dN[a - e] / h : N[a - e];   // d/dxi = (1/h) d/ds
+        double fb = db ? dN[b - e] / h : N[b - e];
+        double xi = lo + h * s;
+        double lc = 1.0;
+        for (int k = 0; k < nq; ++k)
+          if (k != c) lc *= (xi - prm.nodes[k]) / (prm.nodes[c] - prm.nodes[k]);
+        acc += prm.gw[g] / ne * h * fa * fb * lc;    // dxi = h ds, element length 1/ne in s
+      }
+    }
+  }
+  I1[idx] = acc;
+}
+
+__global__ void table_assemble_kernel(const PairDesc* __restrict__ desc, const double* __restrict__ I1,
+                                      int n_nz, int q, int nf, double* __restrict__ T) {
+  const int nq = q + 1, n_pi = nq * nq * nq, row = 9 * n_pi;
+  const int64_t total = int64_t(n_nz) * row;
+  for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < total;
+       idx += int64_t(gridDim.x) * blockDim.x) {
+    int m = int(idx / row);
+    int k = int(idx % row);
+    int C = k / 9, i = (k % 9) / 3, j = k % 3;
+    int cc[3] = {C % nq, (C / nq) % nq, C / (nq * nq)};
+    PairDesc pd = desc[m];
+    double v = 0.0;
+    for (int s = 0; s < kMaxPairPatches; ++s) {
+      int p = pd.patch[s];
+      if (p < 0) continue;
+      double prod = 1.0;
+      for (int d = 0; d < 3; ++d) {
+        int flag = (i == d ? 2 : 0) + (j == d ? 1 : 0);
+        int64_t off = ((((int64_t(p) * 3 + d) * 4 + flag) * nf + pd.a[s][d]) * nf + pd.b[s][d]) * nq + cc[d];
+        prod *= I1[off];
+      }
+      v += prod;
+    }
+    T[idx] = v;
+  }
+}
+
+msasm_status build_table_gpu(msasm_tables* tab, cudaStream_t stream) {
+  const TileTopology& topo = tab->topo;
+  const int q = tab->q, nq = q + 1;
+  Table1DParams prm{};
+  prm.n_patches = int(topo.patches.size());
+  prm.q = q;
+  int p_T = 0, nf_max = 0;
+  for (int p = 0; p < prm.n_patches; ++p)
+    for (int d = 0; d < 3; ++d) {
+      const Patch& P = topo.patches[p];
+      prm.degree[p][d] = P.degree[d];
+      prm.n_elem[p][d] = P.n_elem[d];
+      prm.lo[p][d] = P.lo[d];
+      prm.hi[p][d] = P.hi[d];
+      p_T = std::max(p_T, P.degree[d]);
+      nf_max = std::max(nf_max, P.n_fun[d]);
+    }
+  prm.nf_max = nf_max;
+  int ng = tab->n_gauss > 0 ? tab->n_gauss : (2 * p_T + q + 2) / 2;
+  if (ng > 16) return fail(MSASM_EINVAL, "n_gauss must be <= 16");
+  tab->n_gauss = ng;
+  std::vector<double> gx, gw;
+  gauss_legendre01(ng, gx, gw);
+  for (int g = 0; g < ng; ++g) { prm.gx[g] = gx[g]; prm.gw[g] = gw[g]; }
+  prm.n_gauss = ng;
+  std::vector<double> nx, nw;
+  gauss_legendre01(nq, nx, nw);
+  for (int c = 0; c < nq; ++c) prm.nodes[c] = nx[c];
+
+  // pair descriptors: patches holding both functions of the pair, with local indices
+  std::vector<std::vector<std::pair<int, int>>> where(topo.n_T);   // (patch, local function)
+  for (int p = 0; p < prm.n_patches; ++p)
+    for (size_t f = 0; f < topo.patches[p].ids.size(); ++f) where[topo.patches[p].ids[f]].push_back({p, int(f)});
+  std::vector<PairDesc> desc(tab->n_nz);
+  for (int m = 0; m < tab->n_nz; ++m) {
+    PairDesc pd;
+    for (int s = 0; s < kMaxPairPatches; ++s) {
+      pd.patch[s] = -1;
+      for (int d = 0; d < 3; ++d) pd.a[s][d] = pd.b[s][d] = 0;
+    }
+    for (int k = 0; k < 4; ++k) pd.pad[k] = 0;
+    int s = 0;
+    for (auto& wa : where[topo.pair_A[m]])
+      for (auto& wb : where[topo.pair_B[m]]) {
+        if (wa.first != wb.first) continue;
+        if (s >= kMaxPairPatches) return fail(MSASM_EUNSUPPORTED, "a pair lies in more than four patches");
+        const Patch& P = topo.patches[wa.first];
+        pd.patch[s] = int8_t(wa.first);
+        int fa = wa.second, fb = wb.second;
+        pd.a[s][0] = int8_t(fa % P.n_fun[0]);
+        pd.a[s][1] = int8_t((fa / P.n_fun[0]) % P.n_fun[1]);
+        pd.a[s][2] = int8_t(fa / (P.n_fun[0] * P.n_fun[1]));
+        pd.b[s][0] = int8_t(fb % P.n_fun[0]);
+        pd.b[s][1] = int8_t((fb / P.n_fun[0]) % P.n_fun[1]);
+        pd.b[s][2] = int8_t(fb / (P.n_fun[0] * P.n_fun[1]));
+        ++s;
+      }
+    desc[m] = pd;
+  }
+  int64_t n1 = int64_t(prm.n_patches) * 3 * 4 * nf_max * nf_max * nq;
+  double* d_I1 = nullptr;
+  PairDesc* d_desc = nullptr;
+  MSASM_CUDA(cudaMallocAsync(&d_I1, n1 * sizeof(double), stream));
+  MSASM_CUDA(cudaMallocAsync(&d_desc, desc.size() * sizeof(PairDesc), stream));
+  MSASM_CUDA(cudaMemcpyAsync(d_desc, desc.data(), desc.size() * sizeof(PairDesc), cudaMemcpyHostToDevice, stream));
+  table_1d_kernel<<<unsigned((n1 + 127) / 128), 128, 0, stream>>>(prm, d_I1);
+  MSASM_CUDA(cudaGetLastError());
+  table_assemble_kernel<<<152 * 8, 256, 0, stream>>>(d_desc, d_I1, tab->n_nz, q, nf_max, tab->d_T);
+  MSASM_CUDA(cudaGetLastError());
+  MSASM_CUDA(cudaFreeAsync(d_I1, stream));
+  MSASM_CUDA(cudaFreeAsync(d_desc, stream));
+  MSASM_CUDA(cudaStreamSynchronize(stream));   // `desc` (host) must outlive the copy
+  return MSASM_OK;
+}
+
+}  // namespace msasm
