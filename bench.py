@@ -34,6 +34,7 @@ WORKLOAD_TEXT = {
     "beam1000": "twisted beam 10x10x10 tiles (90-degree twist), cross cell 7 patches x 3^3 degree-2 elements, "
                 "q=3 (64 nodes), E=1 nu=0.3",
     "cube8": "perturbed cubic cube split 2x2x2, cross cell 7 patches x 2^3 elements, q=2",
+    "beam125": "twisted beam 5x5x5 tiles, cross cell n_e=3, q=3 (profiling case)",
     "beam4000": "twisted beam 40x10x10 tiles, cross cell n_e=3, q=3",
     "cantilever2000": "cantilever plate 20x20x5 tiles, cross cell n_e=2, q=3",
     "arc2000": "quarter arc 20x10x10 tiles, cross cell n_e=3, q=3 (uniform width 0.3)",

@@ -242,6 +242,8 @@ def workload(name: str) -> Workload:
         return Workload(name, macro_perturbed_cube(seed=0), n_e=2, q=2, precisions=("f64",))
     if name == "beam1000":
         return Workload(name, macro_twisted_beam(10, 10, 10), n_e=3, q=3, precisions=("f64", "f32"))
+    if name == "beam125":      # small profiling case of the same shape (inputs still larger than L2)
+        return Workload(name, macro_twisted_beam(5, 5, 5), n_e=3, q=3, precisions=("f64", "f32"))
     if name == "beam4000":
         return Workload(name, macro_twisted_beam(40, 10, 10), n_e=3, q=3,
                         precisions=("split_f16", "split_bf16", "tf32"))
