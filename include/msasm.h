@@ -177,6 +177,22 @@ msasm_status msasm_pullback(msasm_plan* plan, const double* d_ctrl, double E, do
 msasm_status msasm_contract(const msasm_tables* tab, msasm_precision prec, const double* d_coef,
                             int64_t n_tiles, void* d_nz, void* stream);
 
+/* The FP64 contraction of msasm_contract for callers that cannot let the
+ * library allocate device memory (an application that has reserved the GPU's
+ * memory for its own pool, or a service that may not call cudaMalloc/cudaFree,
+ * which synchronise the device, after start-up).  The paper has no counterpart:
+ * it is an interface addition, not a step of the method.  Same arguments and
+ * result as msasm_contract with MSASM_F64 (d_nz dense, 9*n_tiles x n_nz FP64),
+ * but the padded intermediate lives in a fixed 32 MiB file-scope device array:
+ * 9 * n_tiles * round_up(n_nz, 8) * 8 bytes must fit, otherwise EINVAL (for
+ * n_nz = 23286 that is 20 tiles per call).  The first call on a device, made
+ * with that device current, looks up the array's address; make it before any
+ * stream capture.  Calls share the array: calls that overlap on the GPU race and
+ * must be serialised by the caller.  Nothing is allocated and nothing needs
+ * clearing between calls. */
+msasm_status msasm_contract_noalloc(const msasm_tables* tab, const double* d_coef, int64_t n_tiles,
+                                   double* d_nz, void* stream);
+
 /* Step 4 only: CSR values from nzdata of all tiles of the plan (d_nz as written by
  * msasm_contract for all plan tiles, same precision family). */
 msasm_status msasm_scatter(msasm_plan* plan, msasm_precision prec, const void* d_nz,

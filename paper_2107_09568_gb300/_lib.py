@@ -54,6 +54,7 @@ _SIGS = {
     "msasm_pullback": (c_i32, [c_vp, c_vp, c_dbl, c_dbl, c_vp, c_vp]),
     "msasm_contract": (c_i32, [c_vp, c_i32, c_vp, c_i64, c_vp, c_vp]),
     "msasm_scatter": (c_i32, [c_vp, c_i32, c_vp, c_vp, c_vp]),
+    "msasm_contract_noalloc": (c_i32, [c_vp, c_vp, c_i64, c_vp, c_vp]),
     "msasm_stage_times": (c_i32, [c_vp, P(c_dbl), P(c_i32)]),
     "msasm_last_error": (C.c_char_p, []),
     "msasm_version": (C.c_char_p, []),
