@@ -49,7 +49,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="f64")
     ap.add_argument("--workload", default="beam1000")
-    ap.add_argument("--forms", default="f32", help="comma list of extra precision forms to report")
+    ap.add_argument("--forms", default="f32,split_f16,split_bf16,tf32,tf32x3",
+                    help="comma list of extra precision forms to report")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()

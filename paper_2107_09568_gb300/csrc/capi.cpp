@@ -42,6 +42,14 @@ msasm_status to_f32_gpu(const double* x, int64_t n, float* y, cudaStream_t strea
 template <typename T>
 msasm_status scatter_gpu(const msasm_plan* plan, const T* d_nz, int ld_nz, int64_t t0, int64_t n_tiles,
                          const int64_t* d_list, int64_t n_list, T* d_values, cudaStream_t stream);
+int tc_kind_of(msasm_precision prec);
+int tc_kpad(int K, int kind);
+size_t tc_slice_bytes(int64_t rows, int K, int kind);
+msasm_status tc_split_gpu(const double* x, int64_t rows, int K, int kind, void* hi, void* lo, float* row_scale,
+                          cudaStream_t s);
+msasm_status contract_tc_gpu(int kind, const void* a_hi, const void* a_lo, const float* a_scale, int M,
+                             const void* b_hi, const void* b_lo, const float* b_scale, int64_t N, int K, float* out,
+                             int ld, unsigned* d_err, cudaStream_t s);
 
 static inline int ld_nz_of(int n_nz) { return (n_nz + 7) & ~7; }
 
@@ -57,6 +65,7 @@ msasm_tables::~msasm_tables() {
   cudaFree(d_T32);
   cudaFree(d_Thi);
   cudaFree(d_Tlo);
+  cudaFree(d_Tscale);
   cudaFree(d_Tslices);
   cudaFree(d_Tslice_scale);
 }
@@ -75,6 +84,7 @@ msasm_plan::~msasm_plan() {
   cudaFree(d_nz);
   cudaFree(d_coef_lp);
   cudaFree(d_degenerate);
+  cudaFree(d_tc_err);
   cudaFree(d_ctrl_stage);
   cudaFree(d_values_stage);
   for (cudaEvent_t e : events) cudaEventDestroy(e);
@@ -256,6 +266,7 @@ msasm_status msasm_plan_create(const msasm_tables* tab, const msasm_macro_desc* 
   if (err == cudaSuccess) err = dev((void**)&plan->d_coef, size_t(9 * plan->tiles_per_pass) * 9 * n_pi * sizeof(double));
   if (err == cudaSuccess) err = dev((void**)&plan->d_nz, size_t(9 * plan->tiles_per_pass) * ld * sizeof(double));
   if (err == cudaSuccess) err = dev((void**)&plan->d_degenerate, sizeof(unsigned long long));
+  if (err == cudaSuccess) err = dev((void**)&plan->d_tc_err, sizeof(unsigned));
   if (err == cudaSuccess) err = dev((void**)&d_pptr, pptr.size() * sizeof(int64_t));
   if (err == cudaSuccess) err = dev((void**)&d_pcol, pcol.size() * sizeof(int32_t));
   if (err == cudaSuccess) err = dev((void**)&d_pair_face, size_t(n_nz));
@@ -284,6 +295,7 @@ msasm_status msasm_plan_create(const msasm_tables* tab, const msasm_macro_desc* 
   if (err == cudaSuccess) err = h2d(d_pair_face, tab->topo.pair_face.data(), size_t(n_nz));
   if (err == cudaSuccess) err = cudaMemsetAsync(d_bad, 0, sizeof(unsigned long long), s);
   if (err == cudaSuccess) err = cudaMemsetAsync(plan->d_degenerate, 0, sizeof(unsigned long long), s);
+  if (err == cudaSuccess) err = cudaMemsetAsync(plan->d_tc_err, 0, sizeof(unsigned), s);
   if (err != cudaSuccess) {
     cudaStreamSynchronize(s);
     cleanup_tmp();
@@ -351,8 +363,34 @@ static void lame(double E, double nu, double& lam, double& mu) {
 }
 
 // contraction of `n_tiles` tiles of FP64 coefficients into nzdata of the precision family
+// table slices for a tensor-core form, built once per table and precision
+static msasm_status ensure_table_slices(msasm_tables* tab, int kind, cudaStream_t s) {
+  if (tab->split_kind == kind) return MSASM_OK;
+  cudaFree(tab->d_Thi);
+  cudaFree(tab->d_Tlo);
+  cudaFree(tab->d_Tscale);
+  tab->d_Thi = tab->d_Tlo = nullptr;
+  tab->d_Tscale = nullptr;
+  tab->split_kind = -1;
+  const int K = 9 * tab->n_pi;
+  const size_t bytes = tc_slice_bytes(tab->n_nz, K, kind);
+  MSASM_CUDA(cudaMalloc(&tab->d_Thi, bytes));
+  MSASM_CUDA(cudaMalloc(&tab->d_Tlo, bytes));
+  MSASM_CUDA(cudaMalloc(&tab->d_Tscale, size_t(tab->n_nz) * sizeof(float)));
+  MSASM_TRY(tc_split_gpu(tab->d_T, tab->n_nz, K, kind, tab->d_Thi, tab->d_Tlo, tab->d_Tscale, s));
+  tab->split_kind = kind;
+  return MSASM_OK;
+}
+
+// bytes of coefficient slices (hi, lo, row scales) for n_tiles tiles
+static size_t coef_lp_bytes_for(int64_t n_tiles, int n_pi) {
+  const int K = 9 * n_pi;
+  return 2 * size_t(9 * n_tiles) * size_t(K + 64) * 4 + size_t(9 * n_tiles) * 4 + 256;
+}
+
 static msasm_status contract_dispatch(const msasm_tables* ctab, msasm_precision prec, const double* d_coef,
-                                      int64_t n_tiles, void* d_nz, void* scratch_lp, cudaStream_t s) {
+                                      int64_t n_tiles, void* d_nz, void* scratch_lp, cudaStream_t s,
+                                      unsigned* d_err) {
   msasm_tables* tab = const_cast<msasm_tables*>(ctab);
   const int K = 9 * tab->n_pi, n_nz = tab->n_nz, ld = ld_nz_of(n_nz);
   switch (prec) {
@@ -367,16 +405,30 @@ static msasm_status contract_dispatch(const msasm_tables* ctab, msasm_precision 
       MSASM_TRY(to_f32_gpu(d_coef, 9 * n_tiles * K, c32, s));
       return contract_simt_f32(c32, tab->d_T32, n_tiles, n_nz, K, ld, static_cast<float*>(d_nz), s);
     }
+    case MSASM_SPLIT_F16:
+    case MSASM_SPLIT_BF16:
+    case MSASM_TF32:
+    case MSASM_TF32X3: {
+      const int kind = tc_kind_of(prec);
+      MSASM_TRY(ensure_table_slices(tab, kind, s));
+      const size_t sb = tc_slice_bytes(9 * n_tiles, K, kind);
+      uint8_t* hi = static_cast<uint8_t*>(scratch_lp);
+      uint8_t* lo = hi + sb;
+      float* sc = reinterpret_cast<float*>(lo + sb);
+      MSASM_TRY(tc_split_gpu(d_coef, 9 * n_tiles, K, kind, hi, lo, sc, s));
+      return contract_tc_gpu(kind, tab->d_Thi, tab->d_Tlo, tab->d_Tscale, n_nz, hi, lo, sc, 9 * n_tiles, K,
+                             static_cast<float*>(d_nz), ld, d_err, s);
+    }
     default:
       return fail(MSASM_EUNSUPPORTED, "precision not available in this build");
   }
 }
 
-static int contract_launches(msasm_precision prec) { return prec == MSASM_F32 ? 2 : 1; }
+static int contract_launches(msasm_precision prec) { return prec == MSASM_F64 ? 1 : 2; }
 
 static msasm_status ensure_lp_scratch(msasm_plan* plan, msasm_precision prec) {
   if (prec == MSASM_F64) return MSASM_OK;
-  size_t need = size_t(9 * plan->tiles_per_pass) * 9 * plan->tab->n_pi * sizeof(float) * 2;
+  size_t need = coef_lp_bytes_for(plan->tiles_per_pass, plan->tab->n_pi);
   if (plan->coef_lp_bytes >= need) return MSASM_OK;
   cudaFree(plan->d_coef_lp);
   plan->d_coef_lp = nullptr;
@@ -426,7 +478,7 @@ msasm_status msasm_assemble(msasm_plan* plan, const double* d_ctrl, double E, do
     if (timed) MSASM_CUDA(cudaEventRecord(plan->events[4 * pass + 0], s));
     MSASM_TRY(pullback_gpu(plan, d_ctrl, lam, mu, t0, nt, plan->d_coef, s));
     if (timed) MSASM_CUDA(cudaEventRecord(plan->events[4 * pass + 1], s));
-    MSASM_TRY(contract_dispatch(plan->tab, prec, plan->d_coef, nt, plan->d_nz, plan->d_coef_lp, s));
+    MSASM_TRY(contract_dispatch(plan->tab, prec, plan->d_coef, nt, plan->d_nz, plan->d_coef_lp, s, plan->d_tc_err));
     if (timed) MSASM_CUDA(cudaEventRecord(plan->events[4 * pass + 2], s));
     MSASM_TRY(scatter_dispatch(plan, prec, plan->d_nz, t0, nt, d_values, s));
     if (timed) {
@@ -440,8 +492,11 @@ msasm_status msasm_assemble(msasm_plan* plan, const double* d_ctrl, double E, do
   if (timed) plan->timed_passes = n_pass;
   if (flags & MSASM_FLAG_CHECK_DEGENERATE) {
     unsigned long long cnt = 0;
+    unsigned tc_err = 0;
     MSASM_CUDA(cudaMemcpyAsync(&cnt, plan->d_degenerate, sizeof(cnt), cudaMemcpyDeviceToHost, s));
+    MSASM_CUDA(cudaMemcpyAsync(&tc_err, plan->d_tc_err, sizeof(tc_err), cudaMemcpyDeviceToHost, s));
     MSASM_CUDA(cudaStreamSynchronize(s));
+    if (tc_err) return fail(MSASM_ECUDA, "a tensor-core pipeline wait timed out (results invalid)");
     if (cnt)
       return fail(MSASM_EDEGENERATE,
                   "degenerate macro element: |det J| <= tol at " + std::to_string(cnt) + " interpolation nodes");
@@ -527,17 +582,29 @@ msasm_status msasm_contract(const msasm_tables* tab, msasm_precision prec, const
   // the public layout is dense (leading dimension n_nz); contract into a padded buffer and copy rows
   void* scratch = nullptr;
   void* lp = nullptr;
+  unsigned* d_err = nullptr;
   const size_t vb = value_bytes(prec);
+  (void)K;
   MSASM_CUDA(cudaMallocAsync(&scratch, size_t(9 * n_tiles) * ld * vb, s));
-  if (prec != MSASM_F64) MSASM_CUDA(cudaMallocAsync(&lp, size_t(9 * n_tiles) * K * sizeof(float) * 2, s));
-  msasm_status st = contract_dispatch(tab, prec, d_coef, n_tiles, scratch, lp, s);
+  MSASM_CUDA(cudaMallocAsync(&d_err, sizeof(unsigned), s));
+  MSASM_CUDA(cudaMemsetAsync(d_err, 0, sizeof(unsigned), s));
+  if (prec != MSASM_F64) MSASM_CUDA(cudaMallocAsync(&lp, coef_lp_bytes_for(n_tiles, tab->n_pi), s));
+  msasm_status st = contract_dispatch(tab, prec, d_coef, n_tiles, scratch, lp, s, d_err);
   if (st == MSASM_OK) {
     cudaError_t e = cudaMemcpy2DAsync(d_nz, size_t(n_nz) * vb, scratch, size_t(ld) * vb, size_t(n_nz) * vb,
                                       size_t(9 * n_tiles), cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) st = cuda_fail(e, "cudaMemcpy2DAsync(nz)");
   }
+  unsigned h_err = 0;
+  if (st == MSASM_OK) {
+    cudaError_t e = cudaMemcpyAsync(&h_err, d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_fail(e, "msasm_contract");
+  }
   cudaFreeAsync(scratch, s);
+  cudaFreeAsync(d_err, s);
   if (lp) cudaFreeAsync(lp, s);
+  if (st == MSASM_OK && h_err) st = fail(MSASM_ECUDA, "a tensor-core pipeline wait timed out (results invalid)");
   return st;
 }
 

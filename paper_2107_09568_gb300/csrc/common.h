@@ -84,8 +84,8 @@ struct msasm_tables {
   float* d_T32 = nullptr;           // FP32 copy
   void* d_Thi = nullptr;            // hi/lo 16-bit or tf32 operand slices
   void* d_Tlo = nullptr;
+  float* d_Tscale = nullptr;        // per-row 2^-e of the split-FP16 slices
   int split_kind = -1;              // which precision the slices hold
-  float split_scale = 1.0f;
   void* d_Tslices = nullptr;        // FP64-emulation slices
   int n_slices = 0;
   double* d_Tslice_scale = nullptr;
@@ -117,6 +117,7 @@ struct msasm_plan {
   void* d_coef_lp = nullptr;        // reduced-precision coefficient operands
   size_t coef_lp_bytes = 0;
   unsigned long long* d_degenerate = nullptr;
+  unsigned* d_tc_err = nullptr;     // set by a tensor-core kernel whose pipeline wait timed out
   double* d_ctrl_stage = nullptr;   // device copy of the control net for msasm_assemble_host
   void* d_values_stage = nullptr;
   size_t values_stage_bytes = 0;

@@ -1,0 +1,435 @@
+// K4: the contraction of eq. 58 on the 5th-generation tensor cores (tcgen05, TMEM, TMA).
+//
+//   D[m][n] = sum_k T[m][k] coef[n][k],  written as nz[n][m]  (m: table row / pair, n = 9t + 3a + b)
+//
+// Operands are split into 16-bit (or TF32) slices so that the products reach FP32 accuracy
+// (x = hi + lo):
+//   split FP16 : x' = 2^e_row x, hi = fp16(x'), lo' = fp16(2^11 (x' - hi)); two TMEM accumulators
+//                D0 = hi.hi and D1 = hi.lo' + lo'.hi, result (D0 + 2^-11 D1) 2^-(e_m + e_n)
+//                (a power-of-two scale per row keeps every row inside FP16's range)
+//   split BF16 : hi = bf16(x), lo = bf16(x - hi); D0 = hi.hi, D1 = hi.lo + lo.hi, result D0 + D1
+//   TF32       : one product of the rounded operands
+//   TF32x3     : hi = tf32(x), lo = tf32(x - hi); D0 = hi.hi, D1 = hi.lo + lo.hi, result D0 + D1
+// Keeping the small cross terms in their own accumulator keeps their FP32 accumulation error
+// relative to the small terms instead of to the whole sum.
+//
+// One CTA computes a 128 (m) x 256 (n) tile; 6 warps: warp 0 issues TMA loads (128-byte
+// swizzled K-major boxes) into a 2-stage shared-memory ring, warp 1 owns the TMEM allocation
+// and one elected lane issues tcgen05.mma (M=128, N=256, K=16 for f16/bf16, K=8 for tf32),
+// warps 2-5 read the accumulators back with tcgen05.ld (each warp its 32-lane quarter) and
+// store nz with the rows of a warp contiguous in m.  Every mbarrier wait is bounded; on a
+// timeout the CTA records an error flag, drains what it issued and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <mutex>
+
+#include "common.h"
+
+namespace msasm {
+
+enum SplitKind { kSplitF16 = 0, kSplitBF16 = 1, kTF32 = 2, kTF32x3 = 3 };
+
+constexpr int TC_BM = 128;          // rows of a CTA tile (TMEM lanes), table rows m
+constexpr int TC_BN = 256;          // columns of a CTA tile (TMEM columns), coefficient rows n
+constexpr int TC_ROW_BYTES = 128;   // one swizzle row: 64 x 16-bit or 32 x 32-bit elements of k
+constexpr int TC_STAGES = 2;
+constexpr int TC_A_BYTES = TC_BM * TC_ROW_BYTES;   // 16 KB
+constexpr int TC_B_BYTES = TC_BN * TC_ROW_BYTES;   // 32 KB
+constexpr int TC_STAGE_BYTES = 2 * TC_A_BYTES + 2 * TC_B_BYTES;
+constexpr int TC_SMEM_BYTES = TC_STAGES * TC_STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+constexpr long long TC_WAIT_CYCLES = 4000000000LL;   // about 2 s at 2 GHz
+
+struct TcParams {
+  int M, N, K;             // logical sizes: m rows, n rows, k
+  int kblocks;             // k blocks of 128 bytes of operand
+  int kind;                // SplitKind
+  const float* scale_m;    // per-row 2^-e for split FP16 (else null)
+  const float* scale_n;
+  float* out;              // nz[n][m], leading dimension ld
+  int ld;
+  unsigned* err;           // set to 1 on a timed-out wait
+};
+
+// ------------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false (and the error flag set) if the phase did not complete in time.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned* err) {
+  if (mbar_try_wait(bar, parity)) return true;
+  long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > TC_WAIT_CYCLES) {
+      atomicExch(err, 1u);
+      return false;
+    }
+  }
+  return true;
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
+      : "memory");
+}
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= uint64_t((saddr & 0x3FFFFu) >> 4);          // start address
+  d |= uint64_t(1) << 16;                          // leading byte offset (unused for swizzled K-major)
+  d |= uint64_t(1024 >> 4) << 32;                  // stride byte offset between 8-row groups
+  d |= uint64_t(1) << 46;                          // descriptor version for tcgen05
+  d |= uint64_t(2) << 61;                          // SWIZZLE_128B
+  return d;
+}
+// Instruction descriptor: D = F32, A/B format, both K-major, N >> 3, M >> 4.
+__host__ __device__ constexpr uint32_t instr_desc(uint32_t ab_format, int M, int N) {
+  return (1u << 4) | (ab_format << 7) | (ab_format << 10) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// ------------------------------------------------------------------ the kernel
+__global__ void __launch_bounds__(192, 1)
+    contract_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
+                       const __grid_constant__ CUtensorMap tmB_hi, const __grid_constant__ CUtensorMap tmB_lo,
+                       TcParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;               // 1024-B alignment for the swizzle atoms
+  uint8_t* gen_base = smem_raw + (base - raw);
+  const uint32_t bar0 = base + TC_STAGES * TC_STAGE_BYTES;     // barriers after the stages
+  // barrier layout: full[S], empty[S], accum, then the TMEM address slot
+  auto full_bar = [&](int s) { return bar0 + 8u * s; };
+  auto empty_bar = [&](int s) { return bar0 + 8u * (TC_STAGES + s); };
+  const uint32_t accum_bar = bar0 + 8u * (2 * TC_STAGES);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gen_base + TC_STAGES * TC_STAGE_BYTES + 8 * (2 * TC_STAGES + 1));
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * TC_BN;
+  const bool two_acc = (p.kind != kTF32);
+  const bool with_lo = (p.kind != kTF32);
+  const float lo_weight = (p.kind == kSplitF16) ? 1.0f / 2048.0f : 1.0f;
+  const uint32_t tmem_cols = two_acc ? 512u : 256u;
+  const uint32_t stage_tx = with_lo ? TC_STAGE_BYTES : (TC_A_BYTES + TC_B_BYTES);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TC_STAGES; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    mbar_init(accum_bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA_hi)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB_hi)) : "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer
+    int issued = 0;
+    bool ok = true;
+    for (int kb = 0; kb < p.kblocks && ok; ++kb) {
+      const int s = kb % TC_STAGES, it = kb / TC_STAGES;
+      if (it > 0) ok = mbar_wait(empty_bar(s), (it - 1) & 1, p.err);
+      if (!ok) break;
+      const uint32_t st = base + s * TC_STAGE_BYTES;
+      const int kx = kb * (p.kind >= kTF32 ? 32 : 64);       // element coordinate of the block
+      mbar_expect_tx(full_bar(s), stage_tx);
+      tma_load_2d(st, &tmA_hi, kx, m0, full_bar(s));
+      tma_load_2d(st + 2 * TC_A_BYTES, &tmB_hi, kx, n0, full_bar(s));
+      if (with_lo) {
+        tma_load_2d(st + TC_A_BYTES, &tmA_lo, kx, m0, full_bar(s));
+        tma_load_2d(st + 2 * TC_A_BYTES + TC_B_BYTES, &tmB_lo, kx, n0, full_bar(s));
+      }
+      ++issued;
+    }
+    // drain: wait until every issued load has landed before the CTA may exit
+    for (int kb = (issued > TC_STAGES ? issued - TC_STAGES : 0); kb < issued; ++kb)
+      mbar_wait(full_bar(kb % TC_STAGES), (kb / TC_STAGES) & 1, p.err);
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    const bool tf = p.kind >= kTF32;
+    const uint32_t idesc = instr_desc(p.kind == kSplitF16 ? 0u : (tf ? 2u : 1u), TC_BM, TC_BN);
+    const int ksteps = 4;                                       // 4 x 32 B of k per 128-B row
+    const uint32_t acc0 = tmem, acc1 = tmem + (two_acc ? 256u : 0u);
+    bool ok = true;
+    for (int kb = 0; kb < p.kblocks; ++kb) {
+      const int s = kb % TC_STAGES, it = kb / TC_STAGES;
+      ok = mbar_wait(full_bar(s), it & 1, p.err);
+      if (!ok) break;
+      tc_fence_after();
+      const uint32_t st = base + s * TC_STAGE_BYTES;
+      const uint64_t a_hi = sw128_desc(st), a_lo = sw128_desc(st + TC_A_BYTES);
+      const uint64_t b_hi = sw128_desc(st + 2 * TC_A_BYTES), b_lo = sw128_desc(st + 2 * TC_A_BYTES + TC_B_BYTES);
+#pragma unroll
+      for (int j = 0; j < ksteps; ++j) {
+        const uint64_t dk = uint64_t(2 * j);                    // +32 bytes of k, in 16-byte units
+        const uint32_t first = (kb == 0 && j == 0) ? 0u : 1u;
+        if (tf) {
+          mma_tf32(acc0, a_hi + dk, b_hi + dk, idesc, first);
+          if (with_lo) {
+            mma_tf32(acc1, a_hi + dk, b_lo + dk, idesc, first);
+            mma_tf32(acc1, a_lo + dk, b_hi + dk, idesc, 1u);
+          }
+        } else {
+          mma_f16(acc0, a_hi + dk, b_hi + dk, idesc, first);
+          mma_f16(acc1, a_hi + dk, b_lo + dk, idesc, first);
+          mma_f16(acc1, a_lo + dk, b_hi + dk, idesc, 1u);
+        }
+      }
+      mma_commit(empty_bar(s));                                  // stage reusable when these MMAs finish
+    }
+    mma_commit(accum_bar);                                       // accumulators final (or drained on error)
+    mbar_wait(accum_bar, 0, p.err);
+  } else if (warp >= 2) {
+    // ---------------- epilogue: TMEM -> registers -> nz[n][m]
+    const int q = warp & 3;                                      // TMEM lane quarter of this warp
+    const bool ok = mbar_wait(accum_bar, 0, p.err);
+    tc_fence_after();
+    if (ok) {
+      const int m = m0 + 32 * q + lane;
+      const float sm = (p.scale_m && m < p.M) ? p.scale_m[m] : 1.0f;
+      const uint32_t lane_off = uint32_t(32 * q) << 16;
+      for (int c0 = 0; c0 < TC_BN; c0 += 32) {
+        if (n0 + c0 >= p.N) break;
+        float v[32];
+        tmem_ld32(tmem + lane_off + c0, v);
+        if (two_acc) {
+          float w[32];
+          tmem_ld32(tmem + 256u + lane_off + c0, w);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] = fmaf(w[j], lo_weight, v[j]);
+        }
+        if (m < p.M) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int n = n0 + c0 + j;
+            if (n < p.N) {
+              float val = v[j];
+              if (p.scale_m) val *= sm * p.scale_n[n];
+              p.out[size_t(n) * p.ld + m] = val;
+            }
+          }
+        }
+      }
+    }
+    tc_fence_before();
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
+  }
+}
+
+// ------------------------------------------------------------------ operand slicing
+__device__ __forceinline__ float tf32_round(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// One warp per row: hi/lo slices of x[row][0..K) into [row][0..Kpad) (zero padded).
+__global__ void split_rows_kernel(const double* __restrict__ x, int64_t rows, int K, int Kpad, int kind,
+                                  void* __restrict__ hi, void* __restrict__ lo, float* __restrict__ row_scale) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t r = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; r < rows;
+       r += (int64_t(gridDim.x) * blockDim.x) >> 5) {
+    const double* xr = x + r * K;
+    double scale = 1.0;
+    if (kind == kSplitF16) {
+      double mx = 0.0;
+      for (int k = lane; k < K; k += 32) mx = fmax(mx, fabs(xr[k]));
+      for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      int e = 0;
+      if (mx > 0.0) {
+        frexp(mx, &e);                         // mx = f 2^e, f in [0.5, 1)
+        scale = ldexp(1.0, 15 - e);            // scaled max in [2^14, 2^15)
+      }
+      if (lane == 0) row_scale[r] = float(1.0 / scale);
+    }
+    for (int k = lane; k < Kpad; k += 32) {
+      const double v = (k < K) ? xr[k] * scale : 0.0;
+      if (kind == kSplitF16) {
+        const __half h = __double2half(v);
+        const __half l = __double2half((v - double(__half2float(h))) * 2048.0);
+        static_cast<__half*>(hi)[r * Kpad + k] = h;
+        static_cast<__half*>(lo)[r * Kpad + k] = l;
+      } else if (kind == kSplitBF16) {
+        const __nv_bfloat16 h = __double2bfloat16(v);
+        const __nv_bfloat16 l = __double2bfloat16(v - double(__bfloat162float(h)));
+        static_cast<__nv_bfloat16*>(hi)[r * Kpad + k] = h;
+        static_cast<__nv_bfloat16*>(lo)[r * Kpad + k] = l;
+      } else {
+        const float h = tf32_round(float(v));
+        static_cast<float*>(hi)[r * Kpad + k] = h;
+        if (kind == kTF32x3) static_cast<float*>(lo)[r * Kpad + k] = tf32_round(float(v - double(h)));
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ host side
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+static std::mutex g_encode_mutex;
+
+static msasm_status get_encoder() {
+  std::lock_guard<std::mutex> lock(g_encode_mutex);
+  if (g_encode) return MSASM_OK;
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  MSASM_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+  if (q != cudaDriverEntryPointSuccess || !fn) return fail(MSASM_ECUDA, "cuTensorMapEncodeTiled is not available");
+  g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  return MSASM_OK;
+}
+
+// 2-D tensor map over a row-major [rows][Kpad] operand; box = 128 bytes of k x box_rows rows.
+static msasm_status make_map(CUtensorMap* map, const void* ptr, int kind, int64_t rows, int K, int Kpad,
+                             int box_rows) {
+  const bool tf = kind >= kTF32;
+  const int esz = tf ? 4 : 2;
+  CUtensorMapDataType dt = tf ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                              : (kind == kSplitF16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
+  cuuint64_t dims[2] = {cuuint64_t(K), cuuint64_t(rows)};
+  cuuint64_t strides[1] = {cuuint64_t(Kpad) * esz};
+  cuuint32_t box[2] = {cuuint32_t(TC_ROW_BYTES / esz), cuuint32_t(box_rows)};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = g_encode(map, dt, 2, const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(MSASM_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string(int(r)) + ")");
+  return MSASM_OK;
+}
+
+int tc_kind_of(msasm_precision prec) {
+  switch (prec) {
+    case MSASM_SPLIT_F16: return kSplitF16;
+    case MSASM_SPLIT_BF16: return kSplitBF16;
+    case MSASM_TF32: return kTF32;
+    case MSASM_TF32X3: return kTF32x3;
+    default: return -1;
+  }
+}
+
+int tc_kpad(int K, int kind) {
+  const int per_row = (kind >= kTF32) ? 32 : 64;          // elements per 128-byte box row
+  return (K + per_row - 1) / per_row * per_row;
+}
+
+size_t tc_slice_bytes(int64_t rows, int K, int kind) {
+  const int esz = kind >= kTF32 ? 4 : 2;
+  return size_t(rows) * tc_kpad(K, kind) * esz;
+}
+
+msasm_status tc_split_gpu(const double* x, int64_t rows, int K, int kind, void* hi, void* lo, float* row_scale,
+                          cudaStream_t s) {
+  int64_t blocks = (rows * 32 + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  split_rows_kernel<<<unsigned(blocks), 256, 0, s>>>(x, rows, K, tc_kpad(K, kind), kind, hi, lo, row_scale);
+  MSASM_CUDA(cudaGetLastError());
+  return MSASM_OK;
+}
+
+// nz[n][m] (FP32, leading dimension ld) from sliced operands A (table, M rows) and B (coef, N rows).
+msasm_status contract_tc_gpu(int kind, const void* a_hi, const void* a_lo, const float* a_scale, int M,
+                             const void* b_hi, const void* b_lo, const float* b_scale, int64_t N, int K, float* out,
+                             int ld, unsigned* d_err, cudaStream_t s) {
+  MSASM_TRY(get_encoder());
+  if (N > int64_t(65535) * TC_BN) return fail(MSASM_EUNSUPPORTED, "too many coefficient rows for one launch");
+  const int Kpad = tc_kpad(K, kind);
+  CUtensorMap ma_hi, ma_lo, mb_hi, mb_lo;
+  MSASM_TRY(make_map(&ma_hi, a_hi, kind, M, K, Kpad, TC_BM));
+  MSASM_TRY(make_map(&mb_hi, b_hi, kind, N, K, Kpad, TC_BN));
+  if (kind != kTF32) {
+    MSASM_TRY(make_map(&ma_lo, a_lo, kind, M, K, Kpad, TC_BM));
+    MSASM_TRY(make_map(&mb_lo, b_lo, kind, N, K, Kpad, TC_BN));
+  } else {
+    ma_lo = ma_hi;
+    mb_lo = mb_hi;
+  }
+  TcParams p;
+  p.M = M;
+  p.N = int(N);
+  p.K = K;
+  p.kblocks = Kpad / ((kind >= kTF32) ? 32 : 64);
+  p.kind = kind;
+  p.scale_m = (kind == kSplitF16) ? a_scale : nullptr;
+  p.scale_n = (kind == kSplitF16) ? b_scale : nullptr;
+  p.out = out;
+  p.ld = ld;
+  p.err = d_err;
+  MSASM_CUDA(cudaFuncSetAttribute(contract_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BYTES));
+  dim3 grid(unsigned((M + TC_BM - 1) / TC_BM), unsigned((N + TC_BN - 1) / TC_BN));
+  contract_tc_kernel<<<grid, 192, TC_SMEM_BYTES, s>>>(ma_hi, ma_lo, mb_hi, mb_lo, p);
+  MSASM_CUDA(cudaGetLastError());
+  return MSASM_OK;
+}
+
+}  // namespace msasm
