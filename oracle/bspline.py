@@ -80,7 +80,7 @@ def volume_eval(knots3, degree3, ctrl, u3):
     n1, n2, n3 = (b.shape[1] for b in B)
     net = ctrl.reshape(n3, n2, n1, 3)  # net[k, j, i] = ctrl[i + n1*(j + n2*k)]
     x = np.einsum("ni,nj,nk,kjip->np", B[0], B[1], B[2], net)
-    J = np.empty((u3.shape[0], 3, 3))
+    J = np.empty((u3.shape[0], 3, 3), dtype=np.result_type(ctrl, B[0]))   # complex-safe
     J[:, :, 0] = np.einsum("ni,nj,nk,kjip->np", D[0], B[1], B[2], net)
     J[:, :, 1] = np.einsum("ni,nj,nk,kjip->np", B[0], D[1], B[2], net)
     J[:, :, 2] = np.einsum("ni,nj,nk,kjip->np", B[0], B[1], D[2], net)

@@ -32,7 +32,7 @@ def material_contravariant(gcon: np.ndarray, lam: float, mu: float) -> np.ndarra
 
 def voigt_matrix(C4: np.ndarray) -> np.ndarray:
     """The 6x6 matrix of eq. 93 from the 4th-order tensor."""
-    out = np.empty(C4.shape[:-4] + (6, 6))
+    out = np.empty(C4.shape[:-4] + (6, 6), dtype=C4.dtype)
     for I, (i, j) in enumerate(VOIGT):
         for K, (k, l) in enumerate(VOIGT):
             out[..., I, K] = C4[..., i, j, k, l]
@@ -51,11 +51,14 @@ def g_blocks(J: np.ndarray) -> np.ndarray:
 
 def macro_field(J: np.ndarray, lam: float, mu: float) -> np.ndarray:
     """A_ij[alpha, beta] for Jacobians J (..., 3, 3) with J[p, i] = d M_p / d xi_i."""
-    gcov = np.einsum("...pi,...pj->...ij", J, J)              # eq. 81
+    gcov = np.einsum("...pi,...pj->...ij", J, J)              # eq. 81 (g_i . g_j, no conjugation)
     gcon = np.linalg.inv(gcov)
     Cv = voigt_matrix(material_contravariant(gcon, lam, mu))   # eq. 84, 93
     G = g_blocks(J)                                            # eq. 91
-    detJ = np.abs(np.linalg.det(J))
+    detJ = np.linalg.det(J)
+    # |det J| (eq. 37), written as det J * sign(Re det J) so that a complex-step
+    # perturbation of the control net stays analytic; equal to |det J| for real J
+    detJ = detJ * np.sign(np.real(detJ))
     A = np.einsum("...iaV,...VW,...jbW->...ijab", G, Cv, G)    # eq. 37 / 97
     return A * detJ[..., None, None, None, None]
 
