@@ -153,6 +153,31 @@ msasm_status msasm_assemble(msasm_plan* plan, const double* d_ctrl, double E, do
 msasm_status msasm_assemble_host(msasm_plan* plan, const double* h_ctrl, double E, double nu,
                                  msasm_precision prec, void* h_values, uint32_t flags, void* stream);
 
+/* Gradient of L with respect to the macro control net (Sec. 4.1.2, eq. 69-73), through the
+ * lookup form of msasm_assemble.  Give exactly one of
+ *   d_u           (n_rows values): L = u^T K u, the internal-work term of eq. 69-70
+ *                 (with f fixed and u = K^-1 f the compliance gradient is -dL/dP);
+ *   d_grad_values (nnz values): dL/dvalues of an arbitrary L (the chain through step 4).
+ * Both are FP64 for MSASM_F64 / MSASM_F64_EMU and FP32 otherwise; the contraction of the
+ * table with u (W = mat[K]^T G, eq. 73) then runs in FP64 or FP32 on the CUDA cores, and
+ * the chain rule through |det J| and J^-1 to the control points is FP64.
+ * d_grad_ctrl (n_ctrl*3 FP64) is overwritten.  Errors: EINVAL, ECUDA. */
+msasm_status msasm_assemble_grad(msasm_plan* plan, const double* d_ctrl, double E, double nu,
+                                 msasm_precision prec, const void* d_u, const void* d_grad_values,
+                                 double* d_grad_ctrl, void* stream);
+
+/* Global control points on macro face `face` = 2 d + s (the face xi_d = s of the macro
+ * parameter cube), ascending, into h_points (host; *count in: capacity, out: number).
+ * With h_points NULL only the count is returned. */
+msasm_status msasm_face_points(const msasm_plan* plan, int32_t face, int32_t* h_points, int64_t* count);
+
+/* Load vector of a uniform traction t (force per unit physical area, host double[3]) on
+ * macro face `face`: f_{3g+c} = t_c int_Gamma R_g dGamma (eq. 29, 33), by Gauss quadrature on
+ * the micro patch faces lying on the face, for the control net h_ctrl (host, n_ctrl*3).
+ * h_f: n_rows doubles (host), overwritten.  Runs on the host (set-up data). */
+msasm_status msasm_traction_load(const msasm_plan* plan, int32_t face, const double* traction,
+                                 const double* h_ctrl, double* h_f);
+
 /* Number of interpolation nodes with |det J| <= tol found by the last assemble
  * on this plan (reads back from the device; synchronises `stream`). */
 msasm_status msasm_degenerate_count(const msasm_plan* plan, int64_t* count, void* stream);

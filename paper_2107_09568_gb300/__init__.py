@@ -168,3 +168,112 @@ class Plan:
         if getattr(self, "handle", None) and _lib._lib is not None:
             _lib._lib.msasm_plan_destroy(self.handle)
             self.handle = None
+
+
+# ---------------------------------------------------------------------------------------
+# adjoint, boundary data, solve
+def _plan_assemble_grad(self, ctrl, E=1.0, nu=0.3, precision="f64", u=None, grad_values=None, stream=None):
+    """dL/dP (n_ctrl, 3) FP64 for L = u^T K u (u given) or from dL/dvalues (grad_values given)."""
+    import torch
+    out = torch.empty((self.n_ctrl, 3), dtype=torch.float64, device="cuda")
+    check(load().msasm_assemble_grad(self.handle, _ptr(ctrl), float(E), float(nu), PRECISIONS[precision],
+                                     _ptr(u), _ptr(grad_values), _ptr(out), _stream(stream)))
+    return out
+
+
+def _plan_face_points(self, face):
+    n = C.c_int64(0)
+    check(load().msasm_face_points(self.handle, int(face), None, C.byref(n)))
+    out = np.empty(n.value, dtype=np.int32)
+    check(load().msasm_face_points(self.handle, int(face), out.ctypes.data_as(C.c_void_p), C.byref(n)))
+    return out
+
+
+def _plan_traction_load(self, face, traction, ctrl_host):
+    """Load vector (n_rows,) FP64 (host numpy) of a uniform traction on a macro face."""
+    t = np.ascontiguousarray(traction, dtype=np.float64)
+    c = np.ascontiguousarray(ctrl_host, dtype=np.float64)
+    f = np.zeros(self.n_rows, dtype=np.float64)
+    check(load().msasm_traction_load(self.handle, int(face), t.ctypes.data_as(C.c_void_p),
+                                     c.ctypes.data_as(C.c_void_p), f.ctypes.data_as(C.c_void_p)))
+    return f
+
+
+Plan.assemble_grad = _plan_assemble_grad
+Plan.face_points = _plan_face_points
+Plan.traction_load = _plan_traction_load
+
+
+def _autograd_function():
+    import torch
+
+    class AssembleStiffness(torch.autograd.Function):
+        """values = K(ctrl) (CSR values of the plan's pattern); backward runs msasm_assemble_grad."""
+
+        @staticmethod
+        def forward(ctx, ctrl, plan, E, nu, precision):
+            vals = plan.assemble(ctrl.detach(), E, nu, precision)
+            ctx.save_for_backward(ctrl)
+            ctx.plan, ctx.E, ctx.nu, ctx.precision = plan, E, nu, precision
+            return vals
+
+        @staticmethod
+        def backward(ctx, grad_vals):
+            (ctrl,) = ctx.saved_tensors
+            g = ctx.plan.assemble_grad(ctrl.detach(), ctx.E, ctx.nu, ctx.precision,
+                                       grad_values=grad_vals.contiguous().to(Plan.value_dtype(ctx.precision)))
+            return g.to(ctrl.dtype), None, None, None, None
+
+    return AssembleStiffness
+
+
+_ASSEMBLE_FN = None
+
+
+def assemble_stiffness(ctrl, plan, E=1.0, nu=0.3, precision="f64"):
+    """Differentiable K(ctrl): CSR values whose backward is the library's adjoint kernels."""
+    global _ASSEMBLE_FN
+    if _ASSEMBLE_FN is None:
+        _ASSEMBLE_FN = _autograd_function()
+    return _ASSEMBLE_FN.apply(ctrl, plan, E, nu, precision)
+
+
+def csr_matrix(plan, values):
+    """torch sparse CSR matrix of the plan's pattern with the given values."""
+    import torch
+    rowptr, col = plan.csr()
+    return torch.sparse_csr_tensor(rowptr, col.long(), values, size=(plan.n_rows, plan.n_rows))
+
+
+def cg_solve(K, f, fixed_dofs, tol=1e-12, max_iter=20000):
+    """Jacobi-preconditioned conjugate gradients in PyTorch on the GPU for K u = f with u = 0 on
+    fixed_dofs (rows and columns of the fixed DOFs are removed by masking).  Returns (u, iters, rel_res)."""
+    import torch
+    n = f.numel()
+    free = torch.ones(n, dtype=f.dtype, device=f.device)
+    free[fixed_dofs] = 0.0
+    crow, col, val = K.crow_indices(), K.col_indices(), K.values()
+    rows = torch.repeat_interleave(torch.arange(n, device=f.device), crow[1:] - crow[:-1])
+    diag = torch.zeros(n, dtype=f.dtype, device=f.device).index_add_(0, rows, torch.where(col == rows, val, 0.0))
+    dinv = torch.where(free > 0, 1.0 / diag, 0.0)
+    A = lambda x: (K @ (x * free)) * free
+    b = f * free
+    x = torch.zeros_like(b)
+    r = b.clone()
+    z = dinv * r
+    p = z.clone()
+    rz = torch.dot(r, z)
+    bn = torch.linalg.vector_norm(b)
+    it = 0
+    for it in range(1, max_iter + 1):
+        Ap = A(p)
+        alpha = rz / torch.dot(p, Ap)
+        x += alpha * p
+        r -= alpha * Ap
+        if it % 25 == 0 and (torch.linalg.vector_norm(r) / bn).item() < tol:
+            break
+        z = dinv * r
+        rz_new = torch.dot(r, z)
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    return x, it, (torch.linalg.vector_norm(b - A(x)) / bn).item()

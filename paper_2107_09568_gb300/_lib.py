@@ -55,6 +55,9 @@ _SIGS = {
     "msasm_contract": (c_i32, [c_vp, c_i32, c_vp, c_i64, c_vp, c_vp]),
     "msasm_scatter": (c_i32, [c_vp, c_i32, c_vp, c_vp, c_vp]),
     "msasm_contract_noalloc": (c_i32, [c_vp, c_vp, c_i64, c_vp, c_vp]),
+    "msasm_assemble_grad": (c_i32, [c_vp, c_vp, c_dbl, c_dbl, c_i32, c_vp, c_vp, c_vp, c_vp]),
+    "msasm_face_points": (c_i32, [c_vp, c_i32, c_vp, P(c_i64)]),
+    "msasm_traction_load": (c_i32, [c_vp, c_i32, c_vp, c_vp, c_vp]),
     "msasm_stage_times": (c_i32, [c_vp, P(c_dbl), P(c_i32)]),
     "msasm_last_error": (C.c_char_p, []),
     "msasm_version": (C.c_char_p, []),

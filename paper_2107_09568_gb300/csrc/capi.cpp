@@ -42,6 +42,16 @@ msasm_status to_f32_gpu(const double* x, int64_t n, float* y, cudaStream_t strea
 template <typename T>
 msasm_status scatter_gpu(const msasm_plan* plan, const T* d_nz, int ld_nz, int64_t t0, int64_t n_tiles,
                          const int64_t* d_list, int64_t n_list, T* d_values, cudaStream_t stream);
+template <typename T>
+msasm_status gemm_simt(const T* A, int64_t lda, const T* B, int64_t ldb, int64_t N, int M, int K, T* C, int64_t ldc,
+                       cudaStream_t stream);
+template <typename T>
+msasm_status grad_blocks_gpu(const msasm_plan* plan, const T* d_u, const T* d_gv, int64_t t0, int64_t nt, int ld,
+                             T* d_G, cudaStream_t s);
+template <typename T>
+msasm_status transpose_table_gpu(const double* d_T, int n_nz, int K, T* d_Tt, cudaStream_t s);
+msasm_status adjoint_pullback_gpu(const msasm_plan* plan, const double* d_ctrl, double lam, double mu, int64_t t0,
+                                  int64_t nt, const void* d_W, bool w_f32, double* d_dP, cudaStream_t s);
 int tc_kind_of(msasm_precision prec);
 int tc_kpad(int K, int kind);
 size_t tc_slice_bytes(int64_t rows, int K, int kind);
@@ -66,6 +76,8 @@ msasm_tables::~msasm_tables() {
   cudaFree(d_Thi);
   cudaFree(d_Tlo);
   cudaFree(d_Tscale);
+  cudaFree(d_Tt);
+  cudaFree(d_Tt32);
   cudaFree(d_Tslices);
   cudaFree(d_Tslice_scale);
 }
@@ -193,9 +205,11 @@ msasm_status msasm_plan_create(const msasm_tables* tab, const msasm_macro_desc* 
     plan->degree[d] = p;
     plan->n_ctrl_dir[d] = nk - p - 1;
     int ne = 0;
+    plan->knots_host[d].assign(t, t + nk);
     for (int k = p; k < nk - p - 1; ++k) {
       if (!(t[k + 1] > t[k])) continue;
       ++ne;
+      plan->span_host[d].push_back(k);
       first[d].push_back(k - p);
       double u0 = t[k], h = t[k + 1] - t[k];
       for (int c = 0; c < nq; ++c) {
@@ -316,6 +330,7 @@ msasm_status msasm_plan_create(const msasm_tables* tab, const msasm_macro_desc* 
   cleanup_tmp();
   if (st != MSASM_OK) return bail(st);
   if (bad) return bail(fail(MSASM_ECUDA, "index map: a tile pair is missing from the CSR pattern"));
+  plan->gmap_host = std::move(gmap);
   if (n_rows) *n_rows = plan->n_rows;
   if (nnz) *nnz = plan->nnz;
   *out = plan;
@@ -542,6 +557,48 @@ msasm_status msasm_assemble_host(msasm_plan* plan, const double* h_ctrl, double 
   MSASM_TRY(msasm_assemble(plan, plan->d_ctrl_stage, E, nu, prec, plan->d_values_stage, flags, stream));
   MSASM_CUDA(cudaMemcpyAsync(h_values, plan->d_values_stage, vbytes, cudaMemcpyDeviceToHost, s));
   MSASM_CUDA(cudaStreamSynchronize(s));
+  return MSASM_OK;
+}
+
+msasm_status msasm_assemble_grad(msasm_plan* plan, const double* d_ctrl, double E, double nu, msasm_precision prec,
+                                 const void* d_u, const void* d_grad_values, double* d_grad_ctrl, void* stream) {
+  if (!plan || !d_ctrl || !d_grad_ctrl) return fail(MSASM_EINVAL, "plan, d_ctrl or d_grad_ctrl is NULL");
+  if ((d_u == nullptr) == (d_grad_values == nullptr))
+    return fail(MSASM_EINVAL, "give exactly one of d_u and d_grad_values");
+  MSASM_TRY(check_material(E, nu));
+  if (prec < MSASM_F64 || prec > MSASM_F64_EMU) return fail(MSASM_EINVAL, "unknown precision");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  msasm_tables* tab = const_cast<msasm_tables*>(plan->tab);
+  double lam, mu;
+  lame(E, nu, lam, mu);
+  const bool f64 = is_f64_precision(prec);
+  const int n_nz = tab->n_nz, K = 9 * tab->n_pi, ld = ld_nz_of(n_nz);
+  if (f64 && !tab->d_Tt) {
+    MSASM_CUDA(cudaMalloc(&tab->d_Tt, size_t(K) * n_nz * sizeof(double)));
+    MSASM_TRY(transpose_table_gpu<double>(tab->d_T, n_nz, K, tab->d_Tt, s));
+  }
+  if (!f64 && !tab->d_Tt32) {
+    MSASM_CUDA(cudaMalloc(&tab->d_Tt32, size_t(K) * n_nz * sizeof(float)));
+    MSASM_TRY(transpose_table_gpu<float>(tab->d_T, n_nz, K, tab->d_Tt32, s));
+  }
+  MSASM_CUDA(cudaMemsetAsync(d_grad_ctrl, 0, size_t(plan->n_ctrl) * 3 * sizeof(double), s));
+  const int64_t P = plan->tiles_per_pass;
+  for (int64_t t0 = 0; t0 < plan->n_tiles; t0 += P) {
+    const int64_t nt = std::min(P, plan->n_tiles - t0);
+    if (f64) {
+      double* G = static_cast<double*>(plan->d_nz);
+      MSASM_TRY(grad_blocks_gpu<double>(plan, static_cast<const double*>(d_u), static_cast<const double*>(d_grad_values),
+                                        t0, nt, ld, G, s));
+      MSASM_TRY(gemm_simt<double>(G, ld, tab->d_Tt, n_nz, 9 * nt, K, n_nz, plan->d_coef, K, s));
+    } else {
+      float* G = static_cast<float*>(plan->d_nz);
+      float* W = reinterpret_cast<float*>(plan->d_coef);
+      MSASM_TRY(grad_blocks_gpu<float>(plan, static_cast<const float*>(d_u), static_cast<const float*>(d_grad_values),
+                                       t0, nt, ld, G, s));
+      MSASM_TRY(gemm_simt<float>(G, ld, tab->d_Tt32, n_nz, 9 * nt, K, n_nz, W, K, s));
+    }
+    MSASM_TRY(adjoint_pullback_gpu(plan, d_ctrl, lam, mu, t0, nt, plan->d_coef, !f64, d_grad_ctrl, s));
+  }
   return MSASM_OK;
 }
 

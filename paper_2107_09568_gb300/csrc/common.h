@@ -85,6 +85,8 @@ struct msasm_tables {
   void* d_Thi = nullptr;            // hi/lo 16-bit or tf32 operand slices
   void* d_Tlo = nullptr;
   float* d_Tscale = nullptr;        // per-row 2^-e of the split-FP16 slices
+  double* d_Tt = nullptr;           // transposed table [9 n_pi][n_nz] for the adjoint (FP64)
+  float* d_Tt32 = nullptr;          // the same in FP32
   int split_kind = -1;              // which precision the slices hold
   void* d_Tslices = nullptr;        // FP64-emulation slices
   int n_slices = 0;
@@ -111,6 +113,9 @@ struct msasm_plan {
   int64_t* d_second = nullptr;      // t * n_nz + m of second contributors, ascending
   int64_t n_second = 0;
   std::vector<int64_t> second_ptr;  // host: entries of tile t are [second_ptr[t], second_ptr[t+1])
+  std::vector<double> knots_host[3];  // host copies for boundary data
+  std::vector<int> span_host[3];      // knot index of each element's span
+  std::vector<int32_t> gmap_host;
   // scratch
   double* d_coef = nullptr;         // 9 tiles_per_pass x 9 n_pi, FP64
   void* d_nz = nullptr;             // 9 tiles_per_pass x n_nz, FP64-sized

@@ -12,9 +12,12 @@
 
 namespace msasm {
 
+// C[n][m] = sum_k A[n][k] B[m][k] with row strides lda, ldb, ldc (the contraction uses A = coef,
+// B = table, C = nzdata; the adjoint uses A = G, B = the transposed table, C = W).
 template <typename T, int BK>
-__global__ void __launch_bounds__(256) contract_simt_kernel(const T* __restrict__ coef, const T* __restrict__ tab,
-                                                            int64_t N, int M, int K, int ld_nz, T* __restrict__ nz) {
+__global__ void __launch_bounds__(256) contract_simt_kernel(const T* __restrict__ coef, int64_t lda,
+                                                            const T* __restrict__ tab, int64_t ldb, int64_t N, int M,
+                                                            int K, int64_t ld_nz, T* __restrict__ nz) {
   constexpr int BN = 128, BM = 128;
   constexpr int LOADS = BN * BK / 256;          // elements per thread per operand per slab
   __shared__ T As[2][BK][BN + 4];
@@ -36,8 +39,8 @@ __global__ void __launch_bounds__(256) contract_simt_kernel(const T* __restrict_
       int r = e / BK, kk = e % BK;
       int64_t n = n0 + r;
       int m = m0 + r, k = k0 + kk;
-      ra[l] = (n < N && k < K) ? coef[n * K + k] : T(0);
-      rb[l] = (m < M && k < K) ? tab[int64_t(m) * K + k] : T(0);
+      ra[l] = (n < N && k < K) ? coef[n * lda + k] : T(0);
+      rb[l] = (m < M && k < K) ? tab[int64_t(m) * ldb + k] : T(0);
     }
   };
   auto store = [&](int buf) {
@@ -87,24 +90,29 @@ __global__ void __launch_bounds__(256) contract_simt_kernel(const T* __restrict_
   }
 }
 
-msasm_status contract_simt_f64(const double* d_coef, const double* d_T, int64_t n_tiles, int n_nz, int K, int ld_nz,
-                               double* d_nz, cudaStream_t stream) {
-  int64_t N = 9 * n_tiles;
-  dim3 grid(unsigned((n_nz + 127) / 128), unsigned((N + 127) / 128));
-  if (grid.y > 65535) return fail(MSASM_EUNSUPPORTED, "too many tiles for one contraction pass");
-  contract_simt_kernel<double, 8><<<grid, 256, 0, stream>>>(d_coef, d_T, N, n_nz, K, ld_nz, d_nz);
+template <typename T>
+msasm_status gemm_simt(const T* A, int64_t lda, const T* B, int64_t ldb, int64_t N, int M, int K, T* C, int64_t ldc,
+                       cudaStream_t stream) {
+  dim3 grid(unsigned((M + 127) / 128), unsigned((N + 127) / 128));
+  if (grid.y > 65535) return fail(MSASM_EUNSUPPORTED, "too many rows for one CUDA-core contraction");
+  constexpr int BK = sizeof(T) == 8 ? 8 : 16;
+  contract_simt_kernel<T, BK><<<grid, 256, 0, stream>>>(A, lda, B, ldb, N, M, K, ldc, C);
   MSASM_CUDA(cudaGetLastError());
   return MSASM_OK;
+}
+template msasm_status gemm_simt<double>(const double*, int64_t, const double*, int64_t, int64_t, int, int, double*,
+                                        int64_t, cudaStream_t);
+template msasm_status gemm_simt<float>(const float*, int64_t, const float*, int64_t, int64_t, int, int, float*,
+                                       int64_t, cudaStream_t);
+
+msasm_status contract_simt_f64(const double* d_coef, const double* d_T, int64_t n_tiles, int n_nz, int K, int ld_nz,
+                               double* d_nz, cudaStream_t stream) {
+  return gemm_simt<double>(d_coef, K, d_T, K, 9 * n_tiles, n_nz, K, d_nz, ld_nz, stream);
 }
 
 msasm_status contract_simt_f32(const float* d_coef, const float* d_T, int64_t n_tiles, int n_nz, int K, int ld_nz,
                                float* d_nz, cudaStream_t stream) {
-  int64_t N = 9 * n_tiles;
-  dim3 grid(unsigned((n_nz + 127) / 128), unsigned((N + 127) / 128));
-  if (grid.y > 65535) return fail(MSASM_EUNSUPPORTED, "too many tiles for one contraction pass");
-  contract_simt_kernel<float, 16><<<grid, 256, 0, stream>>>(d_coef, d_T, N, n_nz, K, ld_nz, d_nz);
-  MSASM_CUDA(cudaGetLastError());
-  return MSASM_OK;
+  return gemm_simt<float>(d_coef, K, d_T, K, 9 * n_tiles, n_nz, K, d_nz, ld_nz, stream);
 }
 
 // FP64 -> FP32 conversion of an operand (round to nearest).

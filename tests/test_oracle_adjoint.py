@@ -44,3 +44,21 @@ def test_gradient_homogeneity_and_translation(prob):
     P = prob.mmap.macro.ctrl
     assert abs(np.sum(P * g) - Q) < 1e-11 * abs(Q)
     np.testing.assert_allclose(g.sum(axis=0), 0.0, atol=1e-11 * np.abs(g).max())
+
+
+def test_traction_load_total_force_and_area():
+    """sum_A R_A = 1 on the face, so the load sums to t x (area of the strut ends on the face):
+    per tile (c1 - c0)^2 times the area scaling of the (affine, sheared) macro map."""
+    from oracle import loads
+    m = synth.macro_affine_box(3, 2, 2)
+    F = np.array([[1.0, 0.2, 0.1], [0.0, 0.8, 0.3], [0.1, 0.0, 1.3]])
+    m.ctrl = m.ctrl @ F.T
+    P = Problem(synth.micro_cross(2), m, 1, structure=False)
+    t = np.array([0.3, -1.0, 0.5])
+    f = loads.traction_load(P, 1, t)                       # face xi_1 = 1
+    # area of a unit square in the (xi_2, xi_3) plane mapped by F
+    area_unit = np.linalg.norm(np.cross(F[:, 1], F[:, 2]))
+    expect = t * 4 * (0.3 ** 2) * area_unit               # 2 x 2 tiles on the face
+    np.testing.assert_allclose(f.sum(axis=0), expect, rtol=1e-13, atol=1e-14)
+    pts = loads.face_points(P, 1)
+    assert len(pts) == 4 * 16 and np.all(np.abs(f[np.setdiff1d(np.arange(P.n_points), pts)]) == 0)
