@@ -178,6 +178,67 @@ msasm_status msasm_face_points(const msasm_plan* plan, int32_t face, int32_t* h_
 msasm_status msasm_traction_load(const msasm_plan* plan, int32_t face, const double* traction,
                                  const double* h_ctrl, double* h_f);
 
+/* ---------------------------------------------------------------- learned surrogate (graded lattices) */
+
+/* A surrogate of the lookup table for a family of reference tiles with one parameter w
+ * (the strut width): T(w) ~ U V(w)^T, U (n_nz x r, orthonormal columns) fitted once, V(w)
+ * (9 n_pi x r) predicted by an MLP.  Not in the paper: an interface addition for graded
+ * lattices, where the paper's method needs one quadrature table per distinct tile. */
+typedef struct msasm_mlp msasm_mlp;               /* opaque: 1 -> H -> H -> n_out tanh MLP */
+typedef struct msasm_surrogate msasm_surrogate;   /* opaque: basis U + MLP + target scaling */
+
+/* MLP with FP16 weights (FP32 master copy and Adam state), FP32 accumulation; Glorot-uniform
+ * weights from `seed`, zero biases.  Parameter vector layout (FP32, n_params values):
+ * W1[H], b1[H], W2[H][H], b2[H], W3[n_out][H], b3[n_out]; tanh after layers 1 and 2. */
+msasm_status msasm_mlp_create(int32_t n_out, int32_t hidden, uint64_t seed, msasm_mlp** out);
+msasm_status msasm_mlp_info(const msasm_mlp* mlp, int64_t* n_params, int32_t* n_out, int32_t* hidden);
+/* Set the FP32 master parameters (device) and refresh the FP16 copy. */
+msasm_status msasm_mlp_set_params(msasm_mlp* mlp, const float* d_params, void* stream);
+/* Copy the FP32 master parameters and/or the FP16 compute copy (n_params __half) to device buffers. */
+msasm_status msasm_mlp_get_params(const msasm_mlp* mlp, float* d_master, void* d_half, void* stream);
+/* y = MLP(x) for B scalar inputs: d_y (B x n_out) FP32. */
+msasm_status msasm_mlp_forward(msasm_mlp* mlp, const float* d_x, int32_t B, float* d_y, void* stream);
+/* Loss L = mean over B x n_out of (y - t)^2 and dL/dparams (w.r.t. the FP16 weights, FP32 result,
+ * n_params values into d_grad if non-NULL).  Synchronises `stream`. */
+msasm_status msasm_mlp_loss_grad(msasm_mlp* mlp, const float* d_x, const float* d_t, int32_t B, float* h_loss,
+                                 float* d_grad, void* stream);
+/* `steps` full-batch Adam steps (beta 0.9 / 0.999, eps 1e-8) at learning rate lr, one step
+ * replayed as a CUDA graph; h_loss (optional, steps floats) gets the loss before each step. */
+msasm_status msasm_mlp_train(msasm_mlp* mlp, const float* d_x, const float* d_t, int32_t B, int32_t steps, float lr,
+                             float* h_loss, void* stream);
+void msasm_mlp_destroy(msasm_mlp* mlp);
+
+/* Fit the surrogate from n_tables quadrature tables T(w_k) (msasm_build_tables of the tile at
+ * width widths[k], host array) and coefficient rows of the workload (d_coef_samples,
+ * n_sample_rows x 9 n_pi FP64, e.g. rows of msasm_pullback): U spans the dominant left singular
+ * subspace of [T(w_k) C^T] (randomized range finder with `power_iters` power iterations, FP64),
+ * the MLP (hidden width `hidden`, output r x 9 n_pi) is initialised from `seed` and its
+ * training targets are V_k^T = U^T T(w_k), centred and scaled.  Synchronises `stream`. */
+msasm_status msasm_surrogate_create(const msasm_tables* const* tables, const double* widths, int32_t n_tables,
+                                    const double* d_coef_samples, int64_t n_sample_rows, int32_t rank,
+                                    int32_t hidden, int32_t power_iters, uint64_t seed, void* stream,
+                                    msasm_surrogate** out);
+msasm_status msasm_surrogate_info(const msasm_surrogate* sur, int32_t* rank, int32_t* K, int32_t* n_nz);
+/* Train the MLP on the fitted targets (msasm_mlp_train semantics). */
+msasm_status msasm_surrogate_train(msasm_surrogate* sur, int32_t steps, float lr, float* h_loss, void* stream);
+/* The surrogate's MLP (owned by the surrogate). */
+msasm_status msasm_surrogate_mlp(msasm_surrogate* sur, msasm_mlp** mlp);
+/* U as n_nz x r FP32 (row-major) into d_U. */
+msasm_status msasm_surrogate_basis(const msasm_surrogate* sur, float* d_U, void* stream);
+/* V(w)^T for n widths (device FP64): d_Vt (n x r x 9 n_pi) FP32. */
+msasm_status msasm_surrogate_predict(msasm_surrogate* sur, const double* d_widths, int64_t n, float* d_Vt,
+                                     void* stream);
+/* Low-rank eq. 58 with the factor U (d_U, n_nz x rank FP32 row-major): for n_tiles tiles,
+ * nz[9t+ab][m] = sum_r (sum_k Vt_t[r][k] coef[9t+ab][k]) U[m][r], Vt (n_tiles x rank x K FP32),
+ * coef (9 n_tiles x K FP64); d_nz (9 n_tiles x n_nz FP32, dense).  FP32 accumulation. */
+msasm_status msasm_lowrank_contract(const float* d_U, int32_t n_nz, int32_t rank, int32_t K, const float* d_Vt,
+                                    const double* d_coef, int64_t n_tiles, float* d_nz, void* stream);
+/* K of a graded lattice: per-tile widths d_widths (n_tiles FP64, device); pullback, MLP,
+ * low-rank contraction and scatter into d_values (nnz FP32). */
+msasm_status msasm_surrogate_assemble(msasm_plan* plan, msasm_surrogate* sur, const double* d_ctrl, double E,
+                                      double nu, const double* d_widths, float* d_values, void* stream);
+void msasm_surrogate_destroy(msasm_surrogate* sur);
+
 /* Number of interpolation nodes with |det J| <= tol found by the last assemble
  * on this plan (reads back from the device; synchronises `stream`). */
 msasm_status msasm_degenerate_count(const msasm_plan* plan, int64_t* count, void* stream);

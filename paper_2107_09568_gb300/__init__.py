@@ -277,3 +277,121 @@ def cg_solve(K, f, fixed_dofs, tol=1e-12, max_iter=20000):
         p = z + (rz_new / rz) * p
         rz = rz_new
     return x, it, (torch.linalg.vector_norm(b - A(x)) / bn).item()
+
+
+# ---------------------------------------------------------------------------------------
+# learned surrogate (graded lattices)
+class MLP:
+    """Handle of msasm_mlp (1 -> H -> H -> n_out tanh network, FP16 weights, FP32 accumulation)."""
+
+    def __init__(self, n_out=None, hidden=128, seed=0, handle=None, owned=True):
+        lib = load()
+        if handle is None:
+            h = C.c_void_p()
+            check(lib.msasm_mlp_create(int(n_out), int(hidden), C.c_uint64(seed), C.byref(h)))
+            handle = h
+        self.handle, self._owned = handle, owned
+        n, o, H = C.c_int64(), C.c_int32(), C.c_int32()
+        check(lib.msasm_mlp_info(self.handle, C.byref(n), C.byref(o), C.byref(H)))
+        self.n_params, self.n_out, self.hidden = n.value, o.value, H.value
+
+    def params(self, half=False):
+        import torch
+        if half:
+            out = torch.empty(self.n_params, dtype=torch.float16, device="cuda")
+            check(load().msasm_mlp_get_params(self.handle, None, _ptr(out), _stream()))
+        else:
+            out = torch.empty(self.n_params, dtype=torch.float32, device="cuda")
+            check(load().msasm_mlp_get_params(self.handle, _ptr(out), None, _stream()))
+        return out
+
+    def set_params(self, p):
+        check(load().msasm_mlp_set_params(self.handle, _ptr(p.contiguous()), _stream()))
+
+    def forward(self, x):
+        import torch
+        y = torch.empty((x.numel(), self.n_out), dtype=torch.float32, device="cuda")
+        check(load().msasm_mlp_forward(self.handle, _ptr(x), x.numel(), _ptr(y), _stream()))
+        return y
+
+    def loss_grad(self, x, t):
+        import torch
+        g = torch.empty(self.n_params, dtype=torch.float32, device="cuda")
+        loss = C.c_float()
+        check(load().msasm_mlp_loss_grad(self.handle, _ptr(x), _ptr(t), x.numel(), C.byref(loss), _ptr(g),
+                                         _stream()))
+        return loss.value, g
+
+    def train(self, x, t, steps, lr=1e-3):
+        hist = np.zeros(steps, dtype=np.float32)
+        check(load().msasm_mlp_train(self.handle, _ptr(x), _ptr(t), x.numel(), int(steps), float(lr),
+                                     hist.ctypes.data_as(C.c_void_p), _stream()))
+        return hist
+
+    def __del__(self):
+        if self._owned and getattr(self, "handle", None) and _lib._lib is not None:
+            _lib._lib.msasm_mlp_destroy(self.handle)
+            self.handle = None
+
+
+def lowrank_contract(U, Vt, coef):
+    """Low-rank eq. 58: nz (9 n_tiles, n_nz) FP32 from U (n_nz, r), Vt (n_tiles, r, K), coef (9 n_tiles, K) FP64."""
+    import torch
+    n_tiles = coef.shape[0] // 9
+    nz = torch.empty((9 * n_tiles, U.shape[0]), dtype=torch.float32, device="cuda")
+    check(load().msasm_lowrank_contract(_ptr(U.contiguous()), U.shape[0], U.shape[1], coef.shape[1],
+                                        _ptr(Vt.contiguous()), _ptr(coef), n_tiles, _ptr(nz), _stream()))
+    return nz
+
+
+class Surrogate:
+    """Handle of msasm_surrogate: T(w) ~ U V(w)^T with V from an MLP trained on quadrature tables."""
+
+    def __init__(self, tables, widths, coef_samples, rank=32, hidden=128, power_iters=2, seed=0, stream=None):
+        lib = load()
+        self._tables = list(tables)
+        arr = (C.c_void_p * len(tables))(*[t.handle.value for t in tables])
+        w = np.ascontiguousarray(widths, dtype=np.float64)
+        h = C.c_void_p()
+        check(lib.msasm_surrogate_create(arr, w.ctypes.data_as(C.c_void_p), len(tables), _ptr(coef_samples),
+                                         coef_samples.shape[0], int(rank), int(hidden), int(power_iters),
+                                         C.c_uint64(seed), _stream(stream), C.byref(h)))
+        self.handle = h
+        r, K, n = C.c_int32(), C.c_int32(), C.c_int32()
+        check(lib.msasm_surrogate_info(h, C.byref(r), C.byref(K), C.byref(n)))
+        self.rank, self.K, self.n_nz = r.value, K.value, n.value
+        m = C.c_void_p()
+        check(lib.msasm_surrogate_mlp(h, C.byref(m)))
+        self.mlp = MLP(handle=m, owned=False)
+
+    def train(self, steps, lr=1e-3):
+        hist = np.zeros(steps, dtype=np.float32)
+        check(load().msasm_surrogate_train(self.handle, int(steps), float(lr), hist.ctypes.data_as(C.c_void_p),
+                                           _stream()))
+        return hist
+
+    def basis(self):
+        import torch
+        U = torch.empty((self.n_nz, self.rank), dtype=torch.float32, device="cuda")
+        check(load().msasm_surrogate_basis(self.handle, _ptr(U), _stream()))
+        return U
+
+    def predict(self, widths):
+        import torch
+        Vt = torch.empty((widths.numel(), self.rank, self.K), dtype=torch.float32, device="cuda")
+        check(load().msasm_surrogate_predict(self.handle, _ptr(widths), widths.numel(), _ptr(Vt), _stream()))
+        return Vt
+
+
+    def assemble(self, plan, ctrl, widths, E=1.0, nu=0.3, out=None):
+        import torch
+        if out is None:
+            out = torch.empty(plan.nnz, dtype=torch.float32, device="cuda")
+        check(load().msasm_surrogate_assemble(plan.handle, self.handle, _ptr(ctrl), float(E), float(nu),
+                                              _ptr(widths), _ptr(out), _stream()))
+        return out
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib._lib is not None:
+            _lib._lib.msasm_surrogate_destroy(self.handle)
+            self.handle = None

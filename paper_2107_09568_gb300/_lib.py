@@ -59,6 +59,24 @@ _SIGS = {
     "msasm_face_points": (c_i32, [c_vp, c_i32, c_vp, P(c_i64)]),
     "msasm_traction_load": (c_i32, [c_vp, c_i32, c_vp, c_vp, c_vp]),
     "msasm_stage_times": (c_i32, [c_vp, P(c_dbl), P(c_i32)]),
+    "msasm_mlp_create": (c_i32, [c_i32, c_i32, C.c_uint64, P(c_vp)]),
+    "msasm_mlp_info": (c_i32, [c_vp, P(c_i64), P(c_i32), P(c_i32)]),
+    "msasm_mlp_set_params": (c_i32, [c_vp, c_vp, c_vp]),
+    "msasm_mlp_get_params": (c_i32, [c_vp, c_vp, c_vp, c_vp]),
+    "msasm_mlp_forward": (c_i32, [c_vp, c_vp, c_i32, c_vp, c_vp]),
+    "msasm_mlp_loss_grad": (c_i32, [c_vp, c_vp, c_vp, c_i32, P(C.c_float), c_vp, c_vp]),
+    "msasm_mlp_train": (c_i32, [c_vp, c_vp, c_vp, c_i32, c_i32, C.c_float, c_vp, c_vp]),
+    "msasm_mlp_destroy": (None, [c_vp]),
+    "msasm_surrogate_create": (c_i32, [c_vp, c_vp, c_i32, c_vp, c_i64, c_i32, c_i32, c_i32, C.c_uint64, c_vp,
+                                       P(c_vp)]),
+    "msasm_surrogate_info": (c_i32, [c_vp, P(c_i32), P(c_i32), P(c_i32)]),
+    "msasm_surrogate_train": (c_i32, [c_vp, c_i32, C.c_float, c_vp, c_vp]),
+    "msasm_surrogate_mlp": (c_i32, [c_vp, P(c_vp)]),
+    "msasm_surrogate_basis": (c_i32, [c_vp, c_vp, c_vp]),
+    "msasm_surrogate_predict": (c_i32, [c_vp, c_vp, c_i64, c_vp, c_vp]),
+    "msasm_lowrank_contract": (c_i32, [c_vp, c_i32, c_i32, c_i32, c_vp, c_vp, c_i64, c_vp, c_vp]),
+    "msasm_surrogate_assemble": (c_i32, [c_vp, c_vp, c_vp, c_dbl, c_dbl, c_vp, c_vp, c_vp]),
+    "msasm_surrogate_destroy": (None, [c_vp]),
     "msasm_last_error": (C.c_char_p, []),
     "msasm_version": (C.c_char_p, []),
 }

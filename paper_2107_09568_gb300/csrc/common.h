@@ -94,6 +94,9 @@ struct msasm_tables {
   ~msasm_tables();
 };
 
+struct msasm_mlp;
+struct msasm_surrogate;
+
 struct msasm_plan {
   const msasm_tables* tab = nullptr;
   int degree[3] = {0, 0, 0};

@@ -1,0 +1,125 @@
+"""The learned surrogate for graded lattices: MLP kernels against the FP64 oracle, the low-rank
+contraction against the oracle, and the trained surrogate against per-width quadrature tables."""
+import time
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import mlp as omlp
+from oracle.assembly import Problem, coefficient_block
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2107_09568_gb300 as msasm  # noqa: E402
+
+H, RANK, K = 128, 32, 576
+
+
+def test_mlp_loss_and_gradient_match_oracle():
+    """Same (FP16-rounded) weights and data: the GPU's FP32-accumulated loss and gradient against FP64."""
+    n_out = RANK * K
+    rng = synth.rng(11)
+    p = (rng.normal(size=omlp.n_params(H, n_out)) * 0.1).astype(np.float32)
+    x = rng.uniform(-1, 1, size=64).astype(np.float32)
+    t = rng.normal(size=(64, n_out)).astype(np.float32)
+    net = msasm.MLP(n_out, H, seed=1)
+    net.set_params(torch.tensor(p, device="cuda"))
+    loss, g = net.loss_grad(torch.tensor(x, device="cuda"), torch.tensor(t, device="cuda"))
+    p16 = p.astype(np.float16).astype(np.float64)          # the weights the GPU computes with
+    L_ref, g_ref = omlp.loss_grad(p16, H, n_out, x.astype(np.float64), t.astype(np.float64))
+    g = g.cpu().numpy().astype(np.float64)
+    assert abs(loss - L_ref) <= 1e-5 * L_ref
+    err = np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref)
+    print("mlp grad rel err", err)
+    assert err <= 1e-4
+    # forward
+    y = net.forward(torch.tensor(x, device="cuda")).cpu().numpy()
+    y_ref, _ = omlp.forward(p16, H, n_out, x.astype(np.float64))
+    assert np.linalg.norm(y - y_ref) <= 1e-5 * np.linalg.norm(y_ref)
+
+
+def test_mlp_training_fits_a_smooth_family():
+    n_out = 256
+    rng = synth.rng(5)
+    x = np.linspace(-1, 1, 64).astype(np.float32)
+    a, b = rng.normal(size=(2, n_out))
+    t = (np.sin(1.3 * x[:, None] + a[None, :]) * b[None, :] * 0.5).astype(np.float32)
+    net = msasm.MLP(n_out, 64, seed=2)
+    xt, tt = torch.tensor(x, device="cuda"), torch.tensor(t, device="cuda")
+    hist = net.train(xt, tt, 3000, lr=3e-3)
+    assert hist[-1] < 1e-3 * hist[0], (hist[0], hist[-1])
+
+
+def test_lowrank_contract_matches_oracle():
+    rng = synth.rng(3)
+    n_nz, n_tiles = 9192, 7
+    U = rng.normal(size=(n_nz, RANK)).astype(np.float32)
+    Vt = rng.normal(size=(n_tiles, RANK, K)).astype(np.float32)
+    coef = rng.normal(size=(9 * n_tiles, K))
+    nz = msasm.lowrank_contract(torch.tensor(U, device="cuda"), torch.tensor(Vt, device="cuda"),
+                                torch.tensor(coef, device="cuda")).cpu().numpy()
+    Z = np.einsum("trk,tak->tar", Vt.astype(np.float64), coef.reshape(n_tiles, 9, K))
+    ref = np.einsum("tar,mr->tam", Z, U.astype(np.float64)).reshape(9 * n_tiles, n_nz)
+    assert np.linalg.norm(nz - ref) <= 1e-5 * np.linalg.norm(ref)
+
+
+def _graded_setup(nx=6, ny=3, nz=3):
+    m = synth.macro_quarter_arc(nx, ny, nz)
+    widths = synth.width_field(m.n_elem, seed=0)
+    w_train = np.sort(0.15 + 0.25 * synth.rng(0).uniform(size=64))
+    return m, widths, w_train
+
+
+def test_surrogate_against_per_width_quadrature_and_gain():
+    """A quarter arc of 6x3x3 tiles with strut widths from the sinusoidal field in [0.15, 0.40]:
+    the surrogate (trained on 64 quadrature tables) against the per-width quadrature assembly (the
+    method with one table per tile, the error judge), and what it gains over the method without it:
+    one table at the mean width for every tile, or the nearest of the 64 training tables."""
+    m, widths, w_train = _graded_setup()
+    ctrl = torch.tensor(m.ctrl, device="cuda")
+    base = msasm.Tables(synth.micro_cross(3, 0.3), 3)
+    plan = msasm.Plan(base, m)
+    coef = plan.pullback(ctrl)                              # (9 tiles, 576) FP64
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    train_tabs = [msasm.Tables(synth.micro_cross(3, w), 3) for w in w_train]
+    sur = msasm.Surrogate(train_tabs, w_train, coef, rank=RANK, hidden=H, power_iters=2, seed=0)
+    hist = np.concatenate([sur.train(4000, 1e-3), sur.train(3000, 3e-4), sur.train(3000, 1e-4)])
+    torch.cuda.synchronize()
+    t_fit = time.perf_counter() - t0
+    dw = torch.tensor(widths, device="cuda")
+    k_sur = sur.assemble(plan, ctrl, dw)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(3):
+        sur.assemble(plan, ctrl, dw, out=k_sur)
+    torch.cuda.synchronize()
+    t_sur = (time.perf_counter() - t0) / 3
+    # per-width quadrature: one table per tile (the error judge)
+    t0 = time.perf_counter()
+    nz = torch.empty((9 * plan.n_tiles, base.n_nz), dtype=torch.float64, device="cuda")
+    for t in range(plan.n_tiles):
+        tab_t = msasm.Tables(synth.micro_cross(3, float(widths[t])), 3)
+        nz[9 * t:9 * t + 9] = tab_t.contract(coef[9 * t:9 * t + 9], "f64")
+    k_exact = plan.scatter(nz, "f64")
+    torch.cuda.synchronize()
+    t_exact = time.perf_counter() - t0
+    # without the network: mean-width table, or the nearest training table per tile
+    k_mean = msasm.Plan(msasm.Tables(synth.micro_cross(3, 0.275), 3), m).assemble(ctrl)
+    nearest = np.abs(widths[:, None] - w_train[None, :]).argmin(1)
+    for t in range(plan.n_tiles):
+        nz[9 * t:9 * t + 9] = train_tabs[nearest[t]].contract(coef[9 * t:9 * t + 9], "f64")
+    k_near = plan.scatter(nz, "f64")
+    nrm = torch.linalg.vector_norm(k_exact)
+    e_sur = (torch.linalg.vector_norm(k_sur.double() - k_exact) / nrm).item()
+    e_mean = (torch.linalg.vector_norm(k_mean - k_exact) / nrm).item()
+    e_near = (torch.linalg.vector_norm(k_near - k_exact) / nrm).item()
+    print(f"surrogate rel err {e_sur:.3e}  mean-width table {e_mean:.3e}  nearest of 64 tables {e_near:.3e}; "
+          f"loss {hist[0]:.3e} -> {hist[-1]:.3e}; fit {t_fit:.1f} s, assemble {1e3 * t_sur:.2f} ms vs per-width "
+          f"quadrature {1e3 * t_exact:.1f} ms")
+    assert hist[-1] < 1e-3 * hist[0]
+    assert e_sur < 0.1 * e_mean                # the gain in accuracy over one table for all widths
+    assert t_sur < 0.2 * t_exact               # and in time over one quadrature table per tile
+    assert e_sur < 1e-2

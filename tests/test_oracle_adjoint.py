@@ -62,3 +62,24 @@ def test_traction_load_total_force_and_area():
     np.testing.assert_allclose(f.sum(axis=0), expect, rtol=1e-13, atol=1e-14)
     pts = loads.face_points(P, 1)
     assert len(pts) == 4 * 16 and np.all(np.abs(f[np.setdiff1d(np.arange(P.n_points), pts)]) == 0)
+
+
+def test_mlp_oracle_gradient_fd_and_closed_form():
+    from oracle import mlp
+    H, n_out, B = 6, 5, 4
+    rng = np.random.default_rng(7)
+    p = rng.normal(size=mlp.n_params(H, n_out)) * 0.5
+    x = rng.normal(size=B)
+    t = rng.normal(size=(B, n_out))
+    L, g = mlp.loss_grad(p, H, n_out, x, t)
+    h = 1e-6
+    for i in rng.choice(len(p), 25, replace=False):
+        e = np.zeros_like(p); e[i] = h
+        fd = (mlp.loss_grad(p + e, H, n_out, x, t)[0] - mlp.loss_grad(p - e, H, n_out, x, t)[0]) / (2 * h)
+        assert abs(fd - g[i]) < 1e-8 * max(1.0, abs(g[i]))
+    # zero output weights: y = b3, so dL/db3 = 2 sum_b (b3 - t_b) / (B n_out) and dL/dW1 = 0
+    W1, b1, W2, b2, W3, b3 = mlp.unpack(p, H, n_out)
+    W3[:] = 0.0
+    L0, g0 = mlp.loss_grad(p, H, n_out, x, t)
+    np.testing.assert_allclose(g0[-n_out:], 2 * (B * b3 - t.sum(0)) / (B * n_out), rtol=1e-13)
+    assert np.all(g0[:H] == 0.0)
