@@ -40,8 +40,10 @@ msasm_status contract_simt_f32(const float* d_coef, const float* d_T, int64_t n_
                                int ld_nz, float* d_nz, cudaStream_t stream);
 msasm_status to_f32_gpu(const double* x, int64_t n, float* y, cudaStream_t stream);
 template <typename T>
-msasm_status scatter_gpu(const msasm_plan* plan, const T* d_nz, int ld_nz, int64_t t0, int64_t n_tiles,
-                         const int64_t* d_list, int64_t n_list, T* d_values, cudaStream_t stream);
+msasm_status scatter_pass_gpu(const msasm_plan* plan, const T* d_nz, int ld_nz, int64_t t0, int64_t n_tiles,
+                              T* d_values, cudaStream_t stream);
+msasm_status build_scatter_plan(msasm_plan* plan, const std::vector<int32_t>& gmap, const std::vector<int64_t>& pptr,
+                                ScatterPlanHost& out);
 template <typename T>
 msasm_status gemm_simt(const T* A, int64_t lda, const T* B, int64_t ldb, int64_t N, int M, int K, T* C, int64_t ldc,
                        cudaStream_t stream);
@@ -53,6 +55,12 @@ msasm_status transpose_table_gpu(const double* d_T, int n_nz, int K, T* d_Tt, cu
 msasm_status adjoint_pullback_gpu(const msasm_plan* plan, const double* d_ctrl, double lam, double mu, int64_t t0,
                                   int64_t nt, const void* d_W, bool w_f32, double* d_dP, cudaStream_t s);
 int tc_kind_of(msasm_precision prec);
+int emu_kpad(int K);
+size_t emu_slice_bytes(int64_t rows, int K);
+msasm_status emu_slice_gpu(const double* x, int64_t rows, int K, void* slices, double* scale, cudaStream_t s);
+msasm_status contract_emu_gpu(const void* a_slices, const double* a_scale, int M, const void* b_slices,
+                              const double* b_scale, int64_t N, int K, double* out, int ld, unsigned* d_err,
+                              cudaStream_t s);
 int tc_kpad(int K, int kind);
 size_t tc_slice_bytes(int64_t rows, int K, int kind);
 msasm_status tc_split_gpu(const double* x, int64_t rows, int K, int kind, void* hi, void* lo, float* row_scale,
@@ -91,7 +99,13 @@ msasm_plan::~msasm_plan() {
   cudaFree(d_rowptr);
   cudaFree(d_col);
   cudaFree(d_rank);
-  cudaFree(d_second);
+  cudaFree(d_tile_type);
+  cudaFree(d_chunk_info);
+  cudaFree(d_chunk_points);
+  cudaFree(d_prog);
+  cudaFree(d_tmpl);
+  cudaFree(d_tmpl_ptr);
+  cudaFree(d_work);
   cudaFree(d_coef);
   cudaFree(d_nz);
   cudaFree(d_coef_lp);
@@ -242,22 +256,15 @@ msasm_status msasm_plan_create(const msasm_tables* tab, const msasm_macro_desc* 
   plan->n_rows = 3 * plan->n_points;
   plan->nnz = 9 * pptr[plan->n_points];
 
-  // second contributors: pairs on a glued lower face of their tile
-  std::vector<int64_t> second;
-  const int n_nz = tab->n_nz;
-  std::vector<int> face_pairs[8];
-  for (int mask = 1; mask < 8; ++mask)
-    for (int m = 0; m < n_nz; ++m)
-      if (tab->topo.pair_face[m] & mask) face_pairs[mask].push_back(m);
-  plan->second_ptr.assign(size_t(plan->n_tiles) + 1, 0);
-  for (int64_t t = 0; t < plan->n_tiles; ++t) {
-    int64_t ix = t % plan->n_elem[0], iy = (t / plan->n_elem[0]) % plan->n_elem[1],
-            iz = t / (int64_t(plan->n_elem[0]) * plan->n_elem[1]);
-    int mask = (ix > 0 ? 1 : 0) | (iy > 0 ? 2 : 0) | (iz > 0 ? 4 : 0);
-    for (int m : face_pairs[mask]) second.push_back(t * n_nz + m);
-    plan->second_ptr[size_t(t) + 1] = int64_t(second.size());
+  // staged-scatter programs per tile type
+  ScatterPlanHost sp;
+  {
+    msasm_status st0 = build_scatter_plan(plan, gmap, pptr, sp);
+    if (st0 != MSASM_OK) return bail(st0);
   }
-  plan->n_second = int64_t(second.size());
+  plan->work_ptr = sp.work_ptr;
+  plan->max_tmpl = sp.max_tmpl;
+  const int n_nz = tab->n_nz;
 
   // device allocations
   const size_t n_pi = size_t(tab->n_pi);
@@ -276,7 +283,13 @@ msasm_status msasm_plan_create(const msasm_tables* tab, const msasm_macro_desc* 
   if (err == cudaSuccess) err = dev((void**)&plan->d_rowptr, size_t(plan->n_rows + 1) * sizeof(int64_t));
   if (err == cudaSuccess) err = dev((void**)&plan->d_col, size_t(plan->nnz) * sizeof(int32_t));
   if (err == cudaSuccess) err = dev((void**)&plan->d_rank, size_t(plan->n_tiles) * n_nz * sizeof(uint32_t));
-  if (err == cudaSuccess) err = dev((void**)&plan->d_second, second.size() * sizeof(int64_t));
+  if (err == cudaSuccess) err = dev((void**)&plan->d_tile_type, sp.tile_type.size() * sizeof(int32_t));
+  if (err == cudaSuccess) err = dev((void**)&plan->d_chunk_info, sp.chunk_info.size() * sizeof(int32_t));
+  if (err == cudaSuccess) err = dev((void**)&plan->d_chunk_points, sp.chunk_points.size() * sizeof(int32_t));
+  if (err == cudaSuccess) err = dev((void**)&plan->d_prog, sp.prog.size() * sizeof(uint32_t));
+  if (err == cudaSuccess) err = dev((void**)&plan->d_tmpl, sp.tmpl.size() * sizeof(uint32_t));
+  if (err == cudaSuccess) err = dev((void**)&plan->d_tmpl_ptr, sp.tmpl_ptr.size() * sizeof(int64_t));
+  if (err == cudaSuccess) err = dev((void**)&plan->d_work, sp.work.size() * sizeof(int32_t));
   if (err == cudaSuccess) err = dev((void**)&plan->d_coef, size_t(9 * plan->tiles_per_pass) * 9 * n_pi * sizeof(double));
   if (err == cudaSuccess) err = dev((void**)&plan->d_nz, size_t(9 * plan->tiles_per_pass) * ld * sizeof(double));
   if (err == cudaSuccess) err = dev((void**)&plan->d_degenerate, sizeof(unsigned long long));
@@ -303,7 +316,14 @@ msasm_status msasm_plan_create(const msasm_tables* tab, const msasm_macro_desc* 
     if (err == cudaSuccess) err = h2d(plan->d_first[d], first[d].data(), first[d].size() * sizeof(int32_t));
   }
   if (err == cudaSuccess) err = h2d(plan->d_gmap, gmap.data(), gmap.size() * sizeof(int32_t));
-  if (err == cudaSuccess) err = h2d(plan->d_second, second.data(), second.size() * sizeof(int64_t));
+  if (err == cudaSuccess) err = h2d(plan->d_tile_type, sp.tile_type.data(), sp.tile_type.size() * sizeof(int32_t));
+  if (err == cudaSuccess) err = h2d(plan->d_chunk_info, sp.chunk_info.data(), sp.chunk_info.size() * sizeof(int32_t));
+  if (err == cudaSuccess)
+    err = h2d(plan->d_chunk_points, sp.chunk_points.data(), sp.chunk_points.size() * sizeof(int32_t));
+  if (err == cudaSuccess) err = h2d(plan->d_prog, sp.prog.data(), sp.prog.size() * sizeof(uint32_t));
+  if (err == cudaSuccess) err = h2d(plan->d_tmpl, sp.tmpl.data(), sp.tmpl.size() * sizeof(uint32_t));
+  if (err == cudaSuccess) err = h2d(plan->d_tmpl_ptr, sp.tmpl_ptr.data(), sp.tmpl_ptr.size() * sizeof(int64_t));
+  if (err == cudaSuccess) err = h2d(plan->d_work, sp.work.data(), sp.work.size() * sizeof(int32_t));
   if (err == cudaSuccess) err = h2d(d_pptr, pptr.data(), pptr.size() * sizeof(int64_t));
   if (err == cudaSuccess) err = h2d(d_pcol, pcol.data(), pcol.size() * sizeof(int32_t));
   if (err == cudaSuccess) err = h2d(d_pair_face, tab->topo.pair_face.data(), size_t(n_nz));
@@ -397,10 +417,12 @@ static msasm_status ensure_table_slices(msasm_tables* tab, int kind, cudaStream_
   return MSASM_OK;
 }
 
-// bytes of coefficient slices (hi, lo, row scales) for n_tiles tiles
+// bytes of coefficient slices (hi, lo, row scales; or the 7 FP64-emulation slices and scales) for n_tiles tiles
 static size_t coef_lp_bytes_for(int64_t n_tiles, int n_pi) {
   const int K = 9 * n_pi;
-  return 2 * size_t(9 * n_tiles) * size_t(K + 64) * 4 + size_t(9 * n_tiles) * 4 + 256;
+  const size_t split = 2 * size_t(9 * n_tiles) * size_t(K + 64) * 4 + size_t(9 * n_tiles) * 4;
+  const size_t emu = emu_slice_bytes(9 * n_tiles, K) + size_t(9 * n_tiles) * 8;
+  return std::max(split, emu) + 512;
 }
 
 static msasm_status contract_dispatch(const msasm_tables* ctab, msasm_precision prec, const double* d_coef,
@@ -434,6 +456,19 @@ static msasm_status contract_dispatch(const msasm_tables* ctab, msasm_precision 
       return contract_tc_gpu(kind, tab->d_Thi, tab->d_Tlo, tab->d_Tscale, n_nz, hi, lo, sc, 9 * n_tiles, K,
                              static_cast<float*>(d_nz), ld, d_err, s);
     }
+    case MSASM_F64_EMU: {
+      if (!tab->d_Tslices) {
+        MSASM_CUDA(cudaMalloc(&tab->d_Tslices, emu_slice_bytes(n_nz, K)));
+        MSASM_CUDA(cudaMalloc(&tab->d_Tslice_scale, size_t(n_nz) * sizeof(double)));
+        MSASM_TRY(emu_slice_gpu(tab->d_T, n_nz, K, tab->d_Tslices, tab->d_Tslice_scale, s));
+        tab->n_slices = 7;
+      }
+      uint8_t* sl = static_cast<uint8_t*>(scratch_lp);
+      double* sc = reinterpret_cast<double*>(sl + ((emu_slice_bytes(9 * n_tiles, K) + 255) & ~size_t(255)));
+      MSASM_TRY(emu_slice_gpu(d_coef, 9 * n_tiles, K, sl, sc, s));
+      return contract_emu_gpu(tab->d_Tslices, tab->d_Tslice_scale, n_nz, sl, sc, 9 * n_tiles, K,
+                              static_cast<double*>(d_nz), ld, d_err, s);
+    }
     default:
       return fail(MSASM_EUNSUPPORTED, "precision not available in this build");
   }
@@ -456,13 +491,11 @@ static msasm_status ensure_lp_scratch(msasm_plan* plan, msasm_precision prec) {
 static msasm_status scatter_dispatch(msasm_plan* plan, msasm_precision prec, const void* d_nz, int64_t t0,
                                      int64_t nt, void* d_values, cudaStream_t s) {
   const int ld = ld_nz_of(plan->tab->n_nz);
-  const int64_t lo = plan->second_ptr[size_t(t0)], hi = plan->second_ptr[size_t(t0 + nt)];
-  const int64_t* list = plan->d_second + lo;
   if (is_f64_precision(prec))
-    return scatter_gpu<double>(plan, static_cast<const double*>(d_nz), ld, t0, nt, list, hi - lo,
-                               static_cast<double*>(d_values), s);
-  return scatter_gpu<float>(plan, static_cast<const float*>(d_nz), ld, t0, nt, list, hi - lo,
-                            static_cast<float*>(d_values), s);
+    return scatter_pass_gpu<double>(plan, static_cast<const double*>(d_nz), ld, t0, nt,
+                                    static_cast<double*>(d_values), s);
+  return scatter_pass_gpu<float>(plan, static_cast<const float*>(d_nz), ld, t0, nt, static_cast<float*>(d_values),
+                                 s);
 }
 
 msasm_status msasm_assemble(msasm_plan* plan, const double* d_ctrl, double E, double nu, msasm_precision prec,
@@ -498,10 +531,9 @@ msasm_status msasm_assemble(msasm_plan* plan, const double* d_ctrl, double E, do
     MSASM_TRY(scatter_dispatch(plan, prec, plan->d_nz, t0, nt, d_values, s));
     if (timed) {
       MSASM_CUDA(cudaEventRecord(plan->events[4 * pass + 3], s));
-      const int64_t lo = plan->second_ptr[size_t(t0)], hi = plan->second_ptr[size_t(t0 + nt)];
       plan->stage_launches[0] += 1;
       plan->stage_launches[1] += contract_launches(prec);
-      plan->stage_launches[2] += 1 + (hi > lo ? 1 : 0);
+      plan->stage_launches[2] += 1 + (plan->max_tmpl > 0 ? 1 : 0);
     }
   }
   if (timed) plan->timed_passes = n_pass;

@@ -70,6 +70,21 @@ struct PairDesc {       // the patch contributions to one table row
 };
 static_assert(sizeof(PairDesc) == 32, "PairDesc is two 16-byte words");
 
+// staged scatter programs (scatter_plan.cpp)
+constexpr int64_t kChunkValues = 4096;    // values of one chunk of rows held in shared memory
+struct ScatterPlanHost {
+  std::vector<int32_t> tile_type;          // per tile
+  std::vector<int32_t> type_chunk_begin;   // chunks of type ty: [begin[ty], begin[ty+1])
+  std::vector<int32_t> chunk_info;         // per chunk: point offset, point count, program offset, program size
+  std::vector<int32_t> chunk_points;       // owned local ids per chunk
+  std::vector<uint32_t> prog;              // m | lower << 31
+  std::vector<uint32_t> tmpl;              // secondary template per type: m | upper << 30 | lower << 31
+  std::vector<int64_t> tmpl_ptr;
+  int64_t max_tmpl = 0;
+  std::vector<int32_t> work;               // (tile, chunk) pairs
+  std::vector<int64_t> work_ptr;           // per tile
+};
+
 }  // namespace msasm
 
 struct msasm_tables {
@@ -113,9 +128,16 @@ struct msasm_plan {
   int64_t* d_rowptr = nullptr;      // n_rows + 1
   int32_t* d_col = nullptr;         // nnz
   uint32_t* d_rank = nullptr;       // n_tiles x n_nz: rank_u | rank_l << 16, bit 31 = second contributor
-  int64_t* d_second = nullptr;      // t * n_nz + m of second contributors, ascending
-  int64_t n_second = 0;
-  std::vector<int64_t> second_ptr;  // host: entries of tile t are [second_ptr[t], second_ptr[t+1])
+  // staged scatter (device copies of ScatterPlanHost)
+  int32_t* d_tile_type = nullptr;
+  int32_t* d_chunk_info = nullptr;
+  int32_t* d_chunk_points = nullptr;
+  uint32_t* d_prog = nullptr;
+  uint32_t* d_tmpl = nullptr;
+  int64_t* d_tmpl_ptr = nullptr;
+  int32_t* d_work = nullptr;
+  std::vector<int64_t> work_ptr;    // host: work items of tile t are [work_ptr[t], work_ptr[t+1])
+  int64_t max_tmpl = 0;
   std::vector<double> knots_host[3];  // host copies for boundary data
   std::vector<int> span_host[3];      // knot index of each element's span
   std::vector<int32_t> gmap_host;

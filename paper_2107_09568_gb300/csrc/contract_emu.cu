@@ -1,0 +1,258 @@
+// K4 (FP64 form): the contraction of eq. 58 to FP64 accuracy on the BF16 tensor cores.
+//
+// GB300 executes FP64 at about 1.2 TFLOP/s, so the exact-accumulation slicing scheme of Ozaki,
+// Ogita, Oishi and Rump (2012) is used instead: every row x of either operand is scaled by a
+// power of two sigma >= max|x| and cut into S = 7 slices of 7 bits,
+//
+//   x / sigma = sum_{i=0..6} a_i 2^-7(i+1),  a_0 in [-128, 128], a_i in [-64, 64] (i > 0),
+//
+// each stored exactly in BF16 as s_i = a_i 2^-7i.  Then
+//   D[m][n] = sigma_m tau_n 2^-14 sum_{i+j <= 6} sum_k s_i[m][k] t_j[n][k]
+// (the terms with i + j > 6 are below 2^-49 of the result).  Grouping the products by d = i + j,
+// acc_d for d = 0..3 holds a sum of integer multiples of 2^-7d whose magnitude stays below 2^24
+// for K <= 576 (per k: |a_0 b_0| <= 2^14, 2 * 2^13, 2 * 2^13 + 2^12, 2 * 2^13 + 2 * 2^12 in units
+// of the diagonal), so the tensor cores' FP32 accumulation is exact in them whatever its
+// internal rounding; acc4 collects d = 4..6, at most 2^-28 of acc0, where that rounding is
+// harmless.  (Merging d = 3 into the last accumulator, with its mixed scales, measurably loses
+// accuracy: the accumulation truncates relative to the largest term.)  The epilogue adds the
+// five accumulators in FP64 (exact for the first four) and applies the power-of-two scales.
+//
+// CTA tile 128 (m) x 96 (n); per 16-element k block, one 3-D TMA box brings all 7 slices of each
+// operand (32-byte swizzle) into a 4-stage ring; one lane issues the 28 MMAs (M=128, N=96, K=16)
+// into 5 TMEM accumulators of 96 columns; 4 warps read them back.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <mutex>
+
+#include "common.h"
+#include "tc_ptx.cuh"
+
+namespace msasm {
+
+constexpr int EMU_S = 7;                 // slices per operand
+constexpr int EMU_BM = 128, EMU_BN = 96, EMU_KB = 16;    // k block: 16 BF16 = one 32-byte swizzle row
+constexpr int EMU_ACC = 5;                               // accumulators: d = 0, 1, 2, 3 and d >= 4
+constexpr int EMU_STAGES = 4;
+constexpr int EMU_A_SLICE = EMU_BM * 32;                 // one slice tile of A: 128 rows x 32 bytes
+constexpr int EMU_B_SLICE = EMU_BN * 32;                 // one slice tile of B: 96 rows x 32 bytes
+constexpr int EMU_A_BYTES = EMU_S * EMU_A_SLICE;         // 28 KB
+constexpr int EMU_B_BYTES = EMU_S * EMU_B_SLICE;         // 21 KB
+constexpr int EMU_STAGE_BYTES = EMU_A_BYTES + EMU_B_BYTES;
+constexpr int EMU_SMEM_BYTES = EMU_STAGES * EMU_STAGE_BYTES + 1024 + 256;
+
+struct EmuParams {
+  int M, N, kblocks;
+  const double* scale_m;   // sigma_m (power of two)
+  const double* scale_n;   // tau_n
+  double* out;             // nz[n][m], leading dimension ld
+  int ld;
+  unsigned* err;
+};
+
+__global__ void __launch_bounds__(192, 1)
+    contract_emu_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, EmuParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* gen_base = smem_raw + (base - raw);
+  const uint32_t bar0 = base + EMU_STAGES * EMU_STAGE_BYTES;
+  auto full_bar = [&](int s) { return bar0 + 8u * s; };
+  auto empty_bar = [&](int s) { return bar0 + 8u * (EMU_STAGES + s); };
+  const uint32_t accum_bar = bar0 + 8u * (2 * EMU_STAGES);
+  uint32_t* tmem_slot =
+      reinterpret_cast<uint32_t*>(gen_base + EMU_STAGES * EMU_STAGE_BYTES + 8 * (2 * EMU_STAGES + 1));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n0 = blockIdx.x * EMU_BN, m0 = blockIdx.y * EMU_BM;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < EMU_STAGES; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    mbar_init(accum_bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(512u)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer: both operands' 7 slices per k block
+    int issued = 0;
+    bool ok = true;
+    for (int kb = 0; kb < p.kblocks && ok; ++kb) {
+      const int s = kb % EMU_STAGES, it = kb / EMU_STAGES;
+      if (it > 0) ok = mbar_wait(empty_bar(s), (it - 1) & 1, p.err);
+      if (!ok) break;
+      const uint32_t st = base + s * EMU_STAGE_BYTES;
+      mbar_expect_tx(full_bar(s), EMU_STAGE_BYTES);
+      tma_load_3d(st, &tmA, kb * EMU_KB, m0, 0, full_bar(s));
+      tma_load_3d(st + EMU_A_BYTES, &tmB, kb * EMU_KB, n0, 0, full_bar(s));
+      ++issued;
+    }
+    for (int kb = (issued > EMU_STAGES ? issued - EMU_STAGES : 0); kb < issued; ++kb)
+      mbar_wait(full_bar(kb % EMU_STAGES), (kb / EMU_STAGES) & 1, p.err);
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer: 28 products per k block, grouped by i + j
+    const uint32_t idesc = instr_desc(1u, EMU_BM, EMU_BN);        // BF16 x BF16 -> F32
+    uint32_t started = 0;                                         // accumulators already written
+    for (int kb = 0; kb < p.kblocks; ++kb) {
+      const int s = kb % EMU_STAGES, it = kb / EMU_STAGES;
+      if (!mbar_wait(full_bar(s), it & 1, p.err)) break;
+      tc_fence_after();
+      const uint32_t st = base + s * EMU_STAGE_BYTES;
+#pragma unroll
+      for (int i = 0; i < EMU_S; ++i) {
+        const uint64_t a = sw32_desc(st + i * EMU_A_SLICE);
+#pragma unroll
+        for (int j = 0; j + i < EMU_S; ++j) {
+          const int acc = (i + j < EMU_ACC - 1) ? i + j : EMU_ACC - 1;
+          const uint64_t b = sw32_desc(st + EMU_A_BYTES + j * EMU_B_SLICE);
+          const uint32_t accumulate = (started >> acc) & 1u;
+          mma_f16(tmem + uint32_t(acc * EMU_BN), a, b, idesc, accumulate);
+          started |= 1u << acc;
+        }
+      }
+      mma_commit(empty_bar(s));
+    }
+    mma_commit(accum_bar);
+    mbar_wait(accum_bar, 0, p.err);
+  } else if (warp >= 2) {
+    // ---------------- epilogue: five accumulators -> FP64
+    const int q = warp & 3;
+    const bool ok = mbar_wait(accum_bar, 0, p.err);
+    tc_fence_after();
+    if (ok) {
+      const int m = m0 + 32 * q + lane;
+      const double sm = (m < p.M) ? p.scale_m[m] * (1.0 / 16384.0) : 0.0;
+      const uint32_t lane_off = uint32_t(32 * q) << 16;
+      for (int c0 = 0; c0 < EMU_BN; c0 += 16) {
+        if (n0 + c0 >= p.N) break;
+        float a0[16], a1[16], a2[16], a3[16], a4[16];
+        tmem_ld16(tmem + lane_off + 0 * EMU_BN + c0, a0);
+        tmem_ld16(tmem + lane_off + 1 * EMU_BN + c0, a1);
+        tmem_ld16(tmem + lane_off + 2 * EMU_BN + c0, a2);
+        tmem_ld16(tmem + lane_off + 3 * EMU_BN + c0, a3);
+        tmem_ld16(tmem + lane_off + 4 * EMU_BN + c0, a4);
+        if (m < p.M) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int n = n0 + c0 + j;
+            if (n < p.N) {
+              const double v =
+                  (((double(a0[j]) + double(a1[j])) + double(a2[j])) + double(a3[j])) + double(a4[j]);
+              p.out[size_t(n) * p.ld + m] = v * (sm * p.scale_n[n]);
+            }
+          }
+        }
+      }
+    }
+    tc_fence_before();
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u) : "memory");
+  }
+}
+
+// One warp per row: sigma = 2^e >= max|x| and the 7 BF16 slices s_i = a_i 2^-7i, [i][row][Kpad].
+__global__ void emu_slice_kernel(const double* __restrict__ x, int64_t rows, int K, int Kpad,
+                                 __nv_bfloat16* __restrict__ slices, double* __restrict__ scale) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t r = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; r < rows;
+       r += (int64_t(gridDim.x) * blockDim.x) >> 5) {
+    const double* xr = x + r * K;
+    double mx = 0.0;
+    for (int k = lane; k < K; k += 32) mx = fmax(mx, fabs(xr[k]));
+    for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    int e = 0;
+    if (mx > 0.0) frexp(mx, &e);             // mx = f 2^e, f in [0.5, 1): |x| / 2^e < 1
+    if (lane == 0) scale[r] = ldexp(1.0, e);
+    for (int k = lane; k < Kpad; k += 32) {
+      double v = (k < K) ? ldexp(xr[k], -e) : 0.0;
+#pragma unroll
+      for (int i = 0; i < EMU_S; ++i) {
+        const double t = v * 128.0;
+        const double a = rint(t);
+        v = t - a;                             // exact
+        slices[(size_t(i) * rows + r) * Kpad + k] = __double2bfloat16(ldexp(a, -7 * i));   // exact
+      }
+    }
+  }
+}
+
+int emu_kpad(int K) { return (K + EMU_KB - 1) / EMU_KB * EMU_KB; }
+
+size_t emu_slice_bytes(int64_t rows, int K) { return size_t(EMU_S) * rows * emu_kpad(K) * sizeof(__nv_bfloat16); }
+
+msasm_status emu_slice_gpu(const double* x, int64_t rows, int K, void* slices, double* scale, cudaStream_t s) {
+  if (K > 576 + 15) return fail(MSASM_EUNSUPPORTED, "FP64 emulation is exact for K <= 576 (q <= 3)");
+  int64_t blocks = std::min<int64_t>((rows * 32 + 255) / 256, 152 * 16);
+  emu_slice_kernel<<<unsigned(blocks), 256, 0, s>>>(x, rows, K, emu_kpad(K), static_cast<__nv_bfloat16*>(slices),
+                                                    scale);
+  MSASM_CUDA(cudaGetLastError());
+  return MSASM_OK;
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode3 = nullptr;
+static std::mutex g_encode3_mutex;
+
+static msasm_status make_map_3d(CUtensorMap* map, const void* ptr, int64_t rows, int K, int box_rows) {
+  {
+    std::lock_guard<std::mutex> lock(g_encode3_mutex);
+    if (!g_encode3) {
+      void* fn = nullptr;
+      cudaDriverEntryPointQueryResult q;
+      MSASM_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+      if (q != cudaDriverEntryPointSuccess || !fn) return fail(MSASM_ECUDA, "cuTensorMapEncodeTiled unavailable");
+      g_encode3 = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+  }
+  const int Kpad = emu_kpad(K);
+  cuuint64_t dims[3] = {cuuint64_t(K), cuuint64_t(rows), cuuint64_t(EMU_S)};
+  cuuint64_t strides[2] = {cuuint64_t(Kpad) * 2, cuuint64_t(rows) * Kpad * 2};
+  cuuint32_t box[3] = {cuuint32_t(EMU_KB), cuuint32_t(box_rows), cuuint32_t(EMU_S)};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = g_encode3(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(ptr), dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(MSASM_ECUDA, "cuTensorMapEncodeTiled (3-D) failed (" + std::to_string(int(r)) + ")");
+  return MSASM_OK;
+}
+
+// nz[n][m] (FP64, leading dimension ld) = sum_k A[m][k] B[n][k] from the slices of A (M rows) and B (N rows)
+msasm_status contract_emu_gpu(const void* a_slices, const double* a_scale, int M, const void* b_slices,
+                              const double* b_scale, int64_t N, int K, double* out, int ld, unsigned* d_err,
+                              cudaStream_t s) {
+  if (N > int64_t(2147483647) * EMU_BN) return fail(MSASM_EUNSUPPORTED, "too many rows for one launch");
+  CUtensorMap ma, mb;
+  MSASM_TRY(make_map_3d(&ma, a_slices, M, K, EMU_BM));
+  MSASM_TRY(make_map_3d(&mb, b_slices, N, K, EMU_BN));
+  EmuParams p;
+  p.M = M;
+  p.N = int(N);
+  p.kblocks = emu_kpad(K) / EMU_KB;
+  p.scale_m = a_scale;
+  p.scale_n = b_scale;
+  p.out = out;
+  p.ld = ld;
+  p.err = d_err;
+  MSASM_CUDA(cudaFuncSetAttribute(contract_emu_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, EMU_SMEM_BYTES));
+  dim3 grid(unsigned((N + EMU_BN - 1) / EMU_BN), unsigned((M + EMU_BM - 1) / EMU_BM));
+  if (grid.x > 2147483647u || grid.y > 65535u) return fail(MSASM_EUNSUPPORTED, "grid too large");
+  contract_emu_kernel<<<grid, 192, EMU_SMEM_BYTES, s>>>(ma, mb, p);
+  MSASM_CUDA(cudaGetLastError());
+  return MSASM_OK;
+}
+
+}  // namespace msasm

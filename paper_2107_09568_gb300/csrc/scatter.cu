@@ -1,119 +1,140 @@
-// K5: step 4 of Sec. 3.2.4 -- add the tile blocks of nzdata into the global CSR values.
+// K5: step 4 of Sec. 3.2.4 -- the tile blocks of nzdata into the global CSR values.
 //
-// Pair m = (A, B) of tile t owns the 3x3 block at rows 3 g(A) + a, columns
-// 3 g(B) + b, and (A != B) its transpose at rows 3 g(B) + b, columns 3 g(A) + a.
-// With the rank word r_u | r_l << 16 of the plan, the upper entry (a, b) lives at
-// rowptr[3 g(A) + a] + 3 r_u + b and the lower one at rowptr[3 g(B) + b] + 3 r_l + a.
-// Entries shared by two tiles (both points on a glued face) get the lower-indexed
-// tile's value by a plain store here; the second tile adds its value in
-// scatter_second_kernel, launched after this one on the same stream, so every
-// entry is written without atomics and the two-term sum is order independent.
+// Pair m = (A, B) of tile t owns the 3x3 block at rows 3 g(A) + a, columns 3 g(B) + b, and
+// (A != B) its transpose at rows 3 g(B) + b, columns 3 g(A) + a.  With the rank word
+// r_u | r_l << 16 of the plan the upper entry (a, b) lives at rowptr[3 g(A) + a] + 3 r_u + b and
+// the lower one at rowptr[3 g(B) + b] + 3 r_l + a.
+//
+// Staged pass: the rows of the points a tile owns are one contiguous range of values (tile-major
+// numbering).  One CTA per chunk of that range builds the chunk in shared memory from the
+// chunk's program (the pairs whose upper or lower block lands there, in increasing m, so the
+// nzdata loads of neighbouring threads are mostly contiguous), entries no pair of the tile
+// reaches staying zero, and streams it out with coalesced 16-byte stores.  Every CSR value is
+// written exactly once by the staged pass.
+//
+// Secondary pass: blocks of tile t landing in rows owned by a lower tile (points on a glued lower
+// face) are added to the values the owner wrote; it runs after the staged pass on the same
+// stream and each position has at most one such contributor, so no atomics are needed and the
+// two-term sums are order independent.
 #include "common.h"
 
 namespace msasm {
 
-// One CTA per (tile, chunk of kScatterChunk pairs), chunks of a tile adjacent in launch
-// order: the whole GPU works on a few tiles at a time, so the rows being written (about
-// 1.6 MB of FP32 values per 725-point tile) stay in L2 until every sector of them is
-// complete, and no partially written sector is evicted (which would cost a DRAM read).
-// The row starts of the tile's points (rowptr[3 g(A)] and the row length 3 deg(g(A))) are
-// staged in shared memory, so a pair needs only its rank word, its nine values and two
-// shared-memory reads before its stores; every thread keeps kScatterUnroll pairs in flight.
-constexpr int kScatterThreads = 256;
-constexpr int kScatterUnroll = 4;
-constexpr int kScatterChunk = 2048;
+constexpr int kStagedThreads = 256;
+constexpr int kStagedUnroll = 2;
 
 template <typename T>
-__global__ void __launch_bounds__(kScatterThreads) scatter_tile_kernel(
-    const T* __restrict__ nz, int ld_nz, int n_nz, int64_t t0, const int32_t* __restrict__ pairs,
-    const int32_t* __restrict__ gmap, int n_T, const uint32_t* __restrict__ rank, const int64_t* __restrict__ rowptr,
-    T* __restrict__ values) {
-  extern __shared__ int64_t rowbase[];               // [n_T] row start, then [n_T] int32 row lengths
-  int32_t* rowlen = reinterpret_cast<int32_t*>(rowbase + n_T);
-  const int chunks = (n_nz + kScatterChunk - 1) / kScatterChunk;
-  const int64_t tl = blockIdx.x / chunks, t = t0 + tl;
-  const int c_begin = (blockIdx.x % chunks) * kScatterChunk;
-  const int c_end = min(n_nz, c_begin + kScatterChunk);
-  for (int A = threadIdx.x; A < n_T; A += blockDim.x) {
-    const int64_t g = gmap[t * n_T + A];
-    const int64_t b = rowptr[3 * g];
-    rowbase[A] = b;
-    rowlen[A] = int32_t(rowptr[3 * g + 1] - b);
+__global__ void __launch_bounds__(kStagedThreads) scatter_staged_kernel(
+    const T* __restrict__ nz, int ld_nz, int n_nz, int64_t t0, const int32_t* __restrict__ work,
+    const int32_t* __restrict__ chunk_info, const int32_t* __restrict__ chunk_points, const uint32_t* __restrict__ prog,
+    const int32_t* __restrict__ pairs, const int32_t* __restrict__ gmap, int n_T, const uint32_t* __restrict__ rank,
+    const int64_t* __restrict__ rowptr, T* __restrict__ values) {
+  extern __shared__ __align__(16) uint8_t sm_raw[];
+  T* buf = reinterpret_cast<T*>(sm_raw);
+  int32_t* off = reinterpret_cast<int32_t*>(sm_raw + kChunkValues * sizeof(T));   // [n_T]
+  int32_t* len = off + n_T;                                                        // [n_T]
+  const int64_t t = work[2 * blockIdx.x];
+  const int c = work[2 * blockIdx.x + 1];
+  const int64_t tl = t - t0;
+  const int p_begin = chunk_info[4 * c], p_count = chunk_info[4 * c + 1];
+  const int q_begin = chunk_info[4 * c + 2], q_count = chunk_info[4 * c + 3];
+  const int32_t* gt = gmap + t * n_T;
+  const int64_t base = rowptr[3 * int64_t(gt[chunk_points[p_begin]])];
+  const int64_t end = rowptr[3 * int64_t(gt[chunk_points[p_begin + p_count - 1]]) + 3];
+  const int n_vals = int(end - base);
+  for (int i = threadIdx.x; i < p_count; i += blockDim.x) {
+    const int A = chunk_points[p_begin + i];
+    const int64_t g = gt[A];
+    const int64_t r0 = rowptr[3 * g];
+    off[A] = int32_t(r0 - base);
+    len[A] = int32_t(rowptr[3 * g + 1] - r0);
   }
+  for (int i = threadIdx.x; i < n_vals; i += blockDim.x) buf[i] = T(0);
   __syncthreads();
   const T* nzt = nz + 9 * tl * ld_nz;
   const uint32_t* rk = rank + t * n_nz;
-  for (int m0 = c_begin + threadIdx.x; m0 < c_end; m0 += kScatterThreads * kScatterUnroll) {
-    uint32_t w[kScatterUnroll];
-    int2 ab[kScatterUnroll];
-    T v[kScatterUnroll][9];
+  for (int j0 = threadIdx.x; j0 < q_count; j0 += blockDim.x * kStagedUnroll) {
+    uint32_t e[kStagedUnroll], w[kStagedUnroll];
+    int2 ab[kStagedUnroll];
+    T v[kStagedUnroll][9];
 #pragma unroll
-    for (int u = 0; u < kScatterUnroll; ++u) {
-      const int m = m0 + u * kScatterThreads;
-      if (m < c_end) {
+    for (int u = 0; u < kStagedUnroll; ++u) {      // issue every load of UNROLL entries first
+      const int j = j0 + u * blockDim.x;
+      e[u] = (j < q_count) ? prog[q_begin + j] : 0xffffffffu;
+      if (e[u] != 0xffffffffu) {
+        const int m = int(e[u] & 0x7fffffffu);
         w[u] = rk[m];
         ab[u] = reinterpret_cast<const int2*>(pairs)[m];
 #pragma unroll
         for (int k = 0; k < 9; ++k) v[u][k] = nzt[size_t(k) * ld_nz + m];
-      } else {
-        w[u] = 1u << 31;
       }
     }
 #pragma unroll
-    for (int u = 0; u < kScatterUnroll; ++u) {
-      if (w[u] >> 31) continue;
-      const int A = ab[u].x, B = ab[u].y;
-      const int ru = int(w[u] & 0xffffu), rl = int((w[u] >> 16) & 0x7fffu);
-      const int64_t ba = rowbase[A] + 3 * ru;
-      const int64_t la = rowlen[A];
+    for (int u = 0; u < kStagedUnroll; ++u) {
+      if (e[u] == 0xffffffffu) continue;
+      if (!(e[u] >> 31)) {                       // upper block: rows of A
+        const int o = off[ab[u].x] + 3 * int(w[u] & 0xffffu), L = len[ab[u].x];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        T* dst = values + ba + a * la;
-        dst[0] = v[u][3 * a + 0];
-        dst[1] = v[u][3 * a + 1];
-        dst[2] = v[u][3 * a + 2];
-      }
-      if (A != B) {
-        const int64_t bb = rowbase[B] + 3 * rl;
-        const int64_t lb = rowlen[B];
+        for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int b = 0; b < 3; ++b) {
-          T* dst = values + bb + b * lb;
-          dst[0] = v[u][b];
-          dst[1] = v[u][3 + b];
-          dst[2] = v[u][6 + b];
-        }
+          for (int b = 0; b < 3; ++b) buf[o + a * L + b] = v[u][3 * a + b];
+      } else {                                   // lower block: rows of B
+        const int o = off[ab[u].y] + 3 * int((w[u] >> 16) & 0x7fffu), L = len[ab[u].y];
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+#pragma unroll
+          for (int a = 0; a < 3; ++a) buf[o + b * L + a] = v[u][3 * a + b];
       }
     }
   }
+  __syncthreads();
+  // stream out: head up to 16-byte alignment, 16-byte body, tail
+  T* dst = values + base;
+  constexpr int VEC = 16 / sizeof(T);
+  const int head = int((VEC - (base % VEC)) % VEC);
+  const int h = head < n_vals ? head : n_vals;
+  for (int i = threadIdx.x; i < h; i += blockDim.x) dst[i] = buf[i];
+  const int body = (n_vals - h) / VEC;
+  for (int i = threadIdx.x; i < body; i += blockDim.x) {
+    float4 v;
+    T* pv = reinterpret_cast<T*>(&v);
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) pv[k] = buf[h + i * VEC + k];
+    reinterpret_cast<float4*>(dst + h)[i] = v;
+  }
+  for (int i = h + body * VEC + threadIdx.x; i < n_vals; i += blockDim.x) dst[i] = buf[i];
 }
 
 template <typename T>
-__global__ void scatter_second_kernel(const T* __restrict__ nz, int ld_nz, int n_nz, int64_t t0,
-                                      const int64_t* __restrict__ list, int64_t n_list,
-                                      const int32_t* __restrict__ pairs, const int32_t* __restrict__ gmap, int n_T,
-                                      const uint32_t* __restrict__ rank, const int64_t* __restrict__ rowptr,
-                                      T* __restrict__ values) {
-  for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < n_list; s += int64_t(gridDim.x) * blockDim.x) {
-    const int64_t code = list[s];
-    const int64_t t = code / n_nz;
-    const int m = int(code % n_nz);
-    const int64_t tl = t - t0;
-    const uint32_t w = rank[code];
+__global__ void scatter_secondary_kernel(const T* __restrict__ nz, int ld_nz, int n_nz, int64_t t0,
+                                         const int32_t* __restrict__ tile_type, const int64_t* __restrict__ tmpl_ptr,
+                                         const uint32_t* __restrict__ tmpl, const int32_t* __restrict__ pairs,
+                                         const int32_t* __restrict__ gmap, int n_T, const uint32_t* __restrict__ rank,
+                                         const int64_t* __restrict__ rowptr, T* __restrict__ values) {
+  const int64_t tl = blockIdx.y, t = t0 + tl;
+  const int ty = tile_type[t];
+  const int64_t b0 = tmpl_ptr[ty], cnt = tmpl_ptr[ty + 1] - b0;
+  const T* nzt = nz + 9 * tl * ld_nz;
+  for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < cnt; j += int64_t(gridDim.x) * blockDim.x) {
+    const uint32_t e = tmpl[b0 + j];
+    const int m = int(e & 0x3fffffffu);
     const int A = pairs[2 * m], B = pairs[2 * m + 1];
     const int64_t gA = gmap[t * n_T + A], gB = gmap[t * n_T + B];
+    const uint32_t w = rank[t * n_nz + m];
     const int ru = int(w & 0xffffu), rl = int((w >> 16) & 0x7fffu);
     T v[9];
 #pragma unroll
-    for (int ab = 0; ab < 9; ++ab) v[ab] = nz[(9 * tl + ab) * ld_nz + m];
+    for (int k = 0; k < 9; ++k) v[k] = nzt[size_t(k) * ld_nz + m];
+    if (e & (1u << 30)) {
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      T* dst = values + rowptr[3 * gA + a] + 3 * ru;
-      dst[0] += v[3 * a + 0];
-      dst[1] += v[3 * a + 1];
-      dst[2] += v[3 * a + 2];
+      for (int a = 0; a < 3; ++a) {
+        T* dst = values + rowptr[3 * gA + a] + 3 * ru;
+        dst[0] += v[3 * a + 0];
+        dst[1] += v[3 * a + 1];
+        dst[2] += v[3 * a + 2];
+      }
     }
-    if (A != B) {
+    if (e & (1u << 31)) {
 #pragma unroll
       for (int b = 0; b < 3; ++b) {
         T* dst = values + rowptr[3 * gB + b] + 3 * rl;
@@ -125,34 +146,35 @@ __global__ void scatter_second_kernel(const T* __restrict__ nz, int ld_nz, int n
   }
 }
 
+// steps 4 for tiles [t0, t0 + n_tiles) of the plan, nzdata of those tiles in d_nz
 template <typename T>
-msasm_status scatter_gpu(const msasm_plan* plan, const T* d_nz, int ld_nz, int64_t t0, int64_t n_tiles,
-                         const int64_t* d_list, int64_t n_list, T* d_values, cudaStream_t stream) {
+msasm_status scatter_pass_gpu(const msasm_plan* plan, const T* d_nz, int ld_nz, int64_t t0, int64_t n_tiles,
+                              T* d_values, cudaStream_t stream) {
   const msasm_tables* tab = plan->tab;
-  if (n_tiles > 0) {
-    const size_t smem = size_t(tab->topo.n_T) * (sizeof(int64_t) + sizeof(int32_t));
-    if (smem > 200 * 1024) return fail(MSASM_EUNSUPPORTED, "reference tile too large for the scatter kernel");
-    MSASM_CUDA(cudaFuncSetAttribute(scatter_tile_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-    const int64_t chunks = (tab->n_nz + kScatterChunk - 1) / kScatterChunk;
-    scatter_tile_kernel<T><<<unsigned(n_tiles * chunks), kScatterThreads, smem, stream>>>(
-        d_nz, ld_nz, tab->n_nz, t0, tab->d_pairs, plan->d_gmap, tab->topo.n_T, plan->d_rank, plan->d_rowptr,
-        d_values);
+  const int n_T = tab->topo.n_T;
+  const int64_t w0 = plan->work_ptr[size_t(t0)], w1 = plan->work_ptr[size_t(t0 + n_tiles)];
+  if (w1 > w0) {
+    const size_t smem = kChunkValues * sizeof(T) + 2 * size_t(n_T) * sizeof(int32_t);
+    if (smem > 220 * 1024) return fail(MSASM_EUNSUPPORTED, "reference tile too large for the staged scatter");
+    MSASM_CUDA(cudaFuncSetAttribute(scatter_staged_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    scatter_staged_kernel<T><<<unsigned(w1 - w0), kStagedThreads, smem, stream>>>(
+        d_nz, ld_nz, tab->n_nz, t0, plan->d_work + 2 * w0, plan->d_chunk_info, plan->d_chunk_points, plan->d_prog,
+        tab->d_pairs, plan->d_gmap, n_T, plan->d_rank, plan->d_rowptr, d_values);
     MSASM_CUDA(cudaGetLastError());
   }
-  if (n_list > 0) {
-    int64_t b2 = (n_list + 255) / 256;
-    if (b2 > 152 * 8) b2 = 152 * 8;
-    scatter_second_kernel<T><<<unsigned(b2), 256, 0, stream>>>(d_nz, ld_nz, tab->n_nz, t0, d_list, n_list,
-                                                               tab->d_pairs, plan->d_gmap, tab->topo.n_T,
-                                                               plan->d_rank, plan->d_rowptr, d_values);
+  if (plan->max_tmpl > 0 && n_tiles > 0) {
+    dim3 grid(unsigned(std::max<int64_t>(1, std::min<int64_t>((plan->max_tmpl + 255) / 256, 8))), unsigned(n_tiles));
+    scatter_secondary_kernel<T><<<grid, 256, 0, stream>>>(d_nz, ld_nz, tab->n_nz, t0, plan->d_tile_type,
+                                                          plan->d_tmpl_ptr, plan->d_tmpl, tab->d_pairs, plan->d_gmap,
+                                                          n_T, plan->d_rank, plan->d_rowptr, d_values);
     MSASM_CUDA(cudaGetLastError());
   }
   return MSASM_OK;
 }
 
-template msasm_status scatter_gpu<double>(const msasm_plan*, const double*, int, int64_t, int64_t, const int64_t*,
-                                          int64_t, double*, cudaStream_t);
-template msasm_status scatter_gpu<float>(const msasm_plan*, const float*, int, int64_t, int64_t, const int64_t*,
-                                         int64_t, float*, cudaStream_t);
+template msasm_status scatter_pass_gpu<double>(const msasm_plan*, const double*, int, int64_t, int64_t, double*,
+                                               cudaStream_t);
+template msasm_status scatter_pass_gpu<float>(const msasm_plan*, const float*, int, int64_t, int64_t, float*,
+                                              cudaStream_t);
 
 }  // namespace msasm

@@ -29,8 +29,8 @@ void symmetric_eigen(std::vector<double> A, int n, std::vector<double>& w, std::
 msasm_status pullback_gpu(const msasm_plan* plan, const double* d_ctrl, double lam, double mu, int64_t t0,
                           int64_t n_tiles, double* d_coef, cudaStream_t stream);
 template <typename T>
-msasm_status scatter_gpu(const msasm_plan* plan, const T* d_nz, int ld_nz, int64_t t0, int64_t n_tiles,
-                         const int64_t* d_list, int64_t n_list, T* d_values, cudaStream_t stream);
+msasm_status scatter_pass_gpu(const msasm_plan* plan, const T* d_nz, int ld_nz, int64_t t0, int64_t n_tiles,
+                              T* d_values, cudaStream_t stream);
 
 // ------------------------------------------------------------------ MLP layout
 // params (FP32 master and FP16 copy): W1[H], b1[H], W2[H][H], b2[H], W3[n_out][H], b3[n_out]
@@ -762,11 +762,7 @@ msasm_status msasm_surrogate_assemble(msasm_plan* plan, msasm_surrogate* sur, co
     if (st == MSASM_OK)
       st = lowrank_contract_gpu(sur->d_U, sur->n_nz, sur->rank, sur->K, Vt, plan->d_coef, nt, Z,
                                 static_cast<float*>(plan->d_nz), ld, s);
-    if (st == MSASM_OK) {
-      const int64_t lo = plan->second_ptr[size_t(t0)], hi = plan->second_ptr[size_t(t0 + nt)];
-      st = scatter_gpu<float>(plan, static_cast<const float*>(plan->d_nz), ld, t0, nt, plan->d_second + lo, hi - lo,
-                              d_values, s);
-    }
+    if (st == MSASM_OK) st = scatter_pass_gpu<float>(plan, static_cast<const float*>(plan->d_nz), ld, t0, nt, d_values, s);
   }
   cudaFreeAsync(Vt, s);
   cudaFreeAsync(Z, s);

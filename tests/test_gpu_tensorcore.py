@@ -100,3 +100,53 @@ def test_beam4000_full_size_sampled(prec):
     err = rel_fro(np.concatenate(got), np.concatenate(ref))
     print(prec, "beam4000 sampled", err)
     assert err <= TOL[prec], err
+
+
+# ---------------------------------------------------------------- FP64 emulated on BF16 tensor cores
+@pytest.mark.parametrize("n_e,q,n_tiles", [(2, 1, 1), (3, 3, 61), (2, 2, 8), (3, 0, 5)])
+def test_f64_emu_contract_parity(n_e, q, n_tiles):
+    """7 exact BF16 slices per operand: the FP64 bar (1e-12) on random data, where FP32-class
+    arithmetic would give ~1e-7."""
+    tab = msasm.Tables(synth.micro_cross(n_e), q)
+    coef = np.random.default_rng(4).normal(size=(9 * n_tiles, 9 * tab.n_pi))
+    coef[:, ::7] *= 1e-3                            # a spread of magnitudes within rows
+    nz = tab.contract(torch.tensor(coef, device="cuda"), "f64_emu").cpu().numpy()
+    ref = coef @ oracle_table(n_e, q).reshape(tab.n_nz, -1).T
+    err = rel_fro(nz, ref)
+    print("f64_emu", n_e, q, n_tiles, err)
+    assert err <= 1e-12, err
+
+
+@pytest.mark.parametrize("name", ["cube8", "beam3x2x2_q3", "ragged_5x1x3_ne3_q2"])
+def test_f64_emu_assemble_parity(name):
+    from test_gpu_parity import make_case
+    prob, tab, plan, ctrl = make_case(name)
+    vals = plan.assemble(ctrl, 1.0, 0.3, "f64_emu", check_degenerate=True).cpu().numpy()
+    err = rel_fro(vals, prob.assemble_lookup())
+    print("f64_emu assemble", name, err)
+    assert err <= 1e-12, err
+
+
+def test_f64_emu_beam1000_full_size_sampled():
+    w = synth.workload("beam1000")
+    micro = synth.micro_cross(3)
+    prob = Problem(micro, w.macro, 3, table=oracle_table(3, 3), structure=False)
+    tab = msasm.Tables(micro, 3)
+    plan = msasm.Plan(tab, w.macro)
+    ctrl = torch.tensor(w.macro.ctrl, device="cuda")
+    vals = plan.assemble(ctrl, 1.0, 0.3, "f64_emu", check_degenerate=True)
+    ref64 = plan.assemble(ctrl, 1.0, 0.3, "f64")
+    full = (torch.linalg.vector_norm(vals - ref64) / torch.linalg.vector_norm(ref64)).item()
+    rowptr, col = plan.csr()
+    pts = np.random.default_rng(9).choice(plan.n_points, 24, replace=False)
+    rows = point_rows(prob, pts)
+    rp = rowptr.cpu().numpy()
+    got, ref = [], []
+    for g, (hs, blocks) in rows.items():
+        for a in range(3):
+            r0, r1 = rp[3 * g + a], rp[3 * g + a + 1]
+            got.append(vals[r0:r1].cpu().numpy())
+            ref.append(blocks[:, a, :].ravel())
+    err = rel_fro(np.concatenate(got), np.concatenate(ref))
+    print("f64_emu beam1000 sampled vs oracle", err, "whole matrix vs DFMA form", full)
+    assert err <= 1e-12 and full <= 1e-12
