@@ -57,10 +57,9 @@ msasm_status adjoint_pullback_gpu(const msasm_plan* plan, const double* d_ctrl, 
 int tc_kind_of(msasm_precision prec);
 int emu_kpad(int K);
 size_t emu_slice_bytes(int64_t rows, int K);
-msasm_status emu_slice_gpu(const double* x, int64_t rows, int K, void* slices, double* scale, cudaStream_t s);
-msasm_status contract_emu_gpu(const void* a_slices, const double* a_scale, int M, const void* b_slices,
-                              const double* b_scale, int64_t N, int K, double* out, int ld, unsigned* d_err,
-                              cudaStream_t s);
+msasm_status emu_slice_gpu(const double* x, int64_t rows, int K, void* slices, int* scale_exp, cudaStream_t s);
+msasm_status contract_emu_gpu(const void* a_slices, const int* a_exp, int M, const void* b_slices, const int* b_exp,
+                              int64_t N, int K, double* out, int ld, unsigned* d_err, cudaStream_t s);
 int tc_kpad(int K, int kind);
 size_t tc_slice_bytes(int64_t rows, int K, int kind);
 msasm_status tc_split_gpu(const double* x, int64_t rows, int K, int kind, void* hi, void* lo, float* row_scale,
@@ -459,12 +458,12 @@ static msasm_status contract_dispatch(const msasm_tables* ctab, msasm_precision 
     case MSASM_F64_EMU: {
       if (!tab->d_Tslices) {
         MSASM_CUDA(cudaMalloc(&tab->d_Tslices, emu_slice_bytes(n_nz, K)));
-        MSASM_CUDA(cudaMalloc(&tab->d_Tslice_scale, size_t(n_nz) * sizeof(double)));
+        MSASM_CUDA(cudaMalloc(&tab->d_Tslice_scale, size_t(n_nz) * sizeof(int)));
         MSASM_TRY(emu_slice_gpu(tab->d_T, n_nz, K, tab->d_Tslices, tab->d_Tslice_scale, s));
         tab->n_slices = 7;
       }
       uint8_t* sl = static_cast<uint8_t*>(scratch_lp);
-      double* sc = reinterpret_cast<double*>(sl + ((emu_slice_bytes(9 * n_tiles, K) + 255) & ~size_t(255)));
+      int* sc = reinterpret_cast<int*>(sl + ((emu_slice_bytes(9 * n_tiles, K) + 255) & ~size_t(255)));
       MSASM_TRY(emu_slice_gpu(d_coef, 9 * n_tiles, K, sl, sc, s));
       return contract_emu_gpu(tab->d_Tslices, tab->d_Tslice_scale, n_nz, sl, sc, 9 * n_tiles, K,
                               static_cast<double*>(d_nz), ld, d_err, s);

@@ -105,7 +105,7 @@ struct msasm_tables {
   int split_kind = -1;              // which precision the slices hold
   void* d_Tslices = nullptr;        // FP64-emulation slices
   int n_slices = 0;
-  double* d_Tslice_scale = nullptr;
+  int* d_Tslice_scale = nullptr;    // power-of-two exponent per table row of the emulation slices
   ~msasm_tables();
 };
 

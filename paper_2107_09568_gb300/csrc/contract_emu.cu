@@ -14,8 +14,10 @@
 // of the diagonal), so the tensor cores' FP32 accumulation is exact in them whatever its
 // internal rounding; acc4 collects d = 4..6, at most 2^-28 of acc0, where that rounding is
 // harmless.  (Merging d = 3 into the last accumulator, with its mixed scales, measurably loses
-// accuracy: the accumulation truncates relative to the largest term.)  The epilogue adds the
-// five accumulators in FP64 (exact for the first four) and applies the power-of-two scales.
+// accuracy: the accumulation truncates relative to the largest term.)  The epilogue forms the
+// exact fixed-point sum X = sum_d acc_d 2^35 in int64 (acc4 rounded at 2^-35) and writes
+// X 2^(e_m + e_n - 49) as an FP64 bit pattern rounded to nearest even, with integer instructions
+// only: the FP64 pipe, about 1/64 of the FP32 rate per SM on GB300, is not used at all.
 //
 // CTA tile 128 (m) x 96 (n); per 16-element k block, one 3-D TMA box brings all 7 slices of each
 // operand (32-byte swizzle) into a 4-stage ring; one lane issues the 28 MMAs (M=128, N=96, K=16)
@@ -44,12 +46,40 @@ constexpr int EMU_SMEM_BYTES = EMU_STAGES * EMU_STAGE_BYTES + 1024 + 256;
 
 struct EmuParams {
   int M, N, kblocks;
-  const double* scale_m;   // sigma_m (power of two)
-  const double* scale_n;   // tau_n
+  const int* exp_m;        // sigma_m = 2^exp_m
+  const int* exp_n;        // tau_n = 2^exp_n
   double* out;             // nz[n][m], leading dimension ld
   int ld;
   unsigned* err;
 };
+
+// x 2^e as the nearest FP64 (ties to even), by integer operations on the bit pattern.
+__device__ __forceinline__ double ldexp_i64_rn(long long x, int e) {
+  if (x == 0) return 0.0;
+  const unsigned long long sign = x < 0 ? (1ull << 63) : 0ull;
+  unsigned long long u = x < 0 ? 0ull - (unsigned long long)x : (unsigned long long)x;
+  const int nbits = 64 - __clzll(u);
+  long long exp = (long long)nbits - 1 + e;             // unbiased exponent of the result
+  unsigned long long mant;
+  if (nbits <= 53) {
+    mant = u << (53 - nbits);
+  } else {
+    const int sh = nbits - 53;
+    mant = u >> sh;
+    const unsigned long long rem = u & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (mant & 1ull))) {
+      ++mant;
+      if (mant == (1ull << 53)) {
+        mant >>= 1;
+        ++exp;
+      }
+    }
+  }
+  const long long biased = exp + 1023;
+  if (biased <= 0) return __longlong_as_double((long long)sign);                 // below the normal range
+  if (biased >= 2047) return __longlong_as_double((long long)(sign | 0x7FF0000000000000ull));
+  return __longlong_as_double((long long)(sign | ((unsigned long long)biased << 52) | (mant & ((1ull << 52) - 1))));
+}
 
 __global__ void __launch_bounds__(192, 1)
     contract_emu_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, EmuParams p) {
@@ -133,7 +163,7 @@ __global__ void __launch_bounds__(192, 1)
     tc_fence_after();
     if (ok) {
       const int m = m0 + 32 * q + lane;
-      const double sm = (m < p.M) ? p.scale_m[m] * (1.0 / 16384.0) : 0.0;
+      const int em = (m < p.M) ? p.exp_m[m] - 49 : 0;     // D = X 2^(e_m + e_n - 14 - 35)
       const uint32_t lane_off = uint32_t(32 * q) << 16;
       for (int c0 = 0; c0 < EMU_BN; c0 += 16) {
         if (n0 + c0 >= p.N) break;
@@ -148,9 +178,13 @@ __global__ void __launch_bounds__(192, 1)
           for (int j = 0; j < 16; ++j) {
             const int n = n0 + c0 + j;
             if (n < p.N) {
-              const double v =
-                  (((double(a0[j]) + double(a1[j])) + double(a2[j])) + double(a3[j])) + double(a4[j]);
-              p.out[size_t(n) * p.ld + m] = v * (sm * p.scale_n[n]);
+              // exact integers: acc0, acc1 2^7, acc2 2^14, acc3 2^21 (all below 2^24 in magnitude)
+              const long long x = ((long long)__float2int_rn(a0[j]) << 35) +
+                                  ((long long)__float2int_rn(a1[j] * 128.0f) << 28) +
+                                  ((long long)__float2int_rn(a2[j] * 16384.0f) << 21) +
+                                  ((long long)__float2int_rn(a3[j] * 2097152.0f) << 14) +
+                                  __float2ll_rn(a4[j] * 34359738368.0f);
+              p.out[size_t(n) * p.ld + m] = ldexp_i64_rn(x, em + p.exp_n[n]);
             }
           }
         }
@@ -167,7 +201,7 @@ __global__ void __launch_bounds__(192, 1)
 
 // One warp per row: sigma = 2^e >= max|x| and the 7 BF16 slices s_i = a_i 2^-7i, [i][row][Kpad].
 __global__ void emu_slice_kernel(const double* __restrict__ x, int64_t rows, int K, int Kpad,
-                                 __nv_bfloat16* __restrict__ slices, double* __restrict__ scale) {
+                                 __nv_bfloat16* __restrict__ slices, int* __restrict__ scale_exp) {
   const int lane = threadIdx.x & 31;
   for (int64_t r = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; r < rows;
        r += (int64_t(gridDim.x) * blockDim.x) >> 5) {
@@ -177,7 +211,7 @@ __global__ void emu_slice_kernel(const double* __restrict__ x, int64_t rows, int
     for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     int e = 0;
     if (mx > 0.0) frexp(mx, &e);             // mx = f 2^e, f in [0.5, 1): |x| / 2^e < 1
-    if (lane == 0) scale[r] = ldexp(1.0, e);
+    if (lane == 0) scale_exp[r] = e;
     for (int k = lane; k < Kpad; k += 32) {
       double v = (k < K) ? ldexp(xr[k], -e) : 0.0;
 #pragma unroll
@@ -195,11 +229,11 @@ int emu_kpad(int K) { return (K + EMU_KB - 1) / EMU_KB * EMU_KB; }
 
 size_t emu_slice_bytes(int64_t rows, int K) { return size_t(EMU_S) * rows * emu_kpad(K) * sizeof(__nv_bfloat16); }
 
-msasm_status emu_slice_gpu(const double* x, int64_t rows, int K, void* slices, double* scale, cudaStream_t s) {
+msasm_status emu_slice_gpu(const double* x, int64_t rows, int K, void* slices, int* scale_exp, cudaStream_t s) {
   if (K > 576 + 15) return fail(MSASM_EUNSUPPORTED, "FP64 emulation is exact for K <= 576 (q <= 3)");
   int64_t blocks = std::min<int64_t>((rows * 32 + 255) / 256, 152 * 16);
   emu_slice_kernel<<<unsigned(blocks), 256, 0, s>>>(x, rows, K, emu_kpad(K), static_cast<__nv_bfloat16*>(slices),
-                                                    scale);
+                                                    scale_exp);
   MSASM_CUDA(cudaGetLastError());
   return MSASM_OK;
 }
@@ -231,8 +265,8 @@ static msasm_status make_map_3d(CUtensorMap* map, const void* ptr, int64_t rows,
 }
 
 // nz[n][m] (FP64, leading dimension ld) = sum_k A[m][k] B[n][k] from the slices of A (M rows) and B (N rows)
-msasm_status contract_emu_gpu(const void* a_slices, const double* a_scale, int M, const void* b_slices,
-                              const double* b_scale, int64_t N, int K, double* out, int ld, unsigned* d_err,
+msasm_status contract_emu_gpu(const void* a_slices, const int* a_exp, int M, const void* b_slices,
+                              const int* b_exp, int64_t N, int K, double* out, int ld, unsigned* d_err,
                               cudaStream_t s) {
   if (N > int64_t(2147483647) * EMU_BN) return fail(MSASM_EUNSUPPORTED, "too many rows for one launch");
   CUtensorMap ma, mb;
@@ -242,8 +276,8 @@ msasm_status contract_emu_gpu(const void* a_slices, const double* a_scale, int M
   p.M = M;
   p.N = int(N);
   p.kblocks = emu_kpad(K) / EMU_KB;
-  p.scale_m = a_scale;
-  p.scale_n = b_scale;
+  p.exp_m = a_exp;
+  p.exp_n = b_exp;
   p.out = out;
   p.ld = ld;
   p.err = d_err;
