@@ -113,6 +113,9 @@ msasm_plan::~msasm_plan() {
   cudaFree(d_ctrl_stage);
   cudaFree(d_values_stage);
   for (cudaEvent_t e : events) cudaEventDestroy(e);
+  for (cudaEvent_t e : copy_events) cudaEventDestroy(e);
+  for (int k = 0; k < 2; ++k)
+    if (copy_stream[k]) cudaStreamDestroy(copy_stream[k]);
 }
 
 extern "C" {
@@ -254,6 +257,19 @@ msasm_status msasm_plan_create(const msasm_tables* tab, const msasm_macro_desc* 
   if (max_deg >= 32768) return bail(fail(MSASM_EUNSUPPORTED, "a point has more than 32767 neighbours"));
   plan->n_rows = 3 * plan->n_points;
   plan->nnz = 9 * pptr[plan->n_points];
+  // value range of each tile's owned rows: owned points of tile t are the ids assigned while
+  // numbering t, so the ranges are consecutive in tile order
+  plan->tile_vbase.assign(size_t(plan->n_tiles) + 1, plan->nnz);
+  {
+    int64_t next_id = 0;
+    const int n_T = tab->topo.n_T;
+    for (int64_t t = 0; t < plan->n_tiles; ++t) {
+      plan->tile_vbase[size_t(t)] = 9 * pptr[size_t(next_id)];
+      int32_t mx = -1;
+      for (int A = 0; A < n_T; ++A) mx = std::max(mx, gmap[size_t(t) * n_T + A]);
+      if (mx + 1 > next_id) next_id = mx + 1;
+    }
+  }
 
   // staged-scatter programs per tile type
   ScatterPlanHost sp;
@@ -573,9 +589,11 @@ msasm_status msasm_assemble_host(msasm_plan* plan, const double* h_ctrl, double 
                                  void* h_values, uint32_t flags, void* stream) {
   if (!plan || !h_ctrl || !h_values) return fail(MSASM_EINVAL, "plan, h_ctrl or h_values is NULL");
   if (prec < MSASM_F64 || prec > MSASM_F64_EMU) return fail(MSASM_EINVAL, "unknown precision");
+  MSASM_TRY(check_material(E, nu));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t cbytes = size_t(plan->n_ctrl) * 3 * sizeof(double);
-  const size_t vbytes = size_t(plan->nnz) * value_bytes(prec);
+  const size_t vb = value_bytes(prec);
+  const size_t vbytes = size_t(plan->nnz) * vb;
   if (!plan->d_ctrl_stage) MSASM_CUDA(cudaMalloc(&plan->d_ctrl_stage, cbytes));
   if (plan->values_stage_bytes < vbytes) {
     cudaFree(plan->d_values_stage);
@@ -584,10 +602,57 @@ msasm_status msasm_assemble_host(msasm_plan* plan, const double* h_ctrl, double 
     MSASM_CUDA(cudaMalloc(&plan->d_values_stage, vbytes));
     plan->values_stage_bytes = vbytes;
   }
+  for (int k = 0; k < 2; ++k)
+    if (!plan->copy_stream[k]) MSASM_CUDA(cudaStreamCreateWithFlags(&plan->copy_stream[k], cudaStreamNonBlocking));
+  double lam, mu;
+  lame(E, nu, lam, mu);
+  MSASM_TRY(ensure_lp_scratch(plan, prec));
   MSASM_CUDA(cudaMemcpyAsync(plan->d_ctrl_stage, h_ctrl, cbytes, cudaMemcpyHostToDevice, s));
-  MSASM_TRY(msasm_assemble(plan, plan->d_ctrl_stage, E, nu, prec, plan->d_values_stage, flags, stream));
-  MSASM_CUDA(cudaMemcpyAsync(h_values, plan->d_values_stage, vbytes, cudaMemcpyDeviceToHost, s));
+  MSASM_CUDA(cudaMemsetAsync(plan->d_degenerate, 0, sizeof(unsigned long long), s));
+  // Passes of about 1/8 of the tiles: after a pass ending at tile t1, the rows owned by tiles
+  // below t1 - nx*ny can receive no further contribution (their upper neighbours are done), so
+  // that prefix of the values is copied to the host on a side stream while the next pass runs.
+  const int64_t P = std::max<int64_t>(1, std::min<int64_t>(plan->tiles_per_pass, (plan->n_tiles + 7) / 8));
+  const int64_t lag = int64_t(plan->n_elem[0]) * plan->n_elem[1];
+  int64_t copied = 0;
+  int which = 0, ev = 0;
+  auto copy_upto = [&](int64_t upto) -> msasm_status {
+    if (upto <= copied) return MSASM_OK;
+    if (plan->copy_events.size() <= size_t(ev)) {
+      cudaEvent_t e;
+      MSASM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      plan->copy_events.push_back(e);
+    }
+    cudaEvent_t e = plan->copy_events[size_t(ev++)];
+    MSASM_CUDA(cudaEventRecord(e, s));
+    cudaStream_t cs = plan->copy_stream[which];
+    which ^= 1;
+    MSASM_CUDA(cudaStreamWaitEvent(cs, e, 0));
+    MSASM_CUDA(cudaMemcpyAsync(static_cast<uint8_t*>(h_values) + size_t(copied) * vb,
+                               static_cast<uint8_t*>(plan->d_values_stage) + size_t(copied) * vb,
+                               size_t(upto - copied) * vb, cudaMemcpyDeviceToHost, cs));
+    copied = upto;
+    return MSASM_OK;
+  };
+  for (int64_t t0 = 0; t0 < plan->n_tiles; t0 += P) {
+    const int64_t nt = std::min(P, plan->n_tiles - t0);
+    MSASM_TRY(pullback_gpu(plan, plan->d_ctrl_stage, lam, mu, t0, nt, plan->d_coef, s));
+    MSASM_TRY(contract_dispatch(plan->tab, prec, plan->d_coef, nt, plan->d_nz, plan->d_coef_lp, s, plan->d_tc_err));
+    MSASM_TRY(scatter_dispatch(plan, prec, plan->d_nz, t0, nt, plan->d_values_stage, s));
+    const int64_t t_final = t0 + nt - lag;
+    if (t0 + nt < plan->n_tiles && t_final > 0) MSASM_TRY(copy_upto(plan->tile_vbase[size_t(t_final)]));
+  }
+  MSASM_TRY(copy_upto(plan->nnz));
+  for (int k = 0; k < 2; ++k) MSASM_CUDA(cudaStreamSynchronize(plan->copy_stream[k]));
   MSASM_CUDA(cudaStreamSynchronize(s));
+  if (flags & MSASM_FLAG_CHECK_DEGENERATE) {
+    unsigned long long cnt = 0;
+    unsigned tc_err = 0;
+    MSASM_CUDA(cudaMemcpy(&cnt, plan->d_degenerate, sizeof(cnt), cudaMemcpyDeviceToHost));
+    MSASM_CUDA(cudaMemcpy(&tc_err, plan->d_tc_err, sizeof(tc_err), cudaMemcpyDeviceToHost));
+    if (tc_err) return fail(MSASM_ECUDA, "a tensor-core pipeline wait timed out (results invalid)");
+    if (cnt) return fail(MSASM_EDEGENERATE, "degenerate macro element in msasm_assemble_host");
+  }
   return MSASM_OK;
 }
 

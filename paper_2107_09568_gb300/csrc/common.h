@@ -141,6 +141,9 @@ struct msasm_plan {
   std::vector<double> knots_host[3];  // host copies for boundary data
   std::vector<int> span_host[3];      // knot index of each element's span
   std::vector<int32_t> gmap_host;
+  std::vector<int64_t> tile_vbase;    // host: first value index of the rows owned by tile t (n_tiles + 1)
+  cudaStream_t copy_stream[2] = {nullptr, nullptr};   // device->host copies of msasm_assemble_host
+  std::vector<cudaEvent_t> copy_events;
   // scratch
   double* d_coef = nullptr;         // 9 tiles_per_pass x 9 n_pi, FP64
   void* d_nz = nullptr;             // 9 tiles_per_pass x n_nz, FP64-sized

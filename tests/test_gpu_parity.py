@@ -166,12 +166,15 @@ def test_scatter_stage(built):
     assert rel_fro(vals, prob.assemble_lookup()) <= 1e-14
 
 
-def test_assemble_host_buffers(built):
-    prob, tab, plan, ctrl = make_case("cube8")
-    dev = plan.assemble(ctrl, 1.0, 0.3, "f64").cpu()
+@pytest.mark.parametrize("name,prec", [("cube8", "f64"), ("beam3x2x2_q3", "f64_emu"), ("ragged_5x1x3_ne3_q2", "f32")])
+def test_assemble_host_buffers(built, name, prec):
+    """Host-buffer entry point (passes with overlapped device-to-host copies of finished rows)
+    returns exactly the device result."""
+    prob, tab, plan, ctrl = make_case(name)
+    dev = plan.assemble(ctrl, 1.0, 0.3, prec).cpu()
     h_ctrl = torch.tensor(prob.mmap.macro.ctrl).pin_memory()
-    h_vals = torch.empty(plan.nnz, dtype=torch.float64).pin_memory()
-    plan.assemble_host(h_ctrl, h_vals, 1.0, 0.3, "f64")
+    h_vals = torch.full((plan.nnz,), float("nan"), dtype=dev.dtype).pin_memory()
+    plan.assemble_host(h_ctrl, h_vals, 1.0, 0.3, prec)
     assert torch.equal(dev, h_vals)
 
 
