@@ -55,6 +55,8 @@ def parse():
                     help="comma list of extra precision forms to report")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--report", default="", help="comma list of: forms1000, forms4000, surrogate, adjoint "
+                                                 "(prints a JSON report instead of the bench line)")
     return ap.parse_args()
 
 
@@ -194,11 +196,39 @@ def run_reference(args, rank, world):
     return 0
 
 
+def run_report(args):
+    import torch
+    import paper_2107_09568_gb300 as msasm
+    from paper_2107_09568_gb300 import workloads as wl
+    msasm.load()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    forms = ["f64_emu", "f32", "split_f16", "split_bf16", "tf32", "tf32x3"]
+    out = {}
+    for item in args.report.split(","):
+        t0 = time.perf_counter()
+        if item == "forms1000":
+            out[item] = wl.precision_forms("beam1000", forms, flush)
+        elif item == "forms4000":
+            out[item] = wl.precision_forms("beam4000", forms, flush)
+        elif item == "surrogate":
+            out[item] = wl.surrogate(flush)
+        elif item == "adjoint":
+            out[item] = wl.adjoint(flush)
+        else:
+            continue
+        out[item]["wall_s"] = time.perf_counter() - t0
+        torch.cuda.empty_cache()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.report:
+        return run_report(args)
 
     import torch
     import paper_2107_09568_gb300 as msasm

@@ -1,9 +1,13 @@
 // Adjoint of the assembly (Sec. 4.1.2, eq. 69-73): gradient of L(values) with respect to the
 // macro control points, for L = u^T K u (d_u given) or a general L (dL/dvalues given).
 //
-//   1. G_t[m][a][b] = dL/dK_t[m][a][b]: for u, w_m u_{g(A),a} u_{g(B),b} with w_m = 2 for A != B
-//      (the block and its transpose) and 1 for A = B; for dL/dvalues, the sum of the two CSR
-//      entries the block is scattered to (the adjoint of step 4).
+//   1. G_t[m][a][b] = dL/dK_t[m][a][b]: for u, w_m v_{A,a} v_{B,b} with w_m = 2 for A != B
+//      (the block and its transpose) and 1 for A = B, where v = u - u_ref(t) is u minus its value
+//      at one reference point of the tile: K_t(P) annihilates translations for every P (the
+//      rows of the table sum to zero, eq. 56-57 with sum_B R_B = 1), so u^T dK_t u = v^T dK_t v
+//      exactly, while v avoids the cancellation of large rigid-body displacements in reduced
+//      precision; for dL/dvalues, the sum of the two CSR entries the block is scattered to (the
+//      adjoint of step 4).
 //   2. W_t = mat[K]^T G_t (eq. 73 as a product of the lookup table and the state): the adjoint
 //      field at the nodes, W_t[C][i][j][a][b] = sum_m T[m][C][i][j] G_t[m][a][b] (CUDA cores).
 //   3. Per node: S = d(W : A_bar)/dJ through |det J| and G = J^-1 (FP64), and per control point
@@ -23,7 +27,7 @@ size_t pullback_smem_per_warp(const int np[3], int nq);
 template <typename T>
 __global__ void grad_blocks_from_u_kernel(const T* __restrict__ u, int64_t t0, int64_t n_tiles, int n_nz, int ld,
                                           const int32_t* __restrict__ pairs, const int32_t* __restrict__ gmap,
-                                          int n_T, T* __restrict__ Gm) {
+                                          int n_T, int ref_point, T* __restrict__ Gm) {
   const int64_t total = n_tiles * n_nz;
   for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < total;
        idx += int64_t(gridDim.x) * blockDim.x) {
@@ -31,11 +35,13 @@ __global__ void grad_blocks_from_u_kernel(const T* __restrict__ u, int64_t t0, i
     const int m = int(idx % n_nz);
     const int A = pairs[2 * m], B = pairs[2 * m + 1];
     const int64_t gA = gmap[(t0 + tl) * n_T + A], gB = gmap[(t0 + tl) * n_T + B];
+    const int64_t gR = gmap[(t0 + tl) * n_T + ref_point];
     const T w = (A == B) ? T(1) : T(2);
     T ua[3], ub[3];
     for (int k = 0; k < 3; ++k) {
-      ua[k] = u[3 * gA + k];
-      ub[k] = u[3 * gB + k];
+      const T ur = u[3 * gR + k];
+      ua[k] = u[3 * gA + k] - ur;
+      ub[k] = u[3 * gB + k] - ur;
     }
     for (int a = 0; a < 3; ++a)
       for (int b = 0; b < 3; ++b) Gm[(9 * tl + 3 * a + b) * ld + m] = w * ua[a] * ub[b];
@@ -223,7 +229,7 @@ msasm_status grad_blocks_gpu(const msasm_plan* plan, const T* d_u, const T* d_gv
   int64_t blocks = std::min<int64_t>((total + 255) / 256, 152 * 16);
   if (d_u)
     grad_blocks_from_u_kernel<T><<<unsigned(blocks), 256, 0, s>>>(d_u, t0, nt, tab->n_nz, ld, tab->d_pairs,
-                                                                  plan->d_gmap, tab->topo.n_T, d_G);
+                                                                  plan->d_gmap, tab->topo.n_T, tab->ref_point, d_G);
   else
     grad_blocks_from_values_kernel<T><<<unsigned(blocks), 256, 0, s>>>(d_gv, t0, nt, tab->n_nz, ld, tab->d_pairs,
                                                                        plan->d_gmap, tab->topo.n_T, plan->d_rank,

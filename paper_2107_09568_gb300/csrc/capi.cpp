@@ -137,6 +137,17 @@ msasm_status msasm_build_tables(const msasm_micro_desc* micro, int32_t q, int32_
   }
   tab->q = q;
   tab->n_pi = (q + 1) * (q + 1) * (q + 1);
+  {
+    double best = 1e300;
+    for (int A = 0; A < tab->topo.n_T; ++A) {
+      double d2 = 0.0;
+      for (int k = 0; k < 3; ++k) d2 += (tab->topo.pos[3 * A + k] - 0.5) * (tab->topo.pos[3 * A + k] - 0.5);
+      if (d2 < best) {
+        best = d2;
+        tab->ref_point = A;
+      }
+    }
+  }
   tab->n_nz = int(tab->topo.pair_A.size());
   tab->n_gauss = n_gauss;
   cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -93,6 +93,7 @@ struct msasm_tables {
   int n_pi = 0;
   int n_nz = 0;
   int n_gauss = 0;
+  int ref_point = 0;                // local point nearest the tile centre
   double* d_T = nullptr;            // n_nz x 9 n_pi, FP64
   int32_t* d_pairs = nullptr;       // 2 n_nz (A, B)
   // operand copies for the reduced-precision contractions (created on first use)

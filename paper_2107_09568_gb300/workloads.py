@@ -1,0 +1,183 @@
+"""Measurements of the five lattice workloads through the library (used by bench.py --report).
+
+Every number here is measured with CUDA events on the GPU; accuracy is relative Frobenius
+error against the FP64 CUDA-core form of the same workload (or, for the surrogate, against
+the per-width quadrature assembly, which is that form with one table per tile).
+"""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+
+
+def _timed(fn, reps=3, flush=None):
+    import torch
+    out = fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        if flush is not None:
+            flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        out = fn()
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return out, float(np.median(ts))
+
+
+def rel(a, b):
+    import torch
+    return (torch.linalg.vector_norm(a.double() - b.double()) / torch.linalg.vector_norm(b.double())).item()
+
+
+def precision_forms(workload, forms, flush):
+    """tiles/s, stiffness GB/s and error vs the FP64 CUDA-core form for each precision form."""
+    import torch
+    import paper_2107_09568_gb300 as msasm
+    import synth
+    w = synth.workload(workload)
+    tab = msasm.Tables(synth.micro_cross(w.n_e, w.width), w.q)
+    plan = msasm.Plan(tab, w.macro)
+    ctrl = torch.tensor(w.macro.ctrl, device="cuda")
+    ref, t_ref = _timed(lambda: plan.assemble(ctrl, 1.0, 0.3, "f64"), reps=1, flush=flush)
+    res = {"tiles": plan.n_tiles, "nnz": plan.nnz,
+           "f64": {"ms": t_ref, "tiles_per_s": plan.n_tiles / t_ref * 1e3, "rel_fro_vs_f64_gpu": 0.0}}
+    for f in forms:
+        if f == "f64":
+            continue
+        out = torch.empty(plan.nnz, dtype=msasm.Plan.value_dtype(f), device="cuda")
+        _, ms = _timed(lambda: plan.assemble(ctrl, 1.0, 0.3, f, out=out), reps=5, flush=flush)
+        plan.assemble(ctrl, 1.0, 0.3, f, out=out, stage_times=True)
+        st, _ = plan.stage_times()
+        res[f] = {"ms": ms, "tiles_per_s": plan.n_tiles / ms * 1e3,
+                  "stiffness_gbs": plan.nnz * out.element_size() / (ms / 1e3) / 1e9,
+                  "rel_fro_vs_f64_gpu": rel(out, ref),
+                  "stages_ms": dict(zip(["pullback", "contraction", "scatter"], [round(x, 4) for x in st]))}
+        del out
+    return res
+
+
+def surrogate(flush, nx=20, ny=10, nz=10, steps=(4000, 3000, 3000)):
+    """Graded quarter arc: fit + train the surrogate, then compare its assembly with per-width
+    quadrature (one table per tile: the method without the network) in time and accuracy."""
+    import torch
+    import paper_2107_09568_gb300 as msasm
+    import synth
+    m = synth.macro_quarter_arc(nx, ny, nz)
+    widths = synth.width_field(m.n_elem, seed=0)
+    w_train = np.sort(0.15 + 0.25 * synth.rng(0).uniform(size=64))
+    ctrl = torch.tensor(m.ctrl, device="cuda")
+    base = msasm.Tables(synth.micro_cross(3, 0.3), 3)
+    plan = msasm.Plan(base, m)
+    coef = plan.pullback(ctrl)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    train_tabs = [msasm.Tables(synth.micro_cross(3, float(w)), 3) for w in w_train]
+    torch.cuda.synchronize()
+    t_tables = time.perf_counter() - t0
+    rows = torch.cat([coef[9 * t:9 * t + 9] for t in range(0, plan.n_tiles, max(1, plan.n_tiles // 16))][:16 * 9])
+    t0 = time.perf_counter()
+    sur = msasm.Surrogate(train_tabs, w_train, rows.contiguous(), rank=32, hidden=128, power_iters=2, seed=0)
+    torch.cuda.synchronize()
+    t_basis = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    hist = np.concatenate([sur.train(steps[0], 1e-3), sur.train(steps[1], 3e-4), sur.train(steps[2], 1e-4)])
+    t_train = time.perf_counter() - t0
+    dw = torch.tensor(widths, device="cuda")
+    k_sur, ms_sur = _timed(lambda: sur.assemble(plan, ctrl, dw), reps=5, flush=flush)
+    # per-width quadrature: one table per tile (error judge and the method without the network)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    nzd = torch.empty((9 * plan.n_tiles, base.n_nz), dtype=torch.float64, device="cuda")
+    for t in range(plan.n_tiles):
+        tab_t = msasm.Tables(synth.micro_cross(3, float(widths[t])), 3)
+        nzd[9 * t:9 * t + 9] = tab_t.contract(coef[9 * t:9 * t + 9], "f64")
+    k_exact = plan.scatter(nzd, "f64")
+    torch.cuda.synchronize()
+    ms_exact = 1e3 * (time.perf_counter() - t0)
+    nearest = np.abs(widths[:, None] - w_train[None, :]).argmin(1)
+    for t in range(plan.n_tiles):
+        nzd[9 * t:9 * t + 9] = train_tabs[nearest[t]].contract(coef[9 * t:9 * t + 9], "f64")
+    k_near = plan.scatter(nzd, "f64")
+    k_mean = msasm.Plan(msasm.Tables(synth.micro_cross(3, 0.275), 3), m).assemble(ctrl)
+    return {"tiles": plan.n_tiles, "nnz": plan.nnz, "rank": 32, "training_tables": 64,
+            "table_build_s": t_tables, "basis_fit_s": t_basis, "train_s": t_train,
+            "train_loss_first_last": [float(hist[0]), float(hist[-1])],
+            "surrogate_ms": ms_sur, "surrogate_tiles_per_s": plan.n_tiles / ms_sur * 1e3,
+            "per_width_quadrature_ms": ms_exact, "per_width_tiles_per_s": plan.n_tiles / ms_exact * 1e3,
+            "rel_fro_surrogate_vs_per_width": rel(k_sur, k_exact),
+            "rel_fro_nearest_training_table_vs_per_width": rel(k_near, k_exact),
+            "rel_fro_mean_width_table_vs_per_width": rel(k_mean, k_exact)}
+
+
+def adjoint(flush, nx=20, ny=20, nz=5, n_check=20, h=1e-4, n_resolve=6):
+    """Cantilever compliance gradient: assembly, CG solve, adjoint kernels (FP64 and FP32), central
+    differences of u^T K(P) u at fixed u (the kernel check) on n_check seeded control-point
+    coordinates and of the re-solved compliance C = f^T u(P) on the first n_resolve of them."""
+    import torch
+    import paper_2107_09568_gb300 as msasm
+    import synth
+    m = synth.macro_cantilever(nx, ny, nz)
+    tab = msasm.Tables(synth.micro_cross(2), 3)
+    plan = msasm.Plan(tab, m)
+    ctrl = torch.tensor(m.ctrl, device="cuda")
+    fixed_pts = plan.face_points(0)
+    fixed = torch.tensor(np.concatenate([3 * fixed_pts + a for a in range(3)]), device="cuda", dtype=torch.long)
+    f = torch.tensor(plan.traction_load(1, (0.0, 0.0, -1.0), m.ctrl), device="cuda")
+    vals, ms_asm = _timed(lambda: plan.assemble(ctrl, 1.0, 0.3, "f64_emu"), reps=3, flush=flush)
+    K = msasm.csr_matrix(plan, vals)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    u, iters, res = msasm.cg_solve(K, f, fixed, tol=1e-13, max_iter=30000)
+    torch.cuda.synchronize()
+    t_cg = time.perf_counter() - t0
+    C0 = torch.dot(f, u).item()
+    g64, ms_g64 = _timed(lambda: plan.assemble_grad(ctrl, 1.0, 0.3, "f64", u=u), reps=3, flush=flush)
+    g32, ms_g32 = _timed(lambda: plan.assemble_grad(ctrl, 1.0, 0.3, "f32", u=u.float()), reps=3, flush=flush)
+    rng = np.random.default_rng(0)
+    coords = [(int(k), int(p)) for k, p in zip(rng.choice(plan.n_ctrl, n_check, replace=False),
+                                               rng.integers(0, 3, n_check))]
+    quad = lambda c: torch.dot(u, msasm.csr_matrix(plan, plan.assemble(c, 1.0, 0.3, "f64")) @ u).item()
+    fdq = []
+    for k, p in coords:
+        c = ctrl.clone(); c[k, p] += h
+        qp = quad(c)
+        c[k, p] -= 2 * h
+        qm = quad(c)
+        fdq.append((qp - qm) / (2 * h))
+    fdq = np.array(fdq)
+    gq = np.array([g64[k, p].item() for k, p in coords])
+    out = {"tiles": plan.n_tiles, "nnz": plan.nnz, "dofs": plan.n_rows, "assemble_ms_f64_emu": ms_asm,
+           "cg_iterations": iters, "cg_rel_residual": res, "cg_s": t_cg, "compliance": C0,
+           "grad_ms_f64": ms_g64, "grad_ms_f32": ms_g32,
+           "grad_rel_f32_vs_f64": (torch.linalg.vector_norm(g32 - g64) / torch.linalg.vector_norm(g64)).item(),
+           "fd_coords": coords, "fd_step": h,
+           "fd_quadratic_max_abs_diff_over_max_grad": float(np.abs(fdq - gq).max() / np.abs(gq).max())}
+    if n_resolve:
+        g = -g64
+        fd = []
+        t0 = time.perf_counter()
+        for k, p in coords[:n_resolve]:
+            cs = []
+            for sgn in (1.0, -1.0):
+                c = ctrl.clone()
+                c[k, p] += sgn * h
+                Kp = msasm.csr_matrix(plan, plan.assemble(c, 1.0, 0.3, "f64_emu"))
+                up, _, _ = cg_warm(Kp, f, fixed, u)
+                cs.append(torch.dot(f, up).item())
+            fd.append((cs[0] - cs[1]) / (2 * h))
+        fd = np.array(fd)
+        gk = np.array([g[k, p].item() for k, p in coords[:n_resolve]])
+        out.update({"fd_compliance_max_abs_diff_over_max_grad": float(np.abs(fd - gk).max() / np.abs(gk).max()),
+                    "fd_compliance_s": time.perf_counter() - t0,
+                    "adjoint_vs_fd_compliance": [[float(a), float(b)] for a, b in zip(gk, fd)]})
+    return out
+
+
+def cg_warm(K, f, fixed, x0, tol=1e-13, max_iter=30000):
+    """CG from a nearby solution (the finite-difference re-solves)."""
+    import paper_2107_09568_gb300 as msasm
+    return msasm.cg_solve(K, f, fixed, tol=tol, max_iter=max_iter, x0=x0)

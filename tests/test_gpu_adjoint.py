@@ -99,16 +99,18 @@ def compliance(plan, ctrl, f, fixed, tol=1e-13):
 
 def test_cantilever_compliance_gradient_fd_and_oracle():
     """Compliance C = f^T u, u = K^-1 f (clamped x = 0 face, unit traction -z on x = max):
-    dC/dP = -u^T (dK/dP) u, checked by central differences (step 1e-6, re-solved) on 20 seeded
-    control-point coordinates and by the oracle's complex step of u^T K u."""
+    dC/dP = -u^T (dK/dP) u, checked by central differences (step 1e-4, re-solved) on 20 seeded
+    control-point coordinates and by the oracle's complex step of u^T K u.  The step balances the
+    O(h^2) truncation against the CG rounding floor (true residual ~5e-12) divided by h: on this
+    problem h = 1e-6, 1e-5, 1e-4, 1e-3 give relative differences of about 6e-6, 1e-6, 1e-7, 8e-7."""
     m, micro, tab, plan, fixed, f = cantilever_setup()
     ctrl = torch.tensor(m.ctrl, device="cuda")
     C0, u, res = compliance(plan, ctrl, f, fixed)
-    assert res < 1e-10          # true residual; the recurrence is driven below 1e-13
+    assert res < 1e-10          # true residual at its rounding floor (about 5e-12 here)
     g = -plan.assemble_grad(ctrl, 1.0, 0.3, "f64", u=u)
     rng = np.random.default_rng(0)
     coords = [(int(k), int(p)) for k, p in zip(rng.choice(plan.n_ctrl, 20, replace=False), rng.integers(0, 3, 20))]
-    h = 1e-6
+    h = 1e-4
     fd = []
     for k, p in coords:
         c = ctrl.clone(); c[k, p] += h
@@ -120,7 +122,20 @@ def test_cantilever_compliance_gradient_fd_and_oracle():
     gk = np.array([g[k, p].item() for k, p in coords])
     scale = np.abs(gk).max()
     print("compliance", C0, "max |fd - adj| / max|g|", np.abs(fd - gk).max() / scale)
-    assert np.abs(fd - gk).max() <= 2e-5 * scale   # FD limited by the CG solves (true residual ~1e-11)
+    assert np.abs(fd - gk).max() <= 2e-6 * scale
     prob = Problem(micro, m, 3, table=otables.build_table(ReferenceTile(micro), 3), structure=False)
     cs = -oadj.gradient_complex_step(prob, u.cpu().numpy(), coords)
     assert np.abs(cs - gk).max() <= 1e-10 * scale
+
+
+def test_cantilever_f32_adjoint_on_the_solved_state():
+    """The FP32 adjoint on a bending state, whose large rigid-body displacement the translation-free
+    blocks v = u - u_ref(t) remove before the reduced-precision contraction."""
+    m, micro, tab, plan, fixed, f = cantilever_setup()
+    ctrl = torch.tensor(m.ctrl, device="cuda")
+    _, u, _ = compliance(plan, ctrl, f, fixed)
+    g64 = plan.assemble_grad(ctrl, 1.0, 0.3, "f64", u=u)
+    g32 = plan.assemble_grad(ctrl, 1.0, 0.3, "f32", u=u.float())
+    err = (torch.linalg.vector_norm(g32 - g64) / torch.linalg.vector_norm(g64)).item()
+    print("f32 adjoint on the cantilever state: rel err", err)
+    assert err <= 1e-3
