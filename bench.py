@@ -46,7 +46,7 @@ WORKLOAD_TEXT = {
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="f64_emu")
@@ -68,8 +68,9 @@ def dist_env():
 
 
 class Clocks:
-    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+    """nvidia-smi sampling of SM clocks and throttle reasons; only the samples taken inside the
+    timed region (mark_begin .. mark_end, host wall clock) are kept."""
+    Q = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
@@ -77,12 +78,27 @@ class Clocks:
         self.gpu = gpu_index
         self.proc = None
         self.path = os.path.join("/tmp", f"msasm_clocks_{os.getpid()}.csv")
+        self.t_begin = self.t_end = None
+
+    def mark_begin(self):
+        self.t_begin = time.time()
+
+    def mark_end(self):
+        self.t_end = time.time()
+
+    def wait_first_sample(self, timeout=3.0):
+        """Block until nvidia-smi has written a line (it takes a moment to start)."""
+        t0 = time.time()
+        while self.proc is not None and time.time() - t0 < timeout:
+            if os.path.exists(self.path) and os.path.getsize(self.path) > 0:
+                return
+            time.sleep(0.02)
 
     def start(self):
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -98,20 +114,49 @@ class Clocks:
         self.f.close()
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        n_all, kept, other = 0, [], []
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
+            n_all += 1
             try:
-                sm.append(float(parts[1])); smax.append(float(parts[2]))
+                whole, frac = (parts[0].split(".") + ["0"])[:2]
+                ts = time.mktime(time.strptime(whole, "%Y/%m/%d %H:%M:%S")) + float("0." + frac)
+            except (ValueError, IndexError):
+                ts = None
+            try:
+                rec = (float(parts[1]), float(parts[2]), parts[5:9])
             except ValueError:
                 continue
-            for n, v in zip(names, parts[5:9]):
+            inside = ts is not None and self.t_begin is not None and self.t_begin - 0.05 <= ts <= self.t_end + 0.05
+            (kept if inside else other).append(rec)
+        window = "timed region"
+        if not kept:                       # no sample inside a very short region: report the nearest ones
+            kept, window = other[-2:], "just before and after the timed region"
+        for f_sm, f_max, flags in kept:
+            sm.append(f_sm); smax.append(f_max)
+            for n, v in zip(names, flags):
                 if v.lower() == "active":
                     reasons.add(n)
         os.unlink(self.path)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "samples": len(sm), "reasons": sorted(reasons)}
+                "samples": len(sm), "samples_total": n_all, "window": window, "reasons": sorted(reasons)}
+
+
+def max_over_ranks(x, dist, device="cpu"):
+    """The largest of every rank's x (the job ends when its slowest rank does)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, steps, max_ms):
+    """Units all ranks processed per second of the slowest rank (weak scaling: fixed units per rank)."""
+    return units_per_rank * world * steps / (max_ms / 1e3)
 
 
 def peaks():
@@ -259,10 +304,12 @@ def main():
     torch.cuda.synchronize()
 
     clocks = Clocks(local)
+    clocks.start()
+    clocks.wait_first_sample()
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks.start()
+    clocks.mark_begin()
     step_ms, stage_ms, launches = [], np.zeros(3), 0
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     t_wall = time.perf_counter()
@@ -277,18 +324,37 @@ def main():
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
+    clocks.mark_end()
     wall = time.perf_counter() - t_wall
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = float(sum(step_ms))
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    n_tiles = plan.n_tiles * world
-    value = n_tiles * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(step_ms), dist, "cuda")
+    value = whole_job_rate(plan.n_tiles, world, args.steps, total_ms)
     vbytes = 8 if prec in ("f64", "f64_emu") else 4
     stiff_gbs = plan.nnz * vbytes * world * args.steps / (total_ms / 1e3) / 1e9
+
+    # end to end through the public C ABI with host buffers (copies inside the timed region), on
+    # every rank; the job's rate is set by the slowest rank
+    e2e = None
+    if not args.no_e2e:
+        h_ctrl = torch.tensor(w.macro.ctrl, dtype=torch.float64).pin_memory()
+        h_vals = torch.empty(plan.nnz, dtype=msasm.Plan.value_dtype(prec)).pin_memory()
+        plan.assemble_host(h_ctrl, h_vals, 1.0, 0.3, prec)
+        e_steps = max(2, min(args.steps, 5))
+        if dist is not None:
+            dist.barrier()
+        e_ms = []
+        for _ in range(e_steps):
+            flush.zero_(); torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            plan.assemble_host(h_ctrl, h_vals, 1.0, 0.3, prec)
+            e_ms.append(1e3 * (time.perf_counter() - t0))
+        em = max_over_ranks(sum(e_ms), dist, "cuda") / e_steps
+        e2e = {"value": whole_job_rate(plan.n_tiles, world, 1, em), "unit": "tiles/s", "ms_per_step": em,
+               "h2d_bytes_per_step": int(h_ctrl.numel() * 8) * world,
+               "d2h_bytes_per_step": int(plan.nnz * vbytes) * world,
+               "api": "msasm_assemble_host (pinned host buffers)"}
+        del h_vals
 
     if rank != 0:
         if dist is not None:
@@ -312,15 +378,20 @@ def main():
                 "peak_source": "derived: 152 SMs x lanes x 2 flop x 2.07 GHz (DESIGN.md)",
                 "algorithmic": f"2*n_nz*9n_pi*9m = {flops:.4g} flop per launch"}
     elif names[dom] == "contraction":
-        peak = pk["bf16_tflops_sustained"] * TC_PEAK_RATIO.get(prec, 1.0)
+        # the form's own peak: the tensor pipe's measured rate divided by the products one
+        # multiply-add of the emulated type costs (28 BF16 products per FP64-accurate one, 3 per
+        # split-FP32 one, 1 for TF32)
+        n_prod = TC_PRODUCTS.get(prec, 1)
+        tc_peak = pk["bf16_tflops_sustained"] * TC_PEAK_RATIO.get(prec, 1.0)
+        peak = tc_peak / n_prod
         ach = flops / (stage_avg[1] / 1e3) / 1e12
-        hw = ach * TC_PRODUCTS.get(prec, 1)
         roof = {"kernel": "contract_emu_kernel" if prec == "f64_emu" else "contract_tc_kernel", "bound": "tensor",
                 "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
-                "peak_source": f"{pk_kind} bf16 sustained" + (" x 1.1/2.25 (tf32 nominal ratio)"
-                                                                if "tf32" in prec else ""),
-                "algorithmic": f"2*n_nz*9n_pi*9m = {flops:.4g} flop per launch (FP64-equivalent)",
-                "hardware_products": TC_PRODUCTS.get(prec, 1), "hardware_tflops": hw, "hardware_frac": hw / peak}
+                "peak_source": f"{pk_kind} bf16 sustained {pk['bf16_tflops_sustained']}"
+                               + (" x 1.1/2.25 (tf32 nominal ratio)" if "tf32" in prec else "")
+                               + f" / {n_prod} products per {prec} multiply-add",
+                "algorithmic": f"2*n_nz*9n_pi*9m = {flops:.4g} flop per launch",
+                "hardware_products": n_prod, "hardware_tflops": ach * n_prod, "tensor_pipe_peak": tc_peak}
     else:
         byts = scatter_bytes if dom == 2 else pull_bytes
         ach = byts / (stage_avg[dom] / 1e3) / 1e9
@@ -360,24 +431,6 @@ def main():
     main_err = None
     if prec != "f64":
         main_err = (torch.linalg.vector_norm(out.double() - ref64) / torch.linalg.vector_norm(ref64)).item()
-
-    # end to end through the public C ABI with host buffers (copies inside the timed region)
-    e2e = None
-    if not args.no_e2e:
-        h_ctrl = torch.tensor(w.macro.ctrl, dtype=torch.float64).pin_memory()
-        h_vals = torch.empty(plan.nnz, dtype=msasm.Plan.value_dtype(prec)).pin_memory()
-        plan.assemble_host(h_ctrl, h_vals, 1.0, 0.3, prec)
-        e_ms = []
-        for _ in range(max(2, min(args.steps, 5))):
-            flush.zero_(); torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            plan.assemble_host(h_ctrl, h_vals, 1.0, 0.3, prec)
-            e_ms.append(1e3 * (time.perf_counter() - t0))
-        em = statistics.mean(e_ms)
-        e2e = {"value": plan.n_tiles / (em / 1e3), "unit": "tiles/s", "ms_per_step": em,
-               "h2d_bytes_per_step": int(h_ctrl.numel() * 8), "d2h_bytes_per_step": int(plan.nnz * vbytes),
-               "api": "msasm_assemble_host (pinned host buffers)"}
-        del h_vals
 
     cpu = None
     if not args.no_cpu:

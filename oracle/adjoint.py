@@ -17,14 +17,21 @@ import numpy as np
 from .assembly import coefficient_block
 
 
-def tile_quadratic(prob, t, u_pts, ctrl):
-    """u_t^T K_t u_t for tile t, with the tile's lookup-form blocks (eq. 58); complex-safe."""
+def tile_quadratic(prob, t, u_pts, ctrl, relative=False):
+    """u_t^T K_t u_t for tile t, with the tile's lookup-form blocks (eq. 58); complex-safe.
+
+    relative=True evaluates the same number as v_t^T K_t v_t with v_t = u_t - u_t[local point 0]:
+    K_t annihilates translations for any control net (the basis functions sum to one, so their
+    derivatives, and every row of the table, sum to zero; eq. 56-57), and the shifted form avoids
+    the cancellation of a large rigid-body displacement in floating point."""
     n_nz = prob.T.shape[0]
     Kt = (prob.T.reshape(n_nz, -1) @ coefficient_block(prob.mmap, t, prob.q, prob.lam, prob.mu, ctrl)
           ).reshape(n_nz, 3, 3)
     P = prob.tile.pairs
     g = prob.gmap[t]
     ua, ub = u_pts[g[P[:, 0]]], u_pts[g[P[:, 1]]]
+    if relative:
+        ua, ub = ua - u_pts[g[0]], ub - u_pts[g[0]]
     w = np.where(P[:, 0] == P[:, 1], 1.0, 2.0)             # upper block and its transpose
     return np.einsum("m,ma,mab,mb->", w, ua, Kt, ub)
 
@@ -57,15 +64,16 @@ def tiles_of_control_point(prob, k):
     return out
 
 
-def gradient_complex_step(prob, u, coords, h=1e-30):
-    """dQ/dP for the listed (control point, component) pairs by complex step."""
+def gradient_complex_step(prob, u, coords, h=1e-30, relative=False):
+    """dQ/dP for the listed (control point, component) pairs by complex step (relative: see
+    tile_quadratic)."""
     ctrl0 = prob.mmap.macro.ctrl
     u_pts = np.asarray(u).reshape(-1, 3)
     out = []
     for k, p in coords:
         c = ctrl0.astype(np.complex128).copy()
         c[k, p] += 1j * h
-        q = sum(tile_quadratic(prob, t, u_pts, c) for t in tiles_of_control_point(prob, k))
+        q = sum(tile_quadratic(prob, t, u_pts, c, relative) for t in tiles_of_control_point(prob, k))
         out.append(np.imag(q) / h)
     return np.array(out)
 

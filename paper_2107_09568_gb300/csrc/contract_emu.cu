@@ -142,13 +142,22 @@ __global__ void __launch_bounds__(192, 1)
       const uint32_t st = base + s * EMU_STAGE_BYTES;
 #pragma unroll
       for (int i = 0; i < EMU_S; ++i) {
+        // slice i of A stays in the collector buffer for its 7 - i products
         const uint64_t a = sw32_desc(st + i * EMU_A_SLICE);
 #pragma unroll
         for (int j = 0; j + i < EMU_S; ++j) {
           const int acc = (i + j < EMU_ACC - 1) ? i + j : EMU_ACC - 1;
           const uint64_t b = sw32_desc(st + EMU_A_BYTES + j * EMU_B_SLICE);
           const uint32_t accumulate = (started >> acc) & 1u;
-          mma_f16(tmem + uint32_t(acc * EMU_BN), a, b, idesc, accumulate);
+          const uint32_t d = tmem + uint32_t(acc * EMU_BN);
+          if (i + j == EMU_S - 1 && j == 0)
+            mma_f16(d, a, b, idesc, accumulate);                                   // a single product
+          else if (j == 0)
+            mma_f16_collect<CollectorA::FILL>(d, a, b, idesc, accumulate);
+          else if (i + j == EMU_S - 1)
+            mma_f16_collect<CollectorA::LASTUSE>(d, a, b, idesc, accumulate);
+          else
+            mma_f16_collect<CollectorA::USE>(d, a, b, idesc, accumulate);
           started |= 1u << acc;
         }
       }

@@ -139,15 +139,18 @@ __global__ void __launch_bounds__(192, 1)
       for (int j = 0; j < ksteps; ++j) {
         const uint64_t dk = uint64_t(2 * j);                    // +32 bytes of k, in 16-byte units
         const uint32_t first = (kb == 0 && j == 0) ? 0u : 1u;
+        // hi.hi and hi.lo share the A tile: it stays in the collector buffer for the second
         if (tf) {
-          mma_tf32(acc0, a_hi + dk, b_hi + dk, idesc, first);
           if (with_lo) {
-            mma_tf32(acc1, a_hi + dk, b_lo + dk, idesc, first);
+            mma_tf32_collect<CollectorA::FILL>(acc0, a_hi + dk, b_hi + dk, idesc, first);
+            mma_tf32_collect<CollectorA::LASTUSE>(acc1, a_hi + dk, b_lo + dk, idesc, first);
             mma_tf32(acc1, a_lo + dk, b_hi + dk, idesc, 1u);
+          } else {
+            mma_tf32(acc0, a_hi + dk, b_hi + dk, idesc, first);
           }
         } else {
-          mma_f16(acc0, a_hi + dk, b_hi + dk, idesc, first);
-          mma_f16(acc1, a_hi + dk, b_lo + dk, idesc, first);
+          mma_f16_collect<CollectorA::FILL>(acc0, a_hi + dk, b_hi + dk, idesc, first);
+          mma_f16_collect<CollectorA::LASTUSE>(acc1, a_hi + dk, b_lo + dk, idesc, first);
           mma_f16(acc1, a_lo + dk, b_hi + dk, idesc, 1u);
         }
       }

@@ -69,6 +69,32 @@ __device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t a, uint64_t b,
       "l"(a), "l"(b), "r"(idesc), "r"(acc)
       : "memory");
 }
+// The same MMAs with the A operand kept in the tensor core's collector buffer: FILL reads A from
+// shared memory and keeps it, USE and LASTUSE read it from the buffer (same descriptor as the
+// FILL), LASTUSE releasing it.  Consecutive products of one A tile with several B tiles then read
+// only B from shared memory.
+enum class CollectorA { FILL, USE, LASTUSE };
+#define MSASM_MMA_COLLECT(KIND, OPNAME)                                                             \
+  asm volatile(                                                                                    \
+      "{\n\t.reg .pred p;\n\t"                                                                    \
+      "setp.ne.b32 p, %4, 0;\n\t"                                                                 \
+      "tcgen05.mma.cta_group::1.kind::" KIND ".collector::a::" OPNAME " [%0], %1, %2, %3, p;\n\t}" \
+      ::"r"(tmem_d), "l"(a), "l"(b), "r"(idesc), "r"(acc)                                          \
+      : "memory")
+template <CollectorA OP>
+__device__ __forceinline__ void mma_f16_collect(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  if constexpr (OP == CollectorA::FILL) MSASM_MMA_COLLECT("f16", "fill");
+  else if constexpr (OP == CollectorA::USE) MSASM_MMA_COLLECT("f16", "use");
+  else MSASM_MMA_COLLECT("f16", "lastuse");
+}
+template <CollectorA OP>
+__device__ __forceinline__ void mma_tf32_collect(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                                 uint32_t acc) {
+  if constexpr (OP == CollectorA::FILL) MSASM_MMA_COLLECT("tf32", "fill");
+  else if constexpr (OP == CollectorA::USE) MSASM_MMA_COLLECT("tf32", "use");
+  else MSASM_MMA_COLLECT("tf32", "lastuse");
+}
+#undef MSASM_MMA_COLLECT
 __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"

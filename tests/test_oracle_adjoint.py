@@ -35,6 +35,19 @@ def test_complex_step_matches_central_differences(prob):
     np.testing.assert_allclose(cs, fd, rtol=1e-6, atol=1e-8 * np.abs(cs).max())
 
 
+def test_relative_form_equals_plain_form_and_removes_rigid_motion(prob):
+    """The shifted per-tile form v^T K v (v = u - u[local point 0]) is the same function of P: on a
+    random u both complex steps agree to rounding, and adding a large translation to u changes the
+    shifted form's result by rounding only (K annihilates translations)."""
+    u = np.random.default_rng(4).normal(size=(prob.n_points, 3))
+    coords = [(3, 0), (17, 1), (40, 2), (63, 0)]
+    a = adjoint.gradient_complex_step(prob, u, coords)
+    b = adjoint.gradient_complex_step(prob, u, coords, relative=True)
+    np.testing.assert_allclose(a, b, rtol=0, atol=1e-12 * np.abs(a).max())
+    c = adjoint.gradient_complex_step(prob, u + np.array([1e4, -3e4, 2e4]), coords, relative=True)
+    np.testing.assert_allclose(c, b, rtol=0, atol=1e-12 * np.abs(b).max())
+
+
 def test_gradient_homogeneity_and_translation(prob):
     """K(L P) = L K(P) exactly (J -> L J, |det J| -> L^3, G -> G/L), so by Euler's theorem
     sum_a P_a . dQ/dP_a = Q; and translating the net leaves K unchanged, so sum_a dQ/dP_a = 0."""
