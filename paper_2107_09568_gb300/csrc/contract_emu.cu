@@ -19,13 +19,18 @@
 // X 2^(e_m + e_n - 49) as an FP64 bit pattern rounded to nearest even, with integer instructions
 // only: the FP64 pipe, about 1/64 of the FP32 rate per SM on GB300, is not used at all.
 //
-// CTA tile 128 (m) x 96 (n); per 16-element k block, one 3-D TMA box brings all 7 slices of each
-// operand (32-byte swizzle) into a 4-stage ring; one lane issues the 28 MMAs (M=128, N=96, K=16)
-// into 5 TMEM accumulators of 96 columns; 4 warps read them back.
+// Persistent kernel, one CTA per SM looping over 128 (m) x 96 (n) output tiles.  Per 16-element
+// k block, one 3-D TMA box brings all 7 slices of each operand (32-byte swizzle) into a 4-stage
+// ring that runs on across tiles; one lane issues the 28 MMAs (M=128, N=96, K=16, the A slice kept
+// in the collector buffer across its products) into 5 TMEM accumulators of 96 columns (480 of the
+// 512).  Eight epilogue warps (two per TMEM lane quarter, 48 columns each) drain the accumulators
+// into exact int64 sums in registers and release TMEM at once, so the MMAs of the next tile run
+// while they round and store the previous one.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "common.h"
@@ -81,7 +86,30 @@ __device__ __forceinline__ double ldexp_i64_rn(long long x, int e) {
   return __longlong_as_double((long long)(sign | ((unsigned long long)biased << 52) | (mant & ((1ull << 52) - 1))));
 }
 
-__global__ void __launch_bounds__(192, 1)
+constexpr int EMU_EPI_WARPS = 8;                          // two per TMEM lane quarter
+constexpr int EMU_THREADS = 64 + 32 * EMU_EPI_WARPS;      // producer warp, MMA warp, epilogue warps
+constexpr int EMU_EPI_COLS = EMU_BN / 2;                  // columns of one epilogue warp
+
+// Nearest int64 to a float (ties to even) by integer operations on its bits (|y| < 2^62).
+__device__ __forceinline__ long long f32_to_i64_rn(float y) {
+  const uint32_t b = __float_as_uint(y);
+  const uint32_t mag = b & 0x7fffffffu;
+  if (mag < 0x3f000000u) return 0;                         // |y| < 0.5 (and zeros, subnormals)
+  const int ex = int(mag >> 23) - 150;                     // |y| = m 2^ex, m = 24-bit significand
+  const unsigned long long m = (mag & 0x7fffffu) | 0x800000u;
+  unsigned long long r;
+  if (ex >= 0) {
+    r = m << ex;
+  } else {
+    const int sh = -ex;                                    // 1..24
+    r = m >> sh;
+    const unsigned long long rem = m & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (r & 1ull))) ++r;
+  }
+  return (b >> 31) ? -(long long)r : (long long)r;
+}
+
+__global__ void __launch_bounds__(EMU_THREADS, 1)
     contract_emu_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, EmuParams p) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -90,18 +118,21 @@ __global__ void __launch_bounds__(192, 1)
   const uint32_t bar0 = base + EMU_STAGES * EMU_STAGE_BYTES;
   auto full_bar = [&](int s) { return bar0 + 8u * s; };
   auto empty_bar = [&](int s) { return bar0 + 8u * (EMU_STAGES + s); };
-  const uint32_t accum_bar = bar0 + 8u * (2 * EMU_STAGES);
+  const uint32_t accum_full = bar0 + 8u * (2 * EMU_STAGES);      // MMAs of a tile done
+  const uint32_t tmem_empty = bar0 + 8u * (2 * EMU_STAGES + 1);  // accumulators drained
   uint32_t* tmem_slot =
-      reinterpret_cast<uint32_t*>(gen_base + EMU_STAGES * EMU_STAGE_BYTES + 8 * (2 * EMU_STAGES + 1));
+      reinterpret_cast<uint32_t*>(gen_base + EMU_STAGES * EMU_STAGE_BYTES + 8 * (2 * EMU_STAGES + 2));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n0 = blockIdx.x * EMU_BN, m0 = blockIdx.y * EMU_BM;
+  const int n_nt = (p.N + EMU_BN - 1) / EMU_BN, n_mt = (p.M + EMU_BM - 1) / EMU_BM;
+  const long long total = (long long)n_nt * n_mt;               // tile t: m tile t / n_nt, n tile t % n_nt
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < EMU_STAGES; ++s) {
       mbar_init(full_bar(s), 1);
       mbar_init(empty_bar(s), 1);
     }
-    mbar_init(accum_bar, 1);
+    mbar_init(accum_full, 1);
+    mbar_init(tmem_empty, EMU_EPI_WARPS);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -116,91 +147,120 @@ __global__ void __launch_bounds__(192, 1)
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0 && lane == 0) {
-    // ---------------- TMA producer: both operands' 7 slices per k block
-    int issued = 0;
+    // ---------------- TMA producer: both operands' 7 slices per k block, ring across tiles
+    uint32_t g = 0;
     bool ok = true;
-    for (int kb = 0; kb < p.kblocks && ok; ++kb) {
-      const int s = kb % EMU_STAGES, it = kb / EMU_STAGES;
-      if (it > 0) ok = mbar_wait(empty_bar(s), (it - 1) & 1, p.err);
-      if (!ok) break;
-      const uint32_t st = base + s * EMU_STAGE_BYTES;
-      mbar_expect_tx(full_bar(s), EMU_STAGE_BYTES);
-      tma_load_3d(st, &tmA, kb * EMU_KB, m0, 0, full_bar(s));
-      tma_load_3d(st + EMU_A_BYTES, &tmB, kb * EMU_KB, n0, 0, full_bar(s));
-      ++issued;
+    for (long long t = blockIdx.x; t < total && ok; t += gridDim.x) {
+      const int m0 = int(t / n_nt) * EMU_BM, n0 = int(t % n_nt) * EMU_BN;
+      for (int kb = 0; kb < p.kblocks; ++kb, ++g) {
+        const int s = int(g % EMU_STAGES);
+        const uint32_t it = g / EMU_STAGES;
+        if (it > 0 && !mbar_wait_or_abort(empty_bar(s), (it - 1) & 1, p.err)) {
+          ok = false;
+          break;
+        }
+        const uint32_t st = base + s * EMU_STAGE_BYTES;
+        mbar_expect_tx(full_bar(s), EMU_STAGE_BYTES);
+        tma_load_3d(st, &tmA, kb * EMU_KB, m0, 0, full_bar(s));
+        tma_load_3d(st + EMU_A_BYTES, &tmB, kb * EMU_KB, n0, 0, full_bar(s));
+      }
     }
-    for (int kb = (issued > EMU_STAGES ? issued - EMU_STAGES : 0); kb < issued; ++kb)
-      mbar_wait(full_bar(kb % EMU_STAGES), (kb / EMU_STAGES) & 1, p.err);
+    // every issued copy has landed before the CTA can exit (bounded)
+    for (uint32_t q = (g > uint32_t(EMU_STAGES) ? g - EMU_STAGES : 0u); q < g; ++q)
+      mbar_wait(full_bar(int(q % EMU_STAGES)), (q / EMU_STAGES) & 1, p.err);
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer: 28 products per k block, grouped by i + j
     const uint32_t idesc = instr_desc(1u, EMU_BM, EMU_BN);        // BF16 x BF16 -> F32
-    uint32_t started = 0;                                         // accumulators already written
-    for (int kb = 0; kb < p.kblocks; ++kb) {
-      const int s = kb % EMU_STAGES, it = kb / EMU_STAGES;
-      if (!mbar_wait(full_bar(s), it & 1, p.err)) break;
-      tc_fence_after();
-      const uint32_t st = base + s * EMU_STAGE_BYTES;
-#pragma unroll
-      for (int i = 0; i < EMU_S; ++i) {
-        // slice i of A stays in the collector buffer for its 7 - i products
-        const uint64_t a = sw32_desc(st + i * EMU_A_SLICE);
-#pragma unroll
-        for (int j = 0; j + i < EMU_S; ++j) {
-          const int acc = (i + j < EMU_ACC - 1) ? i + j : EMU_ACC - 1;
-          const uint64_t b = sw32_desc(st + EMU_A_BYTES + j * EMU_B_SLICE);
-          const uint32_t accumulate = (started >> acc) & 1u;
-          const uint32_t d = tmem + uint32_t(acc * EMU_BN);
-          if (i + j == EMU_S - 1 && j == 0)
-            mma_f16(d, a, b, idesc, accumulate);                                   // a single product
-          else if (j == 0)
-            mma_f16_collect<CollectorA::FILL>(d, a, b, idesc, accumulate);
-          else if (i + j == EMU_S - 1)
-            mma_f16_collect<CollectorA::LASTUSE>(d, a, b, idesc, accumulate);
-          else
-            mma_f16_collect<CollectorA::USE>(d, a, b, idesc, accumulate);
-          started |= 1u << acc;
-        }
+    uint32_t g = 0, i_tile = 0;
+    bool ok = true;
+    for (long long t = blockIdx.x; t < total && ok; t += gridDim.x, ++i_tile) {
+      if (i_tile > 0) {                                           // the previous tile is drained
+        if (!mbar_wait_or_abort(tmem_empty, (i_tile - 1) & 1, p.err)) break;
+        tc_fence_after();
       }
-      mma_commit(empty_bar(s));
-    }
-    mma_commit(accum_bar);
-    mbar_wait(accum_bar, 0, p.err);
-  } else if (warp >= 2) {
-    // ---------------- epilogue: five accumulators -> FP64
-    const int q = warp & 3;
-    const bool ok = mbar_wait(accum_bar, 0, p.err);
-    tc_fence_after();
-    if (ok) {
-      const int m = m0 + 32 * q + lane;
-      const int em = (m < p.M) ? p.exp_m[m] - 49 : 0;     // D = X 2^(e_m + e_n - 14 - 35)
-      const uint32_t lane_off = uint32_t(32 * q) << 16;
-      for (int c0 = 0; c0 < EMU_BN; c0 += 16) {
-        if (n0 + c0 >= p.N) break;
-        float a0[16], a1[16], a2[16], a3[16], a4[16];
-        tmem_ld16(tmem + lane_off + 0 * EMU_BN + c0, a0);
-        tmem_ld16(tmem + lane_off + 1 * EMU_BN + c0, a1);
-        tmem_ld16(tmem + lane_off + 2 * EMU_BN + c0, a2);
-        tmem_ld16(tmem + lane_off + 3 * EMU_BN + c0, a3);
-        tmem_ld16(tmem + lane_off + 4 * EMU_BN + c0, a4);
-        if (m < p.M) {
+      uint32_t started = 0;                                       // accumulators already written
+      for (int kb = 0; kb < p.kblocks; ++kb, ++g) {
+        const int s = int(g % EMU_STAGES);
+        const uint32_t it = g / EMU_STAGES;
+        if (!mbar_wait_or_abort(full_bar(s), it & 1, p.err)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t st = base + s * EMU_STAGE_BYTES;
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int n = n0 + c0 + j;
-            if (n < p.N) {
-              // exact integers: acc0, acc1 2^7, acc2 2^14, acc3 2^21 (all below 2^24 in magnitude)
-              const long long x = ((long long)__float2int_rn(a0[j]) << 35) +
-                                  ((long long)__float2int_rn(a1[j] * 128.0f) << 28) +
-                                  ((long long)__float2int_rn(a2[j] * 16384.0f) << 21) +
-                                  ((long long)__float2int_rn(a3[j] * 2097152.0f) << 14) +
-                                  __float2ll_rn(a4[j] * 34359738368.0f);
-              p.out[size_t(n) * p.ld + m] = ldexp_i64_rn(x, em + p.exp_n[n]);
-            }
+        for (int i = 0; i < EMU_S; ++i) {
+          // slice i of A stays in the collector buffer for its 7 - i products
+          const uint64_t a = sw32_desc(st + i * EMU_A_SLICE);
+#pragma unroll
+          for (int j = 0; j + i < EMU_S; ++j) {
+            const int acc = (i + j < EMU_ACC - 1) ? i + j : EMU_ACC - 1;
+            const uint64_t b = sw32_desc(st + EMU_A_BYTES + j * EMU_B_SLICE);
+            const uint32_t accumulate = (started >> acc) & 1u;
+            const uint32_t d = tmem + uint32_t(acc * EMU_BN);
+            if (i + j == EMU_S - 1 && j == 0)
+              mma_f16(d, a, b, idesc, accumulate);                                   // a single product
+            else if (j == 0)
+              mma_f16_collect<CollectorA::FILL>(d, a, b, idesc, accumulate);
+            else if (i + j == EMU_S - 1)
+              mma_f16_collect<CollectorA::LASTUSE>(d, a, b, idesc, accumulate);
+            else
+              mma_f16_collect<CollectorA::USE>(d, a, b, idesc, accumulate);
+            started |= 1u << acc;
           }
         }
+        mma_commit(empty_bar(s));                                 // stage reusable when these finish
+      }
+      mma_commit(accum_full);                                     // this tile's accumulators are final
+    }
+    if (i_tile > 0) mbar_wait(accum_full, (i_tile - 1) & 1, p.err);   // nothing in flight at exit
+  } else if (warp >= 2) {
+    // ---------------- epilogue: drain five accumulators into exact int64 sums, release, round, store
+    const int q = warp & 3;                                       // TMEM lane quarter of this warp
+    const int h = (warp - 2) >> 2;                                // column half
+    const uint32_t lane_off = uint32_t(32 * q) << 16;
+    uint32_t i_tile = 0;
+    for (long long t = blockIdx.x; t < total; t += gridDim.x, ++i_tile) {
+      if (!mbar_wait_or_abort(accum_full, i_tile & 1, p.err)) break;
+      tc_fence_after();
+      const int m0 = int(t / n_nt) * EMU_BM, n0 = int(t % n_nt) * EMU_BN + h * EMU_EPI_COLS;
+      long long X[EMU_EPI_COLS];
+#pragma unroll
+      for (int c = 0; c < EMU_EPI_COLS / 8; ++c) {
+        uint32_t v[EMU_ACC][8];
+#pragma unroll
+        for (int a = 0; a < EMU_ACC; ++a)
+          tmem_ld8_nowait(tmem + lane_off + uint32_t(a * EMU_BN + h * EMU_EPI_COLS + 8 * c), v[a]);
+        tmem_wait_ld();
+#pragma unroll
+        for (int a = 0; a < EMU_ACC; ++a)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) asm volatile("" : "+r"(v[a][j]));   // uses stay after the wait
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          // exact integers: acc0, acc1 2^7, acc2 2^14, acc3 2^21 (all below 2^24 in magnitude)
+          X[8 * c + j] = ((long long)__float2int_rn(__uint_as_float(v[0][j])) << 35) +
+                         ((long long)__float2int_rn(__uint_as_float(v[1][j]) * 128.0f) << 28) +
+                         ((long long)__float2int_rn(__uint_as_float(v[2][j]) * 16384.0f) << 21) +
+                         ((long long)__float2int_rn(__uint_as_float(v[3][j]) * 2097152.0f) << 14) +
+                         f32_to_i64_rn(__uint_as_float(v[4][j]) * 34359738368.0f);
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tmem_empty);                     // the MMAs of the next tile may start
+      const int m = m0 + 32 * q + lane;
+      if (m < p.M) {
+        const int em = p.exp_m[m] - 49;                           // D = X 2^(e_m + e_n - 14 - 35)
+#pragma unroll
+        for (int j = 0; j < EMU_EPI_COLS; ++j) {
+          const int n = n0 + j;
+          if (n < p.N) p.out[size_t(n) * p.ld + m] = ldexp_i64_rn(X[j], em + p.exp_n[n]);
+        }
       }
     }
-    tc_fence_before();
   }
+  tc_fence_before();
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
@@ -208,27 +268,76 @@ __global__ void __launch_bounds__(192, 1)
   }
 }
 
-// One warp per row: sigma = 2^e >= max|x| and the 7 BF16 slices s_i = a_i 2^-7i, [i][row][Kpad].
+// x 2^(49 - e) rounded to the nearest integer (ties to even), for |x| < 2^e, from the FP64 bit
+// pattern by integer shifts: the fixed-point value whose base-128 digits are the slices.
+__device__ __forceinline__ long long fixed_point_49(double x, int e) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int E = int((b >> 52) & 0x7ffu);
+  unsigned long long M = b & ((1ull << 52) - 1);
+  if (E == 0 && M == 0) return 0;
+  int Eeff = 1;
+  if (E != 0) {
+    M |= 1ull << 52;
+    Eeff = E;
+  }
+  // |x| = M 2^(Eeff - 1075), so X = M 2^-s with s = 1026 + e - Eeff (s >= 4 for a normal x < 2^e)
+  const int sh = 1026 + e - Eeff;
+  unsigned long long X;
+  if (sh <= 0) {
+    X = M << (-sh);
+  } else if (sh >= 64) {
+    X = 0;
+  } else {
+    X = M >> sh;
+    const unsigned long long rem = M & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (X & 1ull))) ++X;
+  }
+  return (b >> 63) ? -(long long)X : (long long)X;
+}
+
+// One warp per row: sigma = 2^e >= max|x| and the 7 BF16 slices s_i = a_i 2^-7i, [i][row][Kpad],
+// where X = x 2^(49-e) = sum_i a_i 128^(6-i) with balanced digits a_i in [-64, 63] (i > 0) and
+// |a_0| <= 128.  Integer instructions only (the FP64 pipe runs at 1/64 of the FP32 rate).
 __global__ void emu_slice_kernel(const double* __restrict__ x, int64_t rows, int K, int Kpad,
                                  __nv_bfloat16* __restrict__ slices, int* __restrict__ scale_exp) {
   const int lane = threadIdx.x & 31;
   for (int64_t r = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; r < rows;
        r += (int64_t(gridDim.x) * blockDim.x) >> 5) {
     const double* xr = x + r * K;
-    double mx = 0.0;
-    for (int k = lane; k < K; k += 32) mx = fmax(mx, fabs(xr[k]));
-    for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    unsigned long long mb = 0;                 // max |x| as a bit pattern (monotone for x >= 0)
+    for (int k = lane; k < K; k += 32) {
+      const unsigned long long b = (unsigned long long)__double_as_longlong(xr[k]) & 0x7fffffffffffffffull;
+      mb = b > mb ? b : mb;
+    }
+    for (int o = 16; o; o >>= 1) {
+      const unsigned long long y = __shfl_xor_sync(0xffffffffu, mb, o);
+      mb = y > mb ? y : mb;
+    }
     int e = 0;
-    if (mx > 0.0) frexp(mx, &e);             // mx = f 2^e, f in [0.5, 1): |x| / 2^e < 1
+    if (mb != 0) frexp(__longlong_as_double((long long)mb), &e);   // max = f 2^e, f in [0.5, 1)
     if (lane == 0) scale_exp[r] = e;
-    for (int k = lane; k < Kpad; k += 32) {
-      double v = (k < K) ? ldexp(xr[k], -e) : 0.0;
+    for (int k = 2 * lane; k < Kpad; k += 64) {
+      long long X[2];
+      X[0] = (k < K) ? fixed_point_49(xr[k], e) : 0;
+      X[1] = (k + 1 < K) ? fixed_point_49(xr[k + 1], e) : 0;
+      int a[2][EMU_S];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+#pragma unroll
+        for (int i = EMU_S - 1; i >= 1; --i) {
+          const long long d = ((X[h] + 64) & 127) - 64;
+          a[h][i] = int(d);
+          X[h] = (X[h] - d) / 128;             // exact
+        }
+        a[h][0] = int(X[h]);
+      }
 #pragma unroll
       for (int i = 0; i < EMU_S; ++i) {
-        const double t = v * 128.0;
-        const double a = rint(t);
-        v = t - a;                             // exact
-        slices[(size_t(i) * rows + r) * Kpad + k] = __double2bfloat16(ldexp(a, -7 * i));   // exact
+        const float p = __int_as_float((127 - 7 * i) << 23);      // 2^-7i
+        __nv_bfloat162 v;
+        v.x = __float2bfloat16_rn(float(a[0][i]) * p);            // exact: |a| <= 128
+        v.y = __float2bfloat16_rn(float(a[1][i]) * p);
+        *reinterpret_cast<__nv_bfloat162*>(slices + (size_t(i) * rows + r) * Kpad + k) = v;
       }
     }
   }
@@ -291,9 +400,13 @@ msasm_status contract_emu_gpu(const void* a_slices, const int* a_exp, int M, con
   p.ld = ld;
   p.err = d_err;
   MSASM_CUDA(cudaFuncSetAttribute(contract_emu_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, EMU_SMEM_BYTES));
-  dim3 grid(unsigned((N + EMU_BN - 1) / EMU_BN), unsigned((M + EMU_BM - 1) / EMU_BM));
-  if (grid.x > 2147483647u || grid.y > 65535u) return fail(MSASM_EUNSUPPORTED, "grid too large");
-  contract_emu_kernel<<<grid, 192, EMU_SMEM_BYTES, s>>>(ma, mb, p);
+  const long long tiles = ((N + EMU_BN - 1) / EMU_BN) * (long long)((M + EMU_BM - 1) / EMU_BM);
+  if (tiles == 0) return MSASM_OK;
+  int dev = 0, n_sm = 0;
+  MSASM_CUDA(cudaGetDevice(&dev));
+  MSASM_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+  const unsigned grid = unsigned(std::min<long long>(tiles, std::max(n_sm, 1)));   // one CTA per SM
+  contract_emu_kernel<<<grid, EMU_THREADS, EMU_SMEM_BYTES, s>>>(ma, mb, p);
   MSASM_CUDA(cudaGetLastError());
   return MSASM_OK;
 }
