@@ -13,17 +13,20 @@
 // Keeping the small cross terms in their own accumulator keeps their FP32 accumulation error
 // relative to the small terms instead of to the whole sum.
 //
-// One CTA computes a 128 (m) x 256 (n) tile; 6 warps: warp 0 issues TMA loads (128-byte
-// swizzled K-major boxes) into a 2-stage shared-memory ring, warp 1 owns the TMEM allocation
-// and one elected lane issues tcgen05.mma (M=128, N=256, K=16 for f16/bf16, K=8 for tf32),
-// warps 2-5 read the accumulators back with tcgen05.ld (each warp its 32-lane quarter) and
-// store nz with the rows of a warp contiguous in m.  Every mbarrier wait is bounded; on a
-// timeout the CTA records an error flag, drains what it issued and returns.
+// Persistent kernel, one CTA per SM looping over 128 (m) x 256 (n) output tiles; 10 warps: warp 0
+// issues TMA loads (128-byte swizzled K-major boxes) into a 2-stage shared-memory ring that runs
+// on across tiles, warp 1 owns the TMEM allocation and one elected lane issues tcgen05.mma
+// (M=128, N=256, K=16 for f16/bf16, K=8 for tf32), warps 2-9 (two per 32-lane TMEM quarter, 128
+// columns each) drain the accumulators into registers, release TMEM so that the next tile's MMAs
+// start, then scale and store nz with the rows of a warp contiguous in m.  Every mbarrier wait is
+// bounded; on a timeout (or another thread's) the CTA records the error flag, drains what it
+// issued and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "common.h"
@@ -54,7 +57,11 @@ struct TcParams {
 };
 
 // ------------------------------------------------------------------ the kernel
-__global__ void __launch_bounds__(192, 1)
+constexpr int TC_EPI_WARPS = 8;                          // two per TMEM lane quarter
+constexpr int TC_THREADS = 64 + 32 * TC_EPI_WARPS;       // producer warp, MMA warp, epilogue warps
+constexpr int TC_EPI_COLS = TC_BN / 2;                   // columns of one epilogue warp
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
     contract_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
                        const __grid_constant__ CUtensorMap tmB_hi, const __grid_constant__ CUtensorMap tmB_lo,
                        TcParams p) {
@@ -63,14 +70,18 @@ __global__ void __launch_bounds__(192, 1)
   const uint32_t base = (raw + 1023u) & ~1023u;               // 1024-B alignment for the swizzle atoms
   uint8_t* gen_base = smem_raw + (base - raw);
   const uint32_t bar0 = base + TC_STAGES * TC_STAGE_BYTES;     // barriers after the stages
-  // barrier layout: full[S], empty[S], accum, then the TMEM address slot
+  // barrier layout: full[S], empty[S], accum_full, tmem_empty, then the TMEM address slot
   auto full_bar = [&](int s) { return bar0 + 8u * s; };
   auto empty_bar = [&](int s) { return bar0 + 8u * (TC_STAGES + s); };
-  const uint32_t accum_bar = bar0 + 8u * (2 * TC_STAGES);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gen_base + TC_STAGES * TC_STAGE_BYTES + 8 * (2 * TC_STAGES + 1));
+  const uint32_t accum_full = bar0 + 8u * (2 * TC_STAGES);
+  const uint32_t tmem_empty = bar0 + 8u * (2 * TC_STAGES + 1);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gen_base + TC_STAGES * TC_STAGE_BYTES + 8 * (2 * TC_STAGES + 2));
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * TC_BN;
+  const int n_mt = (p.M + TC_BM - 1) / TC_BM, n_nt = (p.N + TC_BN - 1) / TC_BN;
+  // tile t: m tile t % n_mt, n tile t / n_mt (CTAs running together share the coefficient tile and
+  // sweep the table, the smaller operand, which stays in L2)
+  const long long total = (long long)n_mt * n_nt;
   const bool two_acc = (p.kind != kTF32);
   const bool with_lo = (p.kind != kTF32);
   const float lo_weight = (p.kind == kSplitF16) ? 1.0f / 2048.0f : 1.0f;
@@ -82,7 +93,8 @@ __global__ void __launch_bounds__(192, 1)
       mbar_init(full_bar(s), 1);
       mbar_init(empty_bar(s), 1);
     }
-    mbar_init(accum_bar, 1);
+    mbar_init(accum_full, 1);
+    mbar_init(tmem_empty, TC_EPI_WARPS);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA_hi)) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB_hi)) : "memory");
@@ -99,99 +111,123 @@ __global__ void __launch_bounds__(192, 1)
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0 && lane == 0) {
-    // ---------------- TMA producer
-    int issued = 0;
+    // ---------------- TMA producer: the stage ring runs on across tiles
+    uint32_t g = 0;
     bool ok = true;
-    for (int kb = 0; kb < p.kblocks && ok; ++kb) {
-      const int s = kb % TC_STAGES, it = kb / TC_STAGES;
-      if (it > 0) ok = mbar_wait(empty_bar(s), (it - 1) & 1, p.err);
-      if (!ok) break;
-      const uint32_t st = base + s * TC_STAGE_BYTES;
-      const int kx = kb * (p.kind >= kTF32 ? 32 : 64);       // element coordinate of the block
-      mbar_expect_tx(full_bar(s), stage_tx);
-      tma_load_2d(st, &tmA_hi, kx, m0, full_bar(s));
-      tma_load_2d(st + 2 * TC_A_BYTES, &tmB_hi, kx, n0, full_bar(s));
-      if (with_lo) {
-        tma_load_2d(st + TC_A_BYTES, &tmA_lo, kx, m0, full_bar(s));
-        tma_load_2d(st + 2 * TC_A_BYTES + TC_B_BYTES, &tmB_lo, kx, n0, full_bar(s));
+    for (long long t = blockIdx.x; t < total && ok; t += gridDim.x) {
+      const int m0 = int(t % n_mt) * TC_BM, n0 = int(t / n_mt) * TC_BN;
+      for (int kb = 0; kb < p.kblocks; ++kb, ++g) {
+        const int s = int(g % TC_STAGES);
+        const uint32_t it = g / TC_STAGES;
+        if (it > 0 && !mbar_wait_or_abort(empty_bar(s), (it - 1) & 1, p.err)) {
+          ok = false;
+          break;
+        }
+        const uint32_t st = base + s * TC_STAGE_BYTES;
+        const int kx = kb * (p.kind >= kTF32 ? 32 : 64);       // element coordinate of the block
+        mbar_expect_tx(full_bar(s), stage_tx);
+        tma_load_2d(st, &tmA_hi, kx, m0, full_bar(s));
+        tma_load_2d(st + 2 * TC_A_BYTES, &tmB_hi, kx, n0, full_bar(s));
+        if (with_lo) {
+          tma_load_2d(st + TC_A_BYTES, &tmA_lo, kx, m0, full_bar(s));
+          tma_load_2d(st + 2 * TC_A_BYTES + TC_B_BYTES, &tmB_lo, kx, n0, full_bar(s));
+        }
       }
-      ++issued;
     }
-    // drain: wait until every issued load has landed before the CTA may exit
-    for (int kb = (issued > TC_STAGES ? issued - TC_STAGES : 0); kb < issued; ++kb)
-      mbar_wait(full_bar(kb % TC_STAGES), (kb / TC_STAGES) & 1, p.err);
+    // every issued copy has landed before the CTA can exit (bounded)
+    for (uint32_t q = (g > uint32_t(TC_STAGES) ? g - TC_STAGES : 0u); q < g; ++q)
+      mbar_wait(full_bar(int(q % TC_STAGES)), (q / TC_STAGES) & 1, p.err);
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
     const bool tf = p.kind >= kTF32;
     const uint32_t idesc = instr_desc(p.kind == kSplitF16 ? 0u : (tf ? 2u : 1u), TC_BM, TC_BN);
     const int ksteps = 4;                                       // 4 x 32 B of k per 128-B row
     const uint32_t acc0 = tmem, acc1 = tmem + (two_acc ? 256u : 0u);
+    uint32_t g = 0, i_tile = 0;
     bool ok = true;
-    for (int kb = 0; kb < p.kblocks; ++kb) {
-      const int s = kb % TC_STAGES, it = kb / TC_STAGES;
-      ok = mbar_wait(full_bar(s), it & 1, p.err);
-      if (!ok) break;
-      tc_fence_after();
-      const uint32_t st = base + s * TC_STAGE_BYTES;
-      const uint64_t a_hi = sw128_desc(st), a_lo = sw128_desc(st + TC_A_BYTES);
-      const uint64_t b_hi = sw128_desc(st + 2 * TC_A_BYTES), b_lo = sw128_desc(st + 2 * TC_A_BYTES + TC_B_BYTES);
-#pragma unroll
-      for (int j = 0; j < ksteps; ++j) {
-        const uint64_t dk = uint64_t(2 * j);                    // +32 bytes of k, in 16-byte units
-        const uint32_t first = (kb == 0 && j == 0) ? 0u : 1u;
-        // hi.hi and hi.lo share the A tile: it stays in the collector buffer for the second
-        if (tf) {
-          if (with_lo) {
-            mma_tf32_collect<CollectorA::FILL>(acc0, a_hi + dk, b_hi + dk, idesc, first);
-            mma_tf32_collect<CollectorA::LASTUSE>(acc1, a_hi + dk, b_lo + dk, idesc, first);
-            mma_tf32(acc1, a_lo + dk, b_hi + dk, idesc, 1u);
-          } else {
-            mma_tf32(acc0, a_hi + dk, b_hi + dk, idesc, first);
-          }
-        } else {
-          mma_f16_collect<CollectorA::FILL>(acc0, a_hi + dk, b_hi + dk, idesc, first);
-          mma_f16_collect<CollectorA::LASTUSE>(acc1, a_hi + dk, b_lo + dk, idesc, first);
-          mma_f16(acc1, a_lo + dk, b_hi + dk, idesc, 1u);
-        }
+    for (long long t = blockIdx.x; t < total && ok; t += gridDim.x, ++i_tile) {
+      if (i_tile > 0) {                                         // the previous tile is drained
+        if (!mbar_wait_or_abort(tmem_empty, (i_tile - 1) & 1, p.err)) break;
+        tc_fence_after();
       }
-      mma_commit(empty_bar(s));                                  // stage reusable when these MMAs finish
-    }
-    mma_commit(accum_bar);                                       // accumulators final (or drained on error)
-    mbar_wait(accum_bar, 0, p.err);
-  } else if (warp >= 2) {
-    // ---------------- epilogue: TMEM -> registers -> nz[n][m]
-    const int q = warp & 3;                                      // TMEM lane quarter of this warp
-    const bool ok = mbar_wait(accum_bar, 0, p.err);
-    tc_fence_after();
-    if (ok) {
-      const int m = m0 + 32 * q + lane;
-      const float sm = (p.scale_m && m < p.M) ? p.scale_m[m] : 1.0f;
-      const uint32_t lane_off = uint32_t(32 * q) << 16;
-      for (int c0 = 0; c0 < TC_BN; c0 += 32) {
-        if (n0 + c0 >= p.N) break;
-        float v[32];
-        tmem_ld32(tmem + lane_off + c0, v);
-        if (two_acc) {
-          float w[32];
-          tmem_ld32(tmem + 256u + lane_off + c0, w);
-#pragma unroll
-          for (int j = 0; j < 32; ++j) v[j] = fmaf(w[j], lo_weight, v[j]);
+      for (int kb = 0; kb < p.kblocks; ++kb, ++g) {
+        const int s = int(g % TC_STAGES);
+        const uint32_t it = g / TC_STAGES;
+        if (!mbar_wait_or_abort(full_bar(s), it & 1, p.err)) {
+          ok = false;
+          break;
         }
-        if (m < p.M) {
+        tc_fence_after();
+        const uint32_t st = base + s * TC_STAGE_BYTES;
+        const uint64_t a_hi = sw128_desc(st), a_lo = sw128_desc(st + TC_A_BYTES);
+        const uint64_t b_hi = sw128_desc(st + 2 * TC_A_BYTES), b_lo = sw128_desc(st + 2 * TC_A_BYTES + TC_B_BYTES);
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int n = n0 + c0 + j;
-            if (n < p.N) {
-              float val = v[j];
-              if (p.scale_m) val *= sm * p.scale_n[n];
-              p.out[size_t(n) * p.ld + m] = val;
+        for (int j = 0; j < ksteps; ++j) {
+          const uint64_t dk = uint64_t(2 * j);                    // +32 bytes of k, in 16-byte units
+          const uint32_t first = (kb == 0 && j == 0) ? 0u : 1u;
+          // hi.hi and hi.lo share the A tile: it stays in the collector buffer for the second
+          if (tf) {
+            if (with_lo) {
+              mma_tf32_collect<CollectorA::FILL>(acc0, a_hi + dk, b_hi + dk, idesc, first);
+              mma_tf32_collect<CollectorA::LASTUSE>(acc1, a_hi + dk, b_lo + dk, idesc, first);
+              mma_tf32(acc1, a_lo + dk, b_hi + dk, idesc, 1u);
+            } else {
+              mma_tf32(acc0, a_hi + dk, b_hi + dk, idesc, first);
             }
+          } else {
+            mma_f16_collect<CollectorA::FILL>(acc0, a_hi + dk, b_hi + dk, idesc, first);
+            mma_f16_collect<CollectorA::LASTUSE>(acc1, a_hi + dk, b_lo + dk, idesc, first);
+            mma_f16(acc1, a_lo + dk, b_hi + dk, idesc, 1u);
+          }
+        }
+        mma_commit(empty_bar(s));                                  // stage reusable when these MMAs finish
+      }
+      mma_commit(accum_full);                                      // this tile's accumulators are final
+    }
+    if (i_tile > 0) mbar_wait(accum_full, (i_tile - 1) & 1, p.err);   // nothing in flight at exit
+  } else if (warp >= 2) {
+    // ---------------- epilogue: drain TMEM into registers, release it, scale and store nz[n][m]
+    const int q = warp & 3;                                      // TMEM lane quarter of this warp
+    const int h = (warp - 2) >> 2;                               // column half
+    const uint32_t lane_off = uint32_t(32 * q) << 16;
+    uint32_t i_tile = 0;
+    for (long long t = blockIdx.x; t < total; t += gridDim.x, ++i_tile) {
+      if (!mbar_wait_or_abort(accum_full, i_tile & 1, p.err)) break;
+      tc_fence_after();
+      const int m0 = int(t % n_mt) * TC_BM, n0 = int(t / n_mt) * TC_BN + h * TC_EPI_COLS;
+      float R[TC_EPI_COLS];
+#pragma unroll
+      for (int c = 0; c < TC_EPI_COLS / 16; ++c) {
+        float v[16];
+        tmem_ld16(tmem + lane_off + uint32_t(h * TC_EPI_COLS + 16 * c), v);
+        if (two_acc) {
+          float w[16];
+          tmem_ld16(tmem + 256u + lane_off + uint32_t(h * TC_EPI_COLS + 16 * c), w);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) v[j] = fmaf(w[j], lo_weight, v[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) R[16 * c + j] = v[j];
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tmem_empty);                    // the MMAs of the next tile may start
+      const int m = m0 + 32 * q + lane;
+      if (m < p.M) {
+        const float sm = p.scale_m ? p.scale_m[m] : 1.0f;
+#pragma unroll
+        for (int j = 0; j < TC_EPI_COLS; ++j) {
+          const int n = n0 + j;
+          if (n < p.N) {
+            float val = R[j];
+            if (p.scale_m) val *= sm * p.scale_n[n];
+            p.out[size_t(n) * p.ld + m] = val;
           }
         }
       }
     }
-    tc_fence_before();
   }
+  tc_fence_before();
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
@@ -313,7 +349,7 @@ msasm_status contract_tc_gpu(int kind, const void* a_hi, const void* a_lo, const
                              const void* b_hi, const void* b_lo, const float* b_scale, int64_t N, int K, float* out,
                              int ld, unsigned* d_err, cudaStream_t s) {
   MSASM_TRY(get_encoder());
-  if (N > int64_t(65535) * TC_BN) return fail(MSASM_EUNSUPPORTED, "too many coefficient rows for one launch");
+  if (N > int64_t(2147483647)) return fail(MSASM_EUNSUPPORTED, "too many coefficient rows for one launch");
   const int Kpad = tc_kpad(K, kind);
   CUtensorMap ma_hi, ma_lo, mb_hi, mb_lo;
   MSASM_TRY(make_map(&ma_hi, a_hi, kind, M, K, Kpad, TC_BM));
@@ -337,8 +373,13 @@ msasm_status contract_tc_gpu(int kind, const void* a_hi, const void* a_lo, const
   p.ld = ld;
   p.err = d_err;
   MSASM_CUDA(cudaFuncSetAttribute(contract_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BYTES));
-  dim3 grid(unsigned((M + TC_BM - 1) / TC_BM), unsigned((N + TC_BN - 1) / TC_BN));
-  contract_tc_kernel<<<grid, 192, TC_SMEM_BYTES, s>>>(ma_hi, ma_lo, mb_hi, mb_lo, p);
+  const long long tiles = ((M + TC_BM - 1) / TC_BM) * ((N + TC_BN - 1) / TC_BN);
+  if (tiles == 0) return MSASM_OK;
+  int dev = 0, n_sm = 0;
+  MSASM_CUDA(cudaGetDevice(&dev));
+  MSASM_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+  const unsigned grid = unsigned(std::min<long long>(tiles, std::max(n_sm, 1)));   // one CTA per SM
+  contract_tc_kernel<<<grid, TC_THREADS, TC_SMEM_BYTES, s>>>(ma_hi, ma_lo, mb_hi, mb_lo, p);
   MSASM_CUDA(cudaGetLastError());
   return MSASM_OK;
 }
