@@ -105,6 +105,7 @@ msasm_plan::~msasm_plan() {
   cudaFree(d_tmpl);
   cudaFree(d_tmpl_ptr);
   cudaFree(d_work);
+  cudaFree(d_work_base);
   cudaFree(d_coef);
   cudaFree(d_nz);
   cudaFree(d_coef_lp);
@@ -316,6 +317,7 @@ msasm_status msasm_plan_create(const msasm_tables* tab, const msasm_macro_desc* 
   if (err == cudaSuccess) err = dev((void**)&plan->d_tmpl, sp.tmpl.size() * sizeof(uint32_t));
   if (err == cudaSuccess) err = dev((void**)&plan->d_tmpl_ptr, sp.tmpl_ptr.size() * sizeof(int64_t));
   if (err == cudaSuccess) err = dev((void**)&plan->d_work, sp.work.size() * sizeof(int32_t));
+  if (err == cudaSuccess) err = dev((void**)&plan->d_work_base, sp.work_base.size() * sizeof(int64_t));
   if (err == cudaSuccess) err = dev((void**)&plan->d_coef, size_t(9 * plan->tiles_per_pass) * 9 * n_pi * sizeof(double));
   if (err == cudaSuccess) err = dev((void**)&plan->d_nz, size_t(9 * plan->tiles_per_pass) * ld * sizeof(double));
   if (err == cudaSuccess) err = dev((void**)&plan->d_degenerate, sizeof(unsigned long long));
@@ -350,6 +352,7 @@ msasm_status msasm_plan_create(const msasm_tables* tab, const msasm_macro_desc* 
   if (err == cudaSuccess) err = h2d(plan->d_tmpl, sp.tmpl.data(), sp.tmpl.size() * sizeof(uint32_t));
   if (err == cudaSuccess) err = h2d(plan->d_tmpl_ptr, sp.tmpl_ptr.data(), sp.tmpl_ptr.size() * sizeof(int64_t));
   if (err == cudaSuccess) err = h2d(plan->d_work, sp.work.data(), sp.work.size() * sizeof(int32_t));
+  if (err == cudaSuccess) err = h2d(plan->d_work_base, sp.work_base.data(), sp.work_base.size() * sizeof(int64_t));
   if (err == cudaSuccess) err = h2d(d_pptr, pptr.data(), pptr.size() * sizeof(int64_t));
   if (err == cudaSuccess) err = h2d(d_pcol, pcol.data(), pcol.size() * sizeof(int32_t));
   if (err == cudaSuccess) err = h2d(d_pair_face, tab->topo.pair_face.data(), size_t(n_nz));

@@ -76,12 +76,14 @@ struct ScatterPlanHost {
   std::vector<int32_t> tile_type;          // per tile
   std::vector<int32_t> type_chunk_begin;   // chunks of type ty: [begin[ty], begin[ty+1])
   std::vector<int32_t> chunk_info;         // per chunk: point offset, point count, program offset, program size
-  std::vector<int32_t> chunk_points;       // owned local ids per chunk
+  std::vector<int32_t> chunk_points;       // per chunk point: local id A, first value of its rows relative to
+                                           // the chunk, row length (3 ints; the same for every tile of the type)
   std::vector<uint32_t> prog;              // m | lower << 31
   std::vector<uint32_t> tmpl;              // secondary template per type: m | upper << 30 | lower << 31
   std::vector<int64_t> tmpl_ptr;
   int64_t max_tmpl = 0;
   std::vector<int32_t> work;               // (tile, chunk) pairs
+  std::vector<int64_t> work_base;          // per work item: index of its chunk's first CSR value
   std::vector<int64_t> work_ptr;           // per tile
 };
 
@@ -137,6 +139,7 @@ struct msasm_plan {
   uint32_t* d_tmpl = nullptr;
   int64_t* d_tmpl_ptr = nullptr;
   int32_t* d_work = nullptr;
+  int64_t* d_work_base = nullptr;
   std::vector<int64_t> work_ptr;    // host: work items of tile t are [work_ptr[t], work_ptr[t+1])
   int64_t max_tmpl = 0;
   std::vector<double> knots_host[3];  // host copies for boundary data

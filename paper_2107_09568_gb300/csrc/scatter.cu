@@ -6,48 +6,51 @@
 // the lower one at rowptr[3 g(B) + b] + 3 r_l + a.
 //
 // Staged pass: the rows of the points a tile owns are one contiguous range of values (tile-major
-// numbering).  One CTA per chunk of that range builds the chunk in shared memory from the
-// chunk's program (the pairs whose upper or lower block lands there, in increasing m, so the
-// nzdata loads of neighbouring threads are mostly contiguous), entries no pair of the tile
-// reaches staying zero, and streams it out with coalesced 16-byte stores.  Every CSR value is
-// written exactly once by the staged pass.
+// numbering).  One CTA per chunk of that range builds the chunk in shared memory from the chunk's
+// program (the pairs whose upper or lower block lands there, in increasing m, so the nzdata
+// loads of neighbouring threads are mostly contiguous), entries no pair of the tile reaches
+// staying zero, and streams it out with coalesced 16-byte stores.  Every CSR value is written
+// exactly once by the staged pass.
 //
 // Secondary pass: blocks of tile t landing in rows owned by a lower tile (points on a glued lower
 // face) are added to the values the owner wrote; it runs after the staged pass on the same
 // stream and each position has at most one such contributor, so no atomics are needed and the
 // two-term sums are order independent.
+#include <algorithm>
+#include <cstdint>
+
 #include "common.h"
 
 namespace msasm {
 
-constexpr int kStagedThreads = 256;
-constexpr int kStagedUnroll = 2;
+constexpr int kStagedThreads = 128;
+constexpr int kStagedUnroll = 4;
 
+// One CTA per work item (tile, chunk).  The chunk's layout (each point's row offset and length)
+// is the same for every tile of the type and its first value index is precomputed per item, so
+// a CTA starts gathering after two dependent loads.
 template <typename T>
 __global__ void __launch_bounds__(kStagedThreads) scatter_staged_kernel(
     const T* __restrict__ nz, int ld_nz, int n_nz, int64_t t0, const int32_t* __restrict__ work,
-    const int32_t* __restrict__ chunk_info, const int32_t* __restrict__ chunk_points, const uint32_t* __restrict__ prog,
-    const int32_t* __restrict__ pairs, const int32_t* __restrict__ gmap, int n_T, const uint32_t* __restrict__ rank,
-    const int64_t* __restrict__ rowptr, T* __restrict__ values) {
+    const int64_t* __restrict__ work_base, const int32_t* __restrict__ chunk_info,
+    const int32_t* __restrict__ chunk_points, const uint32_t* __restrict__ prog, const int32_t* __restrict__ pairs,
+    int n_T, const uint32_t* __restrict__ rank, T* __restrict__ values) {
   extern __shared__ __align__(16) uint8_t sm_raw[];
   T* buf = reinterpret_cast<T*>(sm_raw);
   int32_t* off = reinterpret_cast<int32_t*>(sm_raw + kChunkValues * sizeof(T));   // [n_T]
   int32_t* len = off + n_T;                                                        // [n_T]
   const int64_t t = work[2 * blockIdx.x];
   const int c = work[2 * blockIdx.x + 1];
+  const int64_t base = work_base[blockIdx.x];
   const int64_t tl = t - t0;
   const int p_begin = chunk_info[4 * c], p_count = chunk_info[4 * c + 1];
   const int q_begin = chunk_info[4 * c + 2], q_count = chunk_info[4 * c + 3];
-  const int32_t* gt = gmap + t * n_T;
-  const int64_t base = rowptr[3 * int64_t(gt[chunk_points[p_begin]])];
-  const int64_t end = rowptr[3 * int64_t(gt[chunk_points[p_begin + p_count - 1]]) + 3];
-  const int n_vals = int(end - base);
+  const int32_t* cp = chunk_points + 3 * p_begin;
+  const int n_vals = cp[3 * (p_count - 1) + 1] + 3 * cp[3 * (p_count - 1) + 2];
   for (int i = threadIdx.x; i < p_count; i += blockDim.x) {
-    const int A = chunk_points[p_begin + i];
-    const int64_t g = gt[A];
-    const int64_t r0 = rowptr[3 * g];
-    off[A] = int32_t(r0 - base);
-    len[A] = int32_t(rowptr[3 * g + 1] - r0);
+    const int A = cp[3 * i];
+    off[A] = cp[3 * i + 1];
+    len[A] = cp[3 * i + 2];
   }
   for (int i = threadIdx.x; i < n_vals; i += blockDim.x) buf[i] = T(0);
   __syncthreads();
@@ -152,14 +155,16 @@ msasm_status scatter_pass_gpu(const msasm_plan* plan, const T* d_nz, int ld_nz, 
                               T* d_values, cudaStream_t stream) {
   const msasm_tables* tab = plan->tab;
   const int n_T = tab->topo.n_T;
+  if (reinterpret_cast<uintptr_t>(d_values) % 16 != 0)
+    return fail(MSASM_EINVAL, "the CSR values buffer must be 16-byte aligned");
   const int64_t w0 = plan->work_ptr[size_t(t0)], w1 = plan->work_ptr[size_t(t0 + n_tiles)];
   if (w1 > w0) {
     const size_t smem = kChunkValues * sizeof(T) + 2 * size_t(n_T) * sizeof(int32_t);
-    if (smem > 220 * 1024) return fail(MSASM_EUNSUPPORTED, "reference tile too large for the staged scatter");
+    if (smem > 48 * 1024) return fail(MSASM_EUNSUPPORTED, "reference tile too large for the staged scatter");
     MSASM_CUDA(cudaFuncSetAttribute(scatter_staged_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
     scatter_staged_kernel<T><<<unsigned(w1 - w0), kStagedThreads, smem, stream>>>(
-        d_nz, ld_nz, tab->n_nz, t0, plan->d_work + 2 * w0, plan->d_chunk_info, plan->d_chunk_points, plan->d_prog,
-        tab->d_pairs, plan->d_gmap, n_T, plan->d_rank, plan->d_rowptr, d_values);
+        d_nz, ld_nz, tab->n_nz, t0, plan->d_work + 2 * w0, plan->d_work_base + w0, plan->d_chunk_info,
+        plan->d_chunk_points, plan->d_prog, tab->d_pairs, n_T, plan->d_rank, d_values);
     MSASM_CUDA(cudaGetLastError());
   }
   if (plan->max_tmpl > 0 && n_tiles > 0) {

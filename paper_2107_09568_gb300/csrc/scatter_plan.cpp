@@ -85,11 +85,18 @@ msasm_status build_scatter_plan(msasm_plan* plan, const std::vector<int32_t>& gm
       if (flags) out.tmpl.push_back(uint32_t(m) | (flags << 30));
     }
     for (int c = 0; c < n_chunks; ++c) {
-      out.chunk_info.push_back(int32_t(out.chunk_points.size()));
+      out.chunk_info.push_back(int32_t(out.chunk_points.size() / 3));
       out.chunk_info.push_back(int32_t(pts[c].size()));
       out.chunk_info.push_back(int32_t(out.prog.size()));
       out.chunk_info.push_back(int32_t(progs[c].size()));
-      out.chunk_points.insert(out.chunk_points.end(), pts[c].begin(), pts[c].end());
+      int32_t off = 0;
+      for (int A : pts[c]) {                       // the owned points' rows follow each other
+        const int32_t row_len = int32_t(3 * (pptr[size_t(g[A]) + 1] - pptr[size_t(g[A])]));
+        out.chunk_points.push_back(A);
+        out.chunk_points.push_back(off);
+        out.chunk_points.push_back(row_len);
+        off += 3 * row_len;
+      }
       out.prog.insert(out.prog.end(), progs[c].begin(), progs[c].end());
     }
     out.type_chunk_begin[size_t(ty) + 1] = base_chunk + n_chunks;
@@ -101,11 +108,24 @@ msasm_status build_scatter_plan(msasm_plan* plan, const std::vector<int32_t>& gm
   out.max_tmpl = 0;
   for (int ty = 0; ty < n_types; ++ty)
     out.max_tmpl = std::max<int64_t>(out.max_tmpl, out.tmpl_ptr[size_t(ty) + 1] - out.tmpl_ptr[size_t(ty)]);
+  out.work_base.clear();
   for (int64_t t = 0; t < plan->n_tiles; ++t) {
     const int ty = out.tile_type[size_t(t)];
+    const int32_t* g = &gmap[size_t(t) * n_T];
     for (int c = out.type_chunk_begin[size_t(ty)]; c < out.type_chunk_begin[size_t(ty) + 1]; ++c) {
+      // the chunk layout of the type holds for this tile: consecutive global ids, same row lengths
+      const int p0 = out.chunk_info[size_t(4 * c)], np = out.chunk_info[size_t(4 * c + 1)];
+      const int64_t g0 = g[out.chunk_points[size_t(3 * p0)]];
+      for (int i = 0; i < np; ++i) {
+        const int32_t* cp = &out.chunk_points[size_t(3 * (p0 + i))];
+        const int64_t gi = g[cp[0]];
+        if (gi != g0 + i || 3 * (pptr[size_t(gi) + 1] - pptr[size_t(gi)]) != cp[2] ||
+            9 * (pptr[size_t(gi)] - pptr[size_t(g0)]) != cp[1])
+          return fail(MSASM_EUNSUPPORTED, "tile numbering is not translation invariant within a tile type");
+      }
       out.work.push_back(int32_t(t));
       out.work.push_back(int32_t(c));
+      out.work_base.push_back(9 * pptr[size_t(g0)]);        // rows 3 g0 .. start at 9 x (entries before g0)
     }
     out.work_ptr[size_t(t) + 1] = int64_t(out.work.size() / 2);
   }
