@@ -172,6 +172,14 @@ FP64_ALU_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
+# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu capture of the kernel
+# as it is now (dram__bytes_read.sum + dram__bytes_write.sum); the profile named beside each
+# figure gives the command.  Keyed by (kernel, workload, precision).
+NCU_TRAFFIC = {
+    ("contract_emu_kernel", "beam1000", "f64_emu"): (958.0e6 + 1634.0e6, "profiles/launches_beam1000_f64_emu.md"),
+}
+
+
 def contraction_flops(n_nz, n_pi, n_tiles):
     return 2.0 * n_nz * 9 * n_pi * 9 * n_tiles
 
@@ -397,6 +405,14 @@ def main():
         ach = byts / (stage_avg[dom] / 1e3) / 1e9
         roof = {"kernel": names[dom], "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / pk["hbm_gbs"], "traffic": None, "peak_source": pk_kind}
+    tr = NCU_TRAFFIC.get((roof["kernel"], args.workload, prec))
+    if tr is not None:
+        roof["traffic"] = tr[0]
+        roof["traffic_source"] = tr[1]
+        if roof["kernel"] == "contract_emu_kernel":
+            # operands' slices read once plus the FP64 nzdata written once
+            alg = 7 * 2 * 9 * tab.n_pi * (tab.n_nz + 9 * plan.n_tiles) + 9 * plan.n_tiles * tab.n_nz * 8
+            roof["algorithmic_bytes"] = alg
     roof["stages_ms"] = dict(zip(names, [round(x, 4) for x in stage_avg]))
     roof["scatter_gbs"] = scatter_bytes / (stage_avg[2] / 1e3) / 1e9
     roof["scatter_frac_hbm"] = roof["scatter_gbs"] / pk["hbm_gbs"]

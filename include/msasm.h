@@ -138,8 +138,7 @@ void msasm_plan_destroy(msasm_plan* plan);
 /* K = sum over tiles of the lookup-form tile matrices (eq. 50, 58) scattered into
  * the CSR pattern of the plan.  d_ctrl: macro control net (n_ctrl*3 FP64).
  * E, nu: isotropic material (Lame constants as in eq. 84).  d_values: nnz values,
- * FP64 for MSASM_F64 / MSASM_F64_EMU, FP32 otherwise, 16-byte aligned (as every
- * cudaMalloc or PyTorch allocation; EINVAL otherwise); overwritten.  The
+ * FP64 for MSASM_F64 / MSASM_F64_EMU, FP32 otherwise; overwritten.  The
  * Jacobian, its determinant and inverse are FP64 in every precision.
  * Errors: EINVAL, EUNSUPPORTED, ECUDA; EDEGENERATE only with
  * MSASM_FLAG_CHECK_DEGENERATE (otherwise degenerate nodes are counted, see
@@ -235,7 +234,7 @@ msasm_status msasm_surrogate_predict(msasm_surrogate* sur, const double* d_width
 msasm_status msasm_lowrank_contract(const float* d_U, int32_t n_nz, int32_t rank, int32_t K, const float* d_Vt,
                                     const double* d_coef, int64_t n_tiles, float* d_nz, void* stream);
 /* K of a graded lattice: per-tile widths d_widths (n_tiles FP64, device); pullback, MLP,
- * low-rank contraction and scatter into d_values (nnz FP32, 16-byte aligned). */
+ * low-rank contraction and scatter into d_values (nnz FP32). */
 msasm_status msasm_surrogate_assemble(msasm_plan* plan, msasm_surrogate* sur, const double* d_ctrl, double E,
                                       double nu, const double* d_widths, float* d_values, void* stream);
 void msasm_surrogate_destroy(msasm_surrogate* sur);
@@ -281,7 +280,7 @@ msasm_status msasm_contract_noalloc(const msasm_tables* tab, const double* d_coe
                                    double* d_nz, void* stream);
 
 /* Step 4 only: CSR values from nzdata of all tiles of the plan (d_nz as written by
- * msasm_contract for all plan tiles, same precision family); d_values 16-byte aligned. */
+ * msasm_contract for all plan tiles, same precision family). */
 msasm_status msasm_scatter(msasm_plan* plan, msasm_precision prec, const void* d_nz,
                            void* d_values, void* stream);
 

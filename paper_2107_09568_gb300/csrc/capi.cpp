@@ -29,6 +29,9 @@ void point_pattern(const TileTopology& topo, const int n_elem[3], const std::vec
                    int64_t n_points, std::vector<int64_t>& pptr, std::vector<int32_t>& pcol);
 msasm_status structure_expand_gpu(int64_t n_points, const int64_t* d_pptr, const int32_t* d_pcol,
                                   int64_t* d_rowptr, int32_t* d_col, cudaStream_t stream);
+msasm_status secondary_entries_gpu(msasm_plan* plan, cudaStream_t stream);
+msasm_status scatter_maps_gpu(msasm_plan* plan, const int64_t* d_type_rep, int n_types, unsigned long long* d_bad,
+                              cudaStream_t stream);
 msasm_status rank_map_gpu(const int32_t* d_gmap, const int32_t* d_pairs, const uint8_t* d_pair_face,
                           const int64_t* d_pptr, const int32_t* d_pcol, int64_t n_tiles, int n_T, int n_nz,
                           int nx, int ny, uint32_t* d_rank, unsigned long long* d_bad, cudaStream_t stream);
@@ -68,7 +71,6 @@ msasm_status contract_tc_gpu(int kind, const void* a_hi, const void* a_lo, const
                              const void* b_hi, const void* b_lo, const float* b_scale, int64_t N, int K, float* out,
                              int ld, unsigned* d_err, cudaStream_t s);
 
-static inline int ld_nz_of(int n_nz) { return (n_nz + 7) & ~7; }
 
 static bool is_f64_precision(msasm_precision p) { return p == MSASM_F64 || p == MSASM_F64_EMU; }
 
@@ -99,13 +101,16 @@ msasm_plan::~msasm_plan() {
   cudaFree(d_col);
   cudaFree(d_rank);
   cudaFree(d_tile_type);
-  cudaFree(d_chunk_info);
-  cudaFree(d_chunk_points);
-  cudaFree(d_prog);
+  cudaFree(d_type_nvals);
+  cudaFree(d_type_map_off);
+  cudaFree(d_maps);
+  cudaFree(d_tile_vbase);
+  cudaFree(d_item_tile);
+  cudaFree(d_item_start);
   cudaFree(d_tmpl);
   cudaFree(d_tmpl_ptr);
-  cudaFree(d_work);
-  cudaFree(d_work_base);
+  cudaFree(d_sec_off);
+  cudaFree(d_sec);
   cudaFree(d_coef);
   cudaFree(d_nz);
   cudaFree(d_coef_lp);
@@ -283,14 +288,15 @@ msasm_status msasm_plan_create(const msasm_tables* tab, const msasm_macro_desc* 
     }
   }
 
-  // staged-scatter programs per tile type
+  // scatter plan: tile types, value maps, work items, secondary templates
   ScatterPlanHost sp;
   {
     msasm_status st0 = build_scatter_plan(plan, gmap, pptr, sp);
     if (st0 != MSASM_OK) return bail(st0);
   }
-  plan->work_ptr = sp.work_ptr;
-  plan->max_tmpl = sp.max_tmpl;
+  plan->item_ptr = sp.item_ptr;
+  plan->sec_off_host = sp.sec_off;
+  const int n_types = int(sp.type_rep.size());
   const int n_nz = tab->n_nz;
 
   // device allocations
@@ -300,6 +306,7 @@ msasm_status msasm_plan_create(const msasm_tables* tab, const msasm_macro_desc* 
   int32_t* d_pcol = nullptr;
   uint8_t* d_pair_face = nullptr;
   unsigned long long* d_bad = nullptr;
+  int64_t* d_type_rep = nullptr;
   auto dev = [&](void** p, size_t bytes) { return cudaMalloc(p, std::max<size_t>(bytes, 16)); };
   cudaError_t err = cudaSuccess;
   for (int d = 0; d < 3 && err == cudaSuccess; ++d) {
@@ -311,13 +318,17 @@ msasm_status msasm_plan_create(const msasm_tables* tab, const msasm_macro_desc* 
   if (err == cudaSuccess) err = dev((void**)&plan->d_col, size_t(plan->nnz) * sizeof(int32_t));
   if (err == cudaSuccess) err = dev((void**)&plan->d_rank, size_t(plan->n_tiles) * n_nz * sizeof(uint32_t));
   if (err == cudaSuccess) err = dev((void**)&plan->d_tile_type, sp.tile_type.size() * sizeof(int32_t));
-  if (err == cudaSuccess) err = dev((void**)&plan->d_chunk_info, sp.chunk_info.size() * sizeof(int32_t));
-  if (err == cudaSuccess) err = dev((void**)&plan->d_chunk_points, sp.chunk_points.size() * sizeof(int32_t));
-  if (err == cudaSuccess) err = dev((void**)&plan->d_prog, sp.prog.size() * sizeof(uint32_t));
+  if (err == cudaSuccess) err = dev((void**)&plan->d_type_nvals, sp.type_nvals.size() * sizeof(int32_t));
+  if (err == cudaSuccess) err = dev((void**)&plan->d_type_map_off, sp.type_map_off.size() * sizeof(int64_t));
+  if (err == cudaSuccess) err = dev((void**)&plan->d_maps, size_t(sp.type_map_off.back()) * sizeof(int32_t));
+  if (err == cudaSuccess) err = dev((void**)&plan->d_tile_vbase, plan->tile_vbase.size() * sizeof(int64_t));
+  if (err == cudaSuccess) err = dev((void**)&plan->d_item_tile, sp.item_tile.size() * sizeof(int32_t));
+  if (err == cudaSuccess) err = dev((void**)&plan->d_item_start, sp.item_start.size() * sizeof(int32_t));
   if (err == cudaSuccess) err = dev((void**)&plan->d_tmpl, sp.tmpl.size() * sizeof(uint32_t));
   if (err == cudaSuccess) err = dev((void**)&plan->d_tmpl_ptr, sp.tmpl_ptr.size() * sizeof(int64_t));
-  if (err == cudaSuccess) err = dev((void**)&plan->d_work, sp.work.size() * sizeof(int32_t));
-  if (err == cudaSuccess) err = dev((void**)&plan->d_work_base, sp.work_base.size() * sizeof(int64_t));
+  if (err == cudaSuccess) err = dev((void**)&d_type_rep, sp.type_rep.size() * sizeof(int64_t));
+  if (err == cudaSuccess) err = dev((void**)&plan->d_sec_off, sp.sec_off.size() * sizeof(int64_t));
+  if (err == cudaSuccess) err = dev((void**)&plan->d_sec, size_t(sp.sec_off.back()) * sizeof(SecondaryEntry));
   if (err == cudaSuccess) err = dev((void**)&plan->d_coef, size_t(9 * plan->tiles_per_pass) * 9 * n_pi * sizeof(double));
   if (err == cudaSuccess) err = dev((void**)&plan->d_nz, size_t(9 * plan->tiles_per_pass) * ld * sizeof(double));
   if (err == cudaSuccess) err = dev((void**)&plan->d_degenerate, sizeof(unsigned long long));
@@ -331,6 +342,7 @@ msasm_status msasm_plan_create(const msasm_tables* tab, const msasm_macro_desc* 
     cudaFree(d_pcol);
     cudaFree(d_pair_face);
     cudaFree(d_bad);
+    cudaFree(d_type_rep);
   };
   if (err != cudaSuccess) {
     cleanup_tmp();
@@ -345,14 +357,19 @@ msasm_status msasm_plan_create(const msasm_tables* tab, const msasm_macro_desc* 
   }
   if (err == cudaSuccess) err = h2d(plan->d_gmap, gmap.data(), gmap.size() * sizeof(int32_t));
   if (err == cudaSuccess) err = h2d(plan->d_tile_type, sp.tile_type.data(), sp.tile_type.size() * sizeof(int32_t));
-  if (err == cudaSuccess) err = h2d(plan->d_chunk_info, sp.chunk_info.data(), sp.chunk_info.size() * sizeof(int32_t));
+  if (err == cudaSuccess) err = h2d(plan->d_type_nvals, sp.type_nvals.data(), sp.type_nvals.size() * sizeof(int32_t));
   if (err == cudaSuccess)
-    err = h2d(plan->d_chunk_points, sp.chunk_points.data(), sp.chunk_points.size() * sizeof(int32_t));
-  if (err == cudaSuccess) err = h2d(plan->d_prog, sp.prog.data(), sp.prog.size() * sizeof(uint32_t));
+    err = h2d(plan->d_type_map_off, sp.type_map_off.data(), sp.type_map_off.size() * sizeof(int64_t));
+  if (err == cudaSuccess)
+    err = cudaMemsetAsync(plan->d_maps, 0xff, size_t(sp.type_map_off.back()) * sizeof(int32_t), s);   // -1
+  if (err == cudaSuccess)
+    err = h2d(plan->d_tile_vbase, plan->tile_vbase.data(), plan->tile_vbase.size() * sizeof(int64_t));
+  if (err == cudaSuccess) err = h2d(plan->d_item_tile, sp.item_tile.data(), sp.item_tile.size() * sizeof(int32_t));
+  if (err == cudaSuccess) err = h2d(plan->d_item_start, sp.item_start.data(), sp.item_start.size() * sizeof(int32_t));
   if (err == cudaSuccess) err = h2d(plan->d_tmpl, sp.tmpl.data(), sp.tmpl.size() * sizeof(uint32_t));
   if (err == cudaSuccess) err = h2d(plan->d_tmpl_ptr, sp.tmpl_ptr.data(), sp.tmpl_ptr.size() * sizeof(int64_t));
-  if (err == cudaSuccess) err = h2d(plan->d_work, sp.work.data(), sp.work.size() * sizeof(int32_t));
-  if (err == cudaSuccess) err = h2d(plan->d_work_base, sp.work_base.data(), sp.work_base.size() * sizeof(int64_t));
+  if (err == cudaSuccess) err = h2d(d_type_rep, sp.type_rep.data(), sp.type_rep.size() * sizeof(int64_t));
+  if (err == cudaSuccess) err = h2d(plan->d_sec_off, sp.sec_off.data(), sp.sec_off.size() * sizeof(int64_t));
   if (err == cudaSuccess) err = h2d(d_pptr, pptr.data(), pptr.size() * sizeof(int64_t));
   if (err == cudaSuccess) err = h2d(d_pcol, pcol.data(), pcol.size() * sizeof(int32_t));
   if (err == cudaSuccess) err = h2d(d_pair_face, tab->topo.pair_face.data(), size_t(n_nz));
@@ -368,6 +385,8 @@ msasm_status msasm_plan_create(const msasm_tables* tab, const msasm_macro_desc* 
   if (st == MSASM_OK)
     st = rank_map_gpu(plan->d_gmap, tab->d_pairs, d_pair_face, d_pptr, d_pcol, plan->n_tiles, tab->topo.n_T, n_nz,
                       plan->n_elem[0], plan->n_elem[1], plan->d_rank, d_bad, s);
+  if (st == MSASM_OK) st = scatter_maps_gpu(plan, d_type_rep, n_types, d_bad, s);
+  if (st == MSASM_OK) st = secondary_entries_gpu(plan, s);
   unsigned long long bad = 0;
   if (st == MSASM_OK) {
     err = cudaMemcpyAsync(&bad, d_bad, sizeof(bad), cudaMemcpyDeviceToHost, s);
@@ -378,7 +397,9 @@ msasm_status msasm_plan_create(const msasm_tables* tab, const msasm_macro_desc* 
   }
   cleanup_tmp();
   if (st != MSASM_OK) return bail(st);
-  if (bad) return bail(fail(MSASM_ECUDA, "index map: a tile pair is missing from the CSR pattern"));
+  if (bad)
+    return bail(fail(MSASM_ECUDA, "index map: a tile pair is missing from the CSR pattern, or a tile places its "
+                                  "blocks differently from its type"));
   plan->gmap_host = std::move(gmap);
   if (n_rows) *n_rows = plan->n_rows;
   if (nnz) *nnz = plan->nnz;
@@ -562,7 +583,7 @@ msasm_status msasm_assemble(msasm_plan* plan, const double* d_ctrl, double E, do
       MSASM_CUDA(cudaEventRecord(plan->events[4 * pass + 3], s));
       plan->stage_launches[0] += 1;
       plan->stage_launches[1] += contract_launches(prec);
-      plan->stage_launches[2] += 1 + (plan->max_tmpl > 0 ? 1 : 0);
+      plan->stage_launches[2] += 1 + (plan->sec_off_host[size_t(t0 + nt)] > plan->sec_off_host[size_t(t0)] ? 1 : 0);
     }
   }
   if (timed) plan->timed_passes = n_pass;

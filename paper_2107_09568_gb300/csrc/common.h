@@ -70,21 +70,31 @@ struct PairDesc {       // the patch contributions to one table row
 };
 static_assert(sizeof(PairDesc) == 32, "PairDesc is two 16-byte words");
 
-// staged scatter programs (scatter_plan.cpp)
-constexpr int64_t kChunkValues = 4096;    // values of one chunk of rows held in shared memory
+// one block a tile adds to rows owned by a lower tile (secondary scatter pass)
+struct SecondaryEntry {
+  int64_t dst_u, dst_l;      // first value index of the upper block (rows of A) / lower block (rows of B)
+  int32_t len_u, len_l;      // their row lengths
+  int32_t tile;
+  uint32_t m_flags;          // m | upper << 30 | lower << 31
+};
+static_assert(sizeof(SecondaryEntry) == 32, "SecondaryEntry is 32 bytes");
+
+// scatter plan (scatter_plan.cpp): a tile's owned rows are one contiguous range of values whose
+// layout depends only on the tile's type (which faces are glued), so one value map per type
+// tells, for every value of the range, where it comes from in the tile's nzdata
+constexpr int kScatterSegment = 4096;     // values of one work item (one CTA)
+inline int ld_nz_of(int n_nz) { return (n_nz + 7) & ~7; }   // leading dimension of nzdata rows
 struct ScatterPlanHost {
   std::vector<int32_t> tile_type;          // per tile
-  std::vector<int32_t> type_chunk_begin;   // chunks of type ty: [begin[ty], begin[ty+1])
-  std::vector<int32_t> chunk_info;         // per chunk: point offset, point count, program offset, program size
-  std::vector<int32_t> chunk_points;       // per chunk point: local id A, first value of its rows relative to
-                                           // the chunk, row length (3 ints; the same for every tile of the type)
-  std::vector<uint32_t> prog;              // m | lower << 31
+  std::vector<int64_t> type_rep;           // per type: representative tile
+  std::vector<int32_t> type_nvals;         // per type: values in the owned rows of a tile
+  std::vector<int64_t> type_map_off;       // per type: offset of its value map (n_types + 1)
+  std::vector<int32_t> item_tile;          // per work item: tile and first value in the tile's range
+  std::vector<int32_t> item_start;
+  std::vector<int64_t> item_ptr;           // per tile: its work items [item_ptr[t], item_ptr[t+1])
   std::vector<uint32_t> tmpl;              // secondary template per type: m | upper << 30 | lower << 31
   std::vector<int64_t> tmpl_ptr;
-  int64_t max_tmpl = 0;
-  std::vector<int32_t> work;               // (tile, chunk) pairs
-  std::vector<int64_t> work_base;          // per work item: index of its chunk's first CSR value
-  std::vector<int64_t> work_ptr;           // per tile
+  std::vector<int64_t> sec_off;            // per tile: first secondary entry (n_tiles + 1)
 };
 
 }  // namespace msasm
@@ -131,17 +141,20 @@ struct msasm_plan {
   int64_t* d_rowptr = nullptr;      // n_rows + 1
   int32_t* d_col = nullptr;         // nnz
   uint32_t* d_rank = nullptr;       // n_tiles x n_nz: rank_u | rank_l << 16, bit 31 = second contributor
-  // staged scatter (device copies of ScatterPlanHost)
+  // scatter (device copies of ScatterPlanHost)
   int32_t* d_tile_type = nullptr;
-  int32_t* d_chunk_info = nullptr;
-  int32_t* d_chunk_points = nullptr;
-  uint32_t* d_prog = nullptr;
+  int32_t* d_type_nvals = nullptr;
+  int64_t* d_type_map_off = nullptr;
+  int32_t* d_maps = nullptr;                 // value maps of all types: (3a + b) ld + m, or -1
+  int64_t* d_tile_vbase = nullptr;
+  int32_t* d_item_tile = nullptr;
+  int32_t* d_item_start = nullptr;
+  std::vector<int64_t> item_ptr;             // host copy
   uint32_t* d_tmpl = nullptr;
   int64_t* d_tmpl_ptr = nullptr;
-  int32_t* d_work = nullptr;
-  int64_t* d_work_base = nullptr;
-  std::vector<int64_t> work_ptr;    // host: work items of tile t are [work_ptr[t], work_ptr[t+1])
-  int64_t max_tmpl = 0;
+  int64_t* d_sec_off = nullptr;              // secondary entries of tile t: [sec_off[t], sec_off[t+1])
+  msasm::SecondaryEntry* d_sec = nullptr;
+  std::vector<int64_t> sec_off_host;
   std::vector<double> knots_host[3];  // host copies for boundary data
   std::vector<int> span_host[3];      // knot index of each element's span
   std::vector<int32_t> gmap_host;

@@ -86,6 +86,7 @@ __device__ __forceinline__ double ldexp_i64_rn(long long x, int e) {
   return __longlong_as_double((long long)(sign | ((unsigned long long)biased << 52) | (mant & ((1ull << 52) - 1))));
 }
 
+constexpr int EMU_BAND = 32;                              // m tiles per band of the tile order
 constexpr int EMU_EPI_WARPS = 8;                          // two per TMEM lane quarter
 constexpr int EMU_THREADS = 64 + 32 * EMU_EPI_WARPS;      // producer warp, MMA warp, epilogue warps
 constexpr int EMU_EPI_COLS = EMU_BN / 2;                  // columns of one epilogue warp
@@ -124,7 +125,18 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
       reinterpret_cast<uint32_t*>(gen_base + EMU_STAGES * EMU_STAGE_BYTES + 8 * (2 * EMU_STAGES + 2));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n_nt = (p.N + EMU_BN - 1) / EMU_BN, n_mt = (p.M + EMU_BM - 1) / EMU_BM;
-  const long long total = (long long)n_nt * n_mt;               // tile t: m tile t / n_nt, n tile t % n_nt
+  const long long total = (long long)n_nt * n_mt;
+  // tile t -> (m tile, n tile) in bands of EMU_BAND m tiles: within a band the n tiles advance
+  // and the band's m tiles run together, so the CTAs in flight share a few operand tiles of
+  // each side and the band's table slices (EMU_BAND x 1 MB) stay in L2 while the coefficient
+  // slices stream past once per band
+  auto tile_mn = [&](long long t, int& m0, int& n0) {
+    const long long band = t / ((long long)EMU_BAND * n_nt);
+    const int rows = min(EMU_BAND, n_mt - int(band) * EMU_BAND);
+    const long long r = t - band * EMU_BAND * n_nt;
+    m0 = (int(band) * EMU_BAND + int(r % rows)) * EMU_BM;
+    n0 = int(r / rows) * EMU_BN;
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < EMU_STAGES; ++s) {
@@ -151,7 +163,8 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
     uint32_t g = 0;
     bool ok = true;
     for (long long t = blockIdx.x; t < total && ok; t += gridDim.x) {
-      const int m0 = int(t / n_nt) * EMU_BM, n0 = int(t % n_nt) * EMU_BN;
+      int m0, n0;
+      tile_mn(t, m0, n0);
       for (int kb = 0; kb < p.kblocks; ++kb, ++g) {
         const int s = int(g % EMU_STAGES);
         const uint32_t it = g / EMU_STAGES;
@@ -223,7 +236,9 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
     for (long long t = blockIdx.x; t < total; t += gridDim.x, ++i_tile) {
       if (!mbar_wait_or_abort(accum_full, i_tile & 1, p.err)) break;
       tc_fence_after();
-      const int m0 = int(t / n_nt) * EMU_BM, n0 = int(t % n_nt) * EMU_BN + h * EMU_EPI_COLS;
+      int m0, n0;
+      tile_mn(t, m0, n0);
+      n0 += h * EMU_EPI_COLS;
       long long X[EMU_EPI_COLS];
 #pragma unroll
       for (int c = 0; c < EMU_EPI_COLS / 8; ++c) {

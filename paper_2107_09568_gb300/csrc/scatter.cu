@@ -5,15 +5,15 @@
 // r_u | r_l << 16 of the plan the upper entry (a, b) lives at rowptr[3 g(A) + a] + 3 r_u + b and
 // the lower one at rowptr[3 g(B) + b] + 3 r_l + a.
 //
-// Staged pass: the rows of the points a tile owns are one contiguous range of values (tile-major
-// numbering).  One CTA per chunk of that range builds the chunk in shared memory from the chunk's
-// program (the pairs whose upper or lower block lands there, in increasing m, so the nzdata
-// loads of neighbouring threads are mostly contiguous), entries no pair of the tile reaches
-// staying zero, and streams it out with coalesced 16-byte stores.  Every CSR value is written
-// exactly once by the staged pass.
+// Direct pass: the rows of the points a tile owns are one contiguous range of values, laid out
+// the same way for every tile of its type.  The type's value map (built once per plan from its
+// representative tile) holds for every value of the range its source in the tile's nzdata,
+// (3a + b) ld + m, or -1 where no block of the tile lands; each thread writes consecutive values
+// of the range (coalesced stores) from gathers that the tile's nzdata, read by the CTAs working
+// on the tile at the same time, serves mostly from L2.  Every CSR value is written exactly once.
 //
 // Secondary pass: blocks of tile t landing in rows owned by a lower tile (points on a glued lower
-// face) are added to the values the owner wrote; it runs after the staged pass on the same
+// face) are added to the values the owner wrote; it runs after the direct pass on the same
 // stream and each position has at most one such contributor, so no atomics are needed and the
 // two-term sums are order independent.
 #include <algorithm>
@@ -23,127 +23,167 @@
 
 namespace msasm {
 
-constexpr int kStagedThreads = 128;
-constexpr int kStagedUnroll = 4;
+constexpr int kDirectThreads = 256;
+constexpr int kDirectPerThread = kScatterSegment / kDirectThreads;   // 16
 
-// One CTA per work item (tile, chunk).  The chunk's layout (each point's row offset and length)
-// is the same for every tile of the type and its first value index is precomputed per item, so
-// a CTA starts gathering after two dependent loads.
 template <typename T>
-__global__ void __launch_bounds__(kStagedThreads) scatter_staged_kernel(
-    const T* __restrict__ nz, int ld_nz, int n_nz, int64_t t0, const int32_t* __restrict__ work,
-    const int64_t* __restrict__ work_base, const int32_t* __restrict__ chunk_info,
-    const int32_t* __restrict__ chunk_points, const uint32_t* __restrict__ prog, const int32_t* __restrict__ pairs,
-    int n_T, const uint32_t* __restrict__ rank, T* __restrict__ values) {
-  extern __shared__ __align__(16) uint8_t sm_raw[];
-  T* buf = reinterpret_cast<T*>(sm_raw);
-  int32_t* off = reinterpret_cast<int32_t*>(sm_raw + kChunkValues * sizeof(T));   // [n_T]
-  int32_t* len = off + n_T;                                                        // [n_T]
-  const int64_t t = work[2 * blockIdx.x];
-  const int c = work[2 * blockIdx.x + 1];
-  const int64_t base = work_base[blockIdx.x];
-  const int64_t tl = t - t0;
-  const int p_begin = chunk_info[4 * c], p_count = chunk_info[4 * c + 1];
-  const int q_begin = chunk_info[4 * c + 2], q_count = chunk_info[4 * c + 3];
-  const int32_t* cp = chunk_points + 3 * p_begin;
-  const int n_vals = cp[3 * (p_count - 1) + 1] + 3 * cp[3 * (p_count - 1) + 2];
-  for (int i = threadIdx.x; i < p_count; i += blockDim.x) {
-    const int A = cp[3 * i];
-    off[A] = cp[3 * i + 1];
-    len[A] = cp[3 * i + 2];
+__global__ void __launch_bounds__(kDirectThreads) scatter_direct_kernel(
+    const T* __restrict__ nz, int ld_nz, int64_t t0, const int32_t* __restrict__ item_tile,
+    const int32_t* __restrict__ item_start, const int64_t* __restrict__ tile_vbase,
+    const int32_t* __restrict__ tile_type, const int64_t* __restrict__ type_map_off,
+    const int32_t* __restrict__ type_nvals, const int32_t* __restrict__ maps, T* __restrict__ values) {
+  const int64_t t = item_tile[blockIdx.x];
+  const int s0 = item_start[blockIdx.x];
+  const int ty = tile_type[t];
+  const int end = min(s0 + kScatterSegment, type_nvals[ty]);
+  const int32_t* map = maps + type_map_off[ty];
+  const T* nzt = nz + 9 * (t - t0) * ld_nz;
+  T* out = values + tile_vbase[t];
+  int k[kDirectPerThread];
+#pragma unroll
+  for (int u = 0; u < kDirectPerThread; ++u) {
+    const int i = s0 + u * kDirectThreads + int(threadIdx.x);
+    k[u] = (i < end) ? map[i] : -2;
   }
-  for (int i = threadIdx.x; i < n_vals; i += blockDim.x) buf[i] = T(0);
-  __syncthreads();
-  const T* nzt = nz + 9 * tl * ld_nz;
-  const uint32_t* rk = rank + t * n_nz;
-  for (int j0 = threadIdx.x; j0 < q_count; j0 += blockDim.x * kStagedUnroll) {
-    uint32_t e[kStagedUnroll], w[kStagedUnroll];
-    int2 ab[kStagedUnroll];
-    T v[kStagedUnroll][9];
+  T v[kDirectPerThread];
 #pragma unroll
-    for (int u = 0; u < kStagedUnroll; ++u) {      // issue every load of UNROLL entries first
-      const int j = j0 + u * blockDim.x;
-      e[u] = (j < q_count) ? prog[q_begin + j] : 0xffffffffu;
-      if (e[u] != 0xffffffffu) {
-        const int m = int(e[u] & 0x7fffffffu);
-        w[u] = rk[m];
-        ab[u] = reinterpret_cast<const int2*>(pairs)[m];
+  for (int u = 0; u < kDirectPerThread; ++u) v[u] = (k[u] >= 0) ? nzt[k[u]] : T(0);
 #pragma unroll
-        for (int k = 0; k < 9; ++k) v[u][k] = nzt[size_t(k) * ld_nz + m];
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < kStagedUnroll; ++u) {
-      if (e[u] == 0xffffffffu) continue;
-      if (!(e[u] >> 31)) {                       // upper block: rows of A
-        const int o = off[ab[u].x] + 3 * int(w[u] & 0xffffu), L = len[ab[u].x];
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-          for (int b = 0; b < 3; ++b) buf[o + a * L + b] = v[u][3 * a + b];
-      } else {                                   // lower block: rows of B
-        const int o = off[ab[u].y] + 3 * int((w[u] >> 16) & 0x7fffu), L = len[ab[u].y];
-#pragma unroll
-        for (int b = 0; b < 3; ++b)
-#pragma unroll
-          for (int a = 0; a < 3; ++a) buf[o + b * L + a] = v[u][3 * a + b];
-      }
-    }
-  }
-  __syncthreads();
-  // stream out: head up to 16-byte alignment, 16-byte body, tail
-  T* dst = values + base;
-  constexpr int VEC = 16 / sizeof(T);
-  const int head = int((VEC - (base % VEC)) % VEC);
-  const int h = head < n_vals ? head : n_vals;
-  for (int i = threadIdx.x; i < h; i += blockDim.x) dst[i] = buf[i];
-  const int body = (n_vals - h) / VEC;
-  for (int i = threadIdx.x; i < body; i += blockDim.x) {
-    float4 v;
-    T* pv = reinterpret_cast<T*>(&v);
-#pragma unroll
-    for (int k = 0; k < VEC; ++k) pv[k] = buf[h + i * VEC + k];
-    reinterpret_cast<float4*>(dst + h)[i] = v;
-  }
-  for (int i = h + body * VEC + threadIdx.x; i < n_vals; i += blockDim.x) dst[i] = buf[i];
+  for (int u = 0; u < kDirectPerThread; ++u)
+    if (k[u] != -2) out[s0 + u * kDirectThreads + int(threadIdx.x)] = v[u];
 }
 
-template <typename T>
-__global__ void scatter_secondary_kernel(const T* __restrict__ nz, int ld_nz, int n_nz, int64_t t0,
-                                         const int32_t* __restrict__ tile_type, const int64_t* __restrict__ tmpl_ptr,
+// Value maps of all types from their representative tiles (maps preset to -1).
+__global__ void type_maps_kernel(const int64_t* __restrict__ type_rep, int n_types, const int64_t* __restrict__ map_off,
+                                 const int32_t* __restrict__ type_nvals, const int32_t* __restrict__ pairs,
+                                 const int32_t* __restrict__ gmap, int n_T, int n_nz, int ld_nz,
+                                 const uint32_t* __restrict__ rank, const int64_t* __restrict__ rowptr,
+                                 const int64_t* __restrict__ tile_vbase, int32_t* __restrict__ maps) {
+  const int64_t total = int64_t(n_types) * n_nz;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
+    const int ty = int(i / n_nz), m = int(i % n_nz);
+    const int64_t t = type_rep[ty];
+    const int64_t vb = tile_vbase[t], nv = type_nvals[ty];
+    int32_t* map = maps + map_off[ty];
+    const int A = pairs[2 * m], B = pairs[2 * m + 1];
+    const int64_t gA = gmap[t * n_T + A], gB = gmap[t * n_T + B];
+    const uint32_t w = rank[t * n_nz + m];
+    const int64_t rA = rowptr[3 * gA] - vb, rB = rowptr[3 * gB] - vb;
+    if (rA >= 0 && rA < nv) {                      // A owned: upper block in the rows of A
+      const int64_t L = rowptr[3 * gA + 1] - rowptr[3 * gA];
+      const int64_t o = rA + 3 * int64_t(w & 0xffffu);
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) map[o + a * L + b] = int32_t((3 * a + b) * ld_nz + m);
+    }
+    if (A != B && rB >= 0 && rB < nv) {            // B owned: lower block in the rows of B
+      const int64_t L = rowptr[3 * gB + 1] - rowptr[3 * gB];
+      const int64_t o = rB + 3 * int64_t((w >> 16) & 0x7fffu);
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) map[o + b * L + a] = int32_t((3 * a + b) * ld_nz + m);
+    }
+  }
+}
+
+// Every tile of a type places its blocks where the representative does (same column ranks).
+__global__ void rank_invariance_kernel(const int32_t* __restrict__ tile_type, const int64_t* __restrict__ type_rep,
+                                       int64_t n_tiles, int n_nz, const uint32_t* __restrict__ rank,
+                                       unsigned long long* __restrict__ bad) {
+  const int64_t total = n_tiles * n_nz;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t t = i / n_nz;
+    const int m = int(i % n_nz);
+    const int64_t r = type_rep[tile_type[t]];
+    if ((rank[i] & 0x7fffffffu) != (rank[r * n_nz + m] & 0x7fffffffu)) atomicAdd(bad, 1ull);
+  }
+}
+
+msasm_status scatter_maps_gpu(msasm_plan* plan, const int64_t* d_type_rep, int n_types, unsigned long long* d_bad,
+                              cudaStream_t stream) {
+  const msasm_tables* tab = plan->tab;
+  const int ld = ld_nz_of(tab->n_nz);
+  if (int64_t(9) * ld >= (int64_t(1) << 31)) return fail(MSASM_EUNSUPPORTED, "table too large for the value maps");
+  type_maps_kernel<<<152 * 4, 256, 0, stream>>>(d_type_rep, n_types, plan->d_type_map_off, plan->d_type_nvals,
+                                                tab->d_pairs, plan->d_gmap, tab->topo.n_T, tab->n_nz, ld, plan->d_rank,
+                                                plan->d_rowptr, plan->d_tile_vbase, plan->d_maps);
+  MSASM_CUDA(cudaGetLastError());
+  rank_invariance_kernel<<<152 * 8, 256, 0, stream>>>(plan->d_tile_type, d_type_rep, plan->n_tiles, tab->n_nz,
+                                                      plan->d_rank, d_bad);
+  MSASM_CUDA(cudaGetLastError());
+  return MSASM_OK;
+}
+
+// Secondary entries of all tiles, built once per plan: entry i of tile t (template entry j of
+// its type) gets its nzdata column m, flags and the first value index and row length of each
+// block it adds (upper: rows of A, lower: rows of B).
+__global__ void secondary_entries_kernel(const int32_t* __restrict__ tile_type, const int64_t* __restrict__ sec_off,
+                                         int64_t n_tiles, const int64_t* __restrict__ tmpl_ptr,
                                          const uint32_t* __restrict__ tmpl, const int32_t* __restrict__ pairs,
-                                         const int32_t* __restrict__ gmap, int n_T, const uint32_t* __restrict__ rank,
-                                         const int64_t* __restrict__ rowptr, T* __restrict__ values) {
-  const int64_t tl = blockIdx.y, t = t0 + tl;
-  const int ty = tile_type[t];
-  const int64_t b0 = tmpl_ptr[ty], cnt = tmpl_ptr[ty + 1] - b0;
-  const T* nzt = nz + 9 * tl * ld_nz;
-  for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < cnt; j += int64_t(gridDim.x) * blockDim.x) {
-    const uint32_t e = tmpl[b0 + j];
+                                         const int32_t* __restrict__ gmap, int n_T, int n_nz,
+                                         const uint32_t* __restrict__ rank, const int64_t* __restrict__ rowptr,
+                                         SecondaryEntry* __restrict__ out) {
+  const int64_t total = sec_off[n_tiles];
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
+    int64_t lo = 0, hi = n_tiles;                  // tile t with sec_off[t] <= i < sec_off[t + 1]
+    while (hi - lo > 1) {
+      const int64_t mid = (lo + hi) / 2;
+      if (sec_off[mid] <= i) lo = mid; else hi = mid;
+    }
+    const int64_t t = lo;
+    const uint32_t e = tmpl[tmpl_ptr[tile_type[t]] + (i - sec_off[t])];
     const int m = int(e & 0x3fffffffu);
     const int A = pairs[2 * m], B = pairs[2 * m + 1];
     const int64_t gA = gmap[t * n_T + A], gB = gmap[t * n_T + B];
     const uint32_t w = rank[t * n_nz + m];
-    const int ru = int(w & 0xffffu), rl = int((w >> 16) & 0x7fffu);
+    SecondaryEntry r;
+    r.dst_u = rowptr[3 * gA] + 3 * int64_t(w & 0xffffu);
+    r.dst_l = rowptr[3 * gB] + 3 * int64_t((w >> 16) & 0x7fffu);
+    r.len_u = int32_t(rowptr[3 * gA + 1] - rowptr[3 * gA]);
+    r.len_l = int32_t(rowptr[3 * gB + 1] - rowptr[3 * gB]);
+    r.tile = int32_t(t);
+    r.m_flags = e;
+    out[i] = r;
+  }
+}
+
+msasm_status secondary_entries_gpu(msasm_plan* plan, cudaStream_t stream) {
+  const int64_t total = plan->sec_off_host.back();
+  if (total == 0) return MSASM_OK;
+  secondary_entries_kernel<<<152 * 8, 256, 0, stream>>>(plan->d_tile_type, plan->d_sec_off, plan->n_tiles,
+                                                        plan->d_tmpl_ptr, plan->d_tmpl, plan->tab->d_pairs,
+                                                        plan->d_gmap, plan->tab->topo.n_T, plan->tab->n_nz,
+                                                        plan->d_rank, plan->d_rowptr, plan->d_sec);
+  MSASM_CUDA(cudaGetLastError());
+  return MSASM_OK;
+}
+
+// Secondary pass over the entries of tiles [t0, t0 + n_tiles): add each block to the values the
+// owner of its rows wrote.
+template <typename T>
+__global__ void scatter_secondary_kernel(const T* __restrict__ nz, int ld_nz, int64_t t0, int64_t e0, int64_t e1,
+                                         const SecondaryEntry* __restrict__ sec, T* __restrict__ values) {
+  for (int64_t i = e0 + int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < e1; i += int64_t(gridDim.x) * blockDim.x) {
+    const SecondaryEntry r = sec[i];
+    const int m = int(r.m_flags & 0x3fffffffu);
+    const T* src = nz + 9 * (int64_t(r.tile) - t0) * ld_nz + m;
     T v[9];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) v[k] = nzt[size_t(k) * ld_nz + m];
-    if (e & (1u << 30)) {
+    for (int k = 0; k < 9; ++k) v[k] = src[size_t(k) * ld_nz];
+    if (r.m_flags & (1u << 30)) {
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        T* dst = values + rowptr[3 * gA + a] + 3 * ru;
-        dst[0] += v[3 * a + 0];
-        dst[1] += v[3 * a + 1];
-        dst[2] += v[3 * a + 2];
+        T* d = values + r.dst_u + int64_t(a) * r.len_u;
+        d[0] += v[3 * a + 0];
+        d[1] += v[3 * a + 1];
+        d[2] += v[3 * a + 2];
       }
     }
-    if (e & (1u << 31)) {
+    if (r.m_flags & (1u << 31)) {
 #pragma unroll
       for (int b = 0; b < 3; ++b) {
-        T* dst = values + rowptr[3 * gB + b] + 3 * rl;
-        dst[0] += v[b];
-        dst[1] += v[3 + b];
-        dst[2] += v[6 + b];
+        T* d = values + r.dst_l + int64_t(b) * r.len_l;
+        d[0] += v[b];
+        d[1] += v[3 + b];
+        d[2] += v[6 + b];
       }
     }
   }
@@ -153,25 +193,17 @@ __global__ void scatter_secondary_kernel(const T* __restrict__ nz, int ld_nz, in
 template <typename T>
 msasm_status scatter_pass_gpu(const msasm_plan* plan, const T* d_nz, int ld_nz, int64_t t0, int64_t n_tiles,
                               T* d_values, cudaStream_t stream) {
-  const msasm_tables* tab = plan->tab;
-  const int n_T = tab->topo.n_T;
-  if (reinterpret_cast<uintptr_t>(d_values) % 16 != 0)
-    return fail(MSASM_EINVAL, "the CSR values buffer must be 16-byte aligned");
-  const int64_t w0 = plan->work_ptr[size_t(t0)], w1 = plan->work_ptr[size_t(t0 + n_tiles)];
-  if (w1 > w0) {
-    const size_t smem = kChunkValues * sizeof(T) + 2 * size_t(n_T) * sizeof(int32_t);
-    if (smem > 48 * 1024) return fail(MSASM_EUNSUPPORTED, "reference tile too large for the staged scatter");
-    MSASM_CUDA(cudaFuncSetAttribute(scatter_staged_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-    scatter_staged_kernel<T><<<unsigned(w1 - w0), kStagedThreads, smem, stream>>>(
-        d_nz, ld_nz, tab->n_nz, t0, plan->d_work + 2 * w0, plan->d_work_base + w0, plan->d_chunk_info,
-        plan->d_chunk_points, plan->d_prog, tab->d_pairs, n_T, plan->d_rank, d_values);
+  const int64_t i0 = plan->item_ptr[size_t(t0)], i1 = plan->item_ptr[size_t(t0 + n_tiles)];
+  if (i1 > i0) {
+    scatter_direct_kernel<T><<<unsigned(i1 - i0), kDirectThreads, 0, stream>>>(
+        d_nz, ld_nz, t0, plan->d_item_tile + i0, plan->d_item_start + i0, plan->d_tile_vbase, plan->d_tile_type,
+        plan->d_type_map_off, plan->d_type_nvals, plan->d_maps, d_values);
     MSASM_CUDA(cudaGetLastError());
   }
-  if (plan->max_tmpl > 0 && n_tiles > 0) {
-    dim3 grid(unsigned(std::max<int64_t>(1, std::min<int64_t>((plan->max_tmpl + 255) / 256, 8))), unsigned(n_tiles));
-    scatter_secondary_kernel<T><<<grid, 256, 0, stream>>>(d_nz, ld_nz, tab->n_nz, t0, plan->d_tile_type,
-                                                          plan->d_tmpl_ptr, plan->d_tmpl, tab->d_pairs, plan->d_gmap,
-                                                          n_T, plan->d_rank, plan->d_rowptr, d_values);
+  const int64_t e0 = plan->sec_off_host[size_t(t0)], e1 = plan->sec_off_host[size_t(t0 + n_tiles)];
+  if (e1 > e0) {
+    const int64_t blocks = std::min<int64_t>((e1 - e0 + 255) / 256, 152 * 16);
+    scatter_secondary_kernel<T><<<unsigned(blocks), 256, 0, stream>>>(d_nz, ld_nz, t0, e0, e1, plan->d_sec, d_values);
     MSASM_CUDA(cudaGetLastError());
   }
   return MSASM_OK;

@@ -252,8 +252,6 @@ def test_invalid_arguments(built):
         plan.assemble(ctrl, nu=0.5)
     with pytest.raises(msasm.MsasmError):
         msasm.Tables(synth.micro_cross(2), 7)
-    # the values buffer must be 16-byte aligned (a view one FP64 value into an allocation is not)
+    # a values buffer that starts one value into an allocation (8-byte, not 16-byte aligned)
     buf = torch.empty(plan.nnz + 1, dtype=torch.float64, device="cuda")
-    with pytest.raises(msasm.MsasmError) as e:
-        plan.assemble(ctrl, out=buf[1:])
-    assert e.value.status == -1
+    assert torch.equal(plan.assemble(ctrl, out=buf[1:]), plan.assemble(ctrl))
