@@ -47,7 +47,8 @@ __global__ void __launch_bounds__(kDirectThreads) scatter_direct_kernel(
   }
   T v[kDirectPerThread];
 #pragma unroll
-  for (int u = 0; u < kDirectPerThread; ++u) v[u] = (k[u] >= 0) ? nzt[k[u]] : T(0);
+  for (int u = 0; u < kDirectPerThread; ++u) v[u] = (k[u] >= 0) ? __ldg(nzt + k[u]) : T(0);
+  asm volatile("" ::: "memory");                  // every gather is issued before the first store
 #pragma unroll
   for (int u = 0; u < kDirectPerThread; ++u)
     if (k[u] != -2) out[s0 + u * kDirectThreads + int(threadIdx.x)] = v[u];
