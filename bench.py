@@ -376,7 +376,7 @@ def main():
     K = 9 * tab.n_pi
     flops = contraction_flops(tab.n_nz, tab.n_pi, plan.n_tiles)
     nz_bytes = 9 * plan.n_tiles * tab.n_nz * vbytes
-    scatter_bytes = nz_bytes + plan.n_tiles * tab.n_nz * 4 + plan.nnz * vbytes   # nz read, rank map, values write
+    scatter_bytes = nz_bytes + plan.nnz * vbytes                   # nzdata read, values written (once each)
     pull_bytes = 9 * plan.n_tiles * K * 8
     if names[dom] == "contraction" and prec in ("f64", "f32"):
         alu_peak = FP64_ALU_PEAK_TFLOPS if prec == "f64" else FP32_ALU_PEAK_TFLOPS
