@@ -158,10 +158,13 @@ msasm_status msasm_assemble_host(msasm_plan* plan, const double* h_ctrl, double 
  *   d_u           (n_rows values): L = u^T K u, the internal-work term of eq. 69-70
  *                 (with f fixed and u = K^-1 f the compliance gradient is -dL/dP);
  *   d_grad_values (nnz values): dL/dvalues of an arbitrary L (the chain through step 4).
- * Both are FP64 for MSASM_F64 / MSASM_F64_EMU and FP32 otherwise; the contraction of the
- * table with u (W = mat[K]^T G, eq. 73) then runs in FP64 or FP32 on the CUDA cores, and
- * the chain rule through |det J| and J^-1 to the control points is FP64.
- * d_grad_ctrl (n_ctrl*3 FP64) is overwritten.  Errors: EINVAL, ECUDA. */
+ * Both are FP64 for MSASM_F64 / MSASM_F64_EMU and FP32 otherwise.  The contraction of the
+ * table with u (W = mat[K]^T G, eq. 73) runs in FP64 on the CUDA cores (MSASM_F64), as
+ * sliced BF16 products on the tensor cores in chunks of 576 pairs summed in FP64
+ * (MSASM_F64_EMU: each row of G is kept to 49 bits of its largest entry, about 1e-11
+ * relative on a bending state), or in FP32 (other precisions); the chain rule through
+ * |det J| and J^-1 to the control points is FP64.
+ * d_grad_ctrl (n_ctrl*3 FP64) is overwritten.  Errors: EINVAL, EUNSUPPORTED, ECUDA. */
 msasm_status msasm_assemble_grad(msasm_plan* plan, const double* d_ctrl, double E, double nu,
                                  msasm_precision prec, const void* d_u, const void* d_grad_values,
                                  double* d_grad_ctrl, void* stream);

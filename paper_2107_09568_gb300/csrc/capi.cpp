@@ -60,9 +60,10 @@ msasm_status adjoint_pullback_gpu(const msasm_plan* plan, const double* d_ctrl, 
 int tc_kind_of(msasm_precision prec);
 int emu_kpad(int K);
 size_t emu_slice_bytes(int64_t rows, int K);
-msasm_status emu_slice_gpu(const double* x, int64_t rows, int K, void* slices, int* scale_exp, cudaStream_t s);
+msasm_status emu_slice_gpu(const double* x, int64_t rows, int64_t ldx, int K, void* slices, int* scale_exp,
+                           cudaStream_t s);
 msasm_status contract_emu_gpu(const void* a_slices, const int* a_exp, int M, const void* b_slices, const int* b_exp,
-                              int64_t N, int K, double* out, int ld, unsigned* d_err, cudaStream_t s);
+                              int64_t N, int K, double* out, int ld, bool accumulate, unsigned* d_err, cudaStream_t s);
 int tc_kpad(int K, int kind);
 size_t tc_slice_bytes(int64_t rows, int K, int kind);
 msasm_status tc_split_gpu(const double* x, int64_t rows, int K, int kind, void* hi, void* lo, float* row_scale,
@@ -114,6 +115,7 @@ msasm_plan::~msasm_plan() {
   cudaFree(d_coef);
   cudaFree(d_nz);
   cudaFree(d_coef_lp);
+  cudaFree(d_adj_lp);
   cudaFree(d_degenerate);
   cudaFree(d_tc_err);
   cudaFree(d_ctrl_stage);
@@ -471,7 +473,8 @@ static msasm_status ensure_table_slices(msasm_tables* tab, int kind, cudaStream_
 static size_t coef_lp_bytes_for(int64_t n_tiles, int n_pi) {
   const int K = 9 * n_pi;
   const size_t split = 2 * size_t(9 * n_tiles) * size_t(K + 64) * 4 + size_t(9 * n_tiles) * 4;
-  const size_t emu = emu_slice_bytes(9 * n_tiles, K) + size_t(9 * n_tiles) * 8;
+  // the emulated forms slice rows of K values (assembly) or of 576-pair chunks (adjoint)
+  const size_t emu = emu_slice_bytes(9 * n_tiles, std::max(K, 576)) + size_t(9 * n_tiles) * 8;
   return std::max(split, emu) + 512;
 }
 
@@ -510,14 +513,14 @@ static msasm_status contract_dispatch(const msasm_tables* ctab, msasm_precision 
       if (!tab->d_Tslices) {
         MSASM_CUDA(cudaMalloc(&tab->d_Tslices, emu_slice_bytes(n_nz, K)));
         MSASM_CUDA(cudaMalloc(&tab->d_Tslice_scale, size_t(n_nz) * sizeof(int)));
-        MSASM_TRY(emu_slice_gpu(tab->d_T, n_nz, K, tab->d_Tslices, tab->d_Tslice_scale, s));
+        MSASM_TRY(emu_slice_gpu(tab->d_T, n_nz, K, K, tab->d_Tslices, tab->d_Tslice_scale, s));
         tab->n_slices = 7;
       }
       uint8_t* sl = static_cast<uint8_t*>(scratch_lp);
       int* sc = reinterpret_cast<int*>(sl + ((emu_slice_bytes(9 * n_tiles, K) + 255) & ~size_t(255)));
-      MSASM_TRY(emu_slice_gpu(d_coef, 9 * n_tiles, K, sl, sc, s));
+      MSASM_TRY(emu_slice_gpu(d_coef, 9 * n_tiles, K, K, sl, sc, s));
       return contract_emu_gpu(tab->d_Tslices, tab->d_Tslice_scale, n_nz, sl, sc, 9 * n_tiles, K,
-                              static_cast<double*>(d_nz), ld, d_err, s);
+                              static_cast<double*>(d_nz), ld, false, d_err, s);
     }
     default:
       return fail(MSASM_EUNSUPPORTED, "precision not available in this build");
@@ -600,6 +603,8 @@ msasm_status msasm_assemble(msasm_plan* plan, const double* d_ctrl, double E, do
   }
   return MSASM_OK;
 }
+
+constexpr int kAdjChunk = 576;   // pairs per exactly accumulated chunk of the emulated adjoint product
 
 static size_t value_bytes(msasm_precision prec) { return is_f64_precision(prec) ? 8 : 4; }
 
@@ -712,11 +717,37 @@ msasm_status msasm_assemble_grad(msasm_plan* plan, const double* d_ctrl, double 
     MSASM_CUDA(cudaMalloc(&tab->d_Tt32, size_t(K) * n_nz * sizeof(float)));
     MSASM_TRY(transpose_table_gpu<float>(tab->d_T, n_nz, K, tab->d_Tt32, s));
   }
+  if (prec == MSASM_F64_EMU) {
+    if (K > 576) return fail(MSASM_EUNSUPPORTED, "FP64 emulation is exact for K <= 576 (q <= 3)");
+    MSASM_TRY(ensure_lp_scratch(plan, MSASM_F64_EMU));       // slices of G (rows 9 nt, chunk of k)
+    if (!plan->d_adj_lp) {
+      const size_t bytes = ((emu_slice_bytes(K, kAdjChunk) + 255) & ~size_t(255)) + size_t(K) * sizeof(int);
+      MSASM_CUDA(cudaMalloc(&plan->d_adj_lp, bytes));
+    }
+    MSASM_CUDA(cudaMemsetAsync(plan->d_tc_err, 0, sizeof(unsigned), s));
+  }
   MSASM_CUDA(cudaMemsetAsync(d_grad_ctrl, 0, size_t(plan->n_ctrl) * 3 * sizeof(double), s));
   const int64_t P = plan->tiles_per_pass;
   for (int64_t t0 = 0; t0 < plan->n_tiles; t0 += P) {
     const int64_t nt = std::min(P, plan->n_tiles - t0);
-    if (f64) {
+    if (prec == MSASM_F64_EMU) {
+      // W = G Tt^T on the tensor cores to FP64 accuracy: the contraction over the n_nz pairs is cut
+      // into chunks of at most 576 (the exactness bound of the slice accumulators); each chunk's
+      // exactly rounded product is added to W in FP64
+      double* G = static_cast<double*>(plan->d_nz);
+      MSASM_TRY(grad_blocks_gpu<double>(plan, static_cast<const double*>(d_u), static_cast<const double*>(d_grad_values),
+                                        t0, nt, ld, G, s));
+      uint8_t* gl = static_cast<uint8_t*>(plan->d_coef_lp);
+      int* g_exp = reinterpret_cast<int*>(gl + ((emu_slice_bytes(9 * nt, kAdjChunk) + 255) & ~size_t(255)));
+      uint8_t* tl = static_cast<uint8_t*>(plan->d_adj_lp);
+      int* t_exp = reinterpret_cast<int*>(tl + ((emu_slice_bytes(K, kAdjChunk) + 255) & ~size_t(255)));
+      for (int m0 = 0; m0 < n_nz; m0 += kAdjChunk) {
+        const int kc = std::min(kAdjChunk, n_nz - m0);
+        MSASM_TRY(emu_slice_gpu(tab->d_Tt + m0, K, n_nz, kc, tl, t_exp, s));
+        MSASM_TRY(emu_slice_gpu(G + m0, 9 * nt, ld, kc, gl, g_exp, s));
+        MSASM_TRY(contract_emu_gpu(tl, t_exp, K, gl, g_exp, 9 * nt, kc, plan->d_coef, K, m0 > 0, plan->d_tc_err, s));
+      }
+    } else if (f64) {
       double* G = static_cast<double*>(plan->d_nz);
       MSASM_TRY(grad_blocks_gpu<double>(plan, static_cast<const double*>(d_u), static_cast<const double*>(d_grad_values),
                                         t0, nt, ld, G, s));

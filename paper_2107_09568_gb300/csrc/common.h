@@ -164,7 +164,8 @@ struct msasm_plan {
   // scratch
   double* d_coef = nullptr;         // 9 tiles_per_pass x 9 n_pi, FP64
   void* d_nz = nullptr;             // 9 tiles_per_pass x n_nz, FP64-sized
-  void* d_coef_lp = nullptr;        // reduced-precision coefficient operands
+  void* d_coef_lp = nullptr;
+  void* d_adj_lp = nullptr;        // slices of one chunk of the transposed table (emulated FP64 adjoint)        // reduced-precision coefficient operands
   size_t coef_lp_bytes = 0;
   unsigned long long* d_degenerate = nullptr;
   unsigned* d_tc_err = nullptr;     // set by a tensor-core kernel whose pipeline wait timed out

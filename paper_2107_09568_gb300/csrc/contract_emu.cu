@@ -55,6 +55,7 @@ struct EmuParams {
   const int* exp_n;        // tau_n = 2^exp_n
   double* out;             // nz[n][m], leading dimension ld
   int ld;
+  int accumulate;          // add to out instead of overwriting it (a K-split product, summed in FP64)
   unsigned* err;
 };
 
@@ -270,7 +271,11 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
 #pragma unroll
         for (int j = 0; j < EMU_EPI_COLS; ++j) {
           const int n = n0 + j;
-          if (n < p.N) p.out[size_t(n) * p.ld + m] = ldexp_i64_rn(X[j], em + p.exp_n[n]);
+          if (n < p.N) {
+            double* o = p.out + size_t(n) * p.ld + m;
+            const double v = ldexp_i64_rn(X[j], em + p.exp_n[n]);
+            *o = p.accumulate ? *o + v : v;
+          }
         }
       }
     }
@@ -313,12 +318,12 @@ __device__ __forceinline__ long long fixed_point_49(double x, int e) {
 // One warp per row: sigma = 2^e >= max|x| and the 7 BF16 slices s_i = a_i 2^-7i, [i][row][Kpad],
 // where X = x 2^(49-e) = sum_i a_i 128^(6-i) with balanced digits a_i in [-64, 63] (i > 0) and
 // |a_0| <= 128.  Integer instructions only (the FP64 pipe runs at 1/64 of the FP32 rate).
-__global__ void emu_slice_kernel(const double* __restrict__ x, int64_t rows, int K, int Kpad,
+__global__ void emu_slice_kernel(const double* __restrict__ x, int64_t rows, int64_t ldx, int K, int Kpad,
                                  __nv_bfloat16* __restrict__ slices, int* __restrict__ scale_exp) {
   const int lane = threadIdx.x & 31;
   for (int64_t r = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; r < rows;
        r += (int64_t(gridDim.x) * blockDim.x) >> 5) {
-    const double* xr = x + r * K;
+    const double* xr = x + r * ldx;
     unsigned long long mb = 0;                 // max |x| as a bit pattern (monotone for x >= 0)
     for (int k = lane; k < K; k += 32) {
       const unsigned long long b = (unsigned long long)__double_as_longlong(xr[k]) & 0x7fffffffffffffffull;
@@ -362,10 +367,12 @@ int emu_kpad(int K) { return (K + EMU_KB - 1) / EMU_KB * EMU_KB; }
 
 size_t emu_slice_bytes(int64_t rows, int K) { return size_t(EMU_S) * rows * emu_kpad(K) * sizeof(__nv_bfloat16); }
 
-msasm_status emu_slice_gpu(const double* x, int64_t rows, int K, void* slices, int* scale_exp, cudaStream_t s) {
+// rows of x with leading dimension ldx (elements), K of them each
+msasm_status emu_slice_gpu(const double* x, int64_t rows, int64_t ldx, int K, void* slices, int* scale_exp,
+                           cudaStream_t s) {
   if (K > 576 + 15) return fail(MSASM_EUNSUPPORTED, "FP64 emulation is exact for K <= 576 (q <= 3)");
   int64_t blocks = std::min<int64_t>((rows * 32 + 255) / 256, 152 * 16);
-  emu_slice_kernel<<<unsigned(blocks), 256, 0, s>>>(x, rows, K, emu_kpad(K), static_cast<__nv_bfloat16*>(slices),
+  emu_slice_kernel<<<unsigned(blocks), 256, 0, s>>>(x, rows, ldx, K, emu_kpad(K), static_cast<__nv_bfloat16*>(slices),
                                                     scale_exp);
   MSASM_CUDA(cudaGetLastError());
   return MSASM_OK;
@@ -399,8 +406,8 @@ static msasm_status make_map_3d(CUtensorMap* map, const void* ptr, int64_t rows,
 
 // nz[n][m] (FP64, leading dimension ld) = sum_k A[m][k] B[n][k] from the slices of A (M rows) and B (N rows)
 msasm_status contract_emu_gpu(const void* a_slices, const int* a_exp, int M, const void* b_slices,
-                              const int* b_exp, int64_t N, int K, double* out, int ld, unsigned* d_err,
-                              cudaStream_t s) {
+                              const int* b_exp, int64_t N, int K, double* out, int ld, bool accumulate,
+                              unsigned* d_err, cudaStream_t s) {
   if (N > int64_t(2147483647) * EMU_BN) return fail(MSASM_EUNSUPPORTED, "too many rows for one launch");
   CUtensorMap ma, mb;
   MSASM_TRY(make_map_3d(&ma, a_slices, M, K, EMU_BM));
@@ -413,6 +420,7 @@ msasm_status contract_emu_gpu(const void* a_slices, const int* a_exp, int M, con
   p.exp_n = b_exp;
   p.out = out;
   p.ld = ld;
+  p.accumulate = accumulate ? 1 : 0;
   p.err = d_err;
   MSASM_CUDA(cudaFuncSetAttribute(contract_emu_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, EMU_SMEM_BYTES));
   const long long tiles = ((N + EMU_BN - 1) / EMU_BN) * (long long)((M + EMU_BM - 1) / EMU_BM);

@@ -243,16 +243,17 @@ __device__ __forceinline__ float tf32_round(float x) {
 }
 
 // One warp per row: hi/lo slices of x[row][0..K) into [row][0..Kpad) (zero padded).
-__global__ void split_rows_kernel(const double* __restrict__ x, int64_t rows, int K, int Kpad, int kind,
+template <typename Tin>
+__global__ void split_rows_kernel(const Tin* __restrict__ x, int64_t rows, int K, int Kpad, int kind,
                                   void* __restrict__ hi, void* __restrict__ lo, float* __restrict__ row_scale) {
   const int lane = threadIdx.x & 31;
   for (int64_t r = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; r < rows;
        r += (int64_t(gridDim.x) * blockDim.x) >> 5) {
-    const double* xr = x + r * K;
+    const Tin* xr = x + r * K;
     double scale = 1.0;
     if (kind == kSplitF16) {
       double mx = 0.0;
-      for (int k = lane; k < K; k += 32) mx = fmax(mx, fabs(xr[k]));
+      for (int k = lane; k < K; k += 32) mx = fmax(mx, fabs(double(xr[k])));
       for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
       int e = 0;
       if (mx > 0.0) {
@@ -262,7 +263,7 @@ __global__ void split_rows_kernel(const double* __restrict__ x, int64_t rows, in
       if (lane == 0) row_scale[r] = float(1.0 / scale);
     }
     for (int k = lane; k < Kpad; k += 32) {
-      const double v = (k < K) ? xr[k] * scale : 0.0;
+      const double v = (k < K) ? double(xr[k]) * scale : 0.0;
       if (kind == kSplitF16) {
         const __half h = __double2half(v);
         const __half l = __double2half((v - double(__half2float(h))) * 2048.0);
@@ -335,13 +336,22 @@ size_t tc_slice_bytes(int64_t rows, int K, int kind) {
   return size_t(rows) * tc_kpad(K, kind) * esz;
 }
 
-msasm_status tc_split_gpu(const double* x, int64_t rows, int K, int kind, void* hi, void* lo, float* row_scale,
-                          cudaStream_t s) {
+template <typename Tin>
+static msasm_status tc_split_any(const Tin* x, int64_t rows, int K, int kind, void* hi, void* lo, float* row_scale,
+                                 cudaStream_t s) {
   int64_t blocks = (rows * 32 + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  split_rows_kernel<<<unsigned(blocks), 256, 0, s>>>(x, rows, K, tc_kpad(K, kind), kind, hi, lo, row_scale);
+  split_rows_kernel<Tin><<<unsigned(blocks), 256, 0, s>>>(x, rows, K, tc_kpad(K, kind), kind, hi, lo, row_scale);
   MSASM_CUDA(cudaGetLastError());
   return MSASM_OK;
+}
+msasm_status tc_split_gpu(const double* x, int64_t rows, int K, int kind, void* hi, void* lo, float* row_scale,
+                          cudaStream_t s) {
+  return tc_split_any<double>(x, rows, K, kind, hi, lo, row_scale, s);
+}
+msasm_status tc_split_f32_gpu(const float* x, int64_t rows, int K, int kind, void* hi, void* lo, float* row_scale,
+                              cudaStream_t s) {
+  return tc_split_any<float>(x, rows, K, kind, hi, lo, row_scale, s);
 }
 
 // nz[n][m] (FP32, leading dimension ld) from sliced operands A (table, M rows) and B (coef, N rows).

@@ -11,6 +11,7 @@
 // weights (FP32 master copy for Adam), FP32 accumulation; all its kernels are below.
 #include <cuda_fp16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <random>
 #include <vector>
@@ -22,6 +23,14 @@ namespace msasm {
 template <typename T>
 msasm_status gemm_simt(const T* A, int64_t lda, const T* B, int64_t ldb, int64_t N, int M, int K, T* C, int64_t ldc,
                        cudaStream_t stream);
+int tc_kpad(int K, int kind);
+size_t tc_slice_bytes(int64_t rows, int K, int kind);
+msasm_status tc_split_f32_gpu(const float* x, int64_t rows, int K, int kind, void* hi, void* lo, float* row_scale,
+                              cudaStream_t s);
+msasm_status contract_tc_gpu(int kind, const void* a_hi, const void* a_lo, const float* a_scale, int M,
+                             const void* b_hi, const void* b_lo, const float* b_scale, int64_t N, int K, float* out,
+                             int ld, unsigned* d_err, cudaStream_t s);
+constexpr int kLowRankSplit = 0;   // split FP16 (hi + 2^-11 lo, three products): about 6e-7 relative
 template <typename T>
 msasm_status transpose_table_gpu(const double* d_T, int n_nz, int K, T* d_Tt, cudaStream_t s);
 bool cholesky_upper_inverse(const std::vector<double>& A, int n, std::vector<double>& Rinv);
@@ -67,22 +76,14 @@ __global__ void mlp_hidden_kernel(const __half* __restrict__ p, const float* __r
   }
 }
 
-__global__ void mlp_out_kernel(const __half* __restrict__ p, const float* __restrict__ h2, int B, int H, int n_out,
-                               size_t oW3, size_t ob3, float* __restrict__ y) {
-  extern __shared__ float sh[];
-  const int b = blockIdx.y;
-  for (int i = threadIdx.x; i < H; i += blockDim.x) sh[i] = h2[size_t(b) * H + i];
-  __syncthreads();
-  const int o = blockIdx.x * blockDim.x + threadIdx.x;
-  if (o >= n_out) return;
-  const __half* w = p + oW3 + size_t(o) * H;
-  float s = __half2float(p[ob3 + o]);
-  for (int i = 0; i < H; i += 2) {
-    const float2 ww = __half22float2(*reinterpret_cast<const __half2*>(w + i));
-    s = fmaf(ww.x, sh[i], s);
-    s = fmaf(ww.y, sh[i + 1], s);
-  }
-  y[size_t(b) * n_out + o] = s;
+__global__ void widen_half_kernel(const __half* __restrict__ x, int64_t n, float* __restrict__ y) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    y[i] = __half2float(x[i]);
+}
+
+__global__ void add_bias_kernel(float* __restrict__ y, int64_t n, int n_out, const __half* __restrict__ b) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    y[i] += __half2float(b[i % n_out]);
 }
 
 // dy = 2 (y - t) / (B n_out) and the mean squared error (block partial sums into loss)
@@ -231,19 +232,33 @@ __global__ void normalise_inputs_kernel(const double* __restrict__ w, int64_t n,
 }
 
 // Z[9t + ab][r] = sum_k Vt_t[r][k] coef[9t + ab][k]  (FP32 result; V FP32, coefficients FP64)
+// Z[9t + ab][r] = sum_k Vt_t[r][k] coef[9t + ab][k]: one CTA per tile, the tile's 9 coefficient rows
+// in shared memory (FP32), one warp per r at a time with the lanes splitting k (coalesced rows of Vt)
 __global__ void lowrank_z_kernel(const float* __restrict__ Vt, const double* __restrict__ coef, int64_t n_tiles,
                                  int rank, int K, float* __restrict__ Z) {
-  const int64_t total = n_tiles * 9 * rank;
-  for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < total;
-       idx += int64_t(gridDim.x) * blockDim.x) {
-    const int r = int(idx % rank);
-    const int64_t row = idx / rank;            // 9 t + ab
-    const int64_t t = row / 9;
-    const float* v = Vt + (t * rank + r) * K;
-    const double* c = coef + row * K;
-    float s = 0.0f;
-    for (int k = 0; k < K; ++k) s = fmaf(v[k], float(c[k]), s);
-    Z[idx] = s;
+  extern __shared__ float cs[];                 // [9][K]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
+  for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    for (int i = threadIdx.x; i < 9 * K; i += blockDim.x) cs[i] = float(coef[9 * t * K + i]);
+    __syncthreads();
+    for (int r = warp; r < rank; r += warps) {
+      const float* v = Vt + (t * rank + r) * K;
+      float acc[9];
+#pragma unroll
+      for (int ab = 0; ab < 9; ++ab) acc[ab] = 0.0f;
+      for (int k = lane; k < K; k += 32) {
+        const float vk = v[k];
+#pragma unroll
+        for (int ab = 0; ab < 9; ++ab) acc[ab] = fmaf(vk, cs[ab * K + k], acc[ab]);
+      }
+#pragma unroll
+      for (int ab = 0; ab < 9; ++ab) {
+        float x = acc[ab];
+        for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) Z[(9 * t + ab) * rank + r] = x;
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -260,6 +275,7 @@ struct msasm_mlp {
   MlpLayout lay;
   float* d_w = nullptr;      // FP32 master
   __half* d_w16 = nullptr;   // FP16 compute copy
+  float* d_w3f = nullptr;    // the output layer's FP16 weights widened to FP32 (exact) for the GEMM
   float* d_g = nullptr;
   float* d_m = nullptr;
   float* d_v = nullptr;
@@ -278,6 +294,7 @@ struct msasm_mlp {
     if (graph) cudaGraphExecDestroy(graph);
     cudaFree(d_w);
     cudaFree(d_w16);
+    cudaFree(d_w3f);
     cudaFree(d_g);
     cudaFree(d_m);
     cudaFree(d_v);
@@ -297,6 +314,10 @@ struct msasm_surrogate {
   double w0 = 0.275, ws = 0.125;   // input normalisation of the width
   float scale = 1.0f;              // target scale
   float* d_U = nullptr;            // n_nz x rank (FP32), row-major
+  void* d_Uhi = nullptr;           // split-FP16 slices of U for the tensor-core low-rank product
+  void* d_Ulo = nullptr;
+  float* d_Uscale = nullptr;
+  unsigned* d_err = nullptr;
   float* d_mean = nullptr;         // n_out
   float* d_x = nullptr;            // normalised training widths
   float* d_targets = nullptr;      // n_train x n_out (normalised)
@@ -304,6 +325,10 @@ struct msasm_surrogate {
   ~msasm_surrogate() {
     delete mlp;
     cudaFree(d_U);
+    cudaFree(d_Uhi);
+    cudaFree(d_Ulo);
+    cudaFree(d_Uscale);
+    cudaFree(d_err);
     cudaFree(d_mean);
     cudaFree(d_x);
     cudaFree(d_targets);
@@ -341,8 +366,15 @@ static msasm_status mlp_forward(msasm_mlp* n, const float* d_x, int B, float* d_
   mlp_hidden_kernel<<<std::min(B, 1024), 128, L.H * sizeof(float), s>>>(n->d_w16, d_x, B, L.H, L.W1, L.b1, L.W2, L.b2,
                                                                         n->d_h1, n->d_h2);
   MSASM_CUDA(cudaGetLastError());
-  dim3 grid(unsigned((L.n_out + 255) / 256), unsigned(B));
-  mlp_out_kernel<<<grid, 256, L.H * sizeof(float), s>>>(n->d_w16, n->d_h2, B, L.H, L.n_out, L.W3, L.b3, d_y);
+  // output layer as one CUDA-core GEMM over the batch: y = h2 W3^T + b3
+  const int64_t nw3 = int64_t(L.n_out) * L.H;
+  widen_half_kernel<<<unsigned(std::min<int64_t>((nw3 + 255) / 256, 152 * 8)), 256, 0, s>>>(n->d_w16 + L.W3, nw3,
+                                                                                             n->d_w3f);
+  MSASM_CUDA(cudaGetLastError());
+  MSASM_TRY(gemm_simt<float>(n->d_h2, L.H, n->d_w3f, L.H, B, L.n_out, L.H, d_y, L.n_out, s));
+  const int64_t ny = int64_t(B) * L.n_out;
+  add_bias_kernel<<<unsigned(std::min<int64_t>((ny + 255) / 256, 152 * 8)), 256, 0, s>>>(d_y, ny, L.n_out,
+                                                                                         n->d_w16 + L.b3);
   MSASM_CUDA(cudaGetLastError());
   return MSASM_OK;
 }
@@ -396,6 +428,7 @@ msasm_status msasm_mlp_create(int32_t n_out, int32_t hidden, uint64_t seed, msas
   fill(n->lay.W3, size_t(n_out) * hidden, hidden, n_out);
   cudaError_t e = cudaMalloc(&n->d_w, P * 4);
   if (e == cudaSuccess) e = cudaMalloc(&n->d_w16, P * 2);
+  if (e == cudaSuccess) e = cudaMalloc(&n->d_w3f, size_t(n_out) * hidden * 4);
   if (e == cudaSuccess) e = cudaMalloc(&n->d_g, P * 4);
   if (e == cudaSuccess) e = cudaMalloc(&n->d_m, P * 4);
   if (e == cudaSuccess) e = cudaMalloc(&n->d_v, P * 4);
@@ -719,24 +752,70 @@ msasm_status msasm_surrogate_predict(msasm_surrogate* sur, const double* d_width
 }
 
 // nzdata of n_tiles tiles from the low-rank factors: nz[9t + ab][m] = sum_r Z[9t + ab][r] U[m][r],
-// Z[9t + ab][r] = sum_k Vt_t[r][k] coef[9t + ab][k]   (FP32; d_nz leading dimension ld)
-static msasm_status lowrank_contract_gpu(const float* d_U, int n_nz, int rank, int K, const float* d_Vt,
-                                         const double* d_coef, int64_t n_tiles, float* d_Z, float* d_nz, int ld,
-                                         cudaStream_t s) {
-  lowrank_z_kernel<<<152 * 8, 256, 0, s>>>(d_Vt, d_coef, n_tiles, rank, K, d_Z);
+// Z[9t + ab][r] = sum_k Vt_t[r][k] coef[9t + ab][k] (FP32), the second product on the tensor cores
+// in split FP16 (U given as its slices; d_nz leading dimension ld).  d_work holds the slices of Z:
+// lowrank_work_bytes(n_tiles, rank).
+static size_t lowrank_work_bytes(int64_t n_tiles, int rank) {
+  return 2 * ((tc_slice_bytes(9 * n_tiles, rank, kLowRankSplit) + 255) & ~size_t(255)) + size_t(9 * n_tiles) * 4;
+}
+static msasm_status lowrank_contract_gpu(const void* U_hi, const void* U_lo, const float* U_scale, int n_nz, int rank,
+                                         int K, const float* d_Vt, const double* d_coef, int64_t n_tiles, float* d_Z,
+                                         void* d_work, float* d_nz, int ld, unsigned* d_err, cudaStream_t s) {
+  const size_t zsm = size_t(9) * K * sizeof(float);
+  if (zsm > 200 * 1024) return fail(MSASM_EUNSUPPORTED, "K too large for the low-rank kernel");
+  MSASM_CUDA(cudaFuncSetAttribute(lowrank_z_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(zsm)));
+  lowrank_z_kernel<<<unsigned(std::min<int64_t>(n_tiles, 152 * 8)), 256, zsm, s>>>(d_Vt, d_coef, n_tiles, rank, K, d_Z);
   MSASM_CUDA(cudaGetLastError());
-  return gemm_simt<float>(d_Z, rank, d_U, rank, 9 * n_tiles, n_nz, rank, d_nz, ld, s);
+  const size_t sb = (tc_slice_bytes(9 * n_tiles, rank, kLowRankSplit) + 255) & ~size_t(255);
+  uint8_t* w = static_cast<uint8_t*>(d_work);
+  float* z_scale = reinterpret_cast<float*>(w + 2 * sb);
+  MSASM_TRY(tc_split_f32_gpu(d_Z, 9 * n_tiles, rank, kLowRankSplit, w, w + sb, z_scale, s));
+  return contract_tc_gpu(kLowRankSplit, U_hi, U_lo, U_scale, n_nz, w, w + sb, z_scale, 9 * n_tiles, rank, d_nz, ld,
+                         d_err, s);
+}
+
+// split-FP16 slices of U, made once per surrogate
+static msasm_status ensure_u_split(msasm_surrogate* sur, cudaStream_t s) {
+  if (sur->d_Uhi) return MSASM_OK;
+  const size_t ub = tc_slice_bytes(sur->n_nz, sur->rank, kLowRankSplit);
+  MSASM_CUDA(cudaMalloc(&sur->d_Uhi, ub));
+  MSASM_CUDA(cudaMalloc(&sur->d_Ulo, ub));
+  MSASM_CUDA(cudaMalloc(&sur->d_Uscale, size_t(sur->n_nz) * 4));
+  MSASM_CUDA(cudaMalloc(&sur->d_err, sizeof(unsigned)));
+  MSASM_CUDA(cudaMemsetAsync(sur->d_err, 0, sizeof(unsigned), s));
+  return tc_split_f32_gpu(sur->d_U, sur->n_nz, sur->rank, kLowRankSplit, sur->d_Uhi, sur->d_Ulo, sur->d_Uscale, s);
 }
 
 msasm_status msasm_lowrank_contract(const float* d_U, int32_t n_nz, int32_t rank, int32_t K, const float* d_Vt,
                                     const double* d_coef, int64_t n_tiles, float* d_nz, void* stream) {
   if (!d_U || !d_Vt || !d_coef || !d_nz || n_tiles <= 0 || n_nz <= 0 || rank <= 0 || K <= 0)
     return fail(MSASM_EINVAL, "bad low-rank contraction arguments");
+  if (rank > 64) return fail(MSASM_EUNSUPPORTED, "rank above 64");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  float* Z = nullptr;
-  MSASM_CUDA(cudaMallocAsync(&Z, size_t(9 * n_tiles) * rank * 4, s));
-  msasm_status st = lowrank_contract_gpu(d_U, n_nz, rank, K, d_Vt, d_coef, n_tiles, Z, d_nz, n_nz, s);
-  cudaFreeAsync(Z, s);
+  const size_t ub = (tc_slice_bytes(n_nz, rank, kLowRankSplit) + 255) & ~size_t(255);
+  const size_t zb = (size_t(9 * n_tiles) * rank * 4 + 255) & ~size_t(255);
+  const size_t bytes = 2 * ub + ((size_t(n_nz) * 4 + 255) & ~size_t(255)) + zb + lowrank_work_bytes(n_tiles, rank) + 256;
+  void* buf = nullptr;
+  MSASM_CUDA(cudaMallocAsync(&buf, bytes, s));
+  uint8_t* b = static_cast<uint8_t*>(buf);
+  float* u_scale = reinterpret_cast<float*>(b + 2 * ub);
+  float* Z = reinterpret_cast<float*>(b + 2 * ub + ((size_t(n_nz) * 4 + 255) & ~size_t(255)));
+  void* work = reinterpret_cast<uint8_t*>(Z) + zb;
+  unsigned* err = reinterpret_cast<unsigned*>(static_cast<uint8_t*>(work) + lowrank_work_bytes(n_tiles, rank));
+  msasm_status st = MSASM_OK;
+  cudaError_t e = cudaMemsetAsync(err, 0, sizeof(unsigned), s);
+  if (e != cudaSuccess) st = cuda_fail(e, "cudaMemsetAsync");
+  if (st == MSASM_OK) st = tc_split_f32_gpu(d_U, n_nz, rank, kLowRankSplit, b, b + ub, u_scale, s);
+  if (st == MSASM_OK)
+    st = lowrank_contract_gpu(b, b + ub, u_scale, n_nz, rank, K, d_Vt, d_coef, n_tiles, Z, work, d_nz, n_nz, err, s);
+  unsigned h_err = 0;
+  if (st == MSASM_OK) {
+    e = cudaMemcpyAsync(&h_err, err, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_fail(e, "low-rank contraction");
+  }
+  cudaFreeAsync(buf, s);
+  if (st == MSASM_OK && h_err) st = fail(MSASM_ECUDA, "a tensor-core pipeline wait timed out (results invalid)");
   return st;
 }
 
@@ -751,21 +830,26 @@ msasm_status msasm_surrogate_assemble(msasm_plan* plan, msasm_surrogate* sur, co
   const double lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)), mu = E / (2.0 * (1.0 + nu));
   const int64_t P = plan->tiles_per_pass;
   const int ld = (sur->n_nz + 7) & ~7;
+  if (sur->rank > 64) return fail(MSASM_EUNSUPPORTED, "rank above 64");
+  MSASM_TRY(ensure_u_split(sur, s));
   float *Vt = nullptr, *Z = nullptr;
+  void* work = nullptr;
   MSASM_CUDA(cudaMallocAsync(&Vt, size_t(P) * sur->rank * sur->K * 4, s));
   MSASM_CUDA(cudaMallocAsync(&Z, size_t(9 * P) * sur->rank * 4, s));
+  MSASM_CUDA(cudaMallocAsync(&work, lowrank_work_bytes(P, sur->rank), s));
   msasm_status st = MSASM_OK;
   for (int64_t t0 = 0; t0 < plan->n_tiles && st == MSASM_OK; t0 += P) {
     const int64_t nt = std::min(P, plan->n_tiles - t0);
     st = pullback_gpu(plan, d_ctrl, lam, mu, t0, nt, plan->d_coef, s);
     if (st == MSASM_OK) st = msasm_surrogate_predict(sur, d_widths + t0, nt, Vt, stream);
     if (st == MSASM_OK)
-      st = lowrank_contract_gpu(sur->d_U, sur->n_nz, sur->rank, sur->K, Vt, plan->d_coef, nt, Z,
-                                static_cast<float*>(plan->d_nz), ld, s);
+      st = lowrank_contract_gpu(sur->d_Uhi, sur->d_Ulo, sur->d_Uscale, sur->n_nz, sur->rank, sur->K, Vt, plan->d_coef,
+                                nt, Z, work, static_cast<float*>(plan->d_nz), ld, sur->d_err, s);
     if (st == MSASM_OK) st = scatter_pass_gpu<float>(plan, static_cast<const float*>(plan->d_nz), ld, t0, nt, d_values, s);
   }
   cudaFreeAsync(Vt, s);
   cudaFreeAsync(Z, s);
+  cudaFreeAsync(work, s);
   return st;
 }
 

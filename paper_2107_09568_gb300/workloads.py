@@ -138,6 +138,7 @@ def adjoint(flush, nx=20, ny=20, nz=5, n_check=20, h=1e-4):
     C0 = torch.dot(f, u).item()
     g64, ms_g64 = _timed(lambda: plan.assemble_grad(ctrl, 1.0, 0.3, "f64", u=u), reps=3, flush=flush)
     g32, ms_g32 = _timed(lambda: plan.assemble_grad(ctrl, 1.0, 0.3, "f32", u=u.float()), reps=3, flush=flush)
+    gemu, ms_gemu = _timed(lambda: plan.assemble_grad(ctrl, 1.0, 0.3, "f64_emu", u=u), reps=3, flush=flush)
     rng = np.random.default_rng(0)
     coords = [(int(k), int(p)) for k, p in zip(rng.choice(plan.n_ctrl, n_check, replace=False),
                                                rng.integers(0, 3, n_check))]
@@ -153,8 +154,9 @@ def adjoint(flush, nx=20, ny=20, nz=5, n_check=20, h=1e-4):
     gq = np.array([g64[k, p].item() for k, p in coords])
     out = {"tiles": plan.n_tiles, "nnz": plan.nnz, "dofs": plan.n_rows, "assemble_ms_f64_emu": ms_asm,
            "cg_iterations": iters, "cg_rel_residual": res, "cg_s": t_cg, "compliance": C0,
-           "grad_ms_f64": ms_g64, "grad_ms_f32": ms_g32,
+           "grad_ms_f64": ms_g64, "grad_ms_f64_emu": ms_gemu, "grad_ms_f32": ms_g32,
            "grad_rel_f32_vs_f64": (torch.linalg.vector_norm(g32 - g64) / torch.linalg.vector_norm(g64)).item(),
+           "grad_rel_f64_emu_vs_f64": (torch.linalg.vector_norm(gemu - g64) / torch.linalg.vector_norm(g64)).item(),
            "fd_coords": coords, "fd_step": h,
            "fd_quadratic_max_abs_diff_over_max_grad": float(np.abs(fdq - gq).max() / np.abs(gq).max())}
     return out

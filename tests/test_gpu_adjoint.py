@@ -23,11 +23,11 @@ def small_case(q=1, macro=None, n_e=2):
     return prob, tab, plan
 
 
-@pytest.mark.parametrize("prec,tol", [("f64", 1e-10), ("f32", 2e-5)])
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-10), ("f64_emu", 1e-10), ("f32", 2e-5)])
 def test_grad_u_matches_oracle_complex_step(prec, tol):
     prob, tab, plan = small_case()
     u = np.random.default_rng(0).normal(size=(plan.n_points, 3))
-    dt = torch.float64 if prec == "f64" else torch.float32
+    dt = torch.float32 if prec == "f32" else torch.float64
     ctrl = torch.tensor(prob.mmap.macro.ctrl, device="cuda")
     g = plan.assemble_grad(ctrl, 1.0, 0.3, prec, u=torch.tensor(u.ravel(), dtype=dt, device="cuda")).cpu().numpy()
     ref = oadj.gradient_all(prob, u)
@@ -151,6 +151,7 @@ def test_cantilever2000_gradient_vs_oracle_complex_step():
     u, it, res = msasm.cg_solve(K, f, fixed, tol=1e-13, max_iter=30000)
     assert res < 1e-8, (it, res)
     g64 = plan.assemble_grad(ctrl, 1.0, 0.3, "f64", u=u)
+    gemu = plan.assemble_grad(ctrl, 1.0, 0.3, "f64_emu", u=u)
     g32 = plan.assemble_grad(ctrl, 1.0, 0.3, "f32", u=u.float())
     rng = np.random.default_rng(0)
     coords = [(int(k), int(p)) for k, p in zip(rng.choice(plan.n_ctrl, 12, replace=False), rng.integers(0, 3, 12))]
@@ -161,8 +162,14 @@ def test_cantilever2000_gradient_vs_oracle_complex_step():
     scale = np.abs(cs).max()
     e64 = np.abs(np.array([g64[k, p].item() for k, p in coords]) - cs).max() / scale
     e32 = np.abs(np.array([g32[k, p].item() for k, p in coords]) - cs).max() / scale
+    eemu = np.abs(np.array([gemu[k, p].item() for k, p in coords]) - cs).max() / scale
+    rel_emu = (torch.linalg.vector_norm(gemu - g64) / torch.linalg.vector_norm(g64)).item()
     rel32 = (torch.linalg.vector_norm(g32 - g64) / torch.linalg.vector_norm(g64)).item()
     print(f"cantilever2000: CG {it} it, residual {res:.2e}; FP64 vs complex step {e64:.2e}, "
-          f"FP32 {e32:.2e}; FP32 vs FP64 over all control points {rel32:.2e}")
-    assert e64 <= 1e-11
+          f"FP64-accurate (tensor cores) {eemu:.2e}, FP32 {e32:.2e}; over all control points FP32 vs FP64 "
+          f"{rel32:.2e}, FP64-accurate vs FP64 {rel_emu:.2e}")
+    # the emulated product slices each row of G = w v_a v_b to 49 bits of its largest entry; G spans a
+    # wide range within a row, so the emulated form lands near 2e-11 here (the assembly's smooth
+    # coefficient rows give 1e-13)
+    assert e64 <= 1e-11 and eemu <= 1e-10 and rel_emu <= 1e-10
     assert e32 <= 1e-3 and rel32 <= 1e-3
