@@ -262,11 +262,6 @@ __global__ void lowrank_z_kernel(const float* __restrict__ Vt, const double* __r
   }
 }
 
-__global__ void f64_to_f32_kernel(const double* __restrict__ x, int64_t n, float* __restrict__ y) {
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
-    y[i] = float(x[i]);
-}
-
 }  // namespace msasm
 
 using namespace msasm;
