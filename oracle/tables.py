@@ -67,3 +67,29 @@ def volume_table(tile, q: int, n_g: int | None = None) -> np.ndarray:
         wgt = np.array([wa * wb * wc for wc in wts[2] for wb in wts[1] for wa in wts[0]]) * np.prod(hi - lo)
         t += wgt @ quadrature.tensor_lagrange(q, lo + (hi - lo) * theta)
     return t
+
+
+def load_table(tile, q: int, n_g: int | None = None) -> np.ndarray:
+    """The body-force part of the load lookup table (eq. 54-55, F = 0):
+    F[A, C] = int_{Omega_T} (R_A o T^r^-1) N_C dxi, shape (n_T, (q+1)^3), by the same element
+    quadrature as the stiffness table (the integrand has degree <= p_T + q per direction)."""
+    p_T = max(max(P["degree"]) for P in tile.patches)
+    n_g = n_g or default_gauss_points(p_T, q)
+    g1, w1 = quadrature.gauss_legendre(n_g)
+    F = np.zeros((tile.n_T, (q + 1) ** 3))
+    for el in tile.elements:
+        P = tile.patches[el["patch"]]
+        lo, hi = P["lo"], P["hi"]
+        pts = [el["th_lo"][d] + (el["th_hi"][d] - el["th_lo"][d]) * g1 for d in range(3)]
+        wts = [(el["th_hi"][d] - el["th_lo"][d]) * w1 for d in range(3)]
+        theta = np.array([(a, b, c) for c in pts[2] for b in pts[1] for a in pts[0]])
+        wgt = np.array([wa * wb * wc for wc in wts[2] for wb in wts[1] for wa in wts[0]]) * np.prod(hi - lo)
+        vals, _ = tile.patch_basis(el["patch"], theta)
+        nf = P["nfun"]
+        cols = [a1 + nf[0] * (a2 + nf[1] * a3) for (a1, a2, a3) in el["loc"]]
+        NC = quadrature.tensor_lagrange(q, lo + (hi - lo) * theta)
+        Floc = np.einsum("g,ga,gc->ac", wgt, vals[:, cols], NC)
+        for a, A in enumerate(el["ids"]):
+            F[A] += Floc[a]
+    return F
+
