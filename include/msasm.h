@@ -287,6 +287,31 @@ msasm_status msasm_contract_noalloc(const msasm_tables* tab, const double* d_coe
 msasm_status msasm_scatter(msasm_plan* plan, msasm_precision prec, const void* d_nz,
                            void* d_values, void* stream);
 
+/* ---------------------------------------------------------------- volume and loads */
+
+/* The load lookup table of eq. 54-55 (body term, F = 0): d_F[A][C] = int_{Omega_T} R_A N_C
+ * (n_T x n_pi FP64, row-major), and the volume table of eq. 18: d_vol[C] = int_{Omega_T} N_C
+ * (n_pi FP64); either may be NULL.  Both are built with the stiffness table. */
+msasm_status msasm_load_table_copy(const msasm_tables* tab, double* d_F, double* d_vol, void* stream);
+
+/* Volume of the lattice (Sec. 3.1, eq. 14-19) through the volume table: per tile
+ * V^(t) = t^h . d^(t), d_C^(t) = |det J^(t)(xi_C)| at the interpolation nodes, into
+ * d_tile_volume (n_tiles FP64, may be NULL), and the total (summed in a fixed order) into
+ * d_total (one FP64, may be NULL; not both NULL).  Errors: EINVAL, EUNSUPPORTED, ECUDA. */
+msasm_status msasm_volume(const msasm_plan* plan, const double* d_ctrl, double* d_tile_volume, double* d_total,
+                          void* stream);
+
+/* Gradient of the volume with respect to the macro control net (Sec. 4.1.1, eq. 66-67): the
+ * adjoint field t^h times d|det J|/dP at the nodes, summed back to the control points;
+ * d_grad_ctrl (n_ctrl*3 FP64) is overwritten.  Errors: EINVAL, EUNSUPPORTED, ECUDA. */
+msasm_status msasm_volume_grad(const msasm_plan* plan, const double* d_ctrl, double* d_grad_ctrl, void* stream);
+
+/* Load vector of a constant body force b = (bx, by, bz) (eq. 39-40 and the F = 0 term of eq. 53):
+ * f_{3g+a} = b_a sum over the tiles holding point g of sum_C F[A][C] |det J^(t)(xi_C)|;
+ * d_f (n_rows FP64) is overwritten.  Errors: EINVAL, EUNSUPPORTED, ECUDA. */
+msasm_status msasm_body_load(const msasm_plan* plan, const double* d_ctrl, double bx, double by, double bz,
+                             double* d_f, void* stream);
+
 /* ---------------------------------------------------------------- diagnostics */
 
 const char* msasm_last_error(void);

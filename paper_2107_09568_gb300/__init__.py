@@ -61,6 +61,15 @@ class Tables:
         check(load().msasm_tables_copy(self.handle, _ptr(out), None, _stream()))
         return out
 
+    def load_table(self):
+        """(F (n_T, n_pi), volume table (n_pi,)) as CUDA tensors (eq. 55 body term, eq. 18)."""
+        import torch
+        n_T = self.n_T
+        F = torch.empty((n_T, self.n_pi), dtype=torch.float64, device="cuda")
+        v = torch.empty(self.n_pi, dtype=torch.float64, device="cuda")
+        check(load().msasm_load_table_copy(self.handle, _ptr(F), _ptr(v), _stream()))
+        return F, v
+
     def pairs(self):
         out = np.empty((self.n_nz, 2), dtype=np.int32)
         check(load().msasm_tables_copy(self.handle, None, out.ctypes.data_as(C.c_void_p), None))
@@ -199,9 +208,38 @@ def _plan_traction_load(self, face, traction, ctrl_host):
     return f
 
 
+def _plan_volume(self, ctrl, stream=None):
+    """(per-tile volumes (n_tiles,), total volume (0-d tensor)) on the GPU (eq. 17, 19)."""
+    import torch
+    vt = torch.empty(self.n_tiles, dtype=torch.float64, device="cuda")
+    tot = torch.empty((), dtype=torch.float64, device="cuda")
+    check(load().msasm_volume(self.handle, _ptr(ctrl), _ptr(vt), _ptr(tot), _stream(stream)))
+    return vt, tot
+
+
+def _plan_volume_grad(self, ctrl, stream=None):
+    """dV/dP (n_ctrl, 3) on the GPU (eq. 66-67)."""
+    import torch
+    g = torch.empty((self.n_ctrl, 3), dtype=torch.float64, device="cuda")
+    check(load().msasm_volume_grad(self.handle, _ptr(ctrl), _ptr(g), _stream(stream)))
+    return g
+
+
+def _plan_body_load(self, ctrl, b, stream=None):
+    """Load vector (n_rows,) FP64 on the GPU of the constant body force b (eq. 53, F = 0 term)."""
+    import torch
+    f = torch.empty(self.n_rows, dtype=torch.float64, device="cuda")
+    check(load().msasm_body_load(self.handle, _ptr(ctrl), float(b[0]), float(b[1]), float(b[2]), _ptr(f),
+                                 _stream(stream)))
+    return f
+
+
 Plan.assemble_grad = _plan_assemble_grad
 Plan.face_points = _plan_face_points
 Plan.traction_load = _plan_traction_load
+Plan.volume = _plan_volume
+Plan.volume_grad = _plan_volume_grad
+Plan.body_load = _plan_body_load
 
 
 def _autograd_function():

@@ -59,6 +59,10 @@ _SIGS = {
     "msasm_face_points": (c_i32, [c_vp, c_i32, c_vp, P(c_i64)]),
     "msasm_traction_load": (c_i32, [c_vp, c_i32, c_vp, c_vp, c_vp]),
     "msasm_stage_times": (c_i32, [c_vp, P(c_dbl), P(c_i32)]),
+    "msasm_load_table_copy": (c_i32, [c_vp, c_vp, c_vp, c_vp]),
+    "msasm_volume": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "msasm_volume_grad": (c_i32, [c_vp, c_vp, c_vp, c_vp]),
+    "msasm_body_load": (c_i32, [c_vp, c_vp, c_dbl, c_dbl, c_dbl, c_vp, c_vp]),
     "msasm_mlp_create": (c_i32, [c_i32, c_i32, C.c_uint64, P(c_vp)]),
     "msasm_mlp_info": (c_i32, [c_vp, P(c_i64), P(c_i32), P(c_i32)]),
     "msasm_mlp_set_params": (c_i32, [c_vp, c_vp, c_vp]),

@@ -10,6 +10,8 @@
 //      adjoint of step 4).
 //   2. W_t = mat[K]^T G_t (eq. 73 as a product of the lookup table and the state): the adjoint
 //      field at the nodes, W_t[C][i][j][a][b] = sum_m T[m][C][i][j] G_t[m][a][b] (CUDA cores).
+//   The same chain gives the volume gradient (Sec. 4.1.1, eq. 66-67) with W : A_bar replaced by
+//   t_C |det J| (t the volume table): the adjoint field of the volume.
 //   3. Per node: S = d(W : A_bar)/dJ through |det J| and G = J^-1 (FP64), and per control point
 //      dL/dP_a,p = sum_C sum_q S_C[p][q] dB_a/dxi_q (xi_C), a transposed sum factorisation; tiles
 //      sharing a control point add with FP64 atomics.
@@ -99,6 +101,7 @@ struct AdjointArgs {
   double lam, mu;
   const void* W;            // [9 tl + 3a + b][9C + 3i + j]
   int w_f32;
+  const double* vol_w;      // volume mode (W unused): psi = t_C, the volume table (eq. 66-67)
   double* dP;               // (n_ctrl, 3), accumulated
 };
 
@@ -125,6 +128,7 @@ __global__ void adjoint_pullback_kernel(AdjointArgs a) {
       inverse3(J, 1.0 / det, G);
       const double adet = fabs(det);
       auto Wv = [&](int i, int j, int al, int be) -> double {
+        if (a.vol_w) return 0.0;
         const size_t off = size_t(9 * tl + 3 * al + be) * K + 9 * c + 3 * i + j;
         return a.w_f32 ? double(static_cast<const float*>(a.W)[off]) : static_cast<const double*>(a.W)[off];
       };
@@ -137,7 +141,8 @@ __global__ void adjoint_pullback_kernel(AdjointArgs a) {
           GG[i * 3 + j] = G[i * 3] * G[j * 3] + G[i * 3 + 1] * G[j * 3 + 1] + G[i * 3 + 2] * G[j * 3 + 2];
       double psi = 0.0, H[9];
       for (int k = 0; k < 9; ++k) H[k] = 0.0;
-      for (int i = 0; i < 3; ++i)
+      if (a.vol_w) psi = a.vol_w[c];      // d(t_C |det J|)/dJ = t_C |det J| G^T: psi = t_C, H = 0
+      for (int i = 0; i < 3 && !a.vol_w; ++i)
         for (int j = 0; j < 3; ++j) {
           psi += mu * Wd[i * 3 + j] * GG[i * 3 + j];
           for (int g = 0; g < 3; ++g) {      // d/dG[i][g] and d/dG[j][g] of mu Wd[i][j] (G G^T)[i][j]
@@ -253,7 +258,8 @@ template msasm_status transpose_table_gpu<double>(const double*, int, int, doubl
 template msasm_status transpose_table_gpu<float>(const double*, int, int, float*, cudaStream_t);
 
 msasm_status adjoint_pullback_gpu(const msasm_plan* plan, const double* d_ctrl, double lam, double mu, int64_t t0,
-                                  int64_t nt, const void* d_W, bool w_f32, double* d_dP, cudaStream_t s) {
+                                  int64_t nt, const void* d_W, bool w_f32, double* d_dP, cudaStream_t s,
+                                  const double* vol_w) {
   AdjointArgs a;
   a.geo = macro_tile_args(plan, d_ctrl);
   a.t0 = t0;
@@ -262,6 +268,7 @@ msasm_status adjoint_pullback_gpu(const msasm_plan* plan, const double* d_ctrl, 
   a.mu = mu;
   a.W = d_W;
   a.w_f32 = w_f32 ? 1 : 0;
+  a.vol_w = vol_w;
   a.dP = d_dP;
   const int warps = 4;
   const size_t smem = warps * pullback_smem_per_warp(a.geo.np, a.geo.nq);

@@ -56,7 +56,10 @@ msasm_status grad_blocks_gpu(const msasm_plan* plan, const T* d_u, const T* d_gv
 template <typename T>
 msasm_status transpose_table_gpu(const double* d_T, int n_nz, int K, T* d_Tt, cudaStream_t s);
 msasm_status adjoint_pullback_gpu(const msasm_plan* plan, const double* d_ctrl, double lam, double mu, int64_t t0,
-                                  int64_t nt, const void* d_W, bool w_f32, double* d_dP, cudaStream_t s);
+                                  int64_t nt, const void* d_W, bool w_f32, double* d_dP, cudaStream_t s,
+                                  const double* vol_w = nullptr);
+msasm_status volume_load_gpu(const msasm_plan* plan, const double* d_ctrl, double* d_tile_vol, double* d_total,
+                             double* d_f, const double b[3], cudaStream_t s);
 int tc_kind_of(msasm_precision prec);
 int emu_kpad(int K);
 size_t emu_slice_bytes(int64_t rows, int K);
@@ -81,6 +84,8 @@ using namespace msasm;
 
 msasm_tables::~msasm_tables() {
   cudaFree(d_T);
+  cudaFree(d_F);
+  cudaFree(d_vol);
   cudaFree(d_pairs);
   cudaFree(d_T32);
   cudaFree(d_Thi);
@@ -762,6 +767,45 @@ msasm_status msasm_assemble_grad(msasm_plan* plan, const double* d_ctrl, double 
     MSASM_TRY(adjoint_pullback_gpu(plan, d_ctrl, lam, mu, t0, nt, plan->d_coef, !f64, d_grad_ctrl, s));
   }
   return MSASM_OK;
+}
+
+msasm_status msasm_load_table_copy(const msasm_tables* tab, double* d_F, double* d_vol, void* stream) {
+  if (!tab || (!d_F && !d_vol)) return fail(MSASM_EINVAL, "tables is NULL or no output given");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t n_pi = size_t(tab->n_pi);
+  if (d_F)
+    MSASM_CUDA(cudaMemcpyAsync(d_F, tab->d_F, size_t(tab->topo.n_T) * n_pi * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  if (d_vol) MSASM_CUDA(cudaMemcpyAsync(d_vol, tab->d_vol, n_pi * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  return MSASM_OK;
+}
+
+msasm_status msasm_volume(const msasm_plan* plan, const double* d_ctrl, double* d_tile_volume, double* d_total,
+                          void* stream) {
+  if (!plan || !d_ctrl || (!d_tile_volume && !d_total)) return fail(MSASM_EINVAL, "NULL argument or no output");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  double* tv = d_tile_volume;
+  if (!tv) MSASM_CUDA(cudaMallocAsync(&tv, size_t(plan->n_tiles) * sizeof(double), s));
+  msasm_status st = volume_load_gpu(plan, d_ctrl, tv, d_total, nullptr, nullptr, s);
+  if (!d_tile_volume) cudaFreeAsync(tv, s);
+  return st;
+}
+
+msasm_status msasm_volume_grad(const msasm_plan* plan, const double* d_ctrl, double* d_grad_ctrl, void* stream) {
+  if (!plan || !d_ctrl || !d_grad_ctrl) return fail(MSASM_EINVAL, "plan, d_ctrl or d_grad_ctrl is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  MSASM_CUDA(cudaMemsetAsync(d_grad_ctrl, 0, size_t(plan->n_ctrl) * 3 * sizeof(double), s));
+  return adjoint_pullback_gpu(plan, d_ctrl, 0.0, 0.0, 0, plan->n_tiles, nullptr, false, d_grad_ctrl, s,
+                              plan->tab->d_vol);
+}
+
+msasm_status msasm_body_load(const msasm_plan* plan, const double* d_ctrl, double bx, double by, double bz,
+                             double* d_f, void* stream) {
+  if (!plan || !d_ctrl || !d_f) return fail(MSASM_EINVAL, "plan, d_ctrl or d_f is NULL");
+  if (!std::isfinite(bx) || !std::isfinite(by) || !std::isfinite(bz)) return fail(MSASM_EINVAL, "body force not finite");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  MSASM_CUDA(cudaMemsetAsync(d_f, 0, size_t(plan->n_rows) * sizeof(double), s));
+  const double b[3] = {bx, by, bz};
+  return volume_load_gpu(plan, d_ctrl, nullptr, nullptr, d_f, b, s);
 }
 
 msasm_status msasm_degenerate_count(const msasm_plan* plan, int64_t* count, void* stream) {

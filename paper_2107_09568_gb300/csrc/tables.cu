@@ -1,4 +1,5 @@
-// K1: the stiffness lookup table mat[K] (eq. 51-52, 57) in FP64 on the GPU.
+// K1: the stiffness lookup table mat[K] (eq. 51-52, 57) in FP64 on the GPU, and the load and
+// volume tables of eq. 54-55 and 18 from the same 1-D integrals.
 //
 // Every micro patch is an axis-aligned box with an affine map and a tensor-product
 // basis, and the projection basis N_C is a tensor product too, so the 3-D
@@ -124,6 +125,44 @@ __global__ void table_assemble_kernel(const PairDesc* __restrict__ desc, const d
   }
 }
 
+// The load table of eq. 54-55 (F = 0): F[A][C] = int R_A N_C over the tile.  The basis of a patch
+// sums to one in each direction, so the 1-D factor int f_a l_c is the sum over b of the value-value
+// table int f_a f_b l_c; the patches holding A are those of the diagonal pair (A, A).
+__global__ void load_table_kernel(const PairDesc* __restrict__ diag, const double* __restrict__ I1, int n_T, int q,
+                                  int nf, double* __restrict__ F) {
+  const int nq = q + 1, n_pi = nq * nq * nq;
+  const int64_t total = int64_t(n_T) * n_pi;
+  for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < total;
+       idx += int64_t(gridDim.x) * blockDim.x) {
+    const int A = int(idx / n_pi), C = int(idx % n_pi);
+    const int cc[3] = {C % nq, (C / nq) % nq, C / (nq * nq)};
+    const PairDesc pd = diag[A];
+    double v = 0.0;
+    for (int s = 0; s < kMaxPairPatches; ++s) {
+      const int p = pd.patch[s];
+      if (p < 0) continue;
+      double prod = 1.0;
+      for (int d = 0; d < 3; ++d) {
+        double f1 = 0.0;
+        for (int b = 0; b < nf; ++b)
+          f1 += I1[((((int64_t(p) * 3 + d) * 4 + 0) * nf + pd.a[s][d]) * nf + b) * nq + cc[d]];
+        prod *= f1;
+      }
+      v += prod;
+    }
+    F[idx] = v;
+  }
+}
+
+// The volume table of eq. 18: t_C = int N_C over the tile = sum_A F[A][C] (the basis sums to one).
+__global__ void volume_table_kernel(const double* __restrict__ F, int n_T, int n_pi, double* __restrict__ vol) {
+  for (int C = blockIdx.x * blockDim.x + threadIdx.x; C < n_pi; C += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int A = 0; A < n_T; ++A) s += F[int64_t(A) * n_pi + C];
+    vol[C] = s;
+  }
+}
+
 msasm_status build_table_gpu(msasm_tables* tab, cudaStream_t stream) {
   const TileTopology& topo = tab->topo;
   const int q = tab->q, nq = q + 1;
@@ -193,9 +232,24 @@ msasm_status build_table_gpu(msasm_tables* tab, cudaStream_t stream) {
   MSASM_CUDA(cudaGetLastError());
   table_assemble_kernel<<<152 * 8, 256, 0, stream>>>(d_desc, d_I1, tab->n_nz, q, nf_max, tab->d_T);
   MSASM_CUDA(cudaGetLastError());
+  // load and volume tables from the same 1-D integrals
+  std::vector<PairDesc> diag(topo.n_T);
+  for (int m = 0; m < tab->n_nz; ++m)
+    if (topo.pair_A[m] == topo.pair_B[m]) diag[topo.pair_A[m]] = desc[m];
+  const int n_pi = nq * nq * nq;
+  PairDesc* d_diag = nullptr;
+  MSASM_CUDA(cudaMallocAsync(&d_diag, diag.size() * sizeof(PairDesc), stream));
+  MSASM_CUDA(cudaMemcpyAsync(d_diag, diag.data(), diag.size() * sizeof(PairDesc), cudaMemcpyHostToDevice, stream));
+  MSASM_CUDA(cudaMalloc(&tab->d_F, size_t(topo.n_T) * n_pi * sizeof(double)));
+  MSASM_CUDA(cudaMalloc(&tab->d_vol, size_t(n_pi) * sizeof(double)));
+  load_table_kernel<<<152 * 2, 256, 0, stream>>>(d_diag, d_I1, topo.n_T, q, nf_max, tab->d_F);
+  MSASM_CUDA(cudaGetLastError());
+  volume_table_kernel<<<(n_pi + 127) / 128, 128, 0, stream>>>(tab->d_F, topo.n_T, n_pi, tab->d_vol);
+  MSASM_CUDA(cudaGetLastError());
   MSASM_CUDA(cudaFreeAsync(d_I1, stream));
   MSASM_CUDA(cudaFreeAsync(d_desc, stream));
-  MSASM_CUDA(cudaStreamSynchronize(stream));   // `desc` (host) must outlive the copy
+  MSASM_CUDA(cudaFreeAsync(d_diag, stream));
+  MSASM_CUDA(cudaStreamSynchronize(stream));   // `desc` and `diag` (host) must outlive the copies
   return MSASM_OK;
 }
 

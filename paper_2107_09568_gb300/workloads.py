@@ -160,3 +160,22 @@ def adjoint(flush, nx=20, ny=20, nz=5, n_check=20, h=1e-4):
            "fd_coords": coords, "fd_step": h,
            "fd_quadratic_max_abs_diff_over_max_grad": float(np.abs(fdq - gq).max() / np.abs(gq).max())}
     return out
+
+
+def volume(flush, workload="beam1000"):
+    """Volume (eq. 17-19), its gradient (eq. 66-67) and a body-force load (eq. 53) of a workload."""
+    import torch
+    import paper_2107_09568_gb300 as msasm
+    import synth
+    w = synth.workload(workload)
+    plan = msasm.Plan(msasm.Tables(synth.micro_cross(w.n_e, w.width), w.q), w.macro)
+    ctrl = torch.tensor(w.macro.ctrl, device="cuda")
+    (vt, V), ms_v = _timed(lambda: plan.volume(ctrl), reps=5, flush=flush)
+    g, ms_g = _timed(lambda: plan.volume_grad(ctrl), reps=5, flush=flush)
+    f, ms_f = _timed(lambda: plan.body_load(ctrl, (0.0, 0.0, -9.81)), reps=5, flush=flush)
+    return {"tiles": plan.n_tiles, "volume": V.item(), "volume_ms": ms_v, "volume_grad_ms": ms_g,
+            "body_load_ms": ms_f,
+            "grad_translation_residual": (g.sum(dim=0).abs().max() / g.abs().max()).item(),
+            "grad_euler_residual": abs((ctrl * g).sum().item() - 3 * V.item()) / V.item(),
+            "load_total_residual": abs(f.sum().item() + 9.81 * V.item()) / (9.81 * V.item())}
+
