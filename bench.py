@@ -55,7 +55,7 @@ def parse():
                     help="comma list of extra precision forms to report")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--report", default="", help="comma list of: forms1000, forms4000, surrogate, adjoint, volume "
+    ap.add_argument("--report", default="", help="comma list of: forms1000, forms4000, surrogate, adjoint, volume, linop "
                                                  "(prints a JSON report instead of the bench line)")
     return ap.parse_args()
 
@@ -269,6 +269,8 @@ def run_report(args):
             out[item] = wl.adjoint(flush)
         elif item == "volume":
             out[item] = wl.volume(flush)
+        elif item == "linop":
+            out[item] = wl.linop(flush)
         else:
             continue
         out[item]["wall_s"] = time.perf_counter() - t0

@@ -287,6 +287,18 @@ msasm_status msasm_contract_noalloc(const msasm_tables* tab, const double* d_coe
 msasm_status msasm_scatter(msasm_plan* plan, msasm_precision prec, const void* d_nz,
                            void* d_values, void* stream);
 
+/* ---------------------------------------------------------------- matrix-free operator */
+
+/* y = K u without the global CSR values (Sec. 4.2, eq. 74): the tile matrices are formed on the
+ * fly from the lookup table and the projection coefficients d_coef (9 n_tiles x 9 n_pi FP64, as
+ * written by msasm_pullback) by the contraction of eq. 58 in precision `prec`, pass by pass in the
+ * plan's scratch, and applied to u.  d_u, d_y: n_rows FP64 (y overwritten; every row is written
+ * by the tile that owns it, then the glued-face blocks are added with atomics, so the last bits of
+ * those rows may vary between calls).  The first call builds per-type column maps.
+ * Errors: EINVAL, EUNSUPPORTED, ECUDA. */
+msasm_status msasm_linop_apply(msasm_plan* plan, const double* d_coef, msasm_precision prec, const double* d_u,
+                               double* d_y, void* stream);
+
 /* ---------------------------------------------------------------- volume and loads */
 
 /* The load lookup table of eq. 54-55 (body term, F = 0): d_F[A][C] = int_{Omega_T} R_A N_C

@@ -234,6 +234,16 @@ def _plan_body_load(self, ctrl, b, stream=None):
     return f
 
 
+def _plan_linop(self, coef, u, precision="f64", out=None, stream=None):
+    """y = K u matrix-free (eq. 74) from the coefficients of plan.pullback(ctrl)."""
+    import torch
+    y = torch.empty(self.n_rows, dtype=torch.float64, device="cuda") if out is None else out
+    check(load().msasm_linop_apply(self.handle, _ptr(coef), PRECISIONS[precision], _ptr(u), _ptr(y),
+                                   _stream(stream)))
+    return y
+
+
+Plan.linop = _plan_linop
 Plan.assemble_grad = _plan_assemble_grad
 Plan.face_points = _plan_face_points
 Plan.traction_load = _plan_traction_load

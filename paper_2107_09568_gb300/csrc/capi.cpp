@@ -58,6 +58,10 @@ msasm_status transpose_table_gpu(const double* d_T, int n_nz, int K, T* d_Tt, cu
 msasm_status adjoint_pullback_gpu(const msasm_plan* plan, const double* d_ctrl, double lam, double mu, int64_t t0,
                                   int64_t nt, const void* d_W, bool w_f32, double* d_dP, cudaStream_t s,
                                   const double* vol_w = nullptr);
+msasm_status linop_prepare_gpu(msasm_plan* plan, cudaStream_t s);
+template <typename T>
+msasm_status linop_pass_gpu(const msasm_plan* plan, const T* d_nz, int ld_nz, int64_t t0, int64_t n_tiles,
+                            const double* d_u, double* d_y, cudaStream_t s);
 msasm_status volume_load_gpu(const msasm_plan* plan, const double* d_ctrl, double* d_tile_vol, double* d_total,
                              double* d_f, const double b[3], cudaStream_t s);
 int tc_kind_of(msasm_precision prec);
@@ -116,6 +120,9 @@ msasm_plan::~msasm_plan() {
   cudaFree(d_tmpl);
   cudaFree(d_tmpl_ptr);
   cudaFree(d_sec_off);
+  cudaFree(d_colmaps);
+  cudaFree(d_type_rows);
+  cudaFree(d_type_row_off);
   cudaFree(d_sec);
   cudaFree(d_coef);
   cudaFree(d_nz);
@@ -303,6 +310,12 @@ msasm_status msasm_plan_create(const msasm_tables* tab, const msasm_macro_desc* 
   }
   plan->item_ptr = sp.item_ptr;
   plan->sec_off_host = sp.sec_off;
+  plan->type_rep_host = sp.type_rep;
+  plan->type_map_off_host = sp.type_map_off;
+  plan->type_row_off_host = sp.type_row_off;
+  plan->type_rows_host = sp.type_rows;
+  for (size_t ty = 0; ty + 1 < sp.type_row_off.size(); ++ty)
+    plan->max_type_rows = std::max<int>(plan->max_type_rows, int(sp.type_row_off[ty + 1] - sp.type_row_off[ty]));
   const int n_types = int(sp.type_rep.size());
   const int n_nz = tab->n_nz;
 
@@ -765,6 +778,27 @@ msasm_status msasm_assemble_grad(msasm_plan* plan, const double* d_ctrl, double 
       MSASM_TRY(gemm_simt<float>(G, ld, tab->d_Tt32, n_nz, 9 * nt, K, n_nz, W, K, s));
     }
     MSASM_TRY(adjoint_pullback_gpu(plan, d_ctrl, lam, mu, t0, nt, plan->d_coef, !f64, d_grad_ctrl, s));
+  }
+  return MSASM_OK;
+}
+
+msasm_status msasm_linop_apply(msasm_plan* plan, const double* d_coef, msasm_precision prec, const double* d_u,
+                               double* d_y, void* stream) {
+  if (!plan || !d_coef || !d_u || !d_y) return fail(MSASM_EINVAL, "plan, d_coef, d_u or d_y is NULL");
+  if (prec < MSASM_F64 || prec > MSASM_F64_EMU) return fail(MSASM_EINVAL, "unknown precision");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  MSASM_TRY(linop_prepare_gpu(plan, s));
+  MSASM_TRY(ensure_lp_scratch(plan, prec));
+  const int K = 9 * plan->tab->n_pi, ld = ld_nz_of(plan->tab->n_nz);
+  const int64_t P = plan->tiles_per_pass;
+  for (int64_t t0 = 0; t0 < plan->n_tiles; t0 += P) {
+    const int64_t nt = std::min(P, plan->n_tiles - t0);
+    MSASM_TRY(contract_dispatch(plan->tab, prec, d_coef + size_t(9 * t0) * K, nt, plan->d_nz, plan->d_coef_lp, s,
+                                plan->d_tc_err));
+    if (is_f64_precision(prec))
+      MSASM_TRY(linop_pass_gpu<double>(plan, static_cast<const double*>(plan->d_nz), ld, t0, nt, d_u, d_y, s));
+    else
+      MSASM_TRY(linop_pass_gpu<float>(plan, reinterpret_cast<const float*>(plan->d_nz), ld, t0, nt, d_u, d_y, s));
   }
   return MSASM_OK;
 }

@@ -95,6 +95,8 @@ struct ScatterPlanHost {
   std::vector<uint32_t> tmpl;              // secondary template per type: m | upper << 30 | lower << 31
   std::vector<int64_t> tmpl_ptr;
   std::vector<int64_t> sec_off;            // per tile: first secondary entry (n_tiles + 1)
+  std::vector<int32_t> type_rows;          // per type, per owned row: offset in the range, length, A << 2 | a
+  std::vector<int64_t> type_row_off;       // per type: first row in type_rows (n_types + 1)
 };
 
 }  // namespace msasm
@@ -157,6 +159,13 @@ struct msasm_plan {
   int64_t* d_sec_off = nullptr;              // secondary entries of tile t: [sec_off[t], sec_off[t+1])
   msasm::SecondaryEntry* d_sec = nullptr;
   std::vector<int64_t> sec_off_host;
+  // matrix-free operator (built at its first use): per-type column maps and row tables
+  std::vector<int64_t> type_rep_host, type_map_off_host, type_row_off_host;
+  std::vector<int32_t> type_rows_host;
+  int max_type_rows = 0;
+  int32_t* d_colmaps = nullptr;              // per value: column point << 2 | beta (same offsets as d_maps)
+  int32_t* d_type_rows = nullptr;
+  int64_t* d_type_row_off = nullptr;
   std::vector<double> knots_host[3];  // host copies for boundary data
   std::vector<int> span_host[3];      // knot index of each element's span
   std::vector<int32_t> gmap_host;

@@ -46,6 +46,8 @@ msasm_status build_scatter_plan(msasm_plan* plan, const std::vector<int32_t>& gm
   out.type_map_off.assign(size_t(n_types) + 1, 0);
   out.tmpl_ptr.assign(size_t(n_types) + 1, 0);
   out.tmpl.clear();
+  out.type_rows.clear();
+  out.type_row_off.assign(1, 0);
   std::vector<std::vector<char>> owned_of(static_cast<size_t>(n_types));
   std::vector<std::vector<int64_t>> deg_of(static_cast<size_t>(n_types));
   for (int ty = 0; ty < n_types; ++ty) {
@@ -67,6 +69,20 @@ msasm_status build_scatter_plan(msasm_plan* plan, const std::vector<int32_t>& gm
     if (vals >= (int64_t(1) << 31)) return fail(MSASM_EUNSUPPORTED, "a tile owns more than 2^31 values");
     out.type_nvals[size_t(ty)] = int32_t(vals);
     out.type_map_off[size_t(ty) + 1] = out.type_map_off[size_t(ty)] + vals;
+    {
+      int32_t off = 0;
+      for (int A = 0; A < n_T; ++A) {
+        if (!owned[size_t(A)]) continue;
+        const int32_t L = int32_t(3 * deg_of[size_t(ty)][size_t(A)]);
+        for (int a = 0; a < 3; ++a) {
+          out.type_rows.push_back(off + a * L);
+          out.type_rows.push_back(L);
+          out.type_rows.push_back((A << 2) | a);
+        }
+        off += 3 * L;
+      }
+      out.type_row_off.push_back(int64_t(out.type_rows.size() / 3));
+    }
     for (int m = 0; m < n_nz; ++m) {
       const int A = topo.pair_A[m], B = topo.pair_B[m];
       uint32_t flags = 0;

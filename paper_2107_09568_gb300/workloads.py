@@ -179,3 +179,29 @@ def volume(flush, workload="beam1000"):
             "grad_euler_residual": abs((ctrl * g).sum().item() - 3 * V.item()) / V.item(),
             "load_total_residual": abs(f.sum().item() + 9.81 * V.item()) / (9.81 * V.item())}
 
+
+def linop(flush, workload="beam1000"):
+    """Matrix-free y = K u (eq. 74) against the CSR product of the assembled matrix: time per product
+    and the memory each needs beyond the tables."""
+    import torch
+    import paper_2107_09568_gb300 as msasm
+    import synth
+    w = synth.workload(workload)
+    plan = msasm.Plan(msasm.Tables(synth.micro_cross(w.n_e, w.width), w.q), w.macro)
+    ctrl = torch.tensor(w.macro.ctrl, device="cuda")
+    coef = plan.pullback(ctrl)
+    u = torch.randn(plan.n_rows, dtype=torch.float64, device="cuda")
+    out = {"tiles": plan.n_tiles, "nnz": plan.nnz,
+           "csr_bytes_f64": plan.nnz * (8 + 4) + (plan.n_rows + 1) * 8,
+           "linop_scratch_bytes_f64": 9 * plan.n_tiles * ((plan.tables.n_nz + 7) // 8 * 8) * 8 + coef.numel() * 8}
+    y = torch.empty_like(u)
+    for prec in ("f64_emu", "split_f16"):
+        _, ms = _timed(lambda: plan.linop(coef, u, prec, out=y), reps=5, flush=flush)
+        out[f"linop_ms_{prec}"] = ms
+    K = msasm.csr_matrix(plan, plan.assemble(ctrl, 1.0, 0.3, "f64_emu"))
+    yk, ms_csr = _timed(lambda: K @ u, reps=5, flush=flush)
+    out["csr_spmv_ms_f64"] = ms_csr
+    out["rel_linop_vs_csr_f64_emu"] = (torch.linalg.vector_norm(plan.linop(coef, u, "f64_emu") - yk)
+                                       / torch.linalg.vector_norm(yk)).item()
+    return out
+
