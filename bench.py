@@ -55,7 +55,7 @@ def parse():
                     help="comma list of extra precision forms to report")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--report", default="", help="comma list of: forms1000, forms4000, surrogate, adjoint, volume, linop "
+    ap.add_argument("--report", default="", help="comma list of: forms1000, forms4000, surrogate, adjoint, volume, linop, projection "
                                                  "(prints a JSON report instead of the bench line)")
     return ap.parse_args()
 
@@ -271,6 +271,8 @@ def run_report(args):
             out[item] = wl.volume(flush)
         elif item == "linop":
             out[item] = wl.linop(flush)
+        elif item == "projection":
+            out[item] = wl.projection(flush)
         else:
             continue
         out[item]["wall_s"] = time.perf_counter() - t0

@@ -299,6 +299,18 @@ msasm_status msasm_scatter(msasm_plan* plan, msasm_precision prec, const void* d
 msasm_status msasm_linop_apply(msasm_plan* plan, const double* d_coef, msasm_precision prec, const double* d_u,
                                double* d_y, void* stream);
 
+/* ---------------------------------------------------------------- projection error */
+
+/* Relative projection error of the macro field (eq. 59, the quantity of eq. 47-48) for the
+ * interpolation degree q (0..7; independent of the plan's own q): per tile, the largest over the
+ * sample points xi_s = (s + 1/2)/n_samples (n_samples per direction, 1..8) of
+ * ||A_bar - Pi A_bar||_F / ||A_bar||_F over the 81 components, into d_err_tiles (n_tiles FP64,
+ * may be NULL) and the largest over the tiles into d_err_max (one FP64, may be NULL; not both).
+ * The degree of eq. 65 is the smallest q whose error is below a tolerance.  Synchronises `stream`.
+ * Errors: EINVAL, EUNSUPPORTED, ECUDA. */
+msasm_status msasm_projection_error(const msasm_plan* plan, const double* d_ctrl, int32_t q, int32_t n_samples,
+                                    double E, double nu, double* d_err_tiles, double* d_err_max, void* stream);
+
 /* ---------------------------------------------------------------- volume and loads */
 
 /* The load lookup table of eq. 54-55 (body term, F = 0): d_F[A][C] = int_{Omega_T} R_A N_C

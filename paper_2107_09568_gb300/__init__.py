@@ -243,6 +243,25 @@ def _plan_linop(self, coef, u, precision="f64", out=None, stream=None):
     return y
 
 
+def _plan_projection_error(self, ctrl, q, n_samples=5, E=1.0, nu=0.3, stream=None):
+    """(per-tile errors (n_tiles,), E_proj) of eq. 59 for interpolation degree q."""
+    import torch
+    e = torch.empty(self.n_tiles, dtype=torch.float64, device="cuda")
+    m = torch.empty((), dtype=torch.float64, device="cuda")
+    check(load().msasm_projection_error(self.handle, _ptr(ctrl), int(q), int(n_samples), float(E), float(nu),
+                                        _ptr(e), _ptr(m), _stream(stream)))
+    return e, m
+
+
+def select_projection_degree(plan, ctrl, tol, q0, q_max, **kw):
+    """Smallest q in [q0, q_max] with E_proj <= tol (eq. 65), else q_max."""
+    for q in range(q0, q_max + 1):
+        if plan.projection_error(ctrl, q, **kw)[1].item() <= tol:
+            return q
+    return q_max
+
+
+Plan.projection_error = _plan_projection_error
 Plan.linop = _plan_linop
 Plan.assemble_grad = _plan_assemble_grad
 Plan.face_points = _plan_face_points

@@ -61,6 +61,7 @@ _SIGS = {
     "msasm_stage_times": (c_i32, [c_vp, P(c_dbl), P(c_i32)]),
     "msasm_load_table_copy": (c_i32, [c_vp, c_vp, c_vp, c_vp]),
     "msasm_linop_apply": (c_i32, [c_vp, c_vp, c_i32, c_vp, c_vp, c_vp]),
+    "msasm_projection_error": (c_i32, [c_vp, c_vp, c_i32, c_i32, c_dbl, c_dbl, c_vp, c_vp, c_vp]),
     "msasm_volume": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp]),
     "msasm_volume_grad": (c_i32, [c_vp, c_vp, c_vp, c_vp]),
     "msasm_body_load": (c_i32, [c_vp, c_vp, c_dbl, c_dbl, c_dbl, c_vp, c_vp]),

@@ -59,6 +59,8 @@ msasm_status adjoint_pullback_gpu(const msasm_plan* plan, const double* d_ctrl, 
                                   int64_t nt, const void* d_W, bool w_f32, double* d_dP, cudaStream_t s,
                                   const double* vol_w = nullptr);
 msasm_status linop_prepare_gpu(msasm_plan* plan, cudaStream_t s);
+msasm_status projection_error_gpu(const msasm_plan* plan, const double* d_ctrl, int q, int n_s, double lam, double mu,
+                                  double* d_err_tiles, double* d_err_max, cudaStream_t s);
 template <typename T>
 msasm_status linop_pass_gpu(const msasm_plan* plan, const T* d_nz, int ld_nz, int64_t t0, int64_t n_tiles,
                             const double* d_u, double* d_y, cudaStream_t s);
@@ -801,6 +803,16 @@ msasm_status msasm_linop_apply(msasm_plan* plan, const double* d_coef, msasm_pre
       MSASM_TRY(linop_pass_gpu<float>(plan, reinterpret_cast<const float*>(plan->d_nz), ld, t0, nt, d_u, d_y, s));
   }
   return MSASM_OK;
+}
+
+msasm_status msasm_projection_error(const msasm_plan* plan, const double* d_ctrl, int32_t q, int32_t n_samples,
+                                    double E, double nu, double* d_err_tiles, double* d_err_max, void* stream) {
+  if (!plan || !d_ctrl || (!d_err_tiles && !d_err_max)) return fail(MSASM_EINVAL, "NULL argument or no output");
+  MSASM_TRY(check_material(E, nu));
+  double lam, mu;
+  lame(E, nu, lam, mu);
+  return projection_error_gpu(plan, d_ctrl, q, n_samples, lam, mu, d_err_tiles, d_err_max,
+                              static_cast<cudaStream_t>(stream));
 }
 
 msasm_status msasm_load_table_copy(const msasm_tables* tab, double* d_F, double* d_vol, void* stream) {

@@ -1,0 +1,191 @@
+// Projection error of the macro field (Sec. 3.2.2, eq. 47-48; Sec. 3.3, eq. 59): for every tile,
+// max over sample points xi_s of ||A_bar(xi_s) - Pi A_bar(xi_s)||_F / ||A_bar(xi_s)||_F over the 81
+// components, Pi the interpolant at the (q+1)^3 nodes of a given degree q (the reading of the
+// projection used throughout).  Samples: the uniform interior grid (s + 1/2)/n_s per direction.
+// The exact field at the samples comes from the node Jacobians of the same sum factorisation
+// with the macro basis tabulated at the samples; the interpolant from the pullback coefficients at
+// the q nodes (computed with the macro basis tabulated at those nodes).  One warp per tile.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "common.h"
+#include "macro_jacobian.cuh"
+
+namespace msasm {
+
+MacroTileArgs macro_tile_args(const msasm_plan* plan, const double* d_ctrl);
+msasm_status pullback_geo_gpu(const MacroTileArgs& geo, int64_t n_tiles, double lam, double mu, double* d_coef,
+                              unsigned long long* d_degenerate, cudaStream_t stream);
+int bspline_find_span(const double* t, int n_knots, int p, double u);
+void bspline_span_basis(const double* t, int p, int span, double u, double* vals, double* ders);
+void gauss_legendre01(int n, std::vector<double>& x, std::vector<double>& w);
+
+struct ProjErrArgs {
+  MacroTileArgs geo;         // macro basis at the samples (n_s per direction)
+  int64_t n_tiles;
+  double lam, mu;
+  const double* coef;        // pullback at the q nodes: [9t + 3a + b][9C + 3i + j]
+  int nq;                    // q + 1
+  const double* lag;         // [s][c]: l_c(x_s), the 1-D Lagrange basis of the nodes at the samples
+  double* err;               // per tile
+};
+
+__global__ void projection_error_kernel(ProjErrArgs a) {
+  extern __shared__ double smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
+  const int ns = a.geo.nq, n_s = ns * ns * ns, nq = a.nq, n_pi = nq * nq * nq, K = 9 * n_pi;
+  int nP, nS, nU, nJ;
+  jac_scratch_sizes(a.geo.np, ns, nP, nS, nU, nJ);
+  double* P = smem + size_t(warp) * (nP + nS + nU + nJ);
+  double* S = P + nP;
+  double* U = S + nS;
+  double* Js = U + nU;
+  for (int64_t t = int64_t(blockIdx.x) * warps + warp; t < a.n_tiles; t += int64_t(gridDim.x) * warps) {
+    tile_node_jacobians(a.geo, t, P, S, U, Js, lane);
+    const double* ct = a.coef + size_t(9 * t) * K;
+    double worst = 0.0;
+    for (int sp = lane; sp < n_s; sp += 32) {
+      const int s1 = sp % ns, s2 = (sp / ns) % ns, s3 = sp / (ns * ns);
+      const double* J = Js + 9 * sp;
+      const double det = det3(J);
+      double G[9];
+      inverse3(J, 1.0 / det, G);
+      const double adet = fabs(det);
+      double GG[9];
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+          GG[i * 3 + j] = G[i * 3] * G[j * 3] + G[i * 3 + 1] * G[j * 3 + 1] + G[i * 3 + 2] * G[j * 3 + 2];
+      double d2 = 0.0, e2 = 0.0;
+      for (int al = 0; al < 3; ++al)
+        for (int be = 0; be < 3; ++be) {
+          const double* row = ct + size_t(3 * al + be) * K;
+          for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+              double ex = adet * (a.lam * G[i * 3 + al] * G[j * 3 + be] + a.mu * G[i * 3 + be] * G[j * 3 + al]);
+              if (al == be) ex += adet * a.mu * GG[i * 3 + j];
+              double ip = 0.0;
+              for (int C = 0; C < n_pi; ++C) {
+                const int c1 = C % nq, c2 = (C / nq) % nq, c3 = C / (nq * nq);
+                const double l = a.lag[s1 * nq + c1] * a.lag[s2 * nq + c2] * a.lag[s3 * nq + c3];
+                ip = fma(l, row[9 * C + 3 * i + j], ip);
+              }
+              d2 = fma(ex - ip, ex - ip, d2);
+              e2 = fma(ex, ex, e2);
+            }
+        }
+      worst = fmax(worst, sqrt(d2 / e2));
+    }
+    for (int o = 16; o; o >>= 1) worst = fmax(worst, __shfl_xor_sync(0xffffffffu, worst, o));
+    if (lane == 0) a.err[t] = worst;
+    __syncwarp();
+  }
+}
+
+__global__ void max_kernel(const double* __restrict__ x, int64_t n, double* __restrict__ out) {
+  __shared__ double part[256];
+  double m = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, x[i]);
+  part[threadIdx.x] = m;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (int(threadIdx.x) < w) part[threadIdx.x] = fmax(part[threadIdx.x], part[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = part[0];
+}
+
+// macro basis tables of the plan's spans at the points x (per direction [e][point][a][value, d/dxi])
+static void basis_tables(const msasm_plan* plan, const std::vector<double>& x, std::vector<double> (&basis)[3]) {
+  for (int d = 0; d < 3; ++d) {
+    const std::vector<double>& t = plan->knots_host[d];
+    const int p = plan->degree[d];
+    basis[d].clear();
+    for (int k : plan->span_host[d]) {
+      const double u0 = t[size_t(k)], h = t[size_t(k) + 1] - t[size_t(k)];
+      for (double xc : x) {
+        double vals[8], ders[8];
+        bspline_span_basis(t.data(), p, k, u0 + h * xc, vals, ders);
+        for (int a = 0; a <= p; ++a) {
+          basis[d].push_back(vals[a]);
+          basis[d].push_back(ders[a] * h);
+        }
+      }
+    }
+  }
+}
+
+msasm_status projection_error_gpu(const msasm_plan* plan, const double* d_ctrl, int q, int n_s, double lam, double mu,
+                                  double* d_err_tiles, double* d_err_max, cudaStream_t s) {
+  if (q < 0 || q > 7 || n_s < 1 || n_s > 8) return fail(MSASM_EINVAL, "need 0 <= q <= 7 and 1 <= n_samples <= 8");
+  const int nq = q + 1, K = 9 * nq * nq * nq;
+  std::vector<double> xn, wn, xs(static_cast<size_t>(n_s));
+  gauss_legendre01(nq, xn, wn);
+  for (int i = 0; i < n_s; ++i) xs[size_t(i)] = (i + 0.5) / n_s;
+  std::vector<double> bn[3], bs[3];
+  basis_tables(plan, xn, bn);
+  basis_tables(plan, xs, bs);
+  std::vector<double> lag(size_t(n_s) * nq);
+  for (int i = 0; i < n_s; ++i)
+    for (int c = 0; c < nq; ++c) {
+      double l = 1.0;
+      for (int k = 0; k < nq; ++k)
+        if (k != c) l *= (xs[size_t(i)] - xn[size_t(k)]) / (xn[size_t(c)] - xn[size_t(k)]);
+      lag[size_t(i) * nq + c] = l;
+    }
+  size_t nb = lag.size();
+  for (int d = 0; d < 3; ++d) nb += bn[d].size() + bs[d].size();
+  const size_t coef_n = size_t(9 * plan->n_tiles) * K;
+  double* buf = nullptr;
+  MSASM_CUDA(cudaMallocAsync(&buf, (nb + coef_n + plan->n_tiles + 2) * sizeof(double), s));
+  double* cur = buf;
+  auto put = [&](const std::vector<double>& v) -> double* {
+    double* p = cur;
+    cudaMemcpyAsync(p, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+    cur += v.size();
+    return p;
+  };
+  MacroTileArgs gn = macro_tile_args(plan, d_ctrl), gs = gn;
+  gn.nq = nq;
+  gs.nq = n_s;
+  for (int d = 0; d < 3; ++d) {
+    gn.basis[d] = put(bn[d]);
+    gs.basis[d] = put(bs[d]);
+  }
+  const double* d_lag = put(lag);
+  double* coef = cur;
+  cur += coef_n;
+  double* err = d_err_tiles ? d_err_tiles : cur;
+  msasm_status st = pullback_geo_gpu(gn, plan->n_tiles, lam, mu, coef, plan->d_degenerate, s);
+  if (st == MSASM_OK) {
+    ProjErrArgs a;
+    a.geo = gs;
+    a.n_tiles = plan->n_tiles;
+    a.lam = lam;
+    a.mu = mu;
+    a.coef = coef;
+    a.nq = nq;
+    a.lag = d_lag;
+    a.err = err;
+    int nP, nS, nU, nJ;
+    jac_scratch_sizes(gs.np, n_s, nP, nS, nU, nJ);
+    const int warps = 2;
+    const size_t smem = warps * size_t(nP + nS + nU + nJ) * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(projection_error_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) st = cuda_fail(e, "projection error kernel");
+    if (st == MSASM_OK) {
+      const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((plan->n_tiles + warps - 1) / warps, 152 * 16));
+      projection_error_kernel<<<unsigned(blocks), 32 * warps, smem, s>>>(a);
+      if ((e = cudaGetLastError()) != cudaSuccess) st = cuda_fail(e, "projection error kernel");
+    }
+    if (st == MSASM_OK && d_err_max) {
+      max_kernel<<<1, 256, 0, s>>>(err, plan->n_tiles, d_err_max);
+      if ((e = cudaGetLastError()) != cudaSuccess) st = cuda_fail(e, "max");
+    }
+  }
+  cudaStreamSynchronize(s);                      // the host tables outlive the copies
+  cudaFreeAsync(buf, s);
+  return st;
+}
+
+}  // namespace msasm

@@ -11,6 +11,7 @@
 //
 // the Cartesian form of G_i C G_j^T |det J| (eq. 37, 84, 91-97), written as the
 // transposed coefficient matrix coef[9t + 3a + b][9C + 3i + j].
+#include <algorithm>
 #include <cmath>
 
 #include "common.h"
@@ -112,6 +113,27 @@ msasm_status pullback_gpu(const msasm_plan* plan, const double* d_ctrl, double l
   int64_t blocks = (n_tiles + warps - 1) / warps;
   if (blocks > 152 * 16) blocks = 152 * 16;
   if (blocks < 1) blocks = 1;
+  pullback_kernel<<<unsigned(blocks), 32 * warps, smem, stream>>>(a);
+  MSASM_CUDA(cudaGetLastError());
+  return MSASM_OK;
+}
+
+// The pullback at another set of nodes (the macro basis tables of geo), for tiles [0, n_tiles).
+msasm_status pullback_geo_gpu(const MacroTileArgs& geo, int64_t n_tiles, double lam, double mu, double* d_coef,
+                              unsigned long long* d_degenerate, cudaStream_t stream) {
+  PullbackArgs a;
+  a.geo = geo;
+  a.t0 = 0;
+  a.n_tiles = n_tiles;
+  a.lam = lam;
+  a.mu = mu;
+  a.coef = d_coef;
+  a.degenerate = d_degenerate;
+  const int warps = 2;
+  const size_t smem = warps * pullback_smem_per_warp(a.geo.np, a.geo.nq);
+  if (smem > 200 * 1024) return fail(MSASM_EUNSUPPORTED, "macro degree / q too large for the pullback kernel");
+  MSASM_CUDA(cudaFuncSetAttribute(pullback_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((n_tiles + warps - 1) / warps, 152 * 16));
   pullback_kernel<<<unsigned(blocks), 32 * warps, smem, stream>>>(a);
   MSASM_CUDA(cudaGetLastError());
   return MSASM_OK;

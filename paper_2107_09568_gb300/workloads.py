@@ -180,6 +180,23 @@ def volume(flush, workload="beam1000"):
             "load_total_residual": abs(f.sum().item() + 9.81 * V.item()) / (9.81 * V.item())}
 
 
+def projection(flush, workload="beam1000"):
+    """E_proj (eq. 59) of a workload for q = 0..6 (5^3 samples per tile) and the degree of eq. 65."""
+    import torch
+    import paper_2107_09568_gb300 as msasm
+    import synth
+    w = synth.workload(workload)
+    plan = msasm.Plan(msasm.Tables(synth.micro_cross(w.n_e, w.width), w.q), w.macro)
+    ctrl = torch.tensor(w.macro.ctrl, device="cuda")
+    out = {"tiles": plan.n_tiles, "samples_per_tile": 125}
+    for q in range(0, 7):
+        (_, m), ms = _timed(lambda: plan.projection_error(ctrl, q, 5), reps=3, flush=flush)
+        out[f"E_proj_q{q}"] = m.item()
+        out[f"ms_q{q}"] = ms
+    out["degree_for_tol_1e-3"] = msasm.select_projection_degree(plan, ctrl, 1e-3, 0, 7)
+    return out
+
+
 def linop(flush, workload="beam1000"):
     """Matrix-free y = K u (eq. 74) against the CSR product of the assembled matrix: time per product
     and the memory each needs beyond the tables."""
