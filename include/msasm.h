@@ -25,8 +25,9 @@
  *    Work is queued on it and the call returns without synchronising, except
  *    where a call is documented to read a result back to the host.
  *  - A plan holds scratch (coefficients, nzdata, slices) that its calls reuse, so
- *    one plan serves one stream at a time; tables are read-only after creation and
- *    may be shared by plans on different streams.
+ *    one plan serves one stream at a time.  Tables make their sliced copies for a
+ *    precision form at the first call that needs them; after that they are only
+ *    read and may be shared by plans on different streams.
  *  - Tile t = (ix, iy, iz) of an nx x ny x nz macro mesh has linear index
  *    ix + nx*(iy + ny*iz).  Interpolation node C = c1 + (q+1)*(c2 + (q+1)*c3)
  *    with the q+1 Gauss-Legendre points of [0,1] ascending per direction.
