@@ -55,7 +55,7 @@ def parse():
                     help="comma list of extra precision forms to report")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--report", default="", help="comma list of: forms1000, forms4000, surrogate, adjoint, volume, linop, projection "
+    ap.add_argument("--report", default="", help="comma list of: forms1000, forms4000, surrogate, adjoint, volume, linop, projection, cpu_forms "
                                                  "(prints a JSON report instead of the bench line)")
     return ap.parse_args()
 
@@ -213,6 +213,25 @@ def cpu_reference_time(workload, n_sample, seed=0):
     return dt, len(tiles)
 
 
+def cpu_forms_report(workload, n_tiles=2):
+    """The oracle's lookup form against its full-quadrature (standard) form on the host cores, per tile
+    (the paper's T_cost of eq. 64, here for the FP64 CPU oracle): context only."""
+    import synth
+    from oracle.assembly import Problem, nzdata_lookup, tile_blocks_quadrature
+    w = synth.workload(workload)
+    prob = Problem(synth.micro_cross(w.n_e), w.macro, w.q, structure=False)
+    tiles = list(range(n_tiles))
+    t0 = time.perf_counter()
+    nzdata_lookup(prob.T, prob.mmap, prob.q, prob.lam, prob.mu, tiles=tiles)
+    t_look = (time.perf_counter() - t0) / n_tiles
+    t0 = time.perf_counter()
+    for t in tiles:
+        tile_blocks_quadrature(prob.tile, prob.mmap, t, prob.lam, prob.mu)
+    t_quad = (time.perf_counter() - t0) / n_tiles
+    return {"tiles": n_tiles, "lookup_s_per_tile": t_look, "quadrature_s_per_tile": t_quad,
+            "t_cost": t_quad / t_look, "cores": threads_used()}
+
+
 def threads_used():
     try:
         import threadpoolctl
@@ -273,6 +292,8 @@ def run_report(args):
             out[item] = wl.linop(flush)
         elif item == "projection":
             out[item] = wl.projection(flush)
+        elif item == "cpu_forms":
+            out[item] = cpu_forms_report(args.workload)
         else:
             continue
         out[item]["wall_s"] = time.perf_counter() - t0
