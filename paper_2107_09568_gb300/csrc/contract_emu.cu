@@ -55,7 +55,6 @@ struct EmuParams {
   const int* exp_n;        // tau_n = 2^exp_n
   double* out;             // nz[n][m], leading dimension ld
   int ld;
-  int accumulate;          // add to out instead of overwriting it (a K-split product, summed in FP64)
   unsigned* err;
 };
 
@@ -111,6 +110,7 @@ __device__ __forceinline__ long long f32_to_i64_rn(float y) {
   return (b >> 31) ? -(long long)r : (long long)r;
 }
 
+template <bool ACCUMULATE>
 __global__ void __launch_bounds__(EMU_THREADS, 1)
     contract_emu_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, EmuParams p) {
   extern __shared__ uint8_t smem_raw[];
@@ -274,7 +274,8 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
           if (n < p.N) {
             double* o = p.out + size_t(n) * p.ld + m;
             const double v = ldexp_i64_rn(X[j], em + p.exp_n[n]);
-            *o = p.accumulate ? *o + v : v;
+            if constexpr (ACCUMULATE) *o += v;
+            else *o = v;
           }
         }
       }
@@ -420,16 +421,16 @@ msasm_status contract_emu_gpu(const void* a_slices, const int* a_exp, int M, con
   p.exp_n = b_exp;
   p.out = out;
   p.ld = ld;
-  p.accumulate = accumulate ? 1 : 0;
   p.err = d_err;
-  MSASM_CUDA(cudaFuncSetAttribute(contract_emu_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, EMU_SMEM_BYTES));
+  auto kernel = accumulate ? contract_emu_kernel<true> : contract_emu_kernel<false>;
+  MSASM_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, EMU_SMEM_BYTES));
   const long long tiles = ((N + EMU_BN - 1) / EMU_BN) * (long long)((M + EMU_BM - 1) / EMU_BM);
   if (tiles == 0) return MSASM_OK;
   int dev = 0, n_sm = 0;
   MSASM_CUDA(cudaGetDevice(&dev));
   MSASM_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
   const unsigned grid = unsigned(std::min<long long>(tiles, std::max(n_sm, 1)));   // one CTA per SM
-  contract_emu_kernel<<<grid, EMU_THREADS, EMU_SMEM_BYTES, s>>>(ma, mb, p);
+  kernel<<<grid, EMU_THREADS, EMU_SMEM_BYTES, s>>>(ma, mb, p);
   MSASM_CUDA(cudaGetLastError());
   return MSASM_OK;
 }
