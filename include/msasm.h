@@ -237,7 +237,8 @@ msasm_status msasm_surrogate_predict(msasm_surrogate* sur, const double* d_width
                                      void* stream);
 /* Low-rank eq. 58 with the factor U (d_U, n_nz x rank FP32 row-major): for n_tiles tiles,
  * nz[9t+ab][m] = sum_r (sum_k Vt_t[r][k] coef[9t+ab][k]) U[m][r], Vt (n_tiles x rank x K FP32),
- * coef (9 n_tiles x K FP64); d_nz (9 n_tiles x n_nz FP32, dense).  FP32 accumulation. */
+ * coef (9 n_tiles x K FP64); d_nz (9 n_tiles x n_nz FP32, dense).  Z in FP32, the product with U on the
+ * tensor cores in split FP16 (about 6e-7 relative); synchronises `stream`. */
 msasm_status msasm_lowrank_contract(const float* d_U, int32_t n_nz, int32_t rank, int32_t K, const float* d_Vt,
                                     const double* d_coef, int64_t n_tiles, float* d_nz, void* stream);
 /* K of a graded lattice: per-tile widths d_widths (n_tiles FP64, device); pullback, MLP,
@@ -298,8 +299,8 @@ msasm_status msasm_scatter(msasm_plan* plan, msasm_precision prec, const void* d
  * written by msasm_pullback) by the contraction of eq. 58 in precision `prec`, pass by pass in the
  * plan's scratch, and applied to u.  d_u, d_y: n_rows FP64 (y overwritten; every row is written
  * by the tile that owns it, then the glued-face blocks are added with atomics, so the last bits of
- * those rows may vary between calls).  The first call builds per-type column maps.
- * Errors: EINVAL, EUNSUPPORTED, ECUDA. */
+ * those rows may vary between calls).  The first call builds per-type column maps and
+ * synchronises `stream`.  Errors: EINVAL, EUNSUPPORTED, ECUDA. */
 msasm_status msasm_linop_apply(msasm_plan* plan, const double* d_coef, msasm_precision prec, const double* d_u,
                                double* d_y, void* stream);
 
