@@ -16,7 +16,7 @@ pytestmark = pytest.mark.gpu
 
 import paper_2107_09568_gb300 as msasm  # noqa: E402
 
-TOL = {"f64": 1e-12, "f32": 1e-6}
+TOL = {"f64": 1e-12, "f64_emu": 1e-12, "f32": 1e-6}
 _TABLE_CACHE = {}
 
 
@@ -195,10 +195,11 @@ def test_translation_null_space_and_symmetry(built):
 
 
 # ---------------------------------------------------------------- full-size launch (sampled outputs)
-@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("prec", ["f64", "f64_emu", "f32"])
 def test_beam1000_full_size_sampled(built, prec):
     """The 10x10x10 twisted beam, n_e = 3, q = 3, in the bench's launch configuration
-    (all 1000 tiles in one pass): exact pattern and values of sampled rows."""
+    (all 1000 tiles in one pass, into a NaN-filled buffer): every value written, exact pattern
+    and values of sampled rows."""
     w = synth.workload("beam1000")
     micro = synth.micro_cross(3)
     prob = Problem(micro, w.macro, 3, table=oracle_table(3, 3), structure=False)
@@ -206,7 +207,9 @@ def test_beam1000_full_size_sampled(built, prec):
     plan = msasm.Plan(tab, w.macro)
     assert plan.nnz == 403850700 and plan.n_points == 657500
     ctrl = torch.tensor(w.macro.ctrl, device="cuda")
-    vals = plan.assemble(ctrl, 1.0, 0.3, prec, check_degenerate=True)
+    out = torch.full((plan.nnz,), float("nan"), dtype=plan.value_dtype(prec), device="cuda")
+    vals = plan.assemble(ctrl, 1.0, 0.3, prec, out=out, check_degenerate=True)
+    assert not torch.isnan(vals).any().item()
     rowptr, col = plan.csr()
     rng = np.random.default_rng(11)
     pts = np.unique(np.concatenate([rng.choice(plan.n_points, 24, replace=False),
@@ -227,7 +230,7 @@ def test_beam1000_full_size_sampled(built, prec):
     u = torch.zeros(plan.n_points, 3, dtype=torch.float64, device="cuda")
     u[:, 1] = 1.0
     r = (K @ u.reshape(-1)).abs().max().item()
-    assert r <= (1e-12 if prec == "f64" else 1e-5) * vals.abs().max().item()
+    assert r <= (1e-12 if prec in ("f64", "f64_emu") else 1e-5) * vals.abs().max().item()
 
 
 # ---------------------------------------------------------------- failure paths
