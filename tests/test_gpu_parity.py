@@ -168,11 +168,13 @@ def test_scatter_stage(built):
     assert rel_fro(vals, prob.assemble_lookup()) <= 1e-14
 
 
-@pytest.mark.parametrize("name,prec", [("cube8", "f64"), ("beam3x2x2_q3", "f64_emu"), ("ragged_5x1x3_ne3_q2", "f32")])
-def test_assemble_host_buffers(built, name, prec):
+@pytest.mark.parametrize("name,prec,per_pass", [("cube8", "f64", 0), ("beam3x2x2_q3", "f64_emu", 0),
+                                                ("beam3x2x2_q3", "f64_emu", 1), ("ragged_5x1x3_ne3_q2", "f32", 0),
+                                                ("ragged_5x1x3_ne3_q2", "split_f16", 2)])
+def test_assemble_host_buffers(built, name, prec, per_pass):
     """Host-buffer entry point (passes with overlapped device-to-host copies of finished rows)
-    returns exactly the device result."""
-    prob, tab, plan, ctrl = make_case(name)
+    returns exactly the device result, also with one or two tiles per pass."""
+    prob, tab, plan, ctrl = make_case(name, tiles_per_pass=per_pass)
     dev = plan.assemble(ctrl, 1.0, 0.3, prec).cpu()
     h_ctrl = torch.tensor(prob.mmap.macro.ctrl).pin_memory()
     h_vals = torch.full((plan.nnz,), float("nan"), dtype=dev.dtype).pin_memory()
