@@ -53,14 +53,16 @@ __global__ void __launch_bounds__(32 * kLinopWarps) linop_direct_kernel(
     const T* __restrict__ nz, int ld_nz, int64_t t0, int64_t n_tiles, const int32_t* __restrict__ tile_type,
     const int64_t* __restrict__ type_map_off, const int32_t* __restrict__ maps, const int32_t* __restrict__ colmaps,
     const int64_t* __restrict__ type_row_off, const int32_t* __restrict__ type_rows, const int32_t* __restrict__ gmap,
-    int n_T, const double* __restrict__ u, double* __restrict__ y) {
+    int n_T, const double* __restrict__ u, double* __restrict__ y, int64_t row_blocks) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t tl = blockIdx.x;
+  // the row blocks of one tile are consecutive blocks: the CTAs in flight share a few tiles'
+  // nzdata in L2 (tile-fastest order would touch every tile's nzdata at once and re-read it)
+  const int64_t tl = int64_t(blockIdx.x) / row_blocks;
   if (tl >= n_tiles) return;
   const int64_t t = t0 + tl;
   const int ty = tile_type[t];
   const int64_t r0 = type_row_off[ty], nr = type_row_off[ty + 1] - r0;
-  const int64_t r = int64_t(blockIdx.y) * kLinopWarps + warp;
+  const int64_t r = (int64_t(blockIdx.x) - tl * row_blocks) * kLinopWarps + warp;
   if (r >= nr) return;
   const int32_t* row = type_rows + 3 * (r0 + r);
   const int off = row[0], len = row[1], code = row[2];
@@ -139,12 +141,10 @@ msasm_status linop_pass_gpu(const msasm_plan* plan, const T* d_nz, int ld_nz, in
                             const double* d_u, double* d_y, cudaStream_t s) {
   if (n_tiles <= 0) return MSASM_OK;
   const int64_t ry = (plan->max_type_rows + kLinopWarps - 1) / kLinopWarps;
-  if (n_tiles > 2147483647LL || ry > 65535) return fail(MSASM_EUNSUPPORTED, "too many tiles or rows per tile");
-  const dim3 grid(static_cast<unsigned>(n_tiles), static_cast<unsigned>(ry), 1u);
-  linop_direct_kernel<T><<<grid, 32 * kLinopWarps, 0, s>>>(d_nz, ld_nz, t0, n_tiles, plan->d_tile_type,
-                                                           plan->d_type_map_off, plan->d_maps, plan->d_colmaps,
-                                                           plan->d_type_row_off, plan->d_type_rows, plan->d_gmap,
-                                                           plan->tab->topo.n_T, d_u, d_y);
+  if (ry < 1 || n_tiles * ry > 2147483647LL) return fail(MSASM_EUNSUPPORTED, "too many tiles or rows per tile");
+  linop_direct_kernel<T><<<static_cast<unsigned>(n_tiles * ry), 32 * kLinopWarps, 0, s>>>(
+      d_nz, ld_nz, t0, n_tiles, plan->d_tile_type, plan->d_type_map_off, plan->d_maps, plan->d_colmaps,
+      plan->d_type_row_off, plan->d_type_rows, plan->d_gmap, plan->tab->topo.n_T, d_u, d_y, ry);
   MSASM_CUDA(cudaGetLastError());
   const int64_t e0 = plan->sec_off_host[size_t(t0)], e1 = plan->sec_off_host[size_t(t0 + n_tiles)];
   if (e1 > e0) {
