@@ -3,9 +3,10 @@ Sec. 3.3, eq. 59, 65) -- test infrastructure.
 
 E_proj = max over tiles and sample points xi of ||A_bar(xi) - Pi A_bar(xi)||_F / ||A_bar(xi)||_F
 (eq. 59), the Frobenius norm over the 81 components (i, j, alpha, beta); Pi is the interpolant at the
-(q+1)^3 Gauss-Legendre nodes (the projection reading used throughout).  The sample set is the uniform
-interior grid xi_s = (s + 1/2) / n_s per direction ("a simple sampling-based approach").  The degree
-is raised from q0 until E_proj <= tol (eq. 65).
+(q+1)^3 Gauss-Legendre nodes (the projection reading used throughout), or the L2 projection onto Q_q
+of eq. 20-24 (l2_coefficients).  The sample set is the uniform interior grid xi_s = (s + 1/2) / n_s
+per direction ("a simple sampling-based approach").  The degree is raised from q0 until
+E_proj <= tol (eq. 65).
 """
 from __future__ import annotations
 
@@ -20,22 +21,55 @@ def sample_points(n_s: int) -> np.ndarray:
     return np.array([(a, b, c) for c in g for b in g for a in g])
 
 
+def tensor_gauss(n: int):
+    """The n^3-point tensor Gauss-Legendre rule on [0,1]^3: points (n^3, 3) in the node order
+    g1 + n (g2 + n g3), and weights (n^3,)."""
+    x, w = quadrature.gauss_legendre(n)
+    pts = np.array([(x[a], x[b], x[c]) for c in range(n) for b in range(n) for a in range(n)])
+    wts = np.array([w[a] * w[b] * w[c] for c in range(n) for b in range(n) for a in range(n)])
+    return pts, wts
+
+
+def l2_coefficients(mmap: MacroMap, t: int, q: int, lam: float, mu: float, n_g: int, ctrl=None):
+    """The L2 projection of tile t's macro field onto Q_q (eq. 20-24): the coefficients a (per node C
+    of the degree-q Lagrange basis N_C, 81 components each) minimising the L2 norm of
+    A_bar - sum_C a_C N_C solve the normal equations M a = b, with the mass matrix M_CD = int N_C N_D
+    (integrated exactly: a rule of 2q+2 points per direction, for its degree-2q integrand) and the
+    load b_C = int N_C A_bar, integrated by the n_g-point Gauss rule per direction.
+    Returns (n_pi, 81) in the layout of the nodal values (n_pi, i, j, alpha, beta)."""
+    xm, wm = tensor_gauss(2 * q + 2)
+    Nm = quadrature.tensor_lagrange(q, xm)                       # (n_m, n_pi)
+    M = Nm.T @ (wm[:, None] * Nm)
+    xg, wg = tensor_gauss(n_g)
+    _, J = mmap.tile_map(t, xg, ctrl)
+    A = pullback.macro_field(J, lam, mu).reshape(len(xg), 81)   # the field at the quadrature points
+    Ng = quadrature.tensor_lagrange(q, xg)
+    b = Ng.T @ (wg[:, None] * A)                                  # (n_pi, 81)
+    return np.linalg.solve(M, b)
+
+
 def tile_projection_error(mmap: MacroMap, t: int, q: int, lam: float, mu: float, n_s: int = 5, ctrl=None,
-                          points=None):
+                          points=None, n_gauss: int = 0):
+    """Largest relative Frobenius error of the projected field over the samples of tile t; the
+    interpolant at the nodes, or (n_gauss > 0) the L2 projection with an n_gauss-point load rule."""
     xi = sample_points(n_s) if points is None else points
     _, Js = mmap.tile_map(t, xi, ctrl)
     exact = pullback.macro_field(Js, lam, mu).reshape(len(xi), 81)
-    _, Jn = mmap.tile_map(t, quadrature.tensor_nodes(q), ctrl)
-    nodes = pullback.macro_field(Jn, lam, mu).reshape(-1, 81)
-    interp = quadrature.tensor_lagrange(q, xi) @ nodes
-    return np.max(np.linalg.norm(exact - interp, axis=1) / np.linalg.norm(exact, axis=1))
+    if n_gauss > 0:
+        coef = l2_coefficients(mmap, t, q, lam, mu, n_gauss, ctrl)
+    else:
+        _, Jn = mmap.tile_map(t, quadrature.tensor_nodes(q), ctrl)
+        coef = pullback.macro_field(Jn, lam, mu).reshape(-1, 81)
+    approx = quadrature.tensor_lagrange(q, xi) @ coef
+    return np.max(np.linalg.norm(exact - approx, axis=1) / np.linalg.norm(exact, axis=1))
 
 
-def projection_error(macro, q: int, E: float = 1.0, nu: float = 0.3, n_s: int = 5, ctrl=None):
-    """(per-tile errors, E_proj) of eq. 59."""
+def projection_error(macro, q: int, E: float = 1.0, nu: float = 0.3, n_s: int = 5, ctrl=None, n_gauss: int = 0):
+    """(per-tile errors, E_proj) of eq. 59 (interpolant, or L2 projection with n_gauss > 0)."""
     lam, mu = pullback.lame(E, nu)
     mmap = MacroMap(macro)
-    e = np.array([tile_projection_error(mmap, t, q, lam, mu, n_s, ctrl) for t in range(mmap.n_tiles)])
+    e = np.array([tile_projection_error(mmap, t, q, lam, mu, n_s, ctrl, n_gauss=n_gauss)
+                  for t in range(mmap.n_tiles)])
     return e, e.max()
 
 
