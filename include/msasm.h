@@ -265,6 +265,18 @@ msasm_status msasm_stage_times(const msasm_plan* plan, double* ms, int32_t* laun
 msasm_status msasm_pullback(msasm_plan* plan, const double* d_ctrl, double E, double nu,
                             double* d_coef, void* stream);
 
+/* Step 1 with the L2 projection onto Q_q of eq. 20-24 instead of interpolation: the coefficients
+ * (same layout as msasm_pullback, q the tables' degree) of the Lagrange basis at the q+1 Gauss-
+ * Legendre nodes that minimise the L2 norm of A_bar - <A_bar> over each tile, with the load
+ * integrals int N_C A_bar taken by the n_gauss-point Gauss rule per direction (1..9).  In that basis
+ * the mass matrix is diagonal (the nodes' rule integrates it exactly), so no system is solved;
+ * n_gauss = q + 1 gives the interpolant exactly.  The result feeds msasm_contract and msasm_scatter
+ * unchanged (the table of eq. 52 does not depend on how the coefficients were obtained).
+ * Synchronises `stream`.  Errors: EINVAL, EUNSUPPORTED (macro degree and n_gauss beyond the
+ * kernel's shared memory), ECUDA. */
+msasm_status msasm_pullback_l2(msasm_plan* plan, const double* d_ctrl, double E, double nu, int32_t n_gauss,
+                               double* d_coef, void* stream);
+
 /* Step 3 only: nz[n][m] = sum_k coef[n][k] T[m][k] (eq. 58) for `n_tiles` tiles of
  * FP64 coefficients d_coef (layout above).  d_nz: 9*n_tiles*n_nz values, FP64
  * for MSASM_F64 / MSASM_F64_EMU, FP32 otherwise. */
@@ -315,6 +327,12 @@ msasm_status msasm_linop_apply(msasm_plan* plan, const double* d_coef, msasm_pre
  * Errors: EINVAL, EUNSUPPORTED, ECUDA. */
 msasm_status msasm_projection_error(const msasm_plan* plan, const double* d_ctrl, int32_t q, int32_t n_samples,
                                     double E, double nu, double* d_err_tiles, double* d_err_max, void* stream);
+
+/* The same error for the L2 projection of degree q (msasm_pullback_l2, load rule of n_gauss points
+ * per direction, 1..9) in place of the interpolant. */
+msasm_status msasm_projection_error_l2(const msasm_plan* plan, const double* d_ctrl, int32_t q, int32_t n_gauss,
+                                       int32_t n_samples, double E, double nu, double* d_err_tiles, double* d_err_max,
+                                       void* stream);
 
 /* ---------------------------------------------------------------- volume and loads */
 

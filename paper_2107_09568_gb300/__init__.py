@@ -243,14 +243,34 @@ def _plan_linop(self, coef, u, precision="f64", out=None, stream=None):
     return y
 
 
-def _plan_projection_error(self, ctrl, q, n_samples=5, E=1.0, nu=0.3, stream=None):
-    """(per-tile errors (n_tiles,), E_proj) of eq. 59 for interpolation degree q."""
+def _plan_projection_error(self, ctrl, q, n_samples=5, E=1.0, nu=0.3, n_gauss=0, stream=None):
+    """(per-tile errors (n_tiles,), E_proj) of eq. 59 for degree q: of the interpolant, or with
+    n_gauss > 0 of the L2 projection (eq. 20-24, load rule of n_gauss points per direction)."""
     import torch
     e = torch.empty(self.n_tiles, dtype=torch.float64, device="cuda")
     m = torch.empty((), dtype=torch.float64, device="cuda")
-    check(load().msasm_projection_error(self.handle, _ptr(ctrl), int(q), int(n_samples), float(E), float(nu),
-                                        _ptr(e), _ptr(m), _stream(stream)))
+    if n_gauss > 0:
+        check(load().msasm_projection_error_l2(self.handle, _ptr(ctrl), int(q), int(n_gauss), int(n_samples),
+                                               float(E), float(nu), _ptr(e), _ptr(m), _stream(stream)))
+    else:
+        check(load().msasm_projection_error(self.handle, _ptr(ctrl), int(q), int(n_samples), float(E), float(nu),
+                                            _ptr(e), _ptr(m), _stream(stream)))
     return e, m
+
+
+def _plan_pullback_l2(self, ctrl, n_gauss, E=1.0, nu=0.3, stream=None):
+    """Step 1 with the L2 projection of eq. 20-24: (9 n_tiles, 9 n_pi) FP64 coefficients."""
+    import torch
+    out = torch.empty((9 * self.n_tiles, 9 * self.tables.n_pi), dtype=torch.float64, device="cuda")
+    check(load().msasm_pullback_l2(self.handle, _ptr(ctrl), float(E), float(nu), int(n_gauss), _ptr(out),
+                                   _stream(stream)))
+    return out
+
+
+def _plan_assemble_l2(self, ctrl, n_gauss, E=1.0, nu=0.3, precision="f64", stream=None):
+    """K with the L2-projected macro field: msasm_pullback_l2, then the contraction and the scatter."""
+    return self.scatter(self.tables.contract(self.pullback_l2(ctrl, n_gauss, E, nu, stream), precision,
+                                             stream=stream), precision, stream=stream)
 
 
 def select_projection_degree(plan, ctrl, tol, q0, q_max, **kw):
@@ -262,6 +282,8 @@ def select_projection_degree(plan, ctrl, tol, q0, q_max, **kw):
 
 
 Plan.projection_error = _plan_projection_error
+Plan.pullback_l2 = _plan_pullback_l2
+Plan.assemble_l2 = _plan_assemble_l2
 Plan.linop = _plan_linop
 Plan.assemble_grad = _plan_assemble_grad
 Plan.face_points = _plan_face_points

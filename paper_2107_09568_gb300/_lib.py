@@ -52,6 +52,7 @@ _SIGS = {
     "msasm_assemble_host": (c_i32, [c_vp, c_vp, c_dbl, c_dbl, c_i32, c_vp, c_u32, c_vp]),
     "msasm_degenerate_count": (c_i32, [c_vp, P(c_i64), c_vp]),
     "msasm_pullback": (c_i32, [c_vp, c_vp, c_dbl, c_dbl, c_vp, c_vp]),
+    "msasm_pullback_l2": (c_i32, [c_vp, c_vp, c_dbl, c_dbl, c_i32, c_vp, c_vp]),
     "msasm_contract": (c_i32, [c_vp, c_i32, c_vp, c_i64, c_vp, c_vp]),
     "msasm_scatter": (c_i32, [c_vp, c_i32, c_vp, c_vp, c_vp]),
     "msasm_contract_noalloc": (c_i32, [c_vp, c_vp, c_i64, c_vp, c_vp]),
@@ -62,6 +63,7 @@ _SIGS = {
     "msasm_load_table_copy": (c_i32, [c_vp, c_vp, c_vp, c_vp]),
     "msasm_linop_apply": (c_i32, [c_vp, c_vp, c_i32, c_vp, c_vp, c_vp]),
     "msasm_projection_error": (c_i32, [c_vp, c_vp, c_i32, c_i32, c_dbl, c_dbl, c_vp, c_vp, c_vp]),
+    "msasm_projection_error_l2": (c_i32, [c_vp, c_vp, c_i32, c_i32, c_i32, c_dbl, c_dbl, c_vp, c_vp, c_vp]),
     "msasm_volume": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp]),
     "msasm_volume_grad": (c_i32, [c_vp, c_vp, c_vp, c_vp]),
     "msasm_body_load": (c_i32, [c_vp, c_vp, c_dbl, c_dbl, c_dbl, c_vp, c_vp]),

@@ -60,7 +60,9 @@ msasm_status adjoint_pullback_gpu(const msasm_plan* plan, const double* d_ctrl, 
                                   const double* vol_w = nullptr);
 msasm_status linop_prepare_gpu(msasm_plan* plan, cudaStream_t s);
 msasm_status projection_error_gpu(const msasm_plan* plan, const double* d_ctrl, int q, int n_s, double lam, double mu,
-                                  double* d_err_tiles, double* d_err_max, cudaStream_t s);
+                                  double* d_err_tiles, double* d_err_max, cudaStream_t s, int n_gauss = 0);
+msasm_status l2_coef_gpu(const msasm_plan* plan, const double* d_ctrl, int q, int n_g, double lam, double mu,
+                         double* d_coef, cudaStream_t s);
 template <typename T>
 msasm_status linop_pass_gpu(const msasm_plan* plan, const T* d_nz, int ld_nz, int64_t t0, int64_t n_tiles,
                             const double* d_u, double* d_y, cudaStream_t s);
@@ -813,6 +815,29 @@ msasm_status msasm_projection_error(const msasm_plan* plan, const double* d_ctrl
   lame(E, nu, lam, mu);
   return projection_error_gpu(plan, d_ctrl, q, n_samples, lam, mu, d_err_tiles, d_err_max,
                               static_cast<cudaStream_t>(stream));
+}
+
+msasm_status msasm_projection_error_l2(const msasm_plan* plan, const double* d_ctrl, int32_t q, int32_t n_gauss,
+                                       int32_t n_samples, double E, double nu, double* d_err_tiles, double* d_err_max,
+                                       void* stream) {
+  if (!plan || !d_ctrl || (!d_err_tiles && !d_err_max)) return fail(MSASM_EINVAL, "NULL argument or no output");
+  if (n_gauss < 1) return fail(MSASM_EINVAL, "n_gauss must be at least 1");
+  MSASM_TRY(check_material(E, nu));
+  double lam, mu;
+  lame(E, nu, lam, mu);
+  return projection_error_gpu(plan, d_ctrl, q, n_samples, lam, mu, d_err_tiles, d_err_max,
+                              static_cast<cudaStream_t>(stream), n_gauss);
+}
+
+msasm_status msasm_pullback_l2(msasm_plan* plan, const double* d_ctrl, double E, double nu, int32_t n_gauss,
+                               double* d_coef, void* stream) {
+  if (!plan || !d_ctrl || !d_coef) return fail(MSASM_EINVAL, "plan, d_ctrl or d_coef is NULL");
+  MSASM_TRY(check_material(E, nu));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  double lam, mu;
+  lame(E, nu, lam, mu);
+  MSASM_CUDA(cudaMemsetAsync(plan->d_degenerate, 0, sizeof(unsigned long long), s));
+  return l2_coef_gpu(plan, d_ctrl, plan->tab->q, n_gauss, lam, mu, d_coef, s);
 }
 
 msasm_status msasm_load_table_copy(const msasm_tables* tab, double* d_F, double* d_vol, void* stream) {

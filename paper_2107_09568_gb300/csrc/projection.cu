@@ -1,7 +1,7 @@
 // Projection error of the macro field (Sec. 3.2.2, eq. 47-48; Sec. 3.3, eq. 59): for every tile,
 // max over sample points xi_s of ||A_bar(xi_s) - Pi A_bar(xi_s)||_F / ||A_bar(xi_s)||_F over the 81
 // components, Pi the interpolant at the (q+1)^3 nodes of a given degree q (the reading of the
-// projection used throughout).  Samples: the uniform interior grid (s + 1/2)/n_s per direction.
+// projection used throughout) or the L2 projection onto Q_q of eq. 20-24 (l2_coef_gpu).  Samples: the uniform interior grid (s + 1/2)/n_s per direction.
 // The exact field at the samples comes from the node Jacobians of the same sum factorisation
 // with the macro basis tabulated at the samples; the interpolant from the pullback coefficients at
 // the q nodes (computed with the macro basis tabulated at those nodes).  One warp per tile.
@@ -82,6 +82,49 @@ __global__ void projection_error_kernel(ProjErrArgs a) {
   }
 }
 
+// L2 projection onto Q_q (eq. 20-24) in the Lagrange basis of the q+1 Gauss-Legendre nodes: the
+// mass matrix int N_C N_D is diagonal there (the nodes' own rule integrates its degree-2q integrand
+// exactly, and N_C vanishes at the other nodes), M = diag(w_c1 w_c2 w_c3), so the coefficients of
+// the projection with the load integrated by an n_g-point rule are
+//   a_C = sum_g P[c1][g1] P[c2][g2] P[c3][g3] A_bar(x_g),   P[c][g] = W_g l_c(x_g) / w_c,
+// evaluated by sum factorisation (direction 1, then 2, then 3) in shared memory, one CTA per
+// coefficient row (9 per tile: alpha, beta), the 9 components (i, j) side by side.
+__global__ void l2_project_kernel(const double* __restrict__ vals, int64_t n_rows, int ng, int nq,
+                                  const double* __restrict__ P1, double* __restrict__ coef) {
+  extern __shared__ double sm[];
+  const int Kg = 9 * ng * ng * ng, K = 9 * nq * nq * nq;
+  double* V = sm;                                // [(g1 + ng (g2 + ng g3)) 9 + k]
+  double* T1 = V + Kg;                           // [(c1 + nq (g2 + ng g3)) 9 + k]
+  double* T2 = T1 + 9 * nq * ng * ng;            // [(c1 + nq (c2 + nq g3)) 9 + k]
+  double* P = T2 + 9 * nq * nq * ng;             // [c][g]
+  for (int i = threadIdx.x; i < nq * ng; i += blockDim.x) P[i] = P1[i];
+  for (int64_t r = blockIdx.x; r < n_rows; r += gridDim.x) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < Kg; i += blockDim.x) V[i] = vals[r * Kg + i];
+    __syncthreads();
+    for (int i = threadIdx.x; i < 9 * nq * ng * ng; i += blockDim.x) {
+      const int k = i % 9, rest = i / 9, c1 = rest % nq, g23 = rest / nq;
+      double acc = 0.0;
+      for (int g1 = 0; g1 < ng; ++g1) acc = fma(P[c1 * ng + g1], V[(g1 + ng * g23) * 9 + k], acc);
+      T1[i] = acc;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 9 * nq * nq * ng; i += blockDim.x) {
+      const int k = i % 9, rest = i / 9, c1 = rest % nq, rest2 = rest / nq, c2 = rest2 % nq, g3 = rest2 / nq;
+      double acc = 0.0;
+      for (int g2 = 0; g2 < ng; ++g2) acc = fma(P[c2 * ng + g2], T1[(c1 + nq * (g2 + ng * g3)) * 9 + k], acc);
+      T2[i] = acc;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < K; i += blockDim.x) {
+      const int k = i % 9, rest = i / 9, c12 = rest % (nq * nq), c3 = rest / (nq * nq);
+      double acc = 0.0;
+      for (int g3 = 0; g3 < ng; ++g3) acc = fma(P[c3 * ng + g3], T2[(c12 + nq * nq * g3) * 9 + k], acc);
+      coef[r * K + i] = acc;
+    }
+  }
+}
+
 __global__ void max_kernel(const double* __restrict__ x, int64_t n, double* __restrict__ out) {
   __shared__ double part[256];
   double m = 0.0;
@@ -115,9 +158,62 @@ static void basis_tables(const msasm_plan* plan, const std::vector<double>& x, s
   }
 }
 
+// The L2-projection coefficients of degree q (layout of the pullback: [9t + 3a + b][9C + 3i + j]) of
+// all tiles, the load integrated by the n_g-point Gauss rule per direction.
+msasm_status l2_coef_gpu(const msasm_plan* plan, const double* d_ctrl, int q, int n_g, double lam, double mu,
+                         double* d_coef, cudaStream_t s) {
+  if (q < 0 || q > 7 || n_g < 1 || n_g > 9) return fail(MSASM_EINVAL, "need 0 <= q <= 7 and 1 <= n_gauss <= 9");
+  const int nq = q + 1;
+  std::vector<double> xn, wn, xg, wg;
+  gauss_legendre01(nq, xn, wn);
+  gauss_legendre01(n_g, xg, wg);
+  std::vector<double> bg[3];
+  basis_tables(plan, xg, bg);
+  std::vector<double> P1(size_t(nq) * n_g);
+  for (int c = 0; c < nq; ++c)
+    for (int g = 0; g < n_g; ++g) {
+      double l = 1.0;
+      for (int k = 0; k < nq; ++k)
+        if (k != c) l *= (xg[size_t(g)] - xn[size_t(k)]) / (xn[size_t(c)] - xn[size_t(k)]);
+      P1[size_t(c) * n_g + g] = wg[size_t(g)] * l / wn[size_t(c)];
+    }
+  const size_t n_rows = size_t(9 * plan->n_tiles), Kg = size_t(9) * n_g * n_g * n_g;
+  size_t nb = P1.size();
+  for (int d = 0; d < 3; ++d) nb += bg[d].size();
+  double* buf = nullptr;
+  MSASM_CUDA(cudaMallocAsync(&buf, (nb + n_rows * Kg) * sizeof(double), s));
+  double* cur = buf;
+  auto put = [&](const std::vector<double>& v) -> double* {
+    double* p = cur;
+    cudaMemcpyAsync(p, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+    cur += v.size();
+    return p;
+  };
+  MacroTileArgs gg = macro_tile_args(plan, d_ctrl);
+  gg.nq = n_g;
+  for (int d = 0; d < 3; ++d) gg.basis[d] = put(bg[d]);
+  const double* d_P = put(P1);
+  double* vals = cur;                              // the field at the n_g^3 points of every tile
+  msasm_status st = pullback_geo_gpu(gg, plan->n_tiles, lam, mu, vals, plan->d_degenerate, s);
+  if (st == MSASM_OK) {
+    const size_t smem = (Kg + size_t(9) * nq * n_g * n_g + size_t(9) * nq * nq * n_g + P1.size()) * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(l2_project_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e == cudaSuccess) {
+      const unsigned blocks = unsigned(std::max<size_t>(1, std::min<size_t>(n_rows, 152 * 8)));
+      l2_project_kernel<<<blocks, 256, smem, s>>>(vals, int64_t(n_rows), n_g, nq, d_P, d_coef);
+      e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) st = cuda_fail(e, "L2 projection kernel");
+  }
+  cudaStreamSynchronize(s);                      // the host tables outlive the copies
+  cudaFreeAsync(buf, s);
+  return st;
+}
+
 msasm_status projection_error_gpu(const msasm_plan* plan, const double* d_ctrl, int q, int n_s, double lam, double mu,
-                                  double* d_err_tiles, double* d_err_max, cudaStream_t s) {
+                                  double* d_err_tiles, double* d_err_max, cudaStream_t s, int n_gauss) {
   if (q < 0 || q > 7 || n_s < 1 || n_s > 8) return fail(MSASM_EINVAL, "need 0 <= q <= 7 and 1 <= n_samples <= 8");
+  if (n_gauss < 0 || n_gauss > 9) return fail(MSASM_EINVAL, "need 0 <= n_gauss <= 9");
   const int nq = q + 1, K = 9 * nq * nq * nq;
   std::vector<double> xn, wn, xs(static_cast<size_t>(n_s));
   gauss_legendre01(nq, xn, wn);
@@ -156,7 +252,8 @@ msasm_status projection_error_gpu(const msasm_plan* plan, const double* d_ctrl, 
   double* coef = cur;
   cur += coef_n;
   double* err = d_err_tiles ? d_err_tiles : cur;
-  msasm_status st = pullback_geo_gpu(gn, plan->n_tiles, lam, mu, coef, plan->d_degenerate, s);
+  msasm_status st = n_gauss > 0 ? l2_coef_gpu(plan, d_ctrl, q, n_gauss, lam, mu, coef, s)
+                                 : pullback_geo_gpu(gn, plan->n_tiles, lam, mu, coef, plan->d_degenerate, s);
   if (st == MSASM_OK) {
     ProjErrArgs a;
     a.geo = gs;
