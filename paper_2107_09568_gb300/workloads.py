@@ -194,6 +194,18 @@ def projection(flush, workload="beam1000"):
         out[f"E_proj_q{q}"] = m.item()
         out[f"ms_q{q}"] = ms
     out["degree_for_tol_1e-3"] = msasm.select_projection_degree(plan, ctrl, 1e-3, 0, 7)
+    # the L2 projection of eq. 20-24 (load rule of q + 3 points per direction, at most 9)
+    for q in range(0, 7):
+        n_g = min(q + 3, 9)
+        (_, m), ms = _timed(lambda: plan.projection_error(ctrl, q, 5, n_gauss=n_g), reps=3, flush=flush)
+        out[f"E_proj_l2_q{q}"] = m.item()
+        out[f"ms_l2_q{q}"] = ms
+    out["l2_load_rule"] = "q + 3 points per direction (at most 9)"
+    _, out["pullback_ms"] = _timed(lambda: plan.pullback(ctrl), reps=5, flush=flush)
+    _, out["pullback_l2_ms_incl_host_tables"] = _timed(lambda: plan.pullback_l2(ctrl, w.q + 3), reps=5, flush=flush)
+    k_int = plan.assemble(ctrl, 1.0, 0.3, "f64_emu")
+    k_l2 = plan.assemble_l2(ctrl, w.q + 3, precision="f64_emu")
+    out["rel_fro_K_l2_vs_K_interpolated"] = rel(k_l2, k_int)
     return out
 
 
