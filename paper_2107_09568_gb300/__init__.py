@@ -334,6 +334,21 @@ def csr_matrix(plan, values):
     return torch.sparse_csr_tensor(rowptr, col.long(), values, size=(plan.n_rows, plan.n_rows))
 
 
+def _inverse3(B):
+    """Inverses of a batch of 3x3 matrices (..., 3, 3) as adjugate / determinant (elementwise ops
+    only, no linear-algebra library)."""
+    import torch
+    a, b, c = B[..., 0, 0], B[..., 0, 1], B[..., 0, 2]
+    d, e, f = B[..., 1, 0], B[..., 1, 1], B[..., 1, 2]
+    g, h, i = B[..., 2, 0], B[..., 2, 1], B[..., 2, 2]
+    A, Bc, C = e * i - f * h, f * g - d * i, d * h - e * g      # cofactors of the first row
+    det = a * A + b * Bc + c * C
+    adj = torch.stack([torch.stack([A, c * h - b * i, b * f - c * e], -1),
+                       torch.stack([Bc, a * i - c * g, c * d - a * f], -1),
+                       torch.stack([C, b * g - a * h, a * e - b * d], -1)], -2)
+    return adj / det[..., None, None]
+
+
 def cg_solve(K, f, fixed_dofs, tol=1e-12, max_iter=20000, x0=None, replace_every=50):
     """Preconditioned conjugate gradients in PyTorch on the GPU for K u = f with u = 0 on fixed_dofs
     (rows and columns of the fixed DOFs removed by masking), optionally from x0.  The
@@ -354,7 +369,7 @@ def cg_solve(K, f, fixed_dofs, tol=1e-12, max_iter=20000, x0=None, replace_every
                                val[same], accumulate=True)
     fm = free.view(-1, 3)
     blocks = blocks * fm[:, :, None] * fm[:, None, :] + torch.diag_embed(1.0 - fm)   # identity on fixed DOFs
-    binv = torch.linalg.inv(blocks)
+    binv = _inverse3(blocks)
     prec = lambda r: (torch.bmm(binv, r.view(-1, 3, 1)).view(-1)) * free
     A = lambda x: (K @ (x * free)) * free
     b = f * free
