@@ -9,7 +9,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import quadrature
+from . import quadrature, tables
 
 
 def face_points(prob, face):
@@ -59,4 +59,30 @@ def traction_load(prob, face, traction, ctrl=None, n_g=5):
                         r = vals[:, a] @ dA
                         if r != 0.0:
                             f[prob.gmap[t, ids[a]]] += r * tr
+    return f
+
+
+def traction_load_lookup(prob, face, traction, q, ctrl=None, F=None):
+    """The traction part of eq. 53: per tile on the macro face xi_d = s, the projected macro
+    traction <t_bar>_C2 = t |det I_M| (eq. 87-88) at the face nodes, where on that face
+    det I_M = (n x g_a) . g_b = |g_a x g_b| with g_k = dM/dxi_k (the unit normal along the
+    contravariant g^d), times the face table: f_A += sum_C2 F_face[A, C2] <t_bar>_C2."""
+    d, s = face // 2, face % 2
+    ia, ib = [k for k in range(3) if k != d]
+    mm, tile = prob.mmap, prob.tile
+    F = tables.face_load_table(tile, q, face) if F is None else F
+    uv = tables.face_nodes(q)
+    xi = np.zeros((len(uv), 3))
+    xi[:, d] = float(s)
+    xi[:, ia], xi[:, ib] = uv[:, 0], uv[:, 1]
+    tr = np.asarray(traction, dtype=np.float64)
+    f = np.zeros((prob.n_points, 3))
+    for t in range(mm.n_tiles):
+        if mm.tile_index(t)[d] != (0 if s == 0 else mm.n_elem[d] - 1):
+            continue
+        _, J = mm.tile_map(t, xi, ctrl)
+        area = np.linalg.norm(np.cross(J[:, :, ia], J[:, :, ib]), axis=1)     # |det I_M| at the nodes
+        fa = F @ area
+        for A in np.nonzero(fa)[0]:
+            f[prob.gmap[t, A]] += fa[A] * tr
     return f

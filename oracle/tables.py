@@ -93,3 +93,53 @@ def load_table(tile, q: int, n_g: int | None = None) -> np.ndarray:
             F[A] += Floc[a]
     return F
 
+
+
+def face_nodes(q: int) -> np.ndarray:
+    """The (q+1)^2 nodes of the face projection space, C2 = c_a + (q+1) c_b in the two in-face
+    directions (ascending axis order); shape ((q+1)^2, 2)."""
+    g = quadrature.interp_nodes(q)
+    n = q + 1
+    return np.array([(g[ca], g[cb]) for cb in range(n) for ca in range(n)])
+
+
+def face_lagrange(q: int, uv) -> np.ndarray:
+    """N_C2(u, v) = l_ca(u) l_cb(v) at points uv (n, 2) -> (n, (q+1)^2)."""
+    g = quadrature.interp_nodes(q)
+    uv = np.atleast_2d(uv)
+    La, Lb = quadrature.lagrange(g, uv[:, 0]), quadrature.lagrange(g, uv[:, 1])
+    return np.einsum("pa,pb->pba", La, Lb).reshape(len(uv), -1)
+
+
+def face_load_table(tile, q: int, face: int, n_g: int | None = None) -> np.ndarray:
+    """The traction part of the load lookup table (eq. 54-55, F = face + 1):
+    F_face[A, C2] = int over the part of the tile boundary on the cube face xi_d = s (face = 2 d + s)
+    of (R_A o T^r^-1) N_C2 dGamma_T, with N_C2 the degree-q Lagrange basis of the face's own
+    Gauss-Legendre nodes in its two in-face coordinates (the reading of the node set I_F for this
+    basis).  Integrated per micro element face by Gauss quadrature (exact: polynomial integrand);
+    shape (n_T, (q+1)^2)."""
+    d, s = face // 2, face % 2
+    ia, ib = [k for k in range(3) if k != d]
+    p_T = max(max(P["degree"]) for P in tile.patches)
+    n_g = n_g or default_gauss_points(p_T, q)
+    g1, w1 = quadrature.gauss_legendre(n_g)
+    F = np.zeros((tile.n_T, (q + 1) ** 2))
+    for p, P in enumerate(tile.patches):
+        lo, hi = P["lo"], P["hi"]
+        if not ((s == 0 and lo[d] == 0.0) or (s == 1 and hi[d] == 1.0)):
+            continue
+        ne = P["n_elem"]
+        for eb in range(ne[ib]):
+            for ea in range(ne[ia]):
+                th = np.zeros((n_g * n_g, 3))
+                th[:, d] = float(s)
+                th[:, ia] = np.tile((ea + g1) / ne[ia], n_g)
+                th[:, ib] = np.repeat((eb + g1) / ne[ib], n_g)
+                w = np.outer(w1, w1).ravel() / (ne[ia] * ne[ib]) * (hi - lo)[ia] * (hi - lo)[ib]
+                xi = lo + (hi - lo) * th
+                vals, _ = tile.patch_basis(p, th)
+                N2 = face_lagrange(q, xi[:, [ia, ib]])
+                Floc = np.einsum("g,ga,gc->ac", w, vals, N2)
+                for a, A in enumerate(P["ids"]):
+                    F[A] += Floc[a]
+    return F
