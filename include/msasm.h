@@ -359,6 +359,22 @@ msasm_status msasm_volume_grad(const msasm_plan* plan, const double* d_ctrl, dou
 msasm_status msasm_body_load(const msasm_plan* plan, const double* d_ctrl, double bx, double by, double bz,
                              double* d_f, void* stream);
 
+/* Load vector of a uniform traction t = (tx, ty, tz) (force per unit physical area) on macro face
+ * `face` = 2 d + s (the tiles' boundary parts on xi_d = s), through the face tables (the F >= 1
+ * terms of eq. 53-55): per tile on the face, t |det I_M| (eq. 87-88, the macro surface element
+ * |dM/dxi_a x dM/dxi_b| on that face) interpolated at the face's (q+1)^2 Gauss-Legendre nodes,
+ * times the table: f_{3g+c} = t_c sum_C2 Ff[A][C2] |det I_M|(node C2).  Equals the direct
+ * quadrature (msasm_traction_load) to roundoff when the surface element is a polynomial of degree
+ * <= q per direction (an affine map), and converges with q otherwise.  d_f (n_rows FP64) is
+ * overwritten.  Points shared by face tiles receive one addition per tile (FP64 atomics).
+ * Synchronises `stream`.  Errors: EINVAL, EUNSUPPORTED, ECUDA. */
+msasm_status msasm_traction_load_lookup(const msasm_plan* plan, const double* d_ctrl, int32_t face, double tx,
+                                        double ty, double tz, double* d_f, void* stream);
+
+/* Copy the face load table of `face` (n_T x (q+1)^2 FP64, row A, column C2 = c_a + (q+1) c_b over
+ * the two in-face directions in ascending order) to d_Ff. */
+msasm_status msasm_face_table_copy(const msasm_tables* tab, int32_t face, double* d_Ff, void* stream);
+
 /* ---------------------------------------------------------------- diagnostics */
 
 const char* msasm_last_error(void);

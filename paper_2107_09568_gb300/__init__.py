@@ -234,6 +234,24 @@ def _plan_body_load(self, ctrl, b, stream=None):
     return f
 
 
+def _plan_traction_load_lookup(self, ctrl, face, traction, stream=None):
+    """Load vector (n_rows,) FP64 on the GPU of a uniform traction on a macro face, through the face
+    tables (eq. 53-55, F >= 1; eq. 87-88)."""
+    import torch
+    f = torch.empty(self.n_rows, dtype=torch.float64, device="cuda")
+    check(load().msasm_traction_load_lookup(self.handle, _ptr(ctrl), int(face), float(traction[0]),
+                                            float(traction[1]), float(traction[2]), _ptr(f), _stream(stream)))
+    return f
+
+
+def _tables_face_table(self, face, stream=None):
+    """The face load table of `face` (n_T, (q+1)^2) FP64 on the GPU."""
+    import torch
+    out = torch.empty((self.n_T, (self.q + 1) ** 2), dtype=torch.float64, device="cuda")
+    check(load().msasm_face_table_copy(self.handle, int(face), _ptr(out), _stream(stream)))
+    return out
+
+
 def _plan_linop(self, coef, u, precision="f64", out=None, stream=None):
     """y = K u matrix-free (eq. 74) from the coefficients of plan.pullback(ctrl)."""
     import torch
@@ -282,6 +300,8 @@ def select_projection_degree(plan, ctrl, tol, q0, q_max, **kw):
 
 
 Plan.projection_error = _plan_projection_error
+Plan.traction_load_lookup = _plan_traction_load_lookup
+Tables.face_table = _tables_face_table
 Plan.pullback_l2 = _plan_pullback_l2
 Plan.assemble_l2 = _plan_assemble_l2
 Plan.linop = _plan_linop

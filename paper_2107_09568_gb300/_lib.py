@@ -67,6 +67,8 @@ _SIGS = {
     "msasm_volume": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp]),
     "msasm_volume_grad": (c_i32, [c_vp, c_vp, c_vp, c_vp]),
     "msasm_body_load": (c_i32, [c_vp, c_vp, c_dbl, c_dbl, c_dbl, c_vp, c_vp]),
+    "msasm_traction_load_lookup": (c_i32, [c_vp, c_vp, c_i32, c_dbl, c_dbl, c_dbl, c_vp, c_vp]),
+    "msasm_face_table_copy": (c_i32, [c_vp, c_i32, c_vp, c_vp]),
     "msasm_mlp_create": (c_i32, [c_i32, c_i32, C.c_uint64, P(c_vp)]),
     "msasm_mlp_info": (c_i32, [c_vp, P(c_i64), P(c_i32), P(c_i32)]),
     "msasm_mlp_set_params": (c_i32, [c_vp, c_vp, c_vp]),

@@ -68,6 +68,8 @@ msasm_status linop_pass_gpu(const msasm_plan* plan, const T* d_nz, int ld_nz, in
                             const double* d_u, double* d_y, cudaStream_t s);
 msasm_status volume_load_gpu(const msasm_plan* plan, const double* d_ctrl, double* d_tile_vol, double* d_total,
                              double* d_f, const double b[3], cudaStream_t s);
+msasm_status traction_load_gpu(const msasm_plan* plan, const double* d_ctrl, int face, const double t[3], double* d_f,
+                               cudaStream_t s);
 int tc_kind_of(msasm_precision prec);
 int emu_kpad(int K);
 size_t emu_slice_bytes(int64_t rows, int K);
@@ -94,6 +96,7 @@ msasm_tables::~msasm_tables() {
   cudaFree(d_T);
   cudaFree(d_F);
   cudaFree(d_vol);
+  cudaFree(d_Fface);
   cudaFree(d_pairs);
   cudaFree(d_T32);
   cudaFree(d_Thi);
@@ -877,6 +880,26 @@ msasm_status msasm_body_load(const msasm_plan* plan, const double* d_ctrl, doubl
   MSASM_CUDA(cudaMemsetAsync(d_f, 0, size_t(plan->n_rows) * sizeof(double), s));
   const double b[3] = {bx, by, bz};
   return volume_load_gpu(plan, d_ctrl, nullptr, nullptr, d_f, b, s);
+}
+
+msasm_status msasm_traction_load_lookup(const msasm_plan* plan, const double* d_ctrl, int32_t face, double tx,
+                                        double ty, double tz, double* d_f, void* stream) {
+  if (!plan || !d_ctrl || !d_f) return fail(MSASM_EINVAL, "plan, d_ctrl or d_f is NULL");
+  if (face < 0 || face > 5) return fail(MSASM_EINVAL, "face must be 0..5");
+  if (!std::isfinite(tx) || !std::isfinite(ty) || !std::isfinite(tz)) return fail(MSASM_EINVAL, "traction not finite");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  MSASM_CUDA(cudaMemsetAsync(d_f, 0, size_t(plan->n_rows) * sizeof(double), s));
+  const double t[3] = {tx, ty, tz};
+  return traction_load_gpu(plan, d_ctrl, face, t, d_f, s);
+}
+
+msasm_status msasm_face_table_copy(const msasm_tables* tab, int32_t face, double* d_Ff, void* stream) {
+  if (!tab || !d_Ff) return fail(MSASM_EINVAL, "tables or d_Ff is NULL");
+  if (face < 0 || face > 5) return fail(MSASM_EINVAL, "face must be 0..5");
+  const size_t n = size_t(tab->topo.n_T) * (tab->q + 1) * (tab->q + 1);
+  MSASM_CUDA(cudaMemcpyAsync(d_Ff, tab->d_Fface + size_t(face) * n, n * sizeof(double), cudaMemcpyDeviceToDevice,
+                             static_cast<cudaStream_t>(stream)));
+  return MSASM_OK;
 }
 
 msasm_status msasm_degenerate_count(const msasm_plan* plan, int64_t* count, void* stream) {

@@ -111,6 +111,7 @@ struct msasm_tables {
   double* d_T = nullptr;            // n_nz x 9 n_pi, FP64
   double* d_F = nullptr;            // load table n_T x n_pi (eq. 55, body term), FP64
   double* d_vol = nullptr;          // volume table n_pi (eq. 18), FP64
+  double* d_Fface = nullptr;        // face load tables 6 x n_T x (q+1)^2 (eq. 55, F >= 1), FP64
   int32_t* d_pairs = nullptr;       // 2 n_nz (A, B)
   // operand copies for the reduced-precision contractions (created on first use)
   float* d_T32 = nullptr;           // FP32 copy

@@ -1,5 +1,5 @@
-// K1: the stiffness lookup table mat[K] (eq. 51-52, 57) in FP64 on the GPU, and the load and
-// volume tables of eq. 54-55 and 18 from the same 1-D integrals.
+// K1: the stiffness lookup table mat[K] (eq. 51-52, 57) in FP64 on the GPU, and the load (body and
+// face terms) and volume tables of eq. 54-55 and 18 from the same 1-D integrals.
 //
 // Every micro patch is an axis-aligned box with an affine map and a tensor-product
 // basis, and the projection basis N_C is a tensor product too, so the 3-D
@@ -154,6 +154,43 @@ __global__ void load_table_kernel(const PairDesc* __restrict__ diag, const doubl
   }
 }
 
+// The face load tables of eq. 54-55 (F >= 1): for the cube face xi_d = s (face 2 d + s),
+// Ff[A][C2] = int over the tile boundary lying on that face of R_A N_C2, N_C2 = l_ca(xi_ia) l_cb(xi_ib)
+// the Lagrange basis of the face's (q+1)^2 nodes (ia < ib the in-face directions).  A patch whose
+// box reaches the face contributes when A's index in the normal direction is the end one there
+// (open knots: that function is 1 on the face, the others 0); the in-face factors are the 1-D
+// integrals int f_a l_c of the load table (sums over b of the value-value table).
+__global__ void face_table_kernel(Table1DParams prm, const PairDesc* __restrict__ diag, const double* __restrict__ I1,
+                                  int n_T, int nf, double* __restrict__ Ff) {
+  const int nq = prm.q + 1, n2 = nq * nq;
+  const int64_t total = int64_t(6) * n_T * n2;
+  for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < total;
+       idx += int64_t(gridDim.x) * blockDim.x) {
+    const int face = int(idx / (int64_t(n_T) * n2));
+    const int rest = int(idx % (int64_t(n_T) * n2));
+    const int A = rest / n2, C2 = rest % n2;
+    const int d = face / 2, sd = face % 2;
+    const int ia = d == 0 ? 1 : 0, ib = d == 2 ? 1 : 2;
+    const int ca = C2 % nq, cb = C2 / nq;
+    const PairDesc pd = diag[A];
+    double v = 0.0;
+    for (int sl = 0; sl < kMaxPairPatches; ++sl) {
+      const int p = pd.patch[sl];
+      if (p < 0) continue;
+      const bool reaches = sd == 0 ? prm.lo[p][d] == 0.0 : prm.hi[p][d] == 1.0;
+      const int end = sd == 0 ? 0 : prm.n_elem[p][d] + prm.degree[p][d] - 1;
+      if (!reaches || pd.a[sl][d] != end) continue;
+      double fa = 0.0, fb = 0.0;
+      for (int b = 0; b < nf; ++b) {
+        fa += I1[((((int64_t(p) * 3 + ia) * 4 + 0) * nf + pd.a[sl][ia]) * nf + b) * nq + ca];
+        fb += I1[((((int64_t(p) * 3 + ib) * 4 + 0) * nf + pd.a[sl][ib]) * nf + b) * nq + cb];
+      }
+      v += fa * fb;
+    }
+    Ff[idx] = v;
+  }
+}
+
 // The volume table of eq. 18: t_C = int N_C over the tile = sum_A F[A][C] (the basis sums to one).
 __global__ void volume_table_kernel(const double* __restrict__ F, int n_T, int n_pi, double* __restrict__ vol) {
   for (int C = blockIdx.x * blockDim.x + threadIdx.x; C < n_pi; C += gridDim.x * blockDim.x) {
@@ -245,6 +282,9 @@ msasm_status build_table_gpu(msasm_tables* tab, cudaStream_t stream) {
   load_table_kernel<<<152 * 2, 256, 0, stream>>>(d_diag, d_I1, topo.n_T, q, nf_max, tab->d_F);
   MSASM_CUDA(cudaGetLastError());
   volume_table_kernel<<<(n_pi + 127) / 128, 128, 0, stream>>>(tab->d_F, topo.n_T, n_pi, tab->d_vol);
+  MSASM_CUDA(cudaGetLastError());
+  MSASM_CUDA(cudaMalloc(&tab->d_Fface, size_t(6) * topo.n_T * nq * nq * sizeof(double)));
+  face_table_kernel<<<152 * 2, 256, 0, stream>>>(prm, d_diag, d_I1, topo.n_T, nf_max, tab->d_Fface);
   MSASM_CUDA(cudaGetLastError());
   MSASM_CUDA(cudaFreeAsync(d_I1, stream));
   MSASM_CUDA(cudaFreeAsync(d_desc, stream));

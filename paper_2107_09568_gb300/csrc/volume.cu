@@ -1,5 +1,5 @@
-// Volume (Sec. 3.1, eq. 14-19) and the body-force load vector (eq. 39-40, 53-55) through lookup
-// tables, for every tile at once.  Both need only the macro-Jacobian determinant at the
+// Volume (Sec. 3.1, eq. 14-19) and the body-force and traction load vectors (eq. 39-41, 53-55,
+// 85-88) through lookup tables, for every tile at once.  Both need only the macro-Jacobian determinant at the
 // interpolation nodes, d_C^(t) = |det J^(t)(xi_C)| (the interpolated |det J| of eq. 15 and of the
 // body-force coefficients b |det J| of eq. 40):
 //
@@ -11,7 +11,9 @@
 // two tiles (a glued face) receives two additions; with exactly two addends the sum does not depend
 // on their order, so the result is deterministic.  The total volume is a fixed-order reduction of
 // the tile volumes.
+#include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "common.h"
 #include "macro_jacobian.cuh"
@@ -66,6 +68,127 @@ __global__ void volume_load_kernel(VolumeArgs a) {
     }
     __syncwarp();
   }
+}
+
+// Traction load through the face tables (eq. 53, F >= 1 terms; eq. 87-88): on the macro face
+// xi_d = s, per tile on it, the macro traction t |det I_M| at the face's (q+1)^2 nodes, where on
+// that face det I_M = (n x g_ia) . g_ib = |g_ia x g_ib| (g_k = dM/dxi_k, n the unit normal along
+// g^d), then f_A = t sum_C2 Ff[A][C2] |g_ia x g_ib|(node C2).  The node Jacobians come from the
+// pullback's sum factorisation with the normal direction tabulated at xi_d = s for every node
+// index (only the slice c_d = 0 is used).  One warp per tile on the face.
+struct TractionArgs {
+  MacroTileArgs geo;
+  int d, ia, ib, s;
+  const double* Ff;        // face table of this face (n_T x nq^2)
+  int n_T;
+  const int32_t* gmap;
+  double t0, t1, t2;
+  double* f;               // load vector (n_rows, accumulated)
+};
+
+__global__ void traction_load_kernel(TractionArgs a) {
+  extern __shared__ double smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
+  const int nq = a.geo.nq, n2 = nq * nq;
+  int nP, nS, nU, nJ;
+  jac_scratch_sizes(a.geo.np, nq, nP, nS, nU, nJ);
+  double* P = smem + size_t(warp) * (nP + nS + nU + nJ + n2);
+  double* S = P + nP;
+  double* U = S + nS;
+  double* Jn = U + nU;
+  double* area = Jn + nJ;
+  const int ne[3] = {a.geo.n_elem[0], a.geo.n_elem[1], a.geo.n_elem[2]};
+  const int64_t n_face = int64_t(ne[a.ia]) * ne[a.ib];
+  for (int64_t k = int64_t(blockIdx.x) * warps + warp; k < n_face; k += int64_t(gridDim.x) * warps) {
+    int e[3];
+    e[a.d] = a.s ? ne[a.d] - 1 : 0;
+    e[a.ia] = int(k % ne[a.ia]);
+    e[a.ib] = int(k / ne[a.ia]);
+    const int64_t t = e[0] + int64_t(ne[0]) * (e[1] + int64_t(ne[1]) * e[2]);
+    tile_node_jacobians(a.geo, t, P, S, U, Jn, lane);
+    for (int C2 = lane; C2 < n2; C2 += 32) {
+      int c[3];
+      c[a.d] = 0;
+      c[a.ia] = C2 % nq;
+      c[a.ib] = C2 / nq;
+      const double* J = Jn + 9 * (c[0] + nq * (c[1] + nq * c[2]));   // J[p * 3 + i] = dM_p / dxi_i
+      const double ga[3] = {J[a.ia], J[3 + a.ia], J[6 + a.ia]};
+      const double gb[3] = {J[a.ib], J[3 + a.ib], J[6 + a.ib]};
+      const double x = ga[1] * gb[2] - ga[2] * gb[1], y = ga[2] * gb[0] - ga[0] * gb[2],
+                   z = ga[0] * gb[1] - ga[1] * gb[0];
+      area[C2] = sqrt(x * x + y * y + z * z);
+    }
+    __syncwarp();
+    for (int A = lane; A < a.n_T; A += 32) {
+      const double* Fa = a.Ff + size_t(A) * n2;
+      double v = 0.0;
+      for (int C2 = 0; C2 < n2; ++C2) v = fma(Fa[C2], area[C2], v);
+      if (v != 0.0) {
+        const int64_t g = a.gmap[t * a.n_T + A];
+        atomicAdd(a.f + 3 * g + 0, a.t0 * v);
+        atomicAdd(a.f + 3 * g + 1, a.t1 * v);
+        atomicAdd(a.f + 3 * g + 2, a.t2 * v);
+      }
+    }
+    __syncwarp();
+  }
+}
+
+void bspline_span_basis(const double* t, int p, int span, double u, double* vals, double* ders);
+
+msasm_status traction_load_gpu(const msasm_plan* plan, const double* d_ctrl, int face, const double tr[3], double* d_f,
+                               cudaStream_t st) {
+  const int d = face / 2, sd = face % 2, nq = plan->tab->q + 1;
+  TractionArgs a;
+  a.geo = macro_tile_args(plan, d_ctrl);
+  a.d = d;
+  a.ia = d == 0 ? 1 : 0;
+  a.ib = d == 2 ? 1 : 2;
+  a.s = sd;
+  a.n_T = plan->tab->topo.n_T;
+  a.Ff = plan->tab->d_Fface + size_t(face) * a.n_T * nq * nq;
+  a.gmap = plan->d_gmap;
+  a.t0 = tr[0];
+  a.t1 = tr[1];
+  a.t2 = tr[2];
+  a.f = d_f;
+  // the normal direction's macro basis at xi_d = s, repeated for every node index
+  const std::vector<double>& t = plan->knots_host[d];
+  const int p = plan->degree[d];
+  std::vector<double> nb;
+  for (int k : plan->span_host[d]) {
+    const double u0 = t[size_t(k)], h = t[size_t(k) + 1] - t[size_t(k)];
+    double vals[8], ders[8];
+    bspline_span_basis(t.data(), p, k, u0 + h * sd, vals, ders);
+    for (int c = 0; c < nq; ++c)
+      for (int j = 0; j <= p; ++j) {
+        nb.push_back(vals[j]);
+        nb.push_back(ders[j] * h);
+      }
+  }
+  double* d_nb = nullptr;
+  MSASM_CUDA(cudaMallocAsync(&d_nb, nb.size() * sizeof(double), st));
+  MSASM_CUDA(cudaMemcpyAsync(d_nb, nb.data(), nb.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  a.geo.basis[d] = d_nb;
+  int nP, nS, nU, nJ;
+  jac_scratch_sizes(a.geo.np, nq, nP, nS, nU, nJ);
+  const int warps = 4;
+  const size_t smem = warps * size_t(nP + nS + nU + nJ + nq * nq) * sizeof(double);
+  msasm_status status = MSASM_OK;
+  if (smem > 200 * 1024) status = fail(MSASM_EUNSUPPORTED, "macro degree / q too large for the traction kernel");
+  cudaError_t e = cudaSuccess;
+  if (status == MSASM_OK)
+    e = cudaFuncSetAttribute(traction_load_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (status == MSASM_OK && e == cudaSuccess) {
+    const int64_t n_face = int64_t(plan->n_elem[a.ia]) * plan->n_elem[a.ib];
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((n_face + warps - 1) / warps, 152 * 16));
+    traction_load_kernel<<<unsigned(blocks), 32 * warps, smem, st>>>(a);
+    e = cudaGetLastError();
+  }
+  if (status == MSASM_OK && e != cudaSuccess) status = cuda_fail(e, "traction load kernel");
+  cudaStreamSynchronize(st);                     // the host table outlives its copy
+  cudaFreeAsync(d_nb, st);
+  return status;
 }
 
 // sum of n values in a fixed order: one block, a strided partial sum per thread, then a tree

@@ -173,8 +173,16 @@ def volume(flush, workload="beam1000"):
     (vt, V), ms_v = _timed(lambda: plan.volume(ctrl), reps=5, flush=flush)
     g, ms_g = _timed(lambda: plan.volume_grad(ctrl), reps=5, flush=flush)
     f, ms_f = _timed(lambda: plan.body_load(ctrl, (0.0, 0.0, -9.81)), reps=5, flush=flush)
+    # traction on the twisted end face (x = n_x) and on a twisted side face (y = max), through the
+    # face tables, against the direct quadrature on the host
+    trac = {}
+    for face in (1, 3):
+        ft, ms_t = _timed(lambda: plan.traction_load_lookup(ctrl, face, (0.0, 0.0, -1.0)), reps=5, flush=flush)
+        ref = torch.tensor(plan.traction_load(face, (0.0, 0.0, -1.0), w.macro.ctrl), device="cuda")
+        trac[f"face{face}"] = {"ms_incl_host_table": ms_t, "rel_max_vs_direct_quadrature":
+                               ((ft - ref).abs().max() / ref.abs().max()).item()}
     return {"tiles": plan.n_tiles, "volume": V.item(), "volume_ms": ms_v, "volume_grad_ms": ms_g,
-            "body_load_ms": ms_f,
+            "body_load_ms": ms_f, "traction_lookup": trac,
             "grad_translation_residual": (g.sum(dim=0).abs().max() / g.abs().max()).item(),
             "grad_euler_residual": abs((ctrl * g).sum().item() - 3 * V.item()) / V.item(),
             "load_total_residual": abs(f.sum().item() + 9.81 * V.item()) / (9.81 * V.item())}

@@ -84,3 +84,40 @@ def test_beam1000_volume_gradient_and_load_invariants():
     g = plan.volume_grad(ctrl)
     assert (g.sum(dim=0).abs().max() / g.abs().max()).item() <= 1e-12
     assert abs((ctrl * g).sum().item() - 3 * V.item()) <= 1e-12 * V.item()
+
+
+# ---------------------------------------------------------------- traction through the face tables
+@pytest.mark.parametrize("n_e,q", [(2, 0), (2, 3), (3, 2)])
+def test_face_tables(n_e, q):
+    micro = synth.micro_cross(n_e)
+    tile = ReferenceTile(micro)
+    tab = msasm.Tables(micro, q)
+    for face in range(6):
+        Fo = otables.face_load_table(tile, q, face)
+        F = tab.face_table(face).cpu().numpy()
+        assert np.abs(F - Fo).max() <= 1e-15, face
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("face", [0, 3, 5])
+def test_traction_load_lookup_parity(name, face):
+    from oracle import loads as oloads
+    n_e, q, macro = CASES[name]()
+    micro = synth.micro_cross(n_e)
+    prob = Problem(micro, macro, q, structure=False)
+    plan = msasm.Plan(msasm.Tables(micro, q), macro)
+    tr = (0.3, -1.0, 0.5)
+    f = plan.traction_load_lookup(torch.tensor(macro.ctrl, device="cuda"), face, tr).cpu().numpy()
+    ref = oloads.traction_load_lookup(prob, face, tr, q).ravel()
+    assert np.abs(f - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+def test_cantilever2000_traction_lookup_equals_direct_quadrature():
+    """The 20x20x5 cantilever's load (unit traction on the x = 20 face): its macro map is affine,
+    so the lookup form equals the direct quadrature of the traction on the strut end faces."""
+    m = synth.macro_cantilever(20, 20, 5)
+    plan = msasm.Plan(msasm.Tables(synth.micro_cross(2), 3), m)
+    f = plan.traction_load_lookup(torch.tensor(m.ctrl, device="cuda"), 1, (0.0, 0.0, -1.0)).cpu().numpy()
+    ref = plan.traction_load(1, (0.0, 0.0, -1.0), m.ctrl)
+    assert np.abs(f - ref).max() <= 1e-13 * np.abs(ref).max()
+    assert abs(f.sum() + 0.09 * 20 * 5) <= 1e-11           # total force: strut end area 0.09 per tile face
