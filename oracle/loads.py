@@ -71,7 +71,7 @@ def traction_load_lookup(prob, face, traction, q, ctrl=None, F=None):
     ia, ib = [k for k in range(3) if k != d]
     mm, tile = prob.mmap, prob.tile
     F = tables.face_load_table(tile, q, face) if F is None else F
-    uv = tables.face_nodes(q)
+    uv = tables.face_nodes(q, face)
     xi = np.zeros((len(uv), 3))
     xi[:, d] = float(s)
     xi[:, ia], xi[:, ib] = uv[:, 0], uv[:, 1]

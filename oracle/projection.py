@@ -37,7 +37,7 @@ def l2_coefficients(mmap: MacroMap, t: int, q: int, lam: float, mu: float, n_g: 
     (integrated exactly: a rule of 2q+2 points per direction, for its degree-2q integrand) and the
     load b_C = int N_C A_bar, integrated by the n_g-point Gauss rule per direction.
     Returns (n_pi, 81) in the layout of the nodal values (n_pi, i, j, alpha, beta)."""
-    xm, wm = tensor_gauss(2 * q + 2)
+    xm, wm = tensor_gauss(2 * max(quadrature.degrees(q)) + 2)
     Nm = quadrature.tensor_lagrange(q, xm)                       # (n_m, n_pi)
     M = Nm.T @ (wm[:, None] * Nm)
     xg, wg = tensor_gauss(n_g)
@@ -79,3 +79,40 @@ def select_degree(macro, tol: float, q0: int, q_max: int, **kw):
         if projection_error(macro, q, **kw)[1] <= tol:
             return q
     return q_max
+
+
+def select_degrees(macro, tol: float, q_init, q_max: int = 7, **kw):
+    """A degree per direction (the anisotropic projection space of Sec. 3.3.4): from q_init (the
+    macro map's degrees), enrich while E_proj > tol, each step raising the one direction whose
+    increase lowers E_proj most; then coarsen while possible, each step lowering the direction whose
+    decrease keeps E_proj lowest, as long as it stays <= tol.  Ties go to the lowest direction.
+    Returns (degrees, E_proj)."""
+    q = list(quadrature.degrees(q_init))
+    err = projection_error(macro, tuple(q), **kw)[1]
+    while err > tol:
+        best = None
+        for d in range(3):
+            if q[d] >= q_max:
+                continue
+            c = q.copy()
+            c[d] += 1
+            e = projection_error(macro, tuple(c), **kw)[1]
+            if best is None or e < best[0]:
+                best = (e, c)
+        if best is None:
+            break
+        err, q = best
+    while True:
+        best = None
+        for d in range(3):
+            if q[d] == 0:
+                continue
+            c = q.copy()
+            c[d] -= 1
+            e = projection_error(macro, tuple(c), **kw)[1]
+            if e <= tol and (best is None or e < best[0]):
+                best = (e, c)
+        if best is None:
+            break
+        err, q = best
+    return tuple(q), err

@@ -4,7 +4,8 @@ The interpolation nodes of degree q are the q+1 Gauss-Legendre points on [0,1]
 (reading of eq. 20-24: interpolation at these nodes equals the discrete L2
 projection onto Q_q with a (q+1)-point Gauss rule, since the mass matrix is
 integrated exactly).  The basis N_C of eq. 42 is then the tensor Lagrange
-basis on those nodes, ordered C = c1 + (q+1)(c2 + (q+1) c3).
+basis on those nodes, ordered C = c1 + (q+1)(c2 + (q+1) c3); with a degree per direction
+(q1, q2, q3) the same with n_d = q_d + 1 nodes in direction d.
 """
 from __future__ import annotations
 
@@ -34,23 +35,39 @@ def interp_nodes(q: int) -> np.ndarray:
     return gauss_legendre(q + 1)[0]
 
 
-def tensor_nodes(q: int) -> np.ndarray:
-    """All (q+1)^3 nodes xi_C, C = c1 + (q+1)(c2 + (q+1) c3); shape ((q+1)^3, 3)."""
-    g = interp_nodes(q)
-    n = q + 1
-    out = np.empty((n ** 3, 3))
-    for c3 in range(n):
-        for c2 in range(n):
-            for c1 in range(n):
-                out[c1 + n * (c2 + n * c3)] = (g[c1], g[c2], g[c3])
+def degrees(q):
+    """Per-direction degrees (q1, q2, q3) of an isotropic degree q or of a 3-sequence."""
+    if np.ndim(q) == 0:
+        return (int(q),) * 3
+    q = tuple(int(v) for v in q)
+    assert len(q) == 3
+    return q
+
+
+def n_nodes(q) -> int:
+    """n_pi = (q1+1)(q2+1)(q3+1)."""
+    q1, q2, q3 = degrees(q)
+    return (q1 + 1) * (q2 + 1) * (q3 + 1)
+
+
+def tensor_nodes(q) -> np.ndarray:
+    """All nodes xi_C of the tensor space Q_(q1,q2,q3), C = c1 + n1 (c2 + n2 c3) with n_d = q_d + 1;
+    shape (n_pi, 3).  An integer q is the isotropic space."""
+    qd = degrees(q)
+    g = [interp_nodes(v) for v in qd]
+    n1, n2, n3 = (v + 1 for v in qd)
+    out = np.empty((n1 * n2 * n3, 3))
+    for c3 in range(n3):
+        for c2 in range(n2):
+            for c1 in range(n1):
+                out[c1 + n1 * (c2 + n2 * c3)] = (g[0][c1], g[1][c2], g[2][c3])
     return out
 
 
-def tensor_lagrange(q: int, xi) -> np.ndarray:
-    """N_C(xi) for all C at points xi (n, 3) -> (n, (q+1)^3)."""
-    g = interp_nodes(q)
+def tensor_lagrange(q, xi) -> np.ndarray:
+    """N_C(xi) = l_c1(xi_1) l_c2(xi_2) l_c3(xi_3) for all C at points xi (n, 3) -> (n, n_pi)."""
+    qd = degrees(q)
     xi = np.atleast_2d(xi)
-    L = [lagrange(g, xi[:, d]) for d in range(3)]
-    n = q + 1
-    out = np.einsum("pa,pb,pc->pcba", L[0], L[1], L[2]).reshape(len(xi), n ** 3)
+    L = [lagrange(interp_nodes(qd[d]), xi[:, d]) for d in range(3)]
+    out = np.einsum("pa,pb,pc->pcba", L[0], L[1], L[2]).reshape(len(xi), n_nodes(qd))
     return out

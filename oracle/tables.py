@@ -23,8 +23,8 @@ def default_gauss_points(p_T: int, q: int) -> int:
 def build_table(tile, q: int, n_g: int | None = None) -> np.ndarray:
     """mat[K] as an array (n_nz, (q+1)^3, 3, 3)."""
     p_T = max(max(P["degree"]) for P in tile.patches)
-    n_g = n_g or default_gauss_points(p_T, q)
-    n_pi = (q + 1) ** 3
+    n_g = n_g or default_gauss_points(p_T, max(quadrature.degrees(q)))
+    n_pi = quadrature.n_nodes(q)
     T = np.zeros((tile.n_nz, n_pi, 3, 3))
     g1, w1 = quadrature.gauss_legendre(n_g)
     for el in tile.elements:
@@ -55,9 +55,9 @@ def build_table(tile, q: int, n_g: int | None = None) -> np.ndarray:
 def volume_table(tile, q: int, n_g: int | None = None) -> np.ndarray:
     """t^h of eq. 18 for the projection basis N_C: t_C = int_{Omega_T} N_C dxi."""
     p_T = max(max(P["degree"]) for P in tile.patches)
-    n_g = n_g or default_gauss_points(p_T, q)
+    n_g = n_g or default_gauss_points(p_T, max(quadrature.degrees(q)))
     g1, w1 = quadrature.gauss_legendre(n_g)
-    t = np.zeros((q + 1) ** 3)
+    t = np.zeros(quadrature.n_nodes(q))
     for el in tile.elements:
         P = tile.patches[el["patch"]]
         lo, hi = P["lo"], P["hi"]
@@ -74,9 +74,9 @@ def load_table(tile, q: int, n_g: int | None = None) -> np.ndarray:
     F[A, C] = int_{Omega_T} (R_A o T^r^-1) N_C dxi, shape (n_T, (q+1)^3), by the same element
     quadrature as the stiffness table (the integrand has degree <= p_T + q per direction)."""
     p_T = max(max(P["degree"]) for P in tile.patches)
-    n_g = n_g or default_gauss_points(p_T, q)
+    n_g = n_g or default_gauss_points(p_T, max(quadrature.degrees(q)))
     g1, w1 = quadrature.gauss_legendre(n_g)
-    F = np.zeros((tile.n_T, (q + 1) ** 3))
+    F = np.zeros((tile.n_T, quadrature.n_nodes(q)))
     for el in tile.elements:
         P = tile.patches[el["patch"]]
         lo, hi = P["lo"], P["hi"]
@@ -95,19 +95,27 @@ def load_table(tile, q: int, n_g: int | None = None) -> np.ndarray:
 
 
 
-def face_nodes(q: int) -> np.ndarray:
-    """The (q+1)^2 nodes of the face projection space, C2 = c_a + (q+1) c_b in the two in-face
-    directions (ascending axis order); shape ((q+1)^2, 2)."""
-    g = quadrature.interp_nodes(q)
-    n = q + 1
-    return np.array([(g[ca], g[cb]) for cb in range(n) for ca in range(n)])
+def _face_degrees(q, face: int):
+    d = face // 2
+    ia, ib = [k for k in range(3) if k != d]
+    qd = quadrature.degrees(q)
+    return qd[ia], qd[ib]
 
 
-def face_lagrange(q: int, uv) -> np.ndarray:
-    """N_C2(u, v) = l_ca(u) l_cb(v) at points uv (n, 2) -> (n, (q+1)^2)."""
-    g = quadrature.interp_nodes(q)
+def face_nodes(q, face: int = 0) -> np.ndarray:
+    """The (q_a+1)(q_b+1) nodes of the face projection space of `face`, C2 = c_a + (q_a+1) c_b in
+    the two in-face directions a < b; shape (n, 2)."""
+    qa, qb = _face_degrees(q, face)
+    ga, gb = quadrature.interp_nodes(qa), quadrature.interp_nodes(qb)
+    return np.array([(ga[ca], gb[cb]) for cb in range(qb + 1) for ca in range(qa + 1)])
+
+
+def face_lagrange(q, uv, face: int = 0) -> np.ndarray:
+    """N_C2(u, v) = l_ca(u) l_cb(v) at points uv (n, 2) of `face` -> (n, (q_a+1)(q_b+1))."""
+    qa, qb = _face_degrees(q, face)
     uv = np.atleast_2d(uv)
-    La, Lb = quadrature.lagrange(g, uv[:, 0]), quadrature.lagrange(g, uv[:, 1])
+    La = quadrature.lagrange(quadrature.interp_nodes(qa), uv[:, 0])
+    Lb = quadrature.lagrange(quadrature.interp_nodes(qb), uv[:, 1])
     return np.einsum("pa,pb->pba", La, Lb).reshape(len(uv), -1)
 
 
@@ -121,9 +129,10 @@ def face_load_table(tile, q: int, face: int, n_g: int | None = None) -> np.ndarr
     d, s = face // 2, face % 2
     ia, ib = [k for k in range(3) if k != d]
     p_T = max(max(P["degree"]) for P in tile.patches)
-    n_g = n_g or default_gauss_points(p_T, q)
+    n_g = n_g or default_gauss_points(p_T, max(quadrature.degrees(q)))
     g1, w1 = quadrature.gauss_legendre(n_g)
-    F = np.zeros((tile.n_T, (q + 1) ** 2))
+    qa, qb = _face_degrees(q, face)
+    F = np.zeros((tile.n_T, (qa + 1) * (qb + 1)))
     for p, P in enumerate(tile.patches):
         lo, hi = P["lo"], P["hi"]
         if not ((s == 0 and lo[d] == 0.0) or (s == 1 and hi[d] == 1.0)):
@@ -138,7 +147,7 @@ def face_load_table(tile, q: int, face: int, n_g: int | None = None) -> np.ndarr
                 w = np.outer(w1, w1).ravel() / (ne[ia] * ne[ib]) * (hi - lo)[ia] * (hi - lo)[ib]
                 xi = lo + (hi - lo) * th
                 vals, _ = tile.patch_basis(p, th)
-                N2 = face_lagrange(q, xi[:, [ia, ib]])
+                N2 = face_lagrange(q, xi[:, [ia, ib]], face)
                 Floc = np.einsum("g,ga,gc->ac", w, vals, N2)
                 for a, A in enumerate(P["ids"]):
                     F[A] += Floc[a]
