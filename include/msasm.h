@@ -105,7 +105,18 @@ typedef struct msasm_plan msasm_plan;       /* opaque: macro mesh, numbering, CS
 msasm_status msasm_build_tables(const msasm_micro_desc* micro, int32_t q, int32_t n_gauss,
                                 void* stream, msasm_tables** out);
 
-/* Sizes of a table: n_T control points, n_nz pairs (eq. 56), n_pi = (q+1)^3. */
+/* The same with a projection degree per direction, q3 = (q1, q2, q3) (host int32[3], each 0..5):
+ * the anisotropic space Q_(q1,q2,q3) of Sec. 3.3.4 (e.g. a higher degree along a twist), n_pi =
+ * (q1+1)(q2+1)(q3+1) nodes C = c1 + (q1+1)(c2 + (q2+1) c3) at each direction's Gauss-Legendre
+ * points.  Every call that takes these tables uses that space (the FP64-accurate tensor-core
+ * contraction needs 9 n_pi <= 576). */
+msasm_status msasm_build_tables_q3(const msasm_micro_desc* micro, const int32_t* q3, int32_t n_gauss,
+                                   void* stream, msasm_tables** out);
+
+/* The tables' degree per direction into q3 (host int32[3]). */
+msasm_status msasm_tables_degrees(const msasm_tables* tab, int32_t* q3);
+
+/* Sizes of a table: n_T control points, n_nz pairs (eq. 56), n_pi = (q1+1)(q2+1)(q3+1). */
 msasm_status msasm_tables_info(const msasm_tables* tab, int32_t* n_T, int32_t* n_nz, int32_t* n_pi);
 
 /* Copy the FP64 table (n_nz * 9 * n_pi values, layout above) to d_table, and the
@@ -328,6 +339,11 @@ msasm_status msasm_linop_apply(msasm_plan* plan, const double* d_coef, msasm_pre
 msasm_status msasm_projection_error(const msasm_plan* plan, const double* d_ctrl, int32_t q, int32_t n_samples,
                                     double E, double nu, double* d_err_tiles, double* d_err_max, void* stream);
 
+/* The same error for a degree per direction, q3 = (q1, q2, q3) (host int32[3], each 0..7). */
+msasm_status msasm_projection_error_q3(const msasm_plan* plan, const double* d_ctrl, const int32_t* q3,
+                                       int32_t n_samples, double E, double nu, double* d_err_tiles, double* d_err_max,
+                                       void* stream);
+
 /* The same error for the L2 projection of degree q (msasm_pullback_l2, load rule of n_gauss points
  * per direction, 1..9) in place of the interpolant. */
 msasm_status msasm_projection_error_l2(const msasm_plan* plan, const double* d_ctrl, int32_t q, int32_t n_gauss,
@@ -371,8 +387,8 @@ msasm_status msasm_body_load(const msasm_plan* plan, const double* d_ctrl, doubl
 msasm_status msasm_traction_load_lookup(const msasm_plan* plan, const double* d_ctrl, int32_t face, double tx,
                                         double ty, double tz, double* d_f, void* stream);
 
-/* Copy the face load table of `face` (n_T x (q+1)^2 FP64, row A, column C2 = c_a + (q+1) c_b over
- * the two in-face directions in ascending order) to d_Ff. */
+/* Copy the face load table of `face` (n_T x (q_a+1)(q_b+1) FP64, row A, column C2 = c_a + (q_a+1) c_b
+ * over the two in-face directions a < b) to d_Ff. */
 msasm_status msasm_face_table_copy(const msasm_tables* tab, int32_t face, double* d_Ff, void* stream);
 
 /* ---------------------------------------------------------------- diagnostics */

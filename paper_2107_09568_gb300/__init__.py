@@ -48,11 +48,19 @@ class Tables:
                             self._keep[2].ctypes.data_as(C.POINTER(C.c_double)),
                             self._keep[3].ctypes.data_as(C.POINTER(C.c_double)))
         h = C.c_void_p()
-        check(lib.msasm_build_tables(C.byref(d), int(q), int(n_gauss), _stream(stream), C.byref(h)))
+        if np.ndim(q) == 0:
+            check(lib.msasm_build_tables(C.byref(d), int(q), int(n_gauss), _stream(stream), C.byref(h)))
+        else:                                     # one projection degree per direction
+            q3 = (C.c_int32 * 3)(*[int(v) for v in q])
+            check(lib.msasm_build_tables_q3(C.byref(d), q3, int(n_gauss), _stream(stream), C.byref(h)))
         self.handle = h
         n_T, n_nz, n_pi = C.c_int32(), C.c_int32(), C.c_int32()
         check(lib.msasm_tables_info(h, C.byref(n_T), C.byref(n_nz), C.byref(n_pi)))
-        self.n_T, self.n_nz, self.n_pi, self.q = n_T.value, n_nz.value, n_pi.value, int(q)
+        qd = (C.c_int32 * 3)()
+        check(lib.msasm_tables_degrees(h, qd))
+        self.n_T, self.n_nz, self.n_pi = n_T.value, n_nz.value, n_pi.value
+        self.qd = tuple(int(v) for v in qd)         # degree per direction
+        self.q = self.qd[0] if len(set(self.qd)) == 1 else self.qd
 
     def table(self):
         """The FP64 table as a (n_nz, n_pi, 3, 3) CUDA tensor (a copy)."""
@@ -247,7 +255,8 @@ def _plan_traction_load_lookup(self, ctrl, face, traction, stream=None):
 def _tables_face_table(self, face, stream=None):
     """The face load table of `face` (n_T, (q+1)^2) FP64 on the GPU."""
     import torch
-    out = torch.empty((self.n_T, (self.q + 1) ** 2), dtype=torch.float64, device="cuda")
+    ia, ib = [k for k in range(3) if k != face // 2]
+    out = torch.empty((self.n_T, (self.qd[ia] + 1) * (self.qd[ib] + 1)), dtype=torch.float64, device="cuda")
     check(load().msasm_face_table_copy(self.handle, int(face), _ptr(out), _stream(stream)))
     return out
 
@@ -267,7 +276,13 @@ def _plan_projection_error(self, ctrl, q, n_samples=5, E=1.0, nu=0.3, n_gauss=0,
     import torch
     e = torch.empty(self.n_tiles, dtype=torch.float64, device="cuda")
     m = torch.empty((), dtype=torch.float64, device="cuda")
-    if n_gauss > 0:
+    if np.ndim(q) != 0:                            # one degree per direction
+        if n_gauss > 0:
+            raise MsasmError(-1, "the L2 projection error takes one degree")
+        q3 = (C.c_int32 * 3)(*[int(v) for v in q])
+        check(load().msasm_projection_error_q3(self.handle, _ptr(ctrl), q3, int(n_samples), float(E), float(nu),
+                                               _ptr(e), _ptr(m), _stream(stream)))
+    elif n_gauss > 0:
         check(load().msasm_projection_error_l2(self.handle, _ptr(ctrl), int(q), int(n_gauss), int(n_samples),
                                                float(E), float(nu), _ptr(e), _ptr(m), _stream(stream)))
     else:
@@ -297,6 +312,43 @@ def select_projection_degree(plan, ctrl, tol, q0, q_max, **kw):
         if plan.projection_error(ctrl, q, **kw)[1].item() <= tol:
             return q
     return q_max
+
+
+def select_projection_degrees(plan, ctrl, tol, q_init, q_max=7, **kw):
+    """A degree per direction (the anisotropic space of Sec. 3.3.4; the projection errors on the
+    GPU): from q_init (the macro map's degrees), raise while E_proj > tol the one direction whose
+    increase lowers E_proj most, then lower while E_proj stays <= tol the direction whose decrease
+    keeps it lowest (ties to the lowest direction).  Returns (degrees, E_proj)."""
+    err_of = lambda q: plan.projection_error(ctrl, tuple(q), **kw)[1].item()
+    q = [int(v) for v in q_init]
+    err = err_of(q)
+    while err > tol:
+        best = None
+        for d in range(3):
+            if q[d] >= q_max:
+                continue
+            c = q.copy()
+            c[d] += 1
+            e = err_of(c)
+            if best is None or e < best[0]:
+                best = (e, c)
+        if best is None:
+            break
+        err, q = best
+    while True:
+        best = None
+        for d in range(3):
+            if q[d] == 0:
+                continue
+            c = q.copy()
+            c[d] -= 1
+            e = err_of(c)
+            if e <= tol and (best is None or e < best[0]):
+                best = (e, c)
+        if best is None:
+            break
+        err, q = best
+    return tuple(q), err
 
 
 Plan.projection_error = _plan_projection_error

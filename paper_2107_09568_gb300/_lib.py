@@ -41,6 +41,9 @@ _lib = None
 _SIGS = {
     "msasm_build_tables": (c_i32, [P(MicroDescC), c_i32, c_i32, c_vp, P(c_vp)]),
     "msasm_tables_info": (c_i32, [c_vp, P(c_i32), P(c_i32), P(c_i32)]),
+    "msasm_build_tables_q3": (c_i32, [P(MicroDescC), P(c_i32), c_i32, c_vp, P(c_vp)]),
+    "msasm_tables_degrees": (c_i32, [c_vp, P(c_i32)]),
+    "msasm_projection_error_q3": (c_i32, [c_vp, c_vp, P(c_i32), c_i32, c_dbl, c_dbl, c_vp, c_vp, c_vp]),
     "msasm_tables_copy": (c_i32, [c_vp, c_vp, c_vp, c_vp]),
     "msasm_tables_destroy": (None, [c_vp]),
     "msasm_plan_create": (c_i32, [c_vp, P(MacroDescC), c_i32, c_vp, P(c_vp), P(c_i64), P(c_i64)]),

@@ -23,7 +23,7 @@
 namespace msasm {
 
 MacroTileArgs macro_tile_args(const msasm_plan* plan, const double* d_ctrl);
-size_t pullback_smem_per_warp(const int np[3], int nq);
+size_t pullback_smem_per_warp(const int np[3], const int nq[3]);
 
 // ------------------------------------------------------------------ step 1: G from u or from dL/dvalues
 template <typename T>
@@ -108,10 +108,10 @@ struct AdjointArgs {
 __global__ void adjoint_pullback_kernel(AdjointArgs a) {
   extern __shared__ double smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
-  const int nq = a.geo.nq, n_pi = nq * nq * nq, K = 9 * n_pi;
+  const int nq1 = a.geo.nq[0], nq2 = a.geo.nq[1], nq3 = a.geo.nq[2], n_pi = nq1 * nq2 * nq3, K = 9 * n_pi;
   const int np1 = a.geo.np[0], np2 = a.geo.np[1], np3 = a.geo.np[2];
   int nP, nS, nU, nJ;
-  jac_scratch_sizes(a.geo.np, nq, nP, nS, nU, nJ);
+  jac_scratch_sizes(a.geo.np, a.geo.nq, nP, nS, nU, nJ);
   double* P = smem + size_t(warp) * (nP + nS + nU + nJ);
   double* S = P + nP;
   double* U = S + nS;
@@ -173,21 +173,21 @@ __global__ void adjoint_pullback_kernel(AdjointArgs a) {
     __syncwarp();
     int e1, e2, e3;
     tile_coords(a.geo, t, e1, e2, e3);
-    const double* B1 = a.geo.basis[0] + size_t(e1) * nq * np1 * 2;
-    const double* B2 = a.geo.basis[1] + size_t(e2) * nq * np2 * 2;
-    const double* B3 = a.geo.basis[2] + size_t(e3) * nq * np3 * 2;
+    const double* B1 = a.geo.basis[0] + size_t(e1) * nq1 * np1 * 2;
+    const double* B2 = a.geo.basis[1] + size_t(e2) * nq2 * np2 * 2;
+    const double* B3 = a.geo.basis[2] + size_t(e3) * nq3 * np3 * 2;
     double* X = U;   // [q][c1][c2][a3][p]  (nU doubles)
     double* Y = S;   // [v][c1][a2][a3][p]  (nS doubles)
     for (int o = lane; o < nU; o += 32) {     // contract c3
       int p = o % 3, r = o / 3;
       int a3 = r % np3; r /= np3;
-      int c2 = r % nq; r /= nq;
-      int c1 = r % nq;
-      int q = r / nq;
+      int c2 = r % nq2; r /= nq2;
+      int c1 = r % nq1;
+      int q = r / nq1;
       const int v3 = (q == 2);
       double s = 0.0;
-      for (int c3 = 0; c3 < nq; ++c3)
-        s = fma(Jn[(c1 + nq * (c2 + nq * c3)) * 9 + p * 3 + q], B3[(c3 * np3 + a3) * 2 + v3], s);
+      for (int c3 = 0; c3 < nq3; ++c3)
+        s = fma(Jn[(c1 + nq1 * (c2 + nq2 * c3)) * 9 + p * 3 + q], B3[(c3 * np3 + a3) * 2 + v3], s);
       X[o] = s;
     }
     __syncwarp();
@@ -195,13 +195,13 @@ __global__ void adjoint_pullback_kernel(AdjointArgs a) {
       int p = o % 3, r = o / 3;
       int a3 = r % np3; r /= np3;
       int a2 = r % np2; r /= np2;
-      int c1 = r % nq;
-      int v = r / nq;
+      int c1 = r % nq1;
+      int v = r / nq1;
       double s = 0.0;
-      for (int c2 = 0; c2 < nq; ++c2) {
-        const double x0 = X[(((0 * nq + c1) * nq + c2) * np3 + a3) * 3 + p];
-        const double x1 = X[(((1 * nq + c1) * nq + c2) * np3 + a3) * 3 + p];
-        const double x2 = X[(((2 * nq + c1) * nq + c2) * np3 + a3) * 3 + p];
+      for (int c2 = 0; c2 < nq2; ++c2) {
+        const double x0 = X[(((0 * nq1 + c1) * nq2 + c2) * np3 + a3) * 3 + p];
+        const double x1 = X[(((1 * nq1 + c1) * nq2 + c2) * np3 + a3) * 3 + p];
+        const double x2 = X[(((2 * nq1 + c1) * nq2 + c2) * np3 + a3) * 3 + p];
         if (v == 0) s = fma(x0, B2[(c2 * np2 + a2) * 2], s);
         else s += x1 * B2[(c2 * np2 + a2) * 2 + 1] + x2 * B2[(c2 * np2 + a2) * 2];
       }
@@ -213,9 +213,9 @@ __global__ void adjoint_pullback_kernel(AdjointArgs a) {
       int p = o % 3, c = o / 3;
       int a1 = c % np1, a2 = (c / np1) % np2, a3 = c / (np1 * np2);
       double s = 0.0;
-      for (int c1 = 0; c1 < nq; ++c1) {
-        const double y0 = Y[(((0 * nq + c1) * np2 + a2) * np3 + a3) * 3 + p];
-        const double y12 = Y[(((1 * nq + c1) * np2 + a2) * np3 + a3) * 3 + p];
+      for (int c1 = 0; c1 < nq1; ++c1) {
+        const double y0 = Y[(((0 * nq1 + c1) * np2 + a2) * np3 + a3) * 3 + p];
+        const double y12 = Y[(((1 * nq1 + c1) * np2 + a2) * np3 + a3) * 3 + p];
         s += y0 * B1[(c1 * np1 + a1) * 2 + 1] + y12 * B1[(c1 * np1 + a1) * 2];
       }
       const int64_t gi = (f1 + a1) + int64_t(a.geo.n_ctrl_dir[0]) * ((f2 + a2) + int64_t(a.geo.n_ctrl_dir[1]) * (f3 + a3));

@@ -59,9 +59,9 @@ msasm_status adjoint_pullback_gpu(const msasm_plan* plan, const double* d_ctrl, 
                                   int64_t nt, const void* d_W, bool w_f32, double* d_dP, cudaStream_t s,
                                   const double* vol_w = nullptr);
 msasm_status linop_prepare_gpu(msasm_plan* plan, cudaStream_t s);
-msasm_status projection_error_gpu(const msasm_plan* plan, const double* d_ctrl, int q, int n_s, double lam, double mu,
-                                  double* d_err_tiles, double* d_err_max, cudaStream_t s, int n_gauss = 0);
-msasm_status l2_coef_gpu(const msasm_plan* plan, const double* d_ctrl, int q, int n_g, double lam, double mu,
+msasm_status projection_error_gpu(const msasm_plan* plan, const double* d_ctrl, const int q3[3], int n_s, double lam,
+                                  double mu, double* d_err_tiles, double* d_err_max, cudaStream_t s, int n_gauss = 0);
+msasm_status l2_coef_gpu(const msasm_plan* plan, const double* d_ctrl, const int q3[3], int n_g, double lam, double mu,
                          double* d_coef, cudaStream_t s);
 template <typename T>
 msasm_status linop_pass_gpu(const msasm_plan* plan, const T* d_nz, int ld_nz, int64_t t0, int64_t n_tiles,
@@ -152,9 +152,22 @@ const char* msasm_version(void) { return "msasm 0.1 (sm_103a)"; }
 
 msasm_status msasm_build_tables(const msasm_micro_desc* micro, int32_t q, int32_t n_gauss, void* stream,
                                 msasm_tables** out) {
-  if (!out) return fail(MSASM_EINVAL, "out is NULL");
+  const int32_t q3[3] = {q, q, q};
+  return msasm_build_tables_q3(micro, q3, n_gauss, stream, out);
+}
+
+msasm_status msasm_tables_degrees(const msasm_tables* tab, int32_t* q3) {
+  if (!tab || !q3) return fail(MSASM_EINVAL, "tables or q3 is NULL");
+  for (int d = 0; d < 3; ++d) q3[d] = tab->qd[d];
+  return MSASM_OK;
+}
+
+msasm_status msasm_build_tables_q3(const msasm_micro_desc* micro, const int32_t* q3, int32_t n_gauss, void* stream,
+                                   msasm_tables** out) {
+  if (!out || !q3) return fail(MSASM_EINVAL, "out or q3 is NULL");
   *out = nullptr;
-  if (q < 0 || q > 5) return fail(MSASM_EINVAL, "interpolation degree q must be in 0..5");
+  for (int d = 0; d < 3; ++d)
+    if (q3[d] < 0 || q3[d] > 5) return fail(MSASM_EINVAL, "interpolation degrees must be in 0..5");
   if (n_gauss > 16) return fail(MSASM_EINVAL, "n_gauss must be <= 16");
   msasm_tables* tab = new msasm_tables();
   msasm_status st = build_topology(micro, tab->topo);
@@ -162,8 +175,14 @@ msasm_status msasm_build_tables(const msasm_micro_desc* micro, int32_t q, int32_
     delete tab;
     return st;
   }
-  tab->q = q;
-  tab->n_pi = (q + 1) * (q + 1) * (q + 1);
+  for (int d = 0; d < 3; ++d) tab->qd[d] = q3[d];
+  tab->q = std::max({q3[0], q3[1], q3[2]});
+  tab->n_pi = (q3[0] + 1) * (q3[1] + 1) * (q3[2] + 1);
+  tab->face_off[0] = 0;
+  for (int f = 0; f < 6; ++f) {
+    const int d = f / 2, ia = d == 0 ? 1 : 0, ib = d == 2 ? 1 : 2;
+    tab->face_off[f + 1] = tab->face_off[f] + int64_t(tab->topo.n_T) * (q3[ia] + 1) * (q3[ib] + 1);
+  }
   {
     double best = 1e300;
     for (int A = 0; A < tab->topo.n_T; ++A) {
@@ -241,12 +260,12 @@ msasm_status msasm_plan_create(const msasm_tables* tab, const msasm_macro_desc* 
     delete plan;
     return st;
   };
-  const int nq = tab->q + 1;
-  std::vector<double> xn, wn;
-  gauss_legendre01(nq, xn, wn);
   std::vector<double> basis[3];
   std::vector<int32_t> first[3];
   for (int d = 0; d < 3; ++d) {
+    const int nq = tab->qd[d] + 1;                 // the nodes of this direction's projection degree
+    std::vector<double> xn, wn;
+    gauss_legendre01(nq, xn, wn);
     int p = macro->degree[d], nk = macro->n_knots[d];
     const double* t = macro->knots[d];
     if (p < 1 || p > 5) return bail(fail(MSASM_EINVAL, "macro degree must be in 1..5"));
@@ -816,6 +835,19 @@ msasm_status msasm_projection_error(const msasm_plan* plan, const double* d_ctrl
   MSASM_TRY(check_material(E, nu));
   double lam, mu;
   lame(E, nu, lam, mu);
+  const int q3[3] = {q, q, q};
+  return projection_error_gpu(plan, d_ctrl, q3, n_samples, lam, mu, d_err_tiles, d_err_max,
+                              static_cast<cudaStream_t>(stream));
+}
+
+msasm_status msasm_projection_error_q3(const msasm_plan* plan, const double* d_ctrl, const int32_t* q3,
+                                       int32_t n_samples, double E, double nu, double* d_err_tiles, double* d_err_max,
+                                       void* stream) {
+  if (!plan || !d_ctrl || !q3 || (!d_err_tiles && !d_err_max)) return fail(MSASM_EINVAL, "NULL argument or no output");
+  MSASM_TRY(check_material(E, nu));
+  double lam, mu;
+  lame(E, nu, lam, mu);
+  const int q[3] = {q3[0], q3[1], q3[2]};
   return projection_error_gpu(plan, d_ctrl, q, n_samples, lam, mu, d_err_tiles, d_err_max,
                               static_cast<cudaStream_t>(stream));
 }
@@ -828,7 +860,8 @@ msasm_status msasm_projection_error_l2(const msasm_plan* plan, const double* d_c
   MSASM_TRY(check_material(E, nu));
   double lam, mu;
   lame(E, nu, lam, mu);
-  return projection_error_gpu(plan, d_ctrl, q, n_samples, lam, mu, d_err_tiles, d_err_max,
+  const int q3[3] = {q, q, q};
+  return projection_error_gpu(plan, d_ctrl, q3, n_samples, lam, mu, d_err_tiles, d_err_max,
                               static_cast<cudaStream_t>(stream), n_gauss);
 }
 
@@ -840,7 +873,7 @@ msasm_status msasm_pullback_l2(msasm_plan* plan, const double* d_ctrl, double E,
   double lam, mu;
   lame(E, nu, lam, mu);
   MSASM_CUDA(cudaMemsetAsync(plan->d_degenerate, 0, sizeof(unsigned long long), s));
-  return l2_coef_gpu(plan, d_ctrl, plan->tab->q, n_gauss, lam, mu, d_coef, s);
+  return l2_coef_gpu(plan, d_ctrl, plan->tab->qd, n_gauss, lam, mu, d_coef, s);
 }
 
 msasm_status msasm_load_table_copy(const msasm_tables* tab, double* d_F, double* d_vol, void* stream) {
@@ -896,8 +929,8 @@ msasm_status msasm_traction_load_lookup(const msasm_plan* plan, const double* d_
 msasm_status msasm_face_table_copy(const msasm_tables* tab, int32_t face, double* d_Ff, void* stream) {
   if (!tab || !d_Ff) return fail(MSASM_EINVAL, "tables or d_Ff is NULL");
   if (face < 0 || face > 5) return fail(MSASM_EINVAL, "face must be 0..5");
-  const size_t n = size_t(tab->topo.n_T) * (tab->q + 1) * (tab->q + 1);
-  MSASM_CUDA(cudaMemcpyAsync(d_Ff, tab->d_Fface + size_t(face) * n, n * sizeof(double), cudaMemcpyDeviceToDevice,
+  const size_t n = size_t(tab->face_off[face + 1] - tab->face_off[face]);
+  MSASM_CUDA(cudaMemcpyAsync(d_Ff, tab->d_Fface + tab->face_off[face], n * sizeof(double), cudaMemcpyDeviceToDevice,
                              static_cast<cudaStream_t>(stream)));
   return MSASM_OK;
 }

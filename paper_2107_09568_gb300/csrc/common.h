@@ -103,15 +103,17 @@ struct ScatterPlanHost {
 
 struct msasm_tables {
   msasm::TileTopology topo;
-  int q = 0;
-  int n_pi = 0;
+  int q = 0;                        // the largest of the per-direction projection degrees
+  int qd[3] = {0, 0, 0};            // projection degree per direction (q1, q2, q3)
+  int64_t face_off[7] = {0, 0, 0, 0, 0, 0, 0};   // face table f at d_Fface + face_off[f]
+  int n_pi = 0;                     // (q1+1)(q2+1)(q3+1)
   int n_nz = 0;
   int n_gauss = 0;
   int ref_point = 0;                // local point nearest the tile centre
   double* d_T = nullptr;            // n_nz x 9 n_pi, FP64
   double* d_F = nullptr;            // load table n_T x n_pi (eq. 55, body term), FP64
   double* d_vol = nullptr;          // volume table n_pi (eq. 18), FP64
-  double* d_Fface = nullptr;        // face load tables 6 x n_T x (q+1)^2 (eq. 55, F >= 1), FP64
+  double* d_Fface = nullptr;        // face load tables, face f: n_T x (q_a+1)(q_b+1) (eq. 55, F >= 1), FP64
   int32_t* d_pairs = nullptr;       // 2 n_nz (A, B)
   // operand copies for the reduced-precision contractions (created on first use)
   float* d_T32 = nullptr;           // FP32 copy

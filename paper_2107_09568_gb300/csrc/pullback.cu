@@ -1,5 +1,5 @@
 // K2: pullback of the elasticity tensor through each macro element and its
-// interpolation at the (q+1)^3 nodes (eq. 37, 42; appendix A).
+// interpolation at the (q1+1)(q2+1)(q3+1) nodes (eq. 37, 42; appendix A).
 //
 // One warp per tile.  The tile's (p1+1)(p2+1)(p3+1) control points are staged in
 // shared memory and the Jacobian J[p][i] = d M^(t)_p / d xi_i at all nodes is
@@ -23,16 +23,16 @@ struct PullbackArgs {
   MacroTileArgs geo;
   int64_t t0, n_tiles;      // tiles [t0, t0 + n_tiles) of this pass
   double lam, mu;
-  double* coef;             // (9 n_tiles) x (9 nq^3)
+  double* coef;             // (9 n_tiles) x (9 n_pi)
   unsigned long long* degenerate;
 };
 
 __global__ void pullback_kernel(PullbackArgs a) {
   extern __shared__ double smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
-  const int nq = a.geo.nq, n_pi = nq * nq * nq, K = 9 * n_pi;
+  const int n_pi = a.geo.nq[0] * a.geo.nq[1] * a.geo.nq[2], K = 9 * n_pi;
   int nP, nS, nU, nJ;
-  jac_scratch_sizes(a.geo.np, nq, nP, nS, nU, nJ);
+  jac_scratch_sizes(a.geo.np, a.geo.nq, nP, nS, nU, nJ);
   double* P = smem + size_t(warp) * (nP + nS + nU + nJ);
   double* S = P + nP;
   double* U = S + nS;
@@ -76,7 +76,7 @@ __global__ void pullback_kernel(PullbackArgs a) {
   }
 }
 
-size_t pullback_smem_per_warp(const int np[3], int nq) {
+size_t pullback_smem_per_warp(const int np[3], const int nq[3]) {
   int nP, nS, nU, nJ;
   jac_scratch_sizes(np, nq, nP, nS, nU, nJ);
   return size_t(nP + nS + nU + nJ) * sizeof(double);
@@ -92,7 +92,7 @@ MacroTileArgs macro_tile_args(const msasm_plan* plan, const double* d_ctrl) {
     g.n_ctrl_dir[d] = plan->n_ctrl_dir[d];
     g.np[d] = plan->degree[d] + 1;
   }
-  g.nq = plan->tab->q + 1;
+  for (int d = 0; d < 3; ++d) g.nq[d] = plan->tab->qd[d] + 1;
   return g;
 }
 

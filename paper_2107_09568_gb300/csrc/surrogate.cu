@@ -306,6 +306,7 @@ struct msasm_mlp {
 
 struct msasm_surrogate {
   int rank = 0, K = 0, n_nz = 0, n_train = 0;
+  int qd[3] = {0, 0, 0};           // the tables' projection degrees
   double w0 = 0.275, ws = 0.125;   // input normalisation of the width
   float scale = 1.0f;              // target scale
   float* d_U = nullptr;            // n_nz x rank (FP32), row-major
@@ -552,12 +553,14 @@ msasm_status msasm_surrogate_create(const msasm_tables* const* tables, const dou
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int n_nz = tables[0]->n_nz, K = 9 * tables[0]->n_pi;
   for (int k = 0; k < n_tables; ++k)
-    if (!tables[k] || tables[k]->n_nz != n_nz || tables[k]->n_pi != tables[0]->n_pi)
+    if (!tables[k] || tables[k]->n_nz != n_nz || tables[k]->qd[0] != tables[0]->qd[0] ||
+        tables[k]->qd[1] != tables[0]->qd[1] || tables[k]->qd[2] != tables[0]->qd[2])
       return fail(MSASM_EINVAL, "surrogate: all tables must share topology and q");
   const int over = 8, r_s = rank + over;                  // sketch width
   const int64_t J = int64_t(n_tables) * n_sample_rows;     // columns of M = [T_k C^T]
   msasm_surrogate* sur = new msasm_surrogate();
   sur->rank = rank;
+  for (int d = 0; d < 3; ++d) sur->qd[d] = tables[0]->qd[d];
   sur->K = K;
   sur->n_nz = n_nz;
   sur->n_train = n_tables;
@@ -818,7 +821,8 @@ msasm_status msasm_lowrank_contract(const float* d_U, int32_t n_nz, int32_t rank
 msasm_status msasm_surrogate_assemble(msasm_plan* plan, msasm_surrogate* sur, const double* d_ctrl, double E,
                                       double nu, const double* d_widths, float* d_values, void* stream) {
   if (!plan || !sur || !d_ctrl || !d_widths || !d_values) return fail(MSASM_EINVAL, "NULL argument");
-  if (plan->tab->n_nz != sur->n_nz || 9 * plan->tab->n_pi != sur->K)
+  if (plan->tab->n_nz != sur->n_nz || 9 * plan->tab->n_pi != sur->K || plan->tab->qd[0] != sur->qd[0] ||
+      plan->tab->qd[1] != sur->qd[1] || plan->tab->qd[2] != sur->qd[2])
     return fail(MSASM_EINVAL, "surrogate and plan disagree on the table shape");
   if (!(E > 0.0) || !(nu > -1.0 && nu < 0.5)) return fail(MSASM_EINVAL, "material: need E > 0 and -1 < nu < 0.5");
   cudaStream_t s = static_cast<cudaStream_t>(stream);

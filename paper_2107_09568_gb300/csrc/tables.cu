@@ -20,13 +20,22 @@
 namespace msasm {
 
 struct Table1DParams {
-  int n_patches, q, nf_max, n_gauss;
+  int n_patches, nf_max, n_gauss;
+  int nq[3];                 // interpolation nodes per direction (q_d + 1)
+  int nq_max;                // stride of the node index in the 1-D tables
   int degree[16][3];
   int n_elem[16][3];
   double lo[16][3], hi[16][3];
   double gx[16], gw[16];     // Gauss rule on [0,1]
-  double nodes[8];           // interpolation nodes on [0,1]
+  double nodes[3][8];        // interpolation nodes on [0,1], per direction
 };
+
+// node index of table column C, C = c1 + nq1 (c2 + nq2 c3)
+__device__ inline void node_index(int C, const int nq[3], int cc[3]) {
+  cc[0] = C % nq[0];
+  cc[1] = (C / nq[0]) % nq[1];
+  cc[2] = C / (nq[0] * nq[1]);
+}
 
 // Nonzero basis functions (values and d/ds) of the open uniform knot vector with n
 // elements and degree p on element e (span e + p); knot k = clamp((k - p)/n, 0, 1).
@@ -62,7 +71,7 @@ __device__ inline void uniform_span_basis(int p, int n, int e, double s, double*
 }
 
 __global__ void table_1d_kernel(Table1DParams prm, double* __restrict__ I1) {
-  const int nq = prm.q + 1, nf = prm.nf_max;
+  const int nq = prm.nq_max, nf = prm.nf_max;
   const int64_t total = int64_t(prm.n_patches) * 3 * 4 * nf * nf * nq;
   int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (idx >= total) return;
@@ -76,7 +85,7 @@ __global__ void table_1d_kernel(Table1DParams prm, double* __restrict__ I1) {
   int deg = prm.degree[p][d], ne = prm.n_elem[p][d];
   int nfun = ne + deg;
   double acc = 0.0;
-  if (a < nfun && b < nfun) {
+  if (a < nfun && b < nfun && c < prm.nq[d]) {
     double lo = prm.lo[p][d], h = prm.hi[p][d] - prm.lo[p][d];
     int da = flag >> 1, db = flag & 1;
     for (int e = 0; e < ne; ++e) {
@@ -89,8 +98,8 @@ __global__ void table_1d_kernel(Table1DParams prm, double* __restrict__ I1) {
         double fb = db ? dN[b - e] / h : N[b - e];
         double xi = lo + h * s;
         double lc = 1.0;
-        for (int k = 0; k < nq; ++k)
-          if (k != c) lc *= (xi - prm.nodes[k]) / (prm.nodes[c] - prm.nodes[k]);
+        for (int k = 0; k < prm.nq[d]; ++k)
+          if (k != c) lc *= (xi - prm.nodes[d][k]) / (prm.nodes[d][c] - prm.nodes[d][k]);
         acc += prm.gw[g] / ne * h * fa * fb * lc;    // dxi = h ds, element length 1/ne in s
       }
     }
@@ -99,15 +108,16 @@ __global__ void table_1d_kernel(Table1DParams prm, double* __restrict__ I1) {
 }
 
 __global__ void table_assemble_kernel(const PairDesc* __restrict__ desc, const double* __restrict__ I1,
-                                      int n_nz, int q, int nf, double* __restrict__ T) {
-  const int nq = q + 1, n_pi = nq * nq * nq, row = 9 * n_pi;
+                                      int n_nz, Table1DParams prm, double* __restrict__ T) {
+  const int nq = prm.nq_max, nf = prm.nf_max, n_pi = prm.nq[0] * prm.nq[1] * prm.nq[2], row = 9 * n_pi;
   const int64_t total = int64_t(n_nz) * row;
   for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < total;
        idx += int64_t(gridDim.x) * blockDim.x) {
     int m = int(idx / row);
     int k = int(idx % row);
     int C = k / 9, i = (k % 9) / 3, j = k % 3;
-    int cc[3] = {C % nq, (C / nq) % nq, C / (nq * nq)};
+    int cc[3];
+    node_index(C, prm.nq, cc);
     PairDesc pd = desc[m];
     double v = 0.0;
     for (int s = 0; s < kMaxPairPatches; ++s) {
@@ -128,14 +138,15 @@ __global__ void table_assemble_kernel(const PairDesc* __restrict__ desc, const d
 // The load table of eq. 54-55 (F = 0): F[A][C] = int R_A N_C over the tile.  The basis of a patch
 // sums to one in each direction, so the 1-D factor int f_a l_c is the sum over b of the value-value
 // table int f_a f_b l_c; the patches holding A are those of the diagonal pair (A, A).
-__global__ void load_table_kernel(const PairDesc* __restrict__ diag, const double* __restrict__ I1, int n_T, int q,
-                                  int nf, double* __restrict__ F) {
-  const int nq = q + 1, n_pi = nq * nq * nq;
+__global__ void load_table_kernel(const PairDesc* __restrict__ diag, const double* __restrict__ I1, int n_T,
+                                  Table1DParams prm, double* __restrict__ F) {
+  const int nq = prm.nq_max, nf = prm.nf_max, n_pi = prm.nq[0] * prm.nq[1] * prm.nq[2];
   const int64_t total = int64_t(n_T) * n_pi;
   for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < total;
        idx += int64_t(gridDim.x) * blockDim.x) {
     const int A = int(idx / n_pi), C = int(idx % n_pi);
-    const int cc[3] = {C % nq, (C / nq) % nq, C / (nq * nq)};
+    int cc[3];
+    node_index(C, prm.nq, cc);
     const PairDesc pd = diag[A];
     double v = 0.0;
     for (int s = 0; s < kMaxPairPatches; ++s) {
@@ -156,22 +167,31 @@ __global__ void load_table_kernel(const PairDesc* __restrict__ diag, const doubl
 
 // The face load tables of eq. 54-55 (F >= 1): for the cube face xi_d = s (face 2 d + s),
 // Ff[A][C2] = int over the tile boundary lying on that face of R_A N_C2, N_C2 = l_ca(xi_ia) l_cb(xi_ib)
-// the Lagrange basis of the face's (q+1)^2 nodes (ia < ib the in-face directions).  A patch whose
+// the Lagrange basis of the face's (q_ia+1)(q_ib+1) nodes (ia < ib the in-face directions), face f
+// at offset face_off[f] (n_T rows of its node count each).  A patch whose
 // box reaches the face contributes when A's index in the normal direction is the end one there
 // (open knots: that function is 1 on the face, the others 0); the in-face factors are the 1-D
 // integrals int f_a l_c of the load table (sums over b of the value-value table).
 __global__ void face_table_kernel(Table1DParams prm, const PairDesc* __restrict__ diag, const double* __restrict__ I1,
-                                  int n_T, int nf, double* __restrict__ Ff) {
-  const int nq = prm.q + 1, n2 = nq * nq;
-  const int64_t total = int64_t(6) * n_T * n2;
+                                  int n_T, double* __restrict__ Ff) {
+  const int nq = prm.nq_max, nf = prm.nf_max;
+  int64_t face_off[7];
+  face_off[0] = 0;
+  for (int f = 0; f < 6; ++f) {
+    const int d = f / 2, ia = d == 0 ? 1 : 0, ib = d == 2 ? 1 : 2;
+    face_off[f + 1] = face_off[f] + int64_t(n_T) * prm.nq[ia] * prm.nq[ib];
+  }
+  const int64_t total = face_off[6];
   for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < total;
        idx += int64_t(gridDim.x) * blockDim.x) {
-    const int face = int(idx / (int64_t(n_T) * n2));
-    const int rest = int(idx % (int64_t(n_T) * n2));
-    const int A = rest / n2, C2 = rest % n2;
+    int face = 0;
+    while (idx >= face_off[face + 1]) ++face;
     const int d = face / 2, sd = face % 2;
     const int ia = d == 0 ? 1 : 0, ib = d == 2 ? 1 : 2;
-    const int ca = C2 % nq, cb = C2 / nq;
+    const int n2 = prm.nq[ia] * prm.nq[ib];
+    const int rest = int(idx - face_off[face]);
+    const int A = rest / n2, C2 = rest % n2;
+    const int ca = C2 % prm.nq[ia], cb = C2 / prm.nq[ia];
     const PairDesc pd = diag[A];
     double v = 0.0;
     for (int sl = 0; sl < kMaxPairPatches; ++sl) {
@@ -202,10 +222,11 @@ __global__ void volume_table_kernel(const double* __restrict__ F, int n_T, int n
 
 msasm_status build_table_gpu(msasm_tables* tab, cudaStream_t stream) {
   const TileTopology& topo = tab->topo;
-  const int q = tab->q, nq = q + 1;
+  const int q = tab->q, nq = q + 1;             // q: the largest of the per-direction degrees
   Table1DParams prm{};
   prm.n_patches = int(topo.patches.size());
-  prm.q = q;
+  prm.nq_max = nq;
+  for (int d = 0; d < 3; ++d) prm.nq[d] = tab->qd[d] + 1;
   int p_T = 0, nf_max = 0;
   for (int p = 0; p < prm.n_patches; ++p)
     for (int d = 0; d < 3; ++d) {
@@ -225,9 +246,11 @@ msasm_status build_table_gpu(msasm_tables* tab, cudaStream_t stream) {
   gauss_legendre01(ng, gx, gw);
   for (int g = 0; g < ng; ++g) { prm.gx[g] = gx[g]; prm.gw[g] = gw[g]; }
   prm.n_gauss = ng;
-  std::vector<double> nx, nw;
-  gauss_legendre01(nq, nx, nw);
-  for (int c = 0; c < nq; ++c) prm.nodes[c] = nx[c];
+  for (int d = 0; d < 3; ++d) {
+    std::vector<double> nx, nw;
+    gauss_legendre01(prm.nq[d], nx, nw);
+    for (int c = 0; c < prm.nq[d]; ++c) prm.nodes[d][c] = nx[c];
+  }
 
   // pair descriptors: patches holding both functions of the pair, with local indices
   std::vector<std::vector<std::pair<int, int>>> where(topo.n_T);   // (patch, local function)
@@ -267,24 +290,24 @@ msasm_status build_table_gpu(msasm_tables* tab, cudaStream_t stream) {
   MSASM_CUDA(cudaMemcpyAsync(d_desc, desc.data(), desc.size() * sizeof(PairDesc), cudaMemcpyHostToDevice, stream));
   table_1d_kernel<<<unsigned((n1 + 127) / 128), 128, 0, stream>>>(prm, d_I1);
   MSASM_CUDA(cudaGetLastError());
-  table_assemble_kernel<<<152 * 8, 256, 0, stream>>>(d_desc, d_I1, tab->n_nz, q, nf_max, tab->d_T);
+  table_assemble_kernel<<<152 * 8, 256, 0, stream>>>(d_desc, d_I1, tab->n_nz, prm, tab->d_T);
   MSASM_CUDA(cudaGetLastError());
   // load and volume tables from the same 1-D integrals
   std::vector<PairDesc> diag(topo.n_T);
   for (int m = 0; m < tab->n_nz; ++m)
     if (topo.pair_A[m] == topo.pair_B[m]) diag[topo.pair_A[m]] = desc[m];
-  const int n_pi = nq * nq * nq;
+  const int n_pi = tab->n_pi;
   PairDesc* d_diag = nullptr;
   MSASM_CUDA(cudaMallocAsync(&d_diag, diag.size() * sizeof(PairDesc), stream));
   MSASM_CUDA(cudaMemcpyAsync(d_diag, diag.data(), diag.size() * sizeof(PairDesc), cudaMemcpyHostToDevice, stream));
   MSASM_CUDA(cudaMalloc(&tab->d_F, size_t(topo.n_T) * n_pi * sizeof(double)));
   MSASM_CUDA(cudaMalloc(&tab->d_vol, size_t(n_pi) * sizeof(double)));
-  load_table_kernel<<<152 * 2, 256, 0, stream>>>(d_diag, d_I1, topo.n_T, q, nf_max, tab->d_F);
+  load_table_kernel<<<152 * 2, 256, 0, stream>>>(d_diag, d_I1, topo.n_T, prm, tab->d_F);
   MSASM_CUDA(cudaGetLastError());
   volume_table_kernel<<<(n_pi + 127) / 128, 128, 0, stream>>>(tab->d_F, topo.n_T, n_pi, tab->d_vol);
   MSASM_CUDA(cudaGetLastError());
-  MSASM_CUDA(cudaMalloc(&tab->d_Fface, size_t(6) * topo.n_T * nq * nq * sizeof(double)));
-  face_table_kernel<<<152 * 2, 256, 0, stream>>>(prm, d_diag, d_I1, topo.n_T, nf_max, tab->d_Fface);
+  MSASM_CUDA(cudaMalloc(&tab->d_Fface, size_t(tab->face_off[6]) * sizeof(double)));
+  face_table_kernel<<<152 * 2, 256, 0, stream>>>(prm, d_diag, d_I1, topo.n_T, tab->d_Fface);
   MSASM_CUDA(cudaGetLastError());
   MSASM_CUDA(cudaFreeAsync(d_I1, stream));
   MSASM_CUDA(cudaFreeAsync(d_desc, stream));

@@ -37,9 +37,9 @@ struct VolumeArgs {
 __global__ void volume_load_kernel(VolumeArgs a) {
   extern __shared__ double smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
-  const int nq = a.geo.nq, n_pi = nq * nq * nq;
+  const int n_pi = a.geo.nq[0] * a.geo.nq[1] * a.geo.nq[2];
   int nP, nS, nU, nJ;
-  jac_scratch_sizes(a.geo.np, nq, nP, nS, nU, nJ);
+  jac_scratch_sizes(a.geo.np, a.geo.nq, nP, nS, nU, nJ);
   double* P = smem + size_t(warp) * (nP + nS + nU + nJ + n_pi);
   double* S = P + nP;
   double* U = S + nS;
@@ -71,15 +71,15 @@ __global__ void volume_load_kernel(VolumeArgs a) {
 }
 
 // Traction load through the face tables (eq. 53, F >= 1 terms; eq. 87-88): on the macro face
-// xi_d = s, per tile on it, the macro traction t |det I_M| at the face's (q+1)^2 nodes, where on
-// that face det I_M = (n x g_ia) . g_ib = |g_ia x g_ib| (g_k = dM/dxi_k, n the unit normal along
-// g^d), then f_A = t sum_C2 Ff[A][C2] |g_ia x g_ib|(node C2).  The node Jacobians come from the
-// pullback's sum factorisation with the normal direction tabulated at xi_d = s for every node
-// index (only the slice c_d = 0 is used).  One warp per tile on the face.
+// xi_d = s, per tile on it, the macro traction t |det I_M| at the face's (q_ia+1)(q_ib+1) nodes,
+// where on that face det I_M = (n x g_ia) . g_ib = |g_ia x g_ib| (g_k = dM/dxi_k, n the unit normal
+// along g^d), then f_A = t sum_C2 Ff[A][C2] |g_ia x g_ib|(node C2).  The node Jacobians come from
+// the pullback's sum factorisation with a single point, xi_d = s, in the normal direction.  One
+// warp per tile on the face.
 struct TractionArgs {
   MacroTileArgs geo;
   int d, ia, ib, s;
-  const double* Ff;        // face table of this face (n_T x nq^2)
+  const double* Ff;        // face table of this face (n_T x nq[ia] nq[ib])
   int n_T;
   const int32_t* gmap;
   double t0, t1, t2;
@@ -89,9 +89,9 @@ struct TractionArgs {
 __global__ void traction_load_kernel(TractionArgs a) {
   extern __shared__ double smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
-  const int nq = a.geo.nq, n2 = nq * nq;
+  const int n2 = a.geo.nq[a.ia] * a.geo.nq[a.ib];
   int nP, nS, nU, nJ;
-  jac_scratch_sizes(a.geo.np, nq, nP, nS, nU, nJ);
+  jac_scratch_sizes(a.geo.np, a.geo.nq, nP, nS, nU, nJ);
   double* P = smem + size_t(warp) * (nP + nS + nU + nJ + n2);
   double* S = P + nP;
   double* U = S + nS;
@@ -109,9 +109,9 @@ __global__ void traction_load_kernel(TractionArgs a) {
     for (int C2 = lane; C2 < n2; C2 += 32) {
       int c[3];
       c[a.d] = 0;
-      c[a.ia] = C2 % nq;
-      c[a.ib] = C2 / nq;
-      const double* J = Jn + 9 * (c[0] + nq * (c[1] + nq * c[2]));   // J[p * 3 + i] = dM_p / dxi_i
+      c[a.ia] = C2 % a.geo.nq[a.ia];
+      c[a.ib] = C2 / a.geo.nq[a.ia];
+      const double* J = Jn + 9 * (c[0] + a.geo.nq[0] * (c[1] + a.geo.nq[1] * c[2]));   // J[p * 3 + i] = dM_p / dxi_i
       const double ga[3] = {J[a.ia], J[3 + a.ia], J[6 + a.ia]};
       const double gb[3] = {J[a.ib], J[3 + a.ib], J[6 + a.ib]};
       const double x = ga[1] * gb[2] - ga[2] * gb[1], y = ga[2] * gb[0] - ga[0] * gb[2],
@@ -138,7 +138,7 @@ void bspline_span_basis(const double* t, int p, int span, double u, double* vals
 
 msasm_status traction_load_gpu(const msasm_plan* plan, const double* d_ctrl, int face, const double tr[3], double* d_f,
                                cudaStream_t st) {
-  const int d = face / 2, sd = face % 2, nq = plan->tab->q + 1;
+  const int d = face / 2, sd = face % 2;
   TractionArgs a;
   a.geo = macro_tile_args(plan, d_ctrl);
   a.d = d;
@@ -146,13 +146,13 @@ msasm_status traction_load_gpu(const msasm_plan* plan, const double* d_ctrl, int
   a.ib = d == 2 ? 1 : 2;
   a.s = sd;
   a.n_T = plan->tab->topo.n_T;
-  a.Ff = plan->tab->d_Fface + size_t(face) * a.n_T * nq * nq;
+  a.Ff = plan->tab->d_Fface + plan->tab->face_off[face];
   a.gmap = plan->d_gmap;
   a.t0 = tr[0];
   a.t1 = tr[1];
   a.t2 = tr[2];
   a.f = d_f;
-  // the normal direction's macro basis at xi_d = s, repeated for every node index
+  // the normal direction's macro basis at its single point xi_d = s
   const std::vector<double>& t = plan->knots_host[d];
   const int p = plan->degree[d];
   std::vector<double> nb;
@@ -160,20 +160,20 @@ msasm_status traction_load_gpu(const msasm_plan* plan, const double* d_ctrl, int
     const double u0 = t[size_t(k)], h = t[size_t(k) + 1] - t[size_t(k)];
     double vals[8], ders[8];
     bspline_span_basis(t.data(), p, k, u0 + h * sd, vals, ders);
-    for (int c = 0; c < nq; ++c)
-      for (int j = 0; j <= p; ++j) {
-        nb.push_back(vals[j]);
-        nb.push_back(ders[j] * h);
-      }
+    for (int j = 0; j <= p; ++j) {
+      nb.push_back(vals[j]);
+      nb.push_back(ders[j] * h);
+    }
   }
   double* d_nb = nullptr;
   MSASM_CUDA(cudaMallocAsync(&d_nb, nb.size() * sizeof(double), st));
   MSASM_CUDA(cudaMemcpyAsync(d_nb, nb.data(), nb.size() * sizeof(double), cudaMemcpyHostToDevice, st));
   a.geo.basis[d] = d_nb;
+  a.geo.nq[d] = 1;
   int nP, nS, nU, nJ;
-  jac_scratch_sizes(a.geo.np, nq, nP, nS, nU, nJ);
+  jac_scratch_sizes(a.geo.np, a.geo.nq, nP, nS, nU, nJ);
   const int warps = 4;
-  const size_t smem = warps * size_t(nP + nS + nU + nJ + nq * nq) * sizeof(double);
+  const size_t smem = warps * size_t(nP + nS + nU + nJ + a.geo.nq[a.ia] * a.geo.nq[a.ib]) * sizeof(double);
   msasm_status status = MSASM_OK;
   if (smem > 200 * 1024) status = fail(MSASM_EUNSUPPORTED, "macro degree / q too large for the traction kernel");
   cudaError_t e = cudaSuccess;
@@ -208,7 +208,7 @@ __global__ void ordered_sum_kernel(const double* __restrict__ x, int64_t n, doub
 static size_t volume_smem_per_warp(const MacroTileArgs& g) {
   int nP, nS, nU, nJ;
   jac_scratch_sizes(g.np, g.nq, nP, nS, nU, nJ);
-  return size_t(nP + nS + nU + nJ + g.nq * g.nq * g.nq) * sizeof(double);
+  return size_t(nP + nS + nU + nJ + g.nq[0] * g.nq[1] * g.nq[2]) * sizeof(double);
 }
 
 msasm_status volume_load_gpu(const msasm_plan* plan, const double* d_ctrl, double* d_tile_vol, double* d_total,
