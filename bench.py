@@ -60,6 +60,38 @@ def parse():
     return ap.parse_args()
 
 
+def parse_cpulist(text):
+    """'0-3,8,10-11' -> {0, 1, 2, 3, 8, 10, 11}."""
+    cpus = set()
+    for part in text.strip().split(","):
+        if not part:
+            continue
+        a, _, b = part.partition("-")
+        cpus.update(range(int(a), int(b or a) + 1))
+    return cpus
+
+
+def bind_to_gpu_local_cpus(gpu):
+    """Restrict this process to the host CPUs local to GPU `gpu` (its PCI device's local_cpulist),
+    so that pinned host buffers allocated afterwards sit in the host memory next to that GPU (a
+    far NUMA node cuts the device-to-host rate).  Returns a description of what was done."""
+    try:
+        bus = subprocess.run(["nvidia-smi", f"--id={gpu}", "--query-gpu=pci.bus_id", "--format=csv,noheader"],
+                             capture_output=True, text=True, timeout=30).stdout.strip()
+        dom, rest = bus.split(":", 1)
+        dev = f"{int(dom, 16):04x}:{rest.lower()}"
+        with open(f"/sys/bus/pci/devices/{dev}/local_cpulist") as f:
+            local = parse_cpulist(f.read())
+        avail = os.sched_getaffinity(0)
+        use = local & avail
+        if not use or use == avail:
+            return {"pci": dev, "cpus": len(avail), "bound": False}
+        os.sched_setaffinity(0, use)
+        return {"pci": dev, "cpus": len(use), "of": len(avail), "bound": True}
+    except Exception as e:                       # no nvidia-smi, no sysfs entry: leave it as it is
+        return {"bound": False, "why": type(e).__name__}
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -314,6 +346,7 @@ def main():
     import paper_2107_09568_gb300 as msasm
     import synth
 
+    affinity = bind_to_gpu_local_cpus(local)      # before any pinned host buffer exists
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -388,7 +421,7 @@ def main():
         e2e = {"value": whole_job_rate(plan.n_tiles, world, 1, em), "unit": "tiles/s", "ms_per_step": em,
                "h2d_bytes_per_step": int(h_ctrl.numel() * 8) * world,
                "d2h_bytes_per_step": int(plan.nnz * vbytes) * world,
-               "api": "msasm_assemble_host (pinned host buffers)"}
+               "api": "msasm_assemble_host (pinned host buffers)", "host_cpus": affinity}
         del h_vals
 
     if rank != 0:

@@ -84,3 +84,11 @@ def test_clock_samples_are_those_of_the_timed_region(tmp_path):
     assert r["samples"] == 2 and r["samples_total"] == 4 and r["window"] == "timed region"
     assert r["sm_mhz"] == pytest.approx((2070 + 2055) / 2)
     assert r["reasons"] == ["sw_power_cap"]
+
+
+def test_cpulist_parsing_and_binding_fallback():
+    assert bench.parse_cpulist("0-3,8,10-11\n") == {0, 1, 2, 3, 8, 10, 11}
+    assert bench.parse_cpulist("") == set()
+    before = os.sched_getaffinity(0)
+    r = bench.bind_to_gpu_local_cpus(0)           # no GPU here: nothing is changed
+    assert r["bound"] is False and os.sched_getaffinity(0) == before
