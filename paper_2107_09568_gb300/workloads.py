@@ -214,6 +214,18 @@ def projection(flush, workload="beam1000"):
     k_int = plan.assemble(ctrl, 1.0, 0.3, "f64_emu")
     k_l2 = plan.assemble_l2(ctrl, w.q + 3, precision="f64_emu")
     out["rel_fro_K_l2_vs_K_interpolated"] = rel(k_l2, k_int)
+    del k_l2
+    # a degree per direction (Sec. 3.3.4) against one degree, for a tighter tolerance
+    q3, e3 = msasm.select_projection_degrees(plan, ctrl, 1e-5, (w.q, w.q, w.q))
+    out["degrees_per_direction_tol_1e-5"] = list(q3)
+    out["E_proj_per_direction"] = e3
+    out["degree_isotropic_tol_1e-5"] = msasm.select_projection_degree(plan, ctrl, 1e-5, 0, 7)
+    tab3 = msasm.Tables(synth.micro_cross(w.n_e, w.width), q3)
+    plan3 = msasm.Plan(tab3, w.macro)
+    form = "f64_emu" if 9 * tab3.n_pi <= 576 else "f64"
+    _, ms3 = _timed(lambda: plan3.assemble(ctrl, 1.0, 0.3, form), reps=3, flush=flush)
+    out["assembly_per_direction"] = {"n_pi": tab3.n_pi, "form": form, "ms": ms3,
+                                     "tiles_per_s": plan3.n_tiles / ms3 * 1e3}
     return out
 
 
