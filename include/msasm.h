@@ -216,6 +216,12 @@ msasm_status msasm_mlp_set_params(msasm_mlp* mlp, const float* d_params, void* s
 msasm_status msasm_mlp_get_params(const msasm_mlp* mlp, float* d_master, void* d_half, void* stream);
 /* y = MLP(x) for B scalar inputs: d_y (B x n_out) FP32. */
 msasm_status msasm_mlp_forward(msasm_mlp* mlp, const float* d_x, int32_t B, float* d_y, void* stream);
+
+/* The same forward pass with the output layer on the tensor cores (split FP16: the last hidden
+ * layer as hi + 2^-11 lo per row-scaled slice, three products, FP32 accumulation; the FP16 output
+ * weights are exact in the slices, made once per set of weights): about 1e-7 relative to
+ * msasm_mlp_forward.  The surrogate's predictions and assembly use this form. */
+msasm_status msasm_mlp_forward_tc(msasm_mlp* mlp, const float* d_x, int32_t B, float* d_y, void* stream);
 /* Loss L = mean over B x n_out of (y - t)^2 and dL/dparams (w.r.t. the FP16 weights, FP32 result,
  * n_params values into d_grad if non-NULL).  Synchronises `stream`. */
 msasm_status msasm_mlp_loss_grad(msasm_mlp* mlp, const float* d_x, const float* d_t, int32_t B, float* h_loss,

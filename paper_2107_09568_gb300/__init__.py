@@ -504,10 +504,12 @@ class MLP:
     def set_params(self, p):
         check(load().msasm_mlp_set_params(self.handle, _ptr(p.contiguous()), _stream()))
 
-    def forward(self, x):
+    def forward(self, x, tensor_cores=False):
+        """(B, n_out) FP32 outputs; tensor_cores: the output layer as a split-FP16 tensor-core product."""
         import torch
         y = torch.empty((x.numel(), self.n_out), dtype=torch.float32, device="cuda")
-        check(load().msasm_mlp_forward(self.handle, _ptr(x), x.numel(), _ptr(y), _stream()))
+        fn = load().msasm_mlp_forward_tc if tensor_cores else load().msasm_mlp_forward
+        check(fn(self.handle, _ptr(x), x.numel(), _ptr(y), _stream()))
         return y
 
     def loss_grad(self, x, t):

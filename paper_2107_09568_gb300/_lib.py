@@ -77,6 +77,7 @@ _SIGS = {
     "msasm_mlp_set_params": (c_i32, [c_vp, c_vp, c_vp]),
     "msasm_mlp_get_params": (c_i32, [c_vp, c_vp, c_vp, c_vp]),
     "msasm_mlp_forward": (c_i32, [c_vp, c_vp, c_i32, c_vp, c_vp]),
+    "msasm_mlp_forward_tc": (c_i32, [c_vp, c_vp, c_i32, c_vp, c_vp]),
     "msasm_mlp_loss_grad": (c_i32, [c_vp, c_vp, c_vp, c_i32, P(C.c_float), c_vp, c_vp]),
     "msasm_mlp_train": (c_i32, [c_vp, c_vp, c_vp, c_i32, c_i32, C.c_float, c_vp, c_vp]),
     "msasm_mlp_destroy": (None, [c_vp]),

@@ -271,6 +271,13 @@ struct msasm_mlp {
   float* d_w = nullptr;      // FP32 master
   __half* d_w16 = nullptr;   // FP16 compute copy
   float* d_w3f = nullptr;    // the output layer's FP16 weights widened to FP32 (exact) for the GEMM
+  // tensor-core output layer (inference): split-FP16 slices of W3 (exact: W3 is FP16) made once per
+  // set of weights, and of the batch's last hidden layer
+  void *d_w3hi = nullptr, *d_w3lo = nullptr, *d_ahi = nullptr, *d_alo = nullptr;
+  float *d_w3scale = nullptr, *d_ascale = nullptr;
+  unsigned* d_tc_err = nullptr;
+  bool w3_split_ok = false;
+  int act_cap = 0;
   float* d_g = nullptr;
   float* d_m = nullptr;
   float* d_v = nullptr;
@@ -290,6 +297,13 @@ struct msasm_mlp {
     cudaFree(d_w);
     cudaFree(d_w16);
     cudaFree(d_w3f);
+    cudaFree(d_w3hi);
+    cudaFree(d_w3lo);
+    cudaFree(d_w3scale);
+    cudaFree(d_ahi);
+    cudaFree(d_alo);
+    cudaFree(d_ascale);
+    cudaFree(d_tc_err);
     cudaFree(d_g);
     cudaFree(d_m);
     cudaFree(d_v);
@@ -375,6 +389,54 @@ static msasm_status mlp_forward(msasm_mlp* n, const float* d_x, int B, float* d_
   return MSASM_OK;
 }
 
+// The same forward pass with the output layer y = h2 W3^T + b3 on the tensor cores: split FP16
+// (h2 = hi + 2^-11 lo per row-scaled slice, three products, FP32 accumulation; W3 is FP16, so its
+// slices are exact), about 1e-7 relative to the CUDA-core product.
+static msasm_status mlp_forward_tc(msasm_mlp* n, const float* d_x, int B, float* d_y, cudaStream_t s) {
+  const MlpLayout& L = n->lay;
+  constexpr int kind = kLowRankSplit;
+  mlp_hidden_kernel<<<std::min(B, 1024), 128, L.H * sizeof(float), s>>>(n->d_w16, d_x, B, L.H, L.W1, L.b1, L.W2, L.b2,
+                                                                        n->d_h1, n->d_h2);
+  MSASM_CUDA(cudaGetLastError());
+  if (!n->w3_split_ok) {
+    const int64_t nw3 = int64_t(L.n_out) * L.H;
+    widen_half_kernel<<<unsigned(std::min<int64_t>((nw3 + 255) / 256, 152 * 8)), 256, 0, s>>>(n->d_w16 + L.W3, nw3,
+                                                                                               n->d_w3f);
+    MSASM_CUDA(cudaGetLastError());
+    if (!n->d_w3hi) {
+      const size_t wb = tc_slice_bytes(L.n_out, L.H, kind);
+      MSASM_CUDA(cudaMalloc(&n->d_w3hi, wb));
+      MSASM_CUDA(cudaMalloc(&n->d_w3lo, wb));
+      MSASM_CUDA(cudaMalloc(&n->d_w3scale, size_t(L.n_out) * 4));
+      MSASM_CUDA(cudaMalloc(&n->d_tc_err, sizeof(unsigned)));
+      MSASM_CUDA(cudaMemsetAsync(n->d_tc_err, 0, sizeof(unsigned), s));
+    }
+    MSASM_TRY(tc_split_f32_gpu(n->d_w3f, L.n_out, L.H, kind, n->d_w3hi, n->d_w3lo, n->d_w3scale, s));
+    n->w3_split_ok = true;
+  }
+  if (n->act_cap < B) {
+    cudaFree(n->d_ahi);
+    cudaFree(n->d_alo);
+    cudaFree(n->d_ascale);
+    n->d_ahi = n->d_alo = nullptr;
+    n->d_ascale = nullptr;
+    n->act_cap = 0;
+    const size_t ab = tc_slice_bytes(B, L.H, kind);
+    MSASM_CUDA(cudaMalloc(&n->d_ahi, ab));
+    MSASM_CUDA(cudaMalloc(&n->d_alo, ab));
+    MSASM_CUDA(cudaMalloc(&n->d_ascale, size_t(B) * 4));
+    n->act_cap = B;
+  }
+  MSASM_TRY(tc_split_f32_gpu(n->d_h2, B, L.H, kind, n->d_ahi, n->d_alo, n->d_ascale, s));
+  MSASM_TRY(contract_tc_gpu(kind, n->d_w3hi, n->d_w3lo, n->d_w3scale, L.n_out, n->d_ahi, n->d_alo, n->d_ascale, B,
+                            L.H, d_y, L.n_out, n->d_tc_err, s));
+  const int64_t ny = int64_t(B) * L.n_out;
+  add_bias_kernel<<<unsigned(std::min<int64_t>((ny + 255) / 256, 152 * 8)), 256, 0, s>>>(d_y, ny, L.n_out,
+                                                                                         n->d_w16 + L.b3);
+  MSASM_CUDA(cudaGetLastError());
+  return MSASM_OK;
+}
+
 // loss (into n->d_loss, accumulated) and the full gradient (into n->d_g) for targets d_t
 static msasm_status mlp_loss_grad(msasm_mlp* n, const float* d_x, const float* d_t, int B, cudaStream_t s) {
   const MlpLayout& L = n->lay;
@@ -393,6 +455,7 @@ static msasm_status mlp_loss_grad(msasm_mlp* n, const float* d_x, const float* d
 }
 
 static msasm_status mlp_train_step(msasm_mlp* n, const float* d_x, const float* d_t, int B, float lr, cudaStream_t s) {
+  n->w3_split_ok = false;                        // the weights change
   MSASM_TRY(mlp_loss_grad(n, d_x, d_t, B, s));
   adam_kernel<<<152 * 4, 256, 0, s>>>(n->d_w, n->d_g, n->d_m, n->d_v, n->d_w16, n->lay.total, lr, n->d_step);
   MSASM_CUDA(cudaGetLastError());
@@ -459,6 +522,7 @@ msasm_status msasm_mlp_info(const msasm_mlp* n, int64_t* n_params, int32_t* n_ou
 msasm_status msasm_mlp_set_params(msasm_mlp* n, const float* d_params, void* stream) {
   if (!n || !d_params) return fail(MSASM_EINVAL, "NULL argument");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  n->w3_split_ok = false;
   MSASM_CUDA(cudaMemcpyAsync(n->d_w, d_params, n->lay.total * 4, cudaMemcpyDeviceToDevice, s));
   to_half_kernel<<<152 * 4, 256, 0, s>>>(n->d_w, n->lay.total, n->d_w16);
   MSASM_CUDA(cudaGetLastError());
@@ -478,6 +542,12 @@ msasm_status msasm_mlp_forward(msasm_mlp* n, const float* d_x, int32_t B, float*
   if (!n || !d_x || !d_y || B <= 0) return fail(MSASM_EINVAL, "bad MLP forward arguments");
   MSASM_TRY(mlp_ensure_batch(n, B));
   return mlp_forward(n, d_x, B, d_y, static_cast<cudaStream_t>(stream));
+}
+
+msasm_status msasm_mlp_forward_tc(msasm_mlp* n, const float* d_x, int32_t B, float* d_y, void* stream) {
+  if (!n || !d_x || !d_y || B <= 0) return fail(MSASM_EINVAL, "bad MLP forward arguments");
+  MSASM_TRY(mlp_ensure_batch(n, B));
+  return mlp_forward_tc(n, d_x, B, d_y, static_cast<cudaStream_t>(stream));
 }
 
 // mean squared error over B samples and its gradient w.r.t. the (FP16) parameters; synchronises
@@ -502,6 +572,7 @@ msasm_status msasm_mlp_train(msasm_mlp* n, const float* d_x, const float* d_t, i
                              float* h_loss, void* stream) {
   if (!n || !d_x || !d_t || B <= 0 || steps < 0) return fail(MSASM_EINVAL, "bad MLP training arguments");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (steps > 0) n->w3_split_ok = false;         // the weights change
   MSASM_TRY(mlp_ensure_batch(n, B));
   float* d_hist = nullptr;
   if (h_loss && steps > 0) MSASM_CUDA(cudaMallocAsync(&d_hist, size_t(steps) * 4, s));
@@ -740,7 +811,7 @@ msasm_status msasm_surrogate_predict(msasm_surrogate* sur, const double* d_width
   MSASM_CUDA(cudaMallocAsync(&x, size_t(n) * 4, s));
   normalise_inputs_kernel<<<152, 256, 0, s>>>(d_widths, n, sur->w0, sur->ws, x);
   MSASM_TRY(mlp_ensure_batch(sur->mlp, int(n)));
-  msasm_status st = mlp_forward(sur->mlp, x, int(n), d_Vt, s);
+  msasm_status st = mlp_forward_tc(sur->mlp, x, int(n), d_Vt, s);
   if (st == MSASM_OK) {
     denormalise_kernel<<<152 * 4, 256, 0, s>>>(d_Vt, n, sur->mlp->lay.n_out, sur->d_mean, sur->scale);
     if (cudaGetLastError() != cudaSuccess) st = fail(MSASM_ECUDA, "denormalise");

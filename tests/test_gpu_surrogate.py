@@ -34,10 +34,16 @@ def test_mlp_loss_and_gradient_match_oracle():
     err = np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref)
     print("mlp grad rel err", err)
     assert err <= 1e-4
-    # forward
-    y = net.forward(torch.tensor(x, device="cuda")).cpu().numpy()
+    # forward, the output layer on the CUDA cores and on the tensor cores (split FP16), against FP64
     y_ref, _ = omlp.forward(p16, H, n_out, x.astype(np.float64))
-    assert np.linalg.norm(y - y_ref) <= 1e-5 * np.linalg.norm(y_ref)
+    for tc in (False, True):
+        y = net.forward(torch.tensor(x, device="cuda"), tensor_cores=tc).cpu().numpy()
+        assert np.linalg.norm(y - y_ref) <= 1e-5 * np.linalg.norm(y_ref), tc
+    # new weights replace the cached tensor-core slices of the output layer
+    net.set_params(torch.tensor(0.5 * p, device="cuda"))
+    y_ref2, _ = omlp.forward((0.5 * p).astype(np.float16).astype(np.float64), H, n_out, x.astype(np.float64))
+    y2 = net.forward(torch.tensor(x, device="cuda"), tensor_cores=True).cpu().numpy()
+    assert np.linalg.norm(y2 - y_ref2) <= 1e-5 * np.linalg.norm(y_ref2)
 
 
 def test_mlp_training_fits_a_smooth_family():
