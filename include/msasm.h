@@ -8,7 +8,8 @@
  *   (step 2)  build the stiffness lookup table mat[K] of the reference tile
  *             (Sec. 3.2.3, eq. 51-52, 56-57)                -> msasm_build_tables
  *   (step 1)  pull back the elasticity tensor through each macro element and
- *             interpolate it at (q+1)^3 nodes (eq. 37, 42, 79-97)
+ *             interpolate it at the (q+1)^3 nodes, or (q1+1)(q2+1)(q3+1) with a degree per
+ *             direction (eq. 37, 42, 79-97)
  *   (step 3)  contract the table with the coefficients, one GEMM (eq. 58)
  *   (step 4)  add the tile blocks into a global CSR matrix (Sec. 3.2.4)
  *                                                           -> msasm_assemble
@@ -384,7 +385,7 @@ msasm_status msasm_body_load(const msasm_plan* plan, const double* d_ctrl, doubl
 /* Load vector of a uniform traction t = (tx, ty, tz) (force per unit physical area) on macro face
  * `face` = 2 d + s (the tiles' boundary parts on xi_d = s), through the face tables (the F >= 1
  * terms of eq. 53-55): per tile on the face, t |det I_M| (eq. 87-88, the macro surface element
- * |dM/dxi_a x dM/dxi_b| on that face) interpolated at the face's (q+1)^2 Gauss-Legendre nodes,
+ * |dM/dxi_a x dM/dxi_b| on that face) interpolated at the face's (q_a+1)(q_b+1) Gauss-Legendre nodes,
  * times the table: f_{3g+c} = t_c sum_C2 Ff[A][C2] |det I_M|(node C2).  Equals the direct
  * quadrature (msasm_traction_load) to roundoff when the surface element is a polynomial of degree
  * <= q per direction (an affine map), and converges with q otherwise.  d_f (n_rows FP64) is

@@ -253,7 +253,7 @@ def _plan_traction_load_lookup(self, ctrl, face, traction, stream=None):
 
 
 def _tables_face_table(self, face, stream=None):
-    """The face load table of `face` (n_T, (q+1)^2) FP64 on the GPU."""
+    """The face load table of `face` (n_T, (q_a+1)(q_b+1), a < b its in-face directions) FP64 on the GPU."""
     import torch
     ia, ib = [k for k in range(3) if k != face // 2]
     out = torch.empty((self.n_T, (self.qd[ia] + 1) * (self.qd[ib] + 1)), dtype=torch.float64, device="cuda")
