@@ -127,7 +127,11 @@ def adjoint(flush, nx=20, ny=20, nz=5, n_check=20, h=1e-4):
     ctrl = torch.tensor(m.ctrl, device="cuda")
     fixed_pts = plan.face_points(0)
     fixed = torch.tensor(np.concatenate([3 * fixed_pts + a for a in range(3)]), device="cuda", dtype=torch.long)
-    f = torch.tensor(plan.traction_load(1, (0.0, 0.0, -1.0), m.ctrl), device="cuda")
+    # the load through the face lookup tables on the GPU (eq. 53-55, 87-88), checked against the
+    # direct quadrature of the traction on the strut end faces (the map is affine: equal to roundoff)
+    f = plan.traction_load_lookup(ctrl, 1, (0.0, 0.0, -1.0))
+    f_direct = torch.tensor(plan.traction_load(1, (0.0, 0.0, -1.0), m.ctrl), device="cuda")
+    load_check = ((f - f_direct).abs().max() / f_direct.abs().max()).item()
     vals, ms_asm = _timed(lambda: plan.assemble(ctrl, 1.0, 0.3, "f64_emu"), reps=3, flush=flush)
     K = msasm.csr_matrix(plan, vals)
     torch.cuda.synchronize()
@@ -153,6 +157,7 @@ def adjoint(flush, nx=20, ny=20, nz=5, n_check=20, h=1e-4):
     fdq = np.array(fdq)
     gq = np.array([g64[k, p].item() for k, p in coords])
     out = {"tiles": plan.n_tiles, "nnz": plan.nnz, "dofs": plan.n_rows, "assemble_ms_f64_emu": ms_asm,
+           "load": "face lookup tables", "load_rel_max_vs_direct_quadrature": load_check,
            "cg_iterations": iters, "cg_rel_residual": res, "cg_s": t_cg, "compliance": C0,
            "grad_ms_f64": ms_g64, "grad_ms_f64_emu": ms_gemu, "grad_ms_f32": ms_g32,
            "grad_rel_f32_vs_f64": (torch.linalg.vector_norm(g32 - g64) / torch.linalg.vector_norm(g64)).item(),
