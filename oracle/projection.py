@@ -85,7 +85,9 @@ def select_degrees(macro, tol: float, q_init, q_max: int = 7, **kw):
     """A degree per direction (the anisotropic projection space of Sec. 3.3.4): from q_init (the
     macro map's degrees), enrich while E_proj > tol, each step raising the one direction whose
     increase lowers E_proj most; then coarsen while possible, each step lowering the direction whose
-    decrease keeps E_proj lowest, as long as it stays <= tol.  Ties go to the lowest direction.
+    decrease keeps E_proj lowest, as long as it stays <= tol.  Errors within a relative 1e-9 of each
+    other are ties (rounding differences between implementations must not decide); ties go to the
+    lowest direction.
     Returns (degrees, E_proj)."""
     q = list(quadrature.degrees(q_init))
     err = projection_error(macro, tuple(q), **kw)[1]
@@ -97,7 +99,7 @@ def select_degrees(macro, tol: float, q_init, q_max: int = 7, **kw):
             c = q.copy()
             c[d] += 1
             e = projection_error(macro, tuple(c), **kw)[1]
-            if best is None or e < best[0]:
+            if best is None or e < best[0] * (1.0 - 1e-9):   # within 1e-9: a tie, the lower direction
                 best = (e, c)
         if best is None:
             break
@@ -110,7 +112,7 @@ def select_degrees(macro, tol: float, q_init, q_max: int = 7, **kw):
             c = q.copy()
             c[d] -= 1
             e = projection_error(macro, tuple(c), **kw)[1]
-            if e <= tol and (best is None or e < best[0]):
+            if e <= tol and (best is None or e < best[0] * (1.0 - 1e-9)):
                 best = (e, c)
         if best is None:
             break

@@ -318,7 +318,8 @@ def select_projection_degrees(plan, ctrl, tol, q_init, q_max=7, **kw):
     """A degree per direction (the anisotropic space of Sec. 3.3.4; the projection errors on the
     GPU): from q_init (the macro map's degrees), raise while E_proj > tol the one direction whose
     increase lowers E_proj most, then lower while E_proj stays <= tol the direction whose decrease
-    keeps it lowest (ties to the lowest direction).  Returns (degrees, E_proj)."""
+    keeps it lowest (errors within a relative 1e-9 are ties, which go to the lowest direction).  Returns
+    (degrees, E_proj)."""
     err_of = lambda q: plan.projection_error(ctrl, tuple(q), **kw)[1].item()
     q = [int(v) for v in q_init]
     err = err_of(q)
@@ -330,7 +331,7 @@ def select_projection_degrees(plan, ctrl, tol, q_init, q_max=7, **kw):
             c = q.copy()
             c[d] += 1
             e = err_of(c)
-            if best is None or e < best[0]:
+            if best is None or e < best[0] * (1.0 - 1e-9):   # within 1e-9: a tie, the lower direction
                 best = (e, c)
         if best is None:
             break
@@ -343,7 +344,7 @@ def select_projection_degrees(plan, ctrl, tol, q_init, q_max=7, **kw):
             c = q.copy()
             c[d] -= 1
             e = err_of(c)
-            if e <= tol and (best is None or e < best[0]):
+            if e <= tol and (best is None or e < best[0] * (1.0 - 1e-9)):
                 best = (e, c)
         if best is None:
             break
