@@ -44,3 +44,23 @@ def test_host_side_validation_needs_no_gpu():
     assert lib.msasm_plan_create(None, None, 0, None, C.byref(out), None, None) == _lib.EINVAL
     assert lib.msasm_assemble(None, None, 1.0, 0.3, 0, None, 0, None) == _lib.EINVAL
     assert lib.msasm_tables_info(None, None, None, None) == _lib.EINVAL
+
+
+def test_host_side_validation_of_the_later_entry_points():
+    """Argument checks of the per-direction, L2-projection, face-table and tensor-core MLP calls
+    return EINVAL before any CUDA call."""
+    lib = msasm.load()
+    out = C.c_void_p()
+    bad_q = (C.c_int32 * 3)(1, 9, 1)
+    assert lib.msasm_build_tables_q3(None, bad_q, 0, None, C.byref(out)) == _lib.EINVAL
+    assert b"degrees" in lib.msasm_last_error()
+    assert lib.msasm_build_tables_q3(None, None, 0, None, C.byref(out)) == _lib.EINVAL
+    assert lib.msasm_tables_degrees(None, (C.c_int32 * 3)()) == _lib.EINVAL
+    e = C.c_double()
+    assert lib.msasm_projection_error_q3(None, None, (C.c_int32 * 3)(1, 2, 3), 5, 1.0, 0.3,
+                                         None, C.byref(e), None) == _lib.EINVAL
+    assert lib.msasm_projection_error_l2(None, None, 2, 5, 5, 1.0, 0.3, None, C.byref(e), None) == _lib.EINVAL
+    assert lib.msasm_pullback_l2(None, None, 1.0, 0.3, 5, None, None) == _lib.EINVAL
+    assert lib.msasm_traction_load_lookup(None, None, 1, 0.0, 0.0, -1.0, None, None) == _lib.EINVAL
+    assert lib.msasm_face_table_copy(None, 0, None, None) == _lib.EINVAL
+    assert lib.msasm_mlp_forward_tc(None, None, 4, None, None) == _lib.EINVAL
