@@ -4,13 +4,16 @@ One step = one full assembly of the workload's global CSR stiffness through the
 C ABI: pullback + interpolation of the macro field (step 1), the table contraction
 (step 3, eq. 58) and the CSR scatter (step 4), all tiles, inputs resident in HBM.
 
-Default workload: the 10x10x10 twisted beam (1000 tiles, cross cell with 3x3x3
-elements per patch, q = 3) in its FP64-accurate form: the contraction emulates FP64
-exactly with BF16 tensor-core slices (within 1e-12 of the FP64 CUDA-core form, which is
-reported beside it).  Prints ONE JSON line.
+Default workload: the 40x10x10 twisted beam (4000 tiles, cross cell with 3x3x3
+elements per patch, q = 3), the largest of the five lattice workloads that one GPU
+holds, in its FP64-accurate form: the contraction emulates FP64 exactly with BF16
+tensor-core slices (within 1e-12 of the FP64 CUDA-core form).  The same JSON line
+carries every other precision form on that workload, the learned surrogate on the
+graded quarter arc (2000 tiles) and the adjoint gradient on the cantilever plate
+(2000 tiles), each against the plain FP64 GPU form.  Prints ONE JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--precision f64|f32|...] [--workload beam1000|...]
+                  [--precision f64_emu|f64|f32|...] [--workload beam4000|...]
 
 --impl reference times the FP64 CPU oracle (the only baseline there is: the
 paper's code is not available) on a bounded sample of tiles per step.
@@ -18,6 +21,7 @@ paper's code is not available) on a bounded sample of tiles per step.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -37,10 +41,22 @@ WORKLOAD_TEXT = {
                 "q=3 (64 nodes), E=1 nu=0.3",
     "cube8": "perturbed cubic cube split 2x2x2, cross cell 7 patches x 2^3 elements, q=2",
     "beam125": "twisted beam 5x5x5 tiles, cross cell n_e=3, q=3 (profiling case)",
-    "beam4000": "twisted beam 40x10x10 tiles, cross cell n_e=3, q=3",
+    "beam4000": "twisted beam 40x10x10 tiles (90-degree twist), cross cell 7 patches x 3^3 degree-2 elements, "
+                "q=3 (64 nodes), E=1 nu=0.3",
     "cantilever2000": "cantilever plate 20x20x5 tiles, cross cell n_e=2, q=3",
     "arc2000": "quarter arc 20x10x10 tiles, cross cell n_e=3, q=3 (uniform width 0.3)",
 }
+L2_POLICY = "256 MB buffer written between timed steps (L2 is 129 MB); each step also writes the CSR values"
+FORMS = "f64,f32,split_f16,split_bf16,tf32,tf32x3,f64_emu"
+
+
+def workload_config(name):
+    """The `config` object of the JSON line: the workload alone, identical in both arms."""
+    import synth
+    w = synth.workload(name)
+    n = tuple(int(x) for x in w.macro.n_elem)
+    return {"workload": name, "text": WORKLOAD_TEXT.get(name, ""), "tiles": n[0] * n[1] * n[2],
+            "mesh": list(n), "micro_elements_per_patch_dir": w.n_e, "q": w.q, "l2": L2_POLICY}
 
 
 def parse():
@@ -50,11 +66,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="f64_emu")
-    ap.add_argument("--workload", default="beam1000")
-    ap.add_argument("--forms", default="f64,f32,split_f16,split_bf16,tf32,tf32x3",
-                    help="comma list of extra precision forms to report")
+    ap.add_argument("--workload", default="beam4000")
+    ap.add_argument("--forms", default=FORMS, help="comma list of precision forms to report beside the headline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the surrogate and adjoint workloads")
     ap.add_argument("--report", default="", help="comma list of: forms1000, forms4000, surrogate, adjoint, volume, linop, projection, cpu_forms "
                                                  "(prints a JSON report instead of the bench line)")
     return ap.parse_args()
@@ -106,8 +122,9 @@ class Clocks:
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index):
+    def __init__(self, gpu_index, period_ms=40):
         self.gpu = gpu_index
+        self.period_ms = period_ms
         self.proc = None
         self.path = os.path.join("/tmp", f"msasm_clocks_{os.getpid()}.csv")
         self.t_begin = self.t_end = None
@@ -130,7 +147,7 @@ class Clocks:
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.period_ms)],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -204,12 +221,26 @@ FP64_ALU_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
-# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu capture of the kernel
-# as it is now (dram__bytes_read.sum + dram__bytes_write.sum); the profile named beside each
-# figure gives the command.  Keyed by (kernel, workload, precision).
-NCU_TRAFFIC = {
-    ("contract_emu_kernel", "beam1000", "f64_emu"): (908.8e6 + 1633.5e6, "profiles/launches_beam1000_f64_emu.md"),
+# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum); the profile named beside each figure gives the
+# command.  Keyed by (kernel, workload, precision); the last field is the digest of the kernel's
+# source files when the counters were taken: when the source has changed since, the figure no
+# longer describes the kernel and the line reports traffic as null.
+NCU_TRAFFIC = {}
+KERNEL_SOURCES = {
+    "contract_emu_kernel": ("contract_emu.cu", "tc_ptx.cuh"),
+    "contract_tc_kernel": ("contract_tc.cu", "tc_ptx.cuh"),
+    "scatter": ("scatter.cu",),
 }
+
+
+def kernel_source_digest(kernel):
+    """sha256 (first 16 hex digits) of the source files a kernel is compiled from."""
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES.get(kernel, ()):
+        with open(os.path.join(ROOT, "paper_2107_09568_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def contraction_flops(n_nz, n_pi, n_tiles):
@@ -221,12 +252,17 @@ TC_PRODUCTS = {"split_f16": 3, "split_bf16": 3, "tf32": 1, "tf32x3": 3, "f64_emu
 TC_PEAK_RATIO = {"split_f16": 1.0, "split_bf16": 1.0, "tf32": 1.1 / 2.25, "tf32x3": 1.1 / 2.25, "f64_emu": 1.0}
 
 
-def cpu_reference_time(workload, n_sample, seed=0):
-    """FP64 oracle (lookup form: pullback, contraction, scatter) on a sample of tiles; returns (s, tiles)."""
+def oracle_problem(workload):
+    """The oracle's lookup-form problem of a workload (tables and numbering; set-up, not timed)."""
     import synth
-    from oracle.assembly import Problem, nzdata_lookup, scatter_csr
+    from oracle.assembly import Problem
     w = synth.workload(workload)
-    prob = Problem(synth.micro_cross(w.n_e), w.macro, w.q, structure=False)
+    return Problem(synth.micro_cross(w.n_e, w.width), w.macro, w.q, structure=False)
+
+
+def cpu_reference_time(prob, n_sample, seed=0):
+    """FP64 oracle (lookup form: pullback, contraction, scatter) on a sample of tiles; returns (s, tiles)."""
+    from oracle.assembly import nzdata_lookup
     rng = np.random.default_rng(seed)
     tiles = np.sort(rng.choice(prob.mmap.n_tiles, min(n_sample, prob.mmap.n_tiles), replace=False))
     t0 = time.perf_counter()
@@ -274,14 +310,17 @@ def threads_used():
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the FP64 oracle on the host cores, a bounded sample of the workload's tiles
+    per step.  Under torchrun only rank 0 runs it; the other ranks exit at once."""
     if rank != 0:
         return 0
+    prob = oracle_problem(args.workload)
     per_step = 16 if args.workload in ("beam1000", "beam4000", "arc2000") else 8
-    for _ in range(args.warmup):
-        cpu_reference_time(args.workload, max(2, per_step // 4))
+    for k in range(args.warmup):
+        cpu_reference_time(prob, max(2, per_step // 4), seed=1000 + k)
     times, tiles = [], 0
     for k in range(args.steps):
-        dt, n = cpu_reference_time(args.workload, per_step, seed=k)
+        dt, n = cpu_reference_time(prob, per_step, seed=k)
         times.append(dt)
         tiles += n
     total = sum(times)
@@ -290,8 +329,8 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "tiles/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "text": WORKLOAD_TEXT.get(args.workload, ""),
-                       "parallelism": "host cores (numpy/BLAS)"},
+            "config": workload_config(args.workload),
+            "execution": "FP64 oracle on the host cores (numpy/BLAS), rank 0 only",
             "cpu_baseline": {"value": value, "unit": "tiles/s", "cores": cores, "kind": "oracle",
                              "sample": f"{per_step} random tiles per step, FP64 lookup form "
                                        "(pullback, contraction, per-tile scatter ordering)"},
@@ -334,6 +373,86 @@ def run_report(args):
     return 0
 
 
+def roofline_of(stage_avg, prec, tab, n_tiles, nnz, pk, pk_kind, workload):
+    """The dominant kernel's algorithmic rate against its peak (a measured one where there is one)."""
+    names = ["pullback", "contraction", "scatter"]
+    dom = int(np.argmax(stage_avg))
+    vbytes = 8 if prec in ("f64", "f64_emu") else 4
+    K = 9 * tab.n_pi
+    flops = contraction_flops(tab.n_nz, tab.n_pi, n_tiles)
+    nz_bytes = 9 * n_tiles * tab.n_nz * vbytes
+    scatter_bytes = nz_bytes + nnz * vbytes                  # nzdata read, values written (once each)
+    pull_bytes = 9 * n_tiles * K * 8
+    if names[dom] == "contraction" and prec in ("f64", "f32"):
+        alu_peak = FP64_ALU_PEAK_TFLOPS if prec == "f64" else FP32_ALU_PEAK_TFLOPS
+        ach = flops / (stage_avg[1] / 1e3) / 1e12
+        roof = {"kernel": f"contract_simt_{prec}", "bound": "alu", "achieved": ach, "peak": alu_peak,
+                "unit": "TFLOP/s", "frac": ach / alu_peak, "traffic": None,
+                "peak_source": "derived: 152 SMs x lanes per SM x 2 flop x 2.07 GHz",
+                "algorithmic": f"2*n_nz*9n_pi*9m = {flops:.4g} flop per launch"}
+    elif names[dom] == "contraction":
+        # the form's own peak: the tensor pipe's measured burst rate (the kernel is timed in steps of
+        # tens of ms) divided by the products one multiply-add of the emulated type costs (28 BF16
+        # products per FP64-accurate one, 3 per split-FP32 one, 1 for TF32)
+        n_prod = TC_PRODUCTS.get(prec, 1)
+        ratio = TC_PEAK_RATIO.get(prec, 1.0)
+        peak = pk["bf16_tflops"] * ratio / n_prod
+        peak_sus = pk["bf16_tflops_sustained"] * ratio / n_prod
+        ach = flops / (stage_avg[1] / 1e3) / 1e12
+        roof = {"kernel": "contract_emu_kernel" if prec == "f64_emu" else "contract_tc_kernel", "bound": "tensor",
+                "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                "peak_source": f"{pk_kind} bf16 burst {pk['bf16_tflops']}"
+                               + (" x 1.1/2.25 (tf32 nominal ratio)" if "tf32" in prec else "")
+                               + f" / {n_prod} products per {prec} multiply-add",
+                "frac_of_sustained": ach / peak_sus, "sustained_peak": peak_sus,
+                "algorithmic": f"2*n_nz*9n_pi*9m = {flops:.4g} flop per launch",
+                "hardware_products": n_prod, "hardware_tflops": ach * n_prod,
+                "tensor_pipe_peak": pk["bf16_tflops"] * ratio}
+        if prec == "f64_emu":
+            # operands' slices read once plus the FP64 nzdata written once
+            roof["algorithmic_bytes"] = 7 * 2 * K * (tab.n_nz + 9 * n_tiles) + nz_bytes
+    else:
+        byts = scatter_bytes if dom == 2 else pull_bytes
+        ach = byts / (stage_avg[dom] / 1e3) / 1e9
+        roof = {"kernel": names[dom], "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / pk["hbm_gbs"], "traffic": None, "peak_source": pk_kind}
+    tr = NCU_TRAFFIC.get((roof["kernel"], workload, prec))
+    if tr is not None:
+        if tr[2] == kernel_source_digest(roof["kernel"]):
+            roof["traffic"] = tr[0]
+            roof["traffic_source"] = tr[1]
+        else:
+            roof["traffic_stale"] = f"{tr[1]} was captured from an earlier version of the kernel"
+    roof["stages_ms"] = dict(zip(names, [round(float(x), 4) for x in stage_avg]))
+    # the paper times the generation of the nonzero values (steps 1 and 3) without the scatter
+    nz_ms = float(stage_avg[0] + stage_avg[1])
+    roof["nonzeros_only"] = {"ms": round(nz_ms, 4), "tiles_per_s": n_tiles / (nz_ms / 1e3) if nz_ms > 0 else None}
+    roof["scatter_gbs"] = scatter_bytes / (stage_avg[2] / 1e3) / 1e9
+    roof["scatter_frac_hbm"] = roof["scatter_gbs"] / pk["hbm_gbs"]
+    roof["scatter_algorithmic_bytes"] = scatter_bytes
+    roof["pullback_gbs"] = pull_bytes / (stage_avg[0] / 1e3) / 1e9
+    return roof
+
+
+def time_form(plan, ctrl, prec, flush, stream, reps=3):
+    """Median ms of `reps` flushed assemblies in precision `prec` (CUDA events), the output and the
+    per-stage times of the last one."""
+    import torch
+    o = plan.assemble(ctrl, 1.0, 0.3, prec)
+    torch.cuda.synchronize()
+    tms = []
+    for _ in range(reps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        plan.assemble(ctrl, 1.0, 0.3, prec, out=o, stage_times=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        tms.append(a.elapsed_time(b))
+    st, _ = plan.stage_times()
+    return statistics.median(tms), o, st
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -364,7 +483,7 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 256 MB > L2
     stream = torch.cuda.current_stream()
 
-    # correctness of the timed configuration: degenerate check + translation residual
+    # correctness of the timed configuration: degenerate check (and the tensor-core pipeline flag)
     plan.assemble(ctrl, 1.0, 0.3, prec, out=out, check_degenerate=True)
     for _ in range(args.warmup):
         flush.zero_()
@@ -378,7 +497,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     clocks.mark_begin()
-    step_ms, stage_ms, launches = [], np.zeros(3), 0
+    stage_ms, launches = np.zeros(3), 0
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     t_wall = time.perf_counter()
     for k in range(args.steps):
@@ -422,7 +541,7 @@ def main():
                "h2d_bytes_per_step": int(h_ctrl.numel() * 8) * world,
                "d2h_bytes_per_step": int(plan.nnz * vbytes) * world,
                "api": "msasm_assemble_host (pinned host buffers)", "host_cpus": affinity}
-        del h_vals
+        del h_vals, h_ctrl
 
     if rank != 0:
         if dist is not None:
@@ -431,89 +550,70 @@ def main():
 
     pk, pk_kind = peaks()
     stage_avg = stage_ms / args.steps
-    names = ["pullback", "contraction", "scatter"]
-    dom = int(np.argmax(stage_avg))
-    K = 9 * tab.n_pi
-    flops = contraction_flops(tab.n_nz, tab.n_pi, plan.n_tiles)
-    nz_bytes = 9 * plan.n_tiles * tab.n_nz * vbytes
-    scatter_bytes = nz_bytes + plan.nnz * vbytes                   # nzdata read, values written (once each)
-    pull_bytes = 9 * plan.n_tiles * K * 8
-    if names[dom] == "contraction" and prec in ("f64", "f32"):
-        alu_peak = FP64_ALU_PEAK_TFLOPS if prec == "f64" else FP32_ALU_PEAK_TFLOPS
-        ach = flops / (stage_avg[1] / 1e3) / 1e12
-        roof = {"kernel": f"contract_simt_{prec}", "bound": "alu", "achieved": ach, "peak": alu_peak,
-                "unit": "TFLOP/s", "frac": ach / alu_peak, "traffic": None,
-                "peak_source": "derived: 152 SMs x lanes x 2 flop x 2.07 GHz (DESIGN.md)",
-                "algorithmic": f"2*n_nz*9n_pi*9m = {flops:.4g} flop per launch"}
-    elif names[dom] == "contraction":
-        # the form's own peak: the tensor pipe's measured rate divided by the products one
-        # multiply-add of the emulated type costs (28 BF16 products per FP64-accurate one, 3 per
-        # split-FP32 one, 1 for TF32)
-        n_prod = TC_PRODUCTS.get(prec, 1)
-        tc_peak = pk["bf16_tflops_sustained"] * TC_PEAK_RATIO.get(prec, 1.0)
-        peak = tc_peak / n_prod
-        ach = flops / (stage_avg[1] / 1e3) / 1e12
-        roof = {"kernel": "contract_emu_kernel" if prec == "f64_emu" else "contract_tc_kernel", "bound": "tensor",
-                "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
-                "peak_source": f"{pk_kind} bf16 sustained {pk['bf16_tflops_sustained']}"
-                               + (" x 1.1/2.25 (tf32 nominal ratio)" if "tf32" in prec else "")
-                               + f" / {n_prod} products per {prec} multiply-add",
-                "algorithmic": f"2*n_nz*9n_pi*9m = {flops:.4g} flop per launch",
-                "hardware_products": n_prod, "hardware_tflops": ach * n_prod, "tensor_pipe_peak": tc_peak}
-    else:
-        byts = scatter_bytes if dom == 2 else pull_bytes
-        ach = byts / (stage_avg[dom] / 1e3) / 1e9
-        roof = {"kernel": names[dom], "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / pk["hbm_gbs"], "traffic": None, "peak_source": pk_kind}
-    tr = NCU_TRAFFIC.get((roof["kernel"], args.workload, prec))
-    if tr is not None:
-        roof["traffic"] = tr[0]
-        roof["traffic_source"] = tr[1]
-        if roof["kernel"] == "contract_emu_kernel":
-            # operands' slices read once plus the FP64 nzdata written once
-            alg = 7 * 2 * 9 * tab.n_pi * (tab.n_nz + 9 * plan.n_tiles) + 9 * plan.n_tiles * tab.n_nz * 8
-            roof["algorithmic_bytes"] = alg
-    roof["stages_ms"] = dict(zip(names, [round(x, 4) for x in stage_avg]))
-    # the paper times the generation of the nonzero values (steps 1 and 3) without the scatter
-    nz_ms = float(stage_avg[0] + stage_avg[1])
-    roof["nonzeros_only"] = {"ms": round(nz_ms, 4), "tiles_per_s": plan.n_tiles / (nz_ms / 1e3) if nz_ms > 0 else None}
-    roof["scatter_gbs"] = scatter_bytes / (stage_avg[2] / 1e3) / 1e9
-    roof["scatter_frac_hbm"] = roof["scatter_gbs"] / pk["hbm_gbs"]
-    roof["pullback_gbs"] = pull_bytes / (stage_avg[0] / 1e3) / 1e9
+    roof = roofline_of(stage_avg, prec, tab, plan.n_tiles, plan.nnz, pk, pk_kind, args.workload)
 
-    # other precision forms: throughput and relative Frobenius error against the FP64 GPU form
+    # every precision form on the same workload: throughput and relative Frobenius error against the
+    # plain FP64 GPU form (the CUDA-core DFMA contraction)
     forms = {}
-    ref64 = None
-    if prec != "f64":
-        ref64 = plan.assemble(ctrl, 1.0, 0.3, "f64")
-    else:
+    if prec == "f64":
         ref64 = out.clone()
-    for f in [x for x in args.forms.split(",") if x and x != prec]:
-        try:
-            o = plan.assemble(ctrl, 1.0, 0.3, f)
-            torch.cuda.synchronize()
-            tms = []
-            for _ in range(3):
-                flush.zero_()
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream); plan.assemble(ctrl, 1.0, 0.3, f, out=o); b.record(stream)
-                torch.cuda.synchronize()
-                tms.append(a.elapsed_time(b))
-            err = (torch.linalg.vector_norm(o.double() - ref64) / torch.linalg.vector_norm(ref64)).item()
-            ms = statistics.median(tms)
-            forms[f] = {"tiles_per_s": plan.n_tiles / (ms / 1e3), "ms": ms,
-                        "stiffness_gbs": plan.nnz * o.element_size() / (ms / 1e3) / 1e9, "rel_fro_vs_f64_gpu": err}
-            del o
-        except msasm.MsasmError as e:
-            forms[f] = {"unavailable": str(e)}
-
+    else:
+        ms64, ref64, st64 = time_form(plan, ctrl, "f64", flush, stream, reps=2)
+        forms["f64"] = {"tiles_per_s": plan.n_tiles / (ms64 / 1e3), "ms": ms64,
+                        "stiffness_gbs": plan.nnz * 8 / (ms64 / 1e3) / 1e9, "rel_fro_vs_f64_gpu": 0.0,
+                        "stages_ms": [round(x, 4) for x in st64], "note": "the plain FP64 GPU form"}
     main_err = None
     if prec != "f64":
         main_err = (torch.linalg.vector_norm(out.double() - ref64) / torch.linalg.vector_norm(ref64)).item()
+    for f in [x for x in args.forms.split(",") if x and x not in forms]:
+        if f == prec:
+            forms[f] = {"tiles_per_s": value, "ms": total_ms / args.steps, "stiffness_gbs": stiff_gbs,
+                        "rel_fro_vs_f64_gpu": main_err if main_err is not None else 0.0,
+                        "stages_ms": [round(float(x), 4) for x in stage_avg], "note": "the headline (timed above)"}
+            continue
+        try:
+            ms, o, st = time_form(plan, ctrl, f, flush, stream)
+            err = (torch.linalg.vector_norm(o.double() - ref64) / torch.linalg.vector_norm(ref64)).item()
+            forms[f] = {"tiles_per_s": plan.n_tiles / (ms / 1e3), "ms": ms,
+                        "stiffness_gbs": plan.nnz * o.element_size() / (ms / 1e3) / 1e9, "rel_fro_vs_f64_gpu": err,
+                        "stages_ms": [round(x, 4) for x in st]}
+            del o
+        except msasm.MsasmError as e:
+            forms[f] = {"unavailable": str(e)}
+    if "f64" in forms:
+        for f, v in forms.items():
+            if "ms" in v:
+                v["speedup_vs_f64_gpu"] = forms["f64"]["ms"] / v["ms"]
+    del ref64
+    sizes = {"nnz": plan.nnz, "rows": plan.n_rows, "n_nz": tab.n_nz, "n_pi": tab.n_pi,
+             "values_gb": plan.nnz * vbytes / 1e9}
+    n_tiles = plan.n_tiles
+    del out, plan, tab
+    torch.cuda.empty_cache()
+
+    # the other two lattice workloads, each against the plain FP64 GPU form: the learned surrogate of
+    # the graded quarter arc (2000 tiles) and the adjoint gradient of the cantilever plate (2000 tiles)
+    extra = {}
+    if not args.no_extra:
+        from paper_2107_09568_gb300 import workloads as wl
+        t0 = time.perf_counter()
+        extra["surrogate_arc2000"] = wl.surrogate(flush)
+        extra["surrogate_arc2000"]["wall_s"] = time.perf_counter() - t0
+        torch.cuda.empty_cache()
+        t0 = time.perf_counter()
+        a = wl.adjoint(flush, cg_tol=1e-6, fd_precision="f64_emu")
+        a["forms"] = {f: {"grad_ms": a[f"grad_ms_{f}"],
+                          "rel_l2_vs_f64_gpu": 0.0 if f == "f64" else a[f"grad_rel_{f}_vs_f64"],
+                          "speedup_vs_f64_gpu": a["grad_ms_f64"] / a[f"grad_ms_{f}"]}
+                      for f in ("f64", "f64_emu", "f32")}
+        a["wall_s"] = time.perf_counter() - t0
+        extra["adjoint_cantilever2000"] = a
+        torch.cuda.empty_cache()
 
     cpu = None
     if not args.no_cpu:
-        dt, n = cpu_reference_time(args.workload, 400 if plan.n_tiles >= 1000 else plan.n_tiles)
+        prob = oracle_problem(args.workload)
+        dt, n = cpu_reference_time(prob, 400 if n_tiles >= 1000 else n_tiles)
         cpu = {"value": n / dt, "unit": "tiles/s", "cores": threads_used(), "kind": "oracle",
                "sample": f"{n} random tiles of the workload, FP64 lookup form (pullback, contraction, "
                          f"scatter ordering), {dt:.1f} s"}
@@ -521,15 +621,11 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": "tiles/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
-            "config": {"workload": args.workload, "text": WORKLOAD_TEXT.get(args.workload, ""),
-                       "tiles": plan.n_tiles, "nnz": plan.nnz, "rows": plan.n_rows,
-                       "l2": "256 MB buffer written between timed steps; each step also writes "
-                             f"{plan.nnz * vbytes / 1e9:.2f} GB of values",
-                       "parallelism": f"{world} independent replica(s), one per GPU"},
-            "stiffness_gbs": stiff_gbs, "rel_fro_vs_f64_gpu": main_err, "roofline": roof, "cpu_baseline": cpu,
-            "e2e": e2e,
-            "gpu_launches": int(launches), "clocks": clk, "forms": forms,
-            "wall_s_timed_region": wall}
+            "config": workload_config(args.workload),
+            "execution": f"{world} independent replica(s), one per GPU",
+            "sizes": sizes, "stiffness_gbs": stiff_gbs, "rel_fro_vs_f64_gpu": main_err, "roofline": roof,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "forms": forms,
+            "workloads": extra, "wall_s_timed_region": wall}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

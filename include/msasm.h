@@ -76,7 +76,10 @@ typedef enum {
 /* Reference tile T^r (eq. 3): axis-aligned box patches in [0,1]^3, each an
  * open-uniform B-spline with its control points at the Greville abscissae
  * (an affine patch map).  Patches are glued by coincident control points.
- * Arrays are host memory of length 3*n_patches, patch-major. */
+ * Arrays are host memory of length 3*n_patches, patch-major.  Neighbouring tiles
+ * are glued through the points on the faces xi_d = 0, 1; a control point on faces
+ * of two directions (an edge or corner of [0,1]^3, shared by more than two tiles)
+ * is not supported: msasm_build_tables returns MSASM_EUNSUPPORTED. */
 typedef struct {
   int32_t n_patches;
   const int32_t* degree;    /* per patch and direction, 1..4 */

@@ -68,12 +68,11 @@ extern "C" msasm_status msasm_contract_noalloc(const msasm_tables* tab, const do
   if (!tab || !d_coef || !d_nz) return fail(MSASM_EINVAL, "tables, d_coef or d_nz is NULL");
   if (n_tiles <= 0) return fail(MSASM_EINVAL, "n_tiles must be positive");
   const int n_nz = tab->n_nz, K = 9 * tab->n_pi, ld = (n_nz + 7) & ~7;
-  const size_t need = size_t(9) * size_t(n_tiles) * size_t(ld);
-  if (need > kNoAllocScratchDoubles) {
-    const int64_t max_tiles = int64_t(kNoAllocScratchDoubles / (size_t(9) * ld));
-    return fail(MSASM_EINVAL, "msasm_contract_noalloc: " + std::to_string(n_tiles) + " tiles need " +
-                                  std::to_string(need * sizeof(double)) + " bytes of scratch, above the fixed " +
-                                  std::to_string(kNoAllocScratchBytes) + " bytes (at most " +
+  // compare tile counts first, so that no product can wrap around for a huge n_tiles
+  const int64_t max_tiles = int64_t(kNoAllocScratchDoubles / (size_t(9) * size_t(ld)));
+  if (n_tiles > max_tiles) {
+    return fail(MSASM_EINVAL, "msasm_contract_noalloc: " + std::to_string(n_tiles) + " tiles need more than the " +
+                                  std::to_string(kNoAllocScratchBytes) + " bytes of the fixed scratch (at most " +
                                   std::to_string(max_tiles) + " tiles of this table per call)");
   }
   double* scratch = nullptr;

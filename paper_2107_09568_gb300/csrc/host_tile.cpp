@@ -120,6 +120,19 @@ msasm_status build_topology(const msasm_micro_desc* micro, TileTopology& topo) {
         if (e != d && std::fabs(topo.pos[3 * F0[k] + e] - topo.pos[3 * F1[k] + e]) > kPosTol)
           return fail(MSASM_EINVAL, "opposite faces of the reference tile do not match point for point");
   }
+  // Gluing matches tiles face by face: a point owned across one face has exactly one other tile
+  // holding it, so the numbering, the pattern (face neighbours only) and the two-contributor
+  // scatter hold only when no control point lies on faces of two directions (an edge or a corner
+  // of the tile, where three or more tiles would meet).
+  for (int A = 0; A < topo.n_T; ++A) {
+    int dirs = 0;
+    for (int d = 0; d < 3; ++d)
+      if (topo.face_pos[2 * d][A] >= 0 || topo.face_pos[2 * d + 1][A] >= 0) ++dirs;
+    if (dirs > 1)
+      return fail(MSASM_EUNSUPPORTED,
+                  "a control point of the reference tile lies on an edge or corner of [0,1]^3 (on faces of two "
+                  "directions); only tiles glued through face-interior points are supported");
+  }
   size_t n_nz = topo.pair_A.size();
   topo.pair_face.assign(n_nz, 0);
   for (size_t m = 0; m < n_nz; ++m)

@@ -102,7 +102,14 @@ def surrogate(flush, nx=20, ny=10, nz=10, steps=(4000, 3000, 3000)):
     for t in range(plan.n_tiles):
         nzd[9 * t:9 * t + 9] = train_tabs[nearest[t]].contract(coef[9 * t:9 * t + 9], "f64")
     k_near = plan.scatter(nzd, "f64")
-    k_mean = msasm.Plan(msasm.Tables(synth.micro_cross(3, 0.275), 3), m).assemble(ctrl)
+    plan_mean = msasm.Plan(msasm.Tables(synth.micro_cross(3, 0.275), 3), m)
+    k_mean = plan_mean.assemble(ctrl)
+    # the plain FP64 GPU form of the same mesh (one table, the mean width): CUDA-core FP64 and the
+    # FP64-accurate tensor-core form
+    _, ms_f64 = _timed(lambda: plan_mean.assemble(ctrl, 1.0, 0.3, "f64", out=k_mean), reps=2, flush=flush)
+    k_emu = torch.empty_like(k_mean)
+    _, ms_emu = _timed(lambda: plan_mean.assemble(ctrl, 1.0, 0.3, "f64_emu", out=k_emu), reps=3, flush=flush)
+    del k_emu
     return {"tiles": plan.n_tiles, "nnz": plan.nnz, "rank": 32, "training_tables": 64,
             "table_build_s": t_tables, "basis_fit_s": t_basis, "train_s": t_train,
             "train_loss_first_last": [float(hist[0]), float(hist[-1])],
@@ -110,10 +117,12 @@ def surrogate(flush, nx=20, ny=10, nz=10, steps=(4000, 3000, 3000)):
             "per_width_quadrature_ms": ms_exact, "per_width_tiles_per_s": plan.n_tiles / ms_exact * 1e3,
             "rel_fro_surrogate_vs_per_width": rel(k_sur, k_exact),
             "rel_fro_nearest_training_table_vs_per_width": rel(k_near, k_exact),
-            "rel_fro_mean_width_table_vs_per_width": rel(k_mean, k_exact)}
+            "rel_fro_mean_width_table_vs_per_width": rel(k_mean, k_exact),
+            "fp64_gpu_one_table_ms": ms_f64, "fp64_emu_gpu_one_table_ms": ms_emu,
+            "speedup_vs_fp64_gpu_one_table": ms_f64 / ms_sur}
 
 
-def adjoint(flush, nx=20, ny=20, nz=5, n_check=20, h=1e-4):
+def adjoint(flush, nx=20, ny=20, nz=5, n_check=20, h=1e-4, cg_tol=1e-13, fd_precision="f64"):
     """Cantilever compliance gradient: assembly, CG solve, adjoint kernels (FP64 and FP32) and central
     differences of u^T K(P) u at fixed u on n_check seeded control-point coordinates.  (Differences of
     the re-solved compliance are not meaningful at this size: the CG solution's rounding floor, a
@@ -136,7 +145,7 @@ def adjoint(flush, nx=20, ny=20, nz=5, n_check=20, h=1e-4):
     K = msasm.csr_matrix(plan, vals)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    u, iters, res = msasm.cg_solve(K, f, fixed, tol=1e-13, max_iter=30000)
+    u, iters, res = msasm.cg_solve(K, f, fixed, tol=cg_tol, max_iter=30000)
     torch.cuda.synchronize()
     t_cg = time.perf_counter() - t0
     C0 = torch.dot(f, u).item()
@@ -146,7 +155,7 @@ def adjoint(flush, nx=20, ny=20, nz=5, n_check=20, h=1e-4):
     rng = np.random.default_rng(0)
     coords = [(int(k), int(p)) for k, p in zip(rng.choice(plan.n_ctrl, n_check, replace=False),
                                                rng.integers(0, 3, n_check))]
-    quad = lambda c: torch.dot(u, msasm.csr_matrix(plan, plan.assemble(c, 1.0, 0.3, "f64")) @ u).item()
+    quad = lambda c: torch.dot(u, msasm.csr_matrix(plan, plan.assemble(c, 1.0, 0.3, fd_precision)) @ u).item()
     fdq = []
     for k, p in coords:
         c = ctrl.clone(); c[k, p] += h
@@ -162,7 +171,7 @@ def adjoint(flush, nx=20, ny=20, nz=5, n_check=20, h=1e-4):
            "grad_ms_f64": ms_g64, "grad_ms_f64_emu": ms_gemu, "grad_ms_f32": ms_g32,
            "grad_rel_f32_vs_f64": (torch.linalg.vector_norm(g32 - g64) / torch.linalg.vector_norm(g64)).item(),
            "grad_rel_f64_emu_vs_f64": (torch.linalg.vector_norm(gemu - g64) / torch.linalg.vector_norm(g64)).item(),
-           "fd_coords": coords, "fd_step": h,
+           "fd_coords": coords, "fd_step": h, "fd_assembly_form": fd_precision, "cg_tol": cg_tol,
            "fd_quadratic_max_abs_diff_over_max_grad": float(np.abs(fdq - gq).max() / np.abs(gq).max())}
     return out
 

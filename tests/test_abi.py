@@ -64,3 +64,18 @@ def test_host_side_validation_of_the_later_entry_points():
     assert lib.msasm_traction_load_lookup(None, None, 1, 0.0, 0.0, -1.0, None, None) == _lib.EINVAL
     assert lib.msasm_face_table_copy(None, 0, None, None) == _lib.EINVAL
     assert lib.msasm_mlp_forward_tc(None, None, 4, None, None) == _lib.EINVAL
+
+
+def test_edge_and_corner_points_are_rejected_before_any_cuda_call():
+    """A solid-cube micro tile (one patch filling [0,1]^3) has control points on the tile's edges
+    and corners, which three or more tiles share; the face-by-face gluing of the numbering, the
+    pattern and the scatter does not cover them, so the table build refuses the tile."""
+    lib = msasm.load()
+    out = C.c_void_p()
+    deg = np.full(3, 2, np.int32); ne = np.full(3, 2, np.int32)
+    lo = np.zeros(3); hi = np.ones(3)
+    d = _lib.MicroDescC(1, deg.ctypes.data_as(C.POINTER(C.c_int32)), ne.ctypes.data_as(C.POINTER(C.c_int32)),
+                        lo.ctypes.data_as(C.POINTER(C.c_double)), hi.ctypes.data_as(C.POINTER(C.c_double)))
+    assert lib.msasm_build_tables(C.byref(d), 2, 0, None, C.byref(out)) == _lib.EUNSUPPORTED
+    assert b"edge or corner" in lib.msasm_last_error()
+    assert out.value is None
