@@ -601,7 +601,7 @@ def main():
         extra["surrogate_arc2000"]["wall_s"] = time.perf_counter() - t0
         torch.cuda.empty_cache()
         t0 = time.perf_counter()
-        a = wl.adjoint(flush, cg_tol=1e-6, fd_precision="f64_emu")
+        a = wl.adjoint(flush, cg_tol=1e-6, fd_precision="f64")
         a["forms"] = {f: {"grad_ms": a[f"grad_ms_{f}"],
                           "rel_l2_vs_f64_gpu": 0.0 if f == "f64" else a[f"grad_rel_{f}_vs_f64"],
                           "speedup_vs_f64_gpu": a["grad_ms_f64"] / a[f"grad_ms_{f}"]}

@@ -37,7 +37,9 @@
  *    column k = 9*C + 3*i + j.
  *  - Coefficient layout (mat[<A>] of eq. 58, stored transposed): coef[n][k] with
  *    n = 9*t + 3*alpha + beta and k = 9*C + 3*i + j, value A_ij(xi_C)[alpha][beta].
- *  - nzdata layout (eq. 58, stored transposed): nz[n][m], n = 9*t + 3*alpha + beta.
+ *  - nzdata layout (eq. 58, the tile matrices K_t block by block): nz[t][m][3*alpha + beta],
+ *    the 3x3 block of pair m = (A,B) of tile t, value K_t[(A,alpha),(B,beta)], at
+ *    9*(t*n_nz + m) + 3*alpha + beta; the block of (B,A) is its transpose and is not stored.
  *  - Global stiffness: DOF 3*g + alpha of global control point g; CSR with int64
  *    row pointer, int32 ascending column indices, full symmetric storage.
  */
@@ -188,6 +190,38 @@ msasm_status msasm_assemble_grad(msasm_plan* plan, const double* d_ctrl, double 
                                  msasm_precision prec, const void* d_u, const void* d_grad_values,
                                  double* d_grad_ctrl, void* stream);
 
+/* ---------------------------------------------------------------- one mesh across GPUs (tile ranges)
+ *
+ * The tile matrices of eq. 58 are independent per tile, and the tile-major numbering makes the
+ * rows owned by a contiguous tile range [t0, t1) one contiguous range of rows and of CSR values.
+ * A rank assembles the complete rows its tiles own by also recomputing the halo: the tiles of
+ * the next layer above the range (up to t1 + nx*ny), whose blocks on their glued lower faces
+ * land in those rows.  No data moves between ranks for the assembly; the gradient of a range is
+ * a partial sum, added across ranks by one all-reduce (the caller's). */
+
+/* The rows [*row0, *row1) and CSR values [*v0, *v1) owned by tiles [t0, t1) (0 <= t0 <= t1 <=
+ * n_tiles), and the end of the tiles that reach them (*halo_end: t1 plus the next layer, at most
+ * n_tiles).  Any output may be NULL.  Host only.  Errors: EINVAL. */
+msasm_status msasm_plan_range(const msasm_plan* plan, int64_t t0, int64_t t1, int64_t* row0, int64_t* row1,
+                              int64_t* v0, int64_t* v1, int64_t* halo_end);
+
+/* msasm_assemble for the rows owned by tiles [t0, t1): d_values holds the values [v0, v1) of
+ * msasm_plan_range (its first element is value v0), and receives exactly the values a whole-mesh
+ * msasm_assemble writes there (bit for bit: the same kernels, the same sums).  Tiles [t0,
+ * halo_end) are computed; the blocks of tiles outside [t0, t1) are written only where they land
+ * in the window.  t0 == t1 does nothing.  Errors: as msasm_assemble. */
+msasm_status msasm_assemble_range(msasm_plan* plan, const double* d_ctrl, double E, double nu,
+                                  msasm_precision prec, int64_t t0, int64_t t1, void* d_values, uint32_t flags,
+                                  void* stream);
+
+/* msasm_assemble_grad restricted to the tiles [t0, t1): d_grad_ctrl (n_ctrl*3, overwritten) gets
+ * the part of dL/dP that those tiles' blocks contribute (eq. 69-73 summed over the range); the
+ * sum over a partition of the tiles is the whole gradient.  d_u (n_rows) or d_grad_values (nnz)
+ * are the whole-mesh arrays, as in msasm_assemble_grad.  Errors: as msasm_assemble_grad. */
+msasm_status msasm_assemble_grad_range(msasm_plan* plan, const double* d_ctrl, double E, double nu,
+                                       msasm_precision prec, int64_t t0, int64_t t1, const void* d_u,
+                                       const void* d_grad_values, double* d_grad_ctrl, void* stream);
+
 /* Global control points on macro face `face` = 2 d + s (the face xi_d = s of the macro
  * parameter cube), ascending, into h_points (host; *count in: capacity, out: number).
  * With h_points NULL only the count is returned. */
@@ -257,8 +291,8 @@ msasm_status msasm_surrogate_basis(const msasm_surrogate* sur, float* d_U, void*
 msasm_status msasm_surrogate_predict(msasm_surrogate* sur, const double* d_widths, int64_t n, float* d_Vt,
                                      void* stream);
 /* Low-rank eq. 58 with the factor U (d_U, n_nz x rank FP32 row-major): for n_tiles tiles,
- * nz[9t+ab][m] = sum_r (sum_k Vt_t[r][k] coef[9t+ab][k]) U[m][r], Vt (n_tiles x rank x K FP32),
- * coef (9 n_tiles x K FP64); d_nz (9 n_tiles x n_nz FP32, dense).  Z in FP32, the product with U on the
+ * nz[t][m][ab] = sum_r (sum_k Vt_t[r][k] coef[9t+ab][k]) U[m][r], Vt (n_tiles x rank x K FP32),
+ * coef (9 n_tiles x K FP64); d_nz (n_tiles x n_nz x 9 FP32, the nzdata layout above).  Z in FP32, the product with U on the
  * tensor cores in split FP16 (about 6e-7 relative); synchronises `stream`. */
 msasm_status msasm_lowrank_contract(const float* d_U, int32_t n_nz, int32_t rank, int32_t K, const float* d_Vt,
                                     const double* d_coef, int64_t n_tiles, float* d_nz, void* stream);
@@ -298,9 +332,9 @@ msasm_status msasm_pullback(msasm_plan* plan, const double* d_ctrl, double E, do
 msasm_status msasm_pullback_l2(msasm_plan* plan, const double* d_ctrl, double E, double nu, int32_t n_gauss,
                                double* d_coef, void* stream);
 
-/* Step 3 only: nz[n][m] = sum_k coef[n][k] T[m][k] (eq. 58) for `n_tiles` tiles of
- * FP64 coefficients d_coef (layout above).  d_nz: 9*n_tiles*n_nz values, FP64
- * for MSASM_F64 / MSASM_F64_EMU, FP32 otherwise. */
+/* Step 3 only: nz[t][m][3a+b] = sum_k coef[9t+3a+b][k] T[m][k] (eq. 58) for `n_tiles` tiles
+ * of FP64 coefficients d_coef (layout above).  d_nz: n_tiles*n_nz*9 values in the nzdata
+ * layout above, FP64 for MSASM_F64 / MSASM_F64_EMU, FP32 otherwise. */
 msasm_status msasm_contract(const msasm_tables* tab, msasm_precision prec, const double* d_coef,
                             int64_t n_tiles, void* d_nz, void* stream);
 
@@ -309,9 +343,9 @@ msasm_status msasm_contract(const msasm_tables* tab, msasm_precision prec, const
  * memory for its own pool, or a service that may not call cudaMalloc/cudaFree,
  * which synchronise the device, after start-up).  The paper has no counterpart:
  * it is an interface addition, not a step of the method.  Same arguments and
- * result as msasm_contract with MSASM_F64 (d_nz dense, 9*n_tiles x n_nz FP64),
- * but the padded intermediate lives in a fixed 32 MiB file-scope device array:
- * 9 * n_tiles * round_up(n_nz, 8) * 8 bytes must fit, otherwise EINVAL (for
+ * result as msasm_contract with MSASM_F64 (d_nz: n_tiles x n_nz x 9 FP64, the nzdata
+ * layout above), but the padded intermediate lives in a fixed 32 MiB file-scope device
+ * array: n_tiles * 9 * round_up(n_nz, 8) * 8 bytes must fit, otherwise EINVAL (for
  * n_nz = 23286 that is 20 tiles per call).  The first call on a device, made
  * with that device current, looks up the array's address; make it before any
  * stream capture.  Calls share the array: calls that overlap on the GPU race and

@@ -84,11 +84,12 @@ class Tables:
         return out
 
     def contract(self, coef, precision="f64", stream=None):
-        """Step 3 only: nz[n][m] = sum_k coef[n][k] T[m][k] (eq. 58) for FP64 coefficients."""
+        """Step 3 only: the tile blocks of eq. 58 for FP64 coefficients (9 n_tiles, 9 n_pi), as a
+        (n_tiles, n_nz, 3, 3) tensor: [t, m, a, b] = K_t[(A,a),(B,b)] of pair m = (A, B)."""
         import torch
         n_tiles = coef.shape[0] // 9
         dt = torch.float64 if precision in ("f64", "f64_emu") else torch.float32
-        out = torch.empty((9 * n_tiles, self.n_nz), dtype=dt, device="cuda")
+        out = torch.empty((n_tiles, self.n_nz, 3, 3), dtype=dt, device="cuda")
         check(load().msasm_contract(self.handle, PRECISIONS[precision], _ptr(coef), n_tiles, _ptr(out),
                                     _stream(stream)))
         return out
@@ -176,7 +177,9 @@ class Plan:
         return out
 
     def scatter(self, nz, precision="f64", stream=None):
+        """Step 4 only: CSR values from the tile blocks nz (n_tiles, n_nz, 3, 3) of every tile."""
         import torch
+        assert nz.is_contiguous() and nz.numel() == 9 * self.n_tiles * self.tables.n_nz
         out = torch.empty(self.nnz, dtype=self.value_dtype(precision), device="cuda")
         check(load().msasm_scatter(self.handle, PRECISIONS[precision], _ptr(nz), _ptr(out), _stream(stream)))
         return out
@@ -195,6 +198,37 @@ def _plan_assemble_grad(self, ctrl, E=1.0, nu=0.3, precision="f64", u=None, grad
     out = torch.empty((self.n_ctrl, 3), dtype=torch.float64, device="cuda")
     check(load().msasm_assemble_grad(self.handle, _ptr(ctrl), float(E), float(nu), PRECISIONS[precision],
                                      _ptr(u), _ptr(grad_values), _ptr(out), _stream(stream)))
+    return out
+
+
+def _plan_range(self, t0, t1):
+    """(row0, row1, v0, v1, halo_end) of the tile range [t0, t1): the rows and CSR values its tiles own
+    and the end of the tiles whose blocks reach them."""
+    out = [C.c_int64() for _ in range(5)]
+    check(load().msasm_plan_range(self.handle, int(t0), int(t1), *[C.byref(v) for v in out]))
+    return tuple(v.value for v in out)
+
+
+def _plan_assemble_range(self, ctrl, t0, t1, E=1.0, nu=0.3, precision="f64", out=None, stage_times=False,
+                         stream=None):
+    """The CSR values [v0, v1) owned by tiles [t0, t1) (msasm_assemble_range)."""
+    import torch
+    _, _, v0, v1, _ = self.range(t0, t1)
+    if out is None:
+        out = torch.empty(max(v1 - v0, 1), dtype=self.value_dtype(precision), device="cuda")
+    flags = _lib.FLAG_STAGE_TIMES if stage_times else 0
+    check(load().msasm_assemble_range(self.handle, _ptr(ctrl), float(E), float(nu), PRECISIONS[precision], int(t0),
+                                      int(t1), _ptr(out), flags, _stream(stream)))
+    return out[:v1 - v0]
+
+
+def _plan_assemble_grad_range(self, ctrl, t0, t1, E=1.0, nu=0.3, precision="f64", u=None, grad_values=None,
+                              stream=None):
+    """The part of dL/dP (n_ctrl, 3) FP64 contributed by tiles [t0, t1)."""
+    import torch
+    out = torch.empty((self.n_ctrl, 3), dtype=torch.float64, device="cuda")
+    check(load().msasm_assemble_grad_range(self.handle, _ptr(ctrl), float(E), float(nu), PRECISIONS[precision],
+                                           int(t0), int(t1), _ptr(u), _ptr(grad_values), _ptr(out), _stream(stream)))
     return out
 
 
@@ -352,6 +386,9 @@ def select_projection_degrees(plan, ctrl, tol, q_init, q_max=7, **kw):
     return tuple(q), err
 
 
+Plan.range = _plan_range
+Plan.assemble_range = _plan_assemble_range
+Plan.assemble_grad_range = _plan_assemble_grad_range
 Plan.projection_error = _plan_projection_error
 Plan.traction_load_lookup = _plan_traction_load_lookup
 Tables.face_table = _tables_face_table
@@ -534,10 +571,11 @@ class MLP:
 
 
 def lowrank_contract(U, Vt, coef):
-    """Low-rank eq. 58: nz (9 n_tiles, n_nz) FP32 from U (n_nz, r), Vt (n_tiles, r, K), coef (9 n_tiles, K) FP64."""
+    """Low-rank eq. 58: the tile blocks (n_tiles, n_nz, 3, 3) FP32 from U (n_nz, r), Vt (n_tiles, r, K) and
+    coef (9 n_tiles, K) FP64."""
     import torch
     n_tiles = coef.shape[0] // 9
-    nz = torch.empty((9 * n_tiles, U.shape[0]), dtype=torch.float32, device="cuda")
+    nz = torch.empty((n_tiles, U.shape[0], 3, 3), dtype=torch.float32, device="cuda")
     check(load().msasm_lowrank_contract(_ptr(U.contiguous()), U.shape[0], U.shape[1], coef.shape[1],
                                         _ptr(Vt.contiguous()), _ptr(coef), n_tiles, _ptr(nz), _stream()))
     return nz

@@ -45,6 +45,9 @@ msasm_status to_f32_gpu(const double* x, int64_t n, float* y, cudaStream_t strea
 template <typename T>
 msasm_status scatter_pass_gpu(const msasm_plan* plan, const T* d_nz, int ld_nz, int64_t t0, int64_t n_tiles,
                               T* d_values, cudaStream_t stream);
+template <typename T>
+msasm_status scatter_pass_gpu(const msasm_plan* plan, const T* d_nz, int ld_nz, int64_t t0, int64_t n_tiles,
+                              T* d_values, int64_t direct_end, int64_t v_lo, int64_t v_hi, cudaStream_t stream);
 msasm_status build_scatter_plan(msasm_plan* plan, const std::vector<int32_t>& gmap, const std::vector<int64_t>& pptr,
                                 ScatterPlanHost& out);
 template <typename T>
@@ -76,14 +79,15 @@ size_t emu_slice_bytes(int64_t rows, int K);
 msasm_status emu_slice_gpu(const double* x, int64_t rows, int64_t ldx, int K, void* slices, int* scale_exp,
                            cudaStream_t s);
 msasm_status contract_emu_gpu(const void* a_slices, const int* a_exp, int M, const void* b_slices, const int* b_exp,
-                              int64_t N, int K, double* out, int ld, bool accumulate, unsigned* d_err, cudaStream_t s);
+                              int64_t N, int K, double* out, int ld, bool accumulate, bool blocks, unsigned* d_err,
+                              cudaStream_t s);
 int tc_kpad(int K, int kind);
 size_t tc_slice_bytes(int64_t rows, int K, int kind);
 msasm_status tc_split_gpu(const double* x, int64_t rows, int K, int kind, void* hi, void* lo, float* row_scale,
                           cudaStream_t s);
 msasm_status contract_tc_gpu(int kind, const void* a_hi, const void* a_lo, const float* a_scale, int M,
                              const void* b_hi, const void* b_lo, const float* b_scale, int64_t N, int K, float* out,
-                             int ld, unsigned* d_err, cudaStream_t s);
+                             int ld, bool blocks, unsigned* d_err, cudaStream_t s);
 
 
 static bool is_f64_precision(msasm_precision p) { return p == MSASM_F64 || p == MSASM_F64_EMU; }
@@ -317,11 +321,13 @@ msasm_status msasm_plan_create(const msasm_tables* tab, const msasm_macro_desc* 
   // value range of each tile's owned rows: owned points of tile t are the ids assigned while
   // numbering t, so the ranges are consecutive in tile order
   plan->tile_vbase.assign(size_t(plan->n_tiles) + 1, plan->nnz);
+  plan->tile_pbase.assign(size_t(plan->n_tiles) + 1, plan->n_points);
   {
     int64_t next_id = 0;
     const int n_T = tab->topo.n_T;
     for (int64_t t = 0; t < plan->n_tiles; ++t) {
       plan->tile_vbase[size_t(t)] = 9 * pptr[size_t(next_id)];
+      plan->tile_pbase[size_t(t)] = next_id;
       int32_t mx = -1;
       for (int A = 0; A < n_T; ++A) mx = std::max(mx, gmap[size_t(t) * n_T + A]);
       if (mx + 1 > next_id) next_id = mx + 1;
@@ -551,7 +557,7 @@ static msasm_status contract_dispatch(const msasm_tables* ctab, msasm_precision 
       float* sc = reinterpret_cast<float*>(lo + sb);
       MSASM_TRY(tc_split_gpu(d_coef, 9 * n_tiles, K, kind, hi, lo, sc, s));
       return contract_tc_gpu(kind, tab->d_Thi, tab->d_Tlo, tab->d_Tscale, n_nz, hi, lo, sc, 9 * n_tiles, K,
-                             static_cast<float*>(d_nz), ld, d_err, s);
+                             static_cast<float*>(d_nz), ld, true, d_err, s);
     }
     case MSASM_F64_EMU: {
       if (!tab->d_Tslices) {
@@ -564,7 +570,7 @@ static msasm_status contract_dispatch(const msasm_tables* ctab, msasm_precision 
       int* sc = reinterpret_cast<int*>(sl + ((emu_slice_bytes(9 * n_tiles, K) + 255) & ~size_t(255)));
       MSASM_TRY(emu_slice_gpu(d_coef, 9 * n_tiles, K, K, sl, sc, s));
       return contract_emu_gpu(tab->d_Tslices, tab->d_Tslice_scale, n_nz, sl, sc, 9 * n_tiles, K,
-                              static_cast<double*>(d_nz), ld, false, d_err, s);
+                              static_cast<double*>(d_nz), ld, false, true, d_err, s);
     }
     default:
       return fail(MSASM_EUNSUPPORTED, "precision not available in this build");
@@ -585,29 +591,44 @@ static msasm_status ensure_lp_scratch(msasm_plan* plan, msasm_precision prec) {
   return MSASM_OK;
 }
 
+// step 4 of tiles [t0, t0 + nt): direct pass for the tiles below direct_end, secondary pass for all,
+// into the value window [v_lo, v_hi) held by d_values
 static msasm_status scatter_dispatch(msasm_plan* plan, msasm_precision prec, const void* d_nz, int64_t t0,
-                                     int64_t nt, void* d_values, cudaStream_t s) {
+                                     int64_t nt, void* d_values, cudaStream_t s, int64_t direct_end = -1,
+                                     int64_t v_lo = 0, int64_t v_hi = -1) {
   const int ld = ld_nz_of(plan->tab->n_nz);
+  if (direct_end < 0) direct_end = t0 + nt;
+  if (v_hi < 0) v_hi = plan->nnz;
   if (is_f64_precision(prec))
     return scatter_pass_gpu<double>(plan, static_cast<const double*>(d_nz), ld, t0, nt,
-                                    static_cast<double*>(d_values), s);
+                                    static_cast<double*>(d_values), direct_end, v_lo, v_hi, s);
   return scatter_pass_gpu<float>(plan, static_cast<const float*>(d_nz), ld, t0, nt, static_cast<float*>(d_values),
-                                 s);
+                                 direct_end, v_lo, v_hi, s);
 }
 
-msasm_status msasm_assemble(msasm_plan* plan, const double* d_ctrl, double E, double nu, msasm_precision prec,
-                            void* d_values, uint32_t flags, void* stream) {
-  if (!plan || !d_ctrl || !d_values) return fail(MSASM_EINVAL, "plan, d_ctrl or d_values is NULL");
+// the tiles whose blocks reach the rows owned by tiles [t0, t1): the range itself and the tiles
+// of the next layer above it (a tile's lower faces are glued to t - 1, t - nx and t - nx ny)
+static int64_t halo_end_of(const msasm_plan* plan, int64_t t1) {
+  const int64_t layer = int64_t(plan->n_elem[0]) * plan->n_elem[1];
+  return std::min(plan->n_tiles, t1 + layer);
+}
+
+// steps 1, 3, 4 for the rows owned by tiles [t0, t1) (all rows for [0, n_tiles)), into d_values
+// holding the window [tile_vbase[t0], tile_vbase[t1])
+static msasm_status assemble_range_impl(msasm_plan* plan, const double* d_ctrl, double E, double nu,
+                                        msasm_precision prec, int64_t t0, int64_t t1, void* d_values, uint32_t flags,
+                                        cudaStream_t s) {
   MSASM_TRY(check_material(E, nu));
   if (prec < MSASM_F64 || prec > MSASM_F64_EMU) return fail(MSASM_EINVAL, "unknown precision");
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   double lam, mu;
   lame(E, nu, lam, mu);
   MSASM_TRY(ensure_lp_scratch(plan, prec));
   MSASM_CUDA(cudaMemsetAsync(plan->d_degenerate, 0, sizeof(unsigned long long), s));
   const int64_t P = plan->tiles_per_pass;
+  const int64_t t_end = halo_end_of(plan, t1);
+  const int64_t v_lo = plan->tile_vbase[size_t(t0)], v_hi = plan->tile_vbase[size_t(t1)];
   const bool timed = (flags & MSASM_FLAG_STAGE_TIMES) != 0;
-  const int n_pass = int((plan->n_tiles + P - 1) / P);
+  const int n_pass = int((t_end - t0 + P - 1) / P);
   plan->timed_passes = 0;
   if (timed) {
     while (plan->events.size() < size_t(4 * n_pass)) {
@@ -618,19 +639,19 @@ msasm_status msasm_assemble(msasm_plan* plan, const double* d_ctrl, double E, do
     for (int k = 0; k < 3; ++k) plan->stage_launches[k] = 0;
   }
   int pass = 0;
-  for (int64_t t0 = 0; t0 < plan->n_tiles; t0 += P, ++pass) {
-    const int64_t nt = std::min(P, plan->n_tiles - t0);
+  for (int64_t ta = t0; ta < t_end; ta += P, ++pass) {
+    const int64_t nt = std::min(P, t_end - ta);
     if (timed) MSASM_CUDA(cudaEventRecord(plan->events[4 * pass + 0], s));
-    MSASM_TRY(pullback_gpu(plan, d_ctrl, lam, mu, t0, nt, plan->d_coef, s));
+    MSASM_TRY(pullback_gpu(plan, d_ctrl, lam, mu, ta, nt, plan->d_coef, s));
     if (timed) MSASM_CUDA(cudaEventRecord(plan->events[4 * pass + 1], s));
     MSASM_TRY(contract_dispatch(plan->tab, prec, plan->d_coef, nt, plan->d_nz, plan->d_coef_lp, s, plan->d_tc_err));
     if (timed) MSASM_CUDA(cudaEventRecord(plan->events[4 * pass + 2], s));
-    MSASM_TRY(scatter_dispatch(plan, prec, plan->d_nz, t0, nt, d_values, s));
+    MSASM_TRY(scatter_dispatch(plan, prec, plan->d_nz, ta, nt, d_values, s, t1, v_lo, v_hi));
     if (timed) {
       MSASM_CUDA(cudaEventRecord(plan->events[4 * pass + 3], s));
       plan->stage_launches[0] += 1;
       plan->stage_launches[1] += contract_launches(prec);
-      plan->stage_launches[2] += 1 + (plan->sec_off_host[size_t(t0 + nt)] > plan->sec_off_host[size_t(t0)] ? 1 : 0);
+      plan->stage_launches[2] += (ta < t1 ? 1 : 0) + (plan->sec_off_host[size_t(ta + nt)] > plan->sec_off_host[size_t(ta)] ? 1 : 0);
     }
   }
   if (timed) plan->timed_passes = n_pass;
@@ -646,6 +667,33 @@ msasm_status msasm_assemble(msasm_plan* plan, const double* d_ctrl, double E, do
                   "degenerate macro element: |det J| <= tol at " + std::to_string(cnt) + " interpolation nodes");
   }
   return MSASM_OK;
+}
+
+msasm_status msasm_assemble(msasm_plan* plan, const double* d_ctrl, double E, double nu, msasm_precision prec,
+                            void* d_values, uint32_t flags, void* stream) {
+  if (!plan || !d_ctrl || !d_values) return fail(MSASM_EINVAL, "plan, d_ctrl or d_values is NULL");
+  return assemble_range_impl(plan, d_ctrl, E, nu, prec, 0, plan->n_tiles, d_values, flags,
+                             static_cast<cudaStream_t>(stream));
+}
+
+msasm_status msasm_plan_range(const msasm_plan* plan, int64_t t0, int64_t t1, int64_t* row0, int64_t* row1,
+                              int64_t* v0, int64_t* v1, int64_t* halo_end) {
+  if (!plan) return fail(MSASM_EINVAL, "plan is NULL");
+  if (t0 < 0 || t1 < t0 || t1 > plan->n_tiles) return fail(MSASM_EINVAL, "tile range outside [0, n_tiles]");
+  if (row0) *row0 = 3 * plan->tile_pbase[size_t(t0)];
+  if (row1) *row1 = 3 * plan->tile_pbase[size_t(t1)];
+  if (v0) *v0 = plan->tile_vbase[size_t(t0)];
+  if (v1) *v1 = plan->tile_vbase[size_t(t1)];
+  if (halo_end) *halo_end = (t1 > t0) ? halo_end_of(plan, t1) : t1;
+  return MSASM_OK;
+}
+
+msasm_status msasm_assemble_range(msasm_plan* plan, const double* d_ctrl, double E, double nu, msasm_precision prec,
+                                  int64_t t0, int64_t t1, void* d_values, uint32_t flags, void* stream) {
+  if (!plan || !d_ctrl || !d_values) return fail(MSASM_EINVAL, "plan, d_ctrl or d_values is NULL");
+  if (t0 < 0 || t1 < t0 || t1 > plan->n_tiles) return fail(MSASM_EINVAL, "tile range outside [0, n_tiles]");
+  if (t1 == t0) return MSASM_OK;
+  return assemble_range_impl(plan, d_ctrl, E, nu, prec, t0, t1, d_values, flags, static_cast<cudaStream_t>(stream));
 }
 
 constexpr int kAdjChunk = 576;   // pairs per exactly accumulated chunk of the emulated adjoint product
@@ -740,14 +788,16 @@ msasm_status msasm_assemble_host(msasm_plan* plan, const double* h_ctrl, double 
   return MSASM_OK;
 }
 
-msasm_status msasm_assemble_grad(msasm_plan* plan, const double* d_ctrl, double E, double nu, msasm_precision prec,
-                                 const void* d_u, const void* d_grad_values, double* d_grad_ctrl, void* stream) {
+// dL/dP of the tiles [t0, t1) into d_grad_ctrl (overwritten): the whole gradient for [0, n_tiles)
+static msasm_status grad_range_impl(msasm_plan* plan, const double* d_ctrl, double E, double nu, msasm_precision prec,
+                                    int64_t t0, int64_t t1, const void* d_u, const void* d_grad_values,
+                                    double* d_grad_ctrl, cudaStream_t s) {
   if (!plan || !d_ctrl || !d_grad_ctrl) return fail(MSASM_EINVAL, "plan, d_ctrl or d_grad_ctrl is NULL");
   if ((d_u == nullptr) == (d_grad_values == nullptr))
     return fail(MSASM_EINVAL, "give exactly one of d_u and d_grad_values");
+  if (t0 < 0 || t1 < t0 || t1 > plan->n_tiles) return fail(MSASM_EINVAL, "tile range outside [0, n_tiles]");
   MSASM_TRY(check_material(E, nu));
   if (prec < MSASM_F64 || prec > MSASM_F64_EMU) return fail(MSASM_EINVAL, "unknown precision");
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   msasm_tables* tab = const_cast<msasm_tables*>(plan->tab);
   double lam, mu;
   lame(E, nu, lam, mu);
@@ -772,8 +822,9 @@ msasm_status msasm_assemble_grad(msasm_plan* plan, const double* d_ctrl, double 
   }
   MSASM_CUDA(cudaMemsetAsync(d_grad_ctrl, 0, size_t(plan->n_ctrl) * 3 * sizeof(double), s));
   const int64_t P = plan->tiles_per_pass;
-  for (int64_t t0 = 0; t0 < plan->n_tiles; t0 += P) {
-    const int64_t nt = std::min(P, plan->n_tiles - t0);
+  const int64_t t_lo = t0, t_hi = t1;
+  for (int64_t t0 = t_lo; t0 < t_hi; t0 += P) {
+    const int64_t nt = std::min(P, t_hi - t0);
     if (prec == MSASM_F64_EMU) {
       // W = G Tt^T on the tensor cores to FP64 accuracy: the contraction over the n_nz pairs is cut
       // into chunks of at most 576 (the exactness bound of the slice accumulators); each chunk's
@@ -789,7 +840,8 @@ msasm_status msasm_assemble_grad(msasm_plan* plan, const double* d_ctrl, double 
         const int kc = std::min(kAdjChunk, n_nz - m0);
         MSASM_TRY(emu_slice_gpu(tab->d_Tt + m0, K, n_nz, kc, tl, t_exp, s));
         MSASM_TRY(emu_slice_gpu(G + m0, 9 * nt, ld, kc, gl, g_exp, s));
-        MSASM_TRY(contract_emu_gpu(tl, t_exp, K, gl, g_exp, 9 * nt, kc, plan->d_coef, K, m0 > 0, plan->d_tc_err, s));
+        MSASM_TRY(contract_emu_gpu(tl, t_exp, K, gl, g_exp, 9 * nt, kc, plan->d_coef, K, m0 > 0, false,
+                                   plan->d_tc_err, s));
       }
     } else if (f64) {
       double* G = static_cast<double*>(plan->d_nz);
@@ -806,6 +858,21 @@ msasm_status msasm_assemble_grad(msasm_plan* plan, const double* d_ctrl, double 
     MSASM_TRY(adjoint_pullback_gpu(plan, d_ctrl, lam, mu, t0, nt, plan->d_coef, !f64, d_grad_ctrl, s));
   }
   return MSASM_OK;
+}
+
+msasm_status msasm_assemble_grad(msasm_plan* plan, const double* d_ctrl, double E, double nu, msasm_precision prec,
+                                 const void* d_u, const void* d_grad_values, double* d_grad_ctrl, void* stream) {
+  if (!plan) return fail(MSASM_EINVAL, "plan is NULL");
+  return grad_range_impl(plan, d_ctrl, E, nu, prec, 0, plan->n_tiles, d_u, d_grad_values, d_grad_ctrl,
+                         static_cast<cudaStream_t>(stream));
+}
+
+msasm_status msasm_assemble_grad_range(msasm_plan* plan, const double* d_ctrl, double E, double nu,
+                                       msasm_precision prec, int64_t t0, int64_t t1, const void* d_u,
+                                       const void* d_grad_values, double* d_grad_ctrl, void* stream) {
+  if (!plan) return fail(MSASM_EINVAL, "plan is NULL");
+  return grad_range_impl(plan, d_ctrl, E, nu, prec, t0, t1, d_u, d_grad_values, d_grad_ctrl,
+                         static_cast<cudaStream_t>(stream));
 }
 
 msasm_status msasm_linop_apply(msasm_plan* plan, const double* d_coef, msasm_precision prec, const double* d_u,
@@ -969,20 +1036,21 @@ msasm_status msasm_contract(const msasm_tables* tab, msasm_precision prec, const
   if (prec < MSASM_F64 || prec > MSASM_F64_EMU) return fail(MSASM_EINVAL, "unknown precision");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int n_nz = tab->n_nz, K = 9 * tab->n_pi, ld = ld_nz_of(n_nz);
-  // the public layout is dense (leading dimension n_nz); contract into a padded buffer and copy rows
+  // the public layout is dense (tile blocks n_nz x 9 values apart); contract into the kernels'
+  // padded layout (ld x 9 per tile) and copy each tile's run
   void* scratch = nullptr;
   void* lp = nullptr;
   unsigned* d_err = nullptr;
   const size_t vb = value_bytes(prec);
   (void)K;
-  MSASM_CUDA(cudaMallocAsync(&scratch, size_t(9 * n_tiles) * ld * vb, s));
+  MSASM_CUDA(cudaMallocAsync(&scratch, size_t(n_tiles) * 9 * ld * vb, s));
   MSASM_CUDA(cudaMallocAsync(&d_err, sizeof(unsigned), s));
   MSASM_CUDA(cudaMemsetAsync(d_err, 0, sizeof(unsigned), s));
   if (prec != MSASM_F64) MSASM_CUDA(cudaMallocAsync(&lp, coef_lp_bytes_for(n_tiles, tab->n_pi), s));
   msasm_status st = contract_dispatch(tab, prec, d_coef, n_tiles, scratch, lp, s, d_err);
   if (st == MSASM_OK) {
-    cudaError_t e = cudaMemcpy2DAsync(d_nz, size_t(n_nz) * vb, scratch, size_t(ld) * vb, size_t(n_nz) * vb,
-                                      size_t(9 * n_tiles), cudaMemcpyDeviceToDevice, s);
+    cudaError_t e = cudaMemcpy2DAsync(d_nz, size_t(9) * n_nz * vb, scratch, size_t(9) * ld * vb,
+                                      size_t(9) * n_nz * vb, size_t(n_tiles), cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) st = cuda_fail(e, "cudaMemcpy2DAsync(nz)");
   }
   unsigned h_err = 0;
@@ -1004,11 +1072,11 @@ msasm_status msasm_scatter(msasm_plan* plan, msasm_precision prec, const void* d
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int n_nz = plan->tab->n_nz, ld = ld_nz_of(n_nz);
   const size_t vb = value_bytes(prec);
-  // re-pad the dense public layout to the kernels' leading dimension
+  // re-pad the dense public layout to the kernels' (ld x 9 values per tile)
   void* padded = nullptr;
-  MSASM_CUDA(cudaMallocAsync(&padded, size_t(9 * plan->n_tiles) * ld * vb, s));
-  cudaError_t e = cudaMemcpy2DAsync(padded, size_t(ld) * vb, d_nz, size_t(n_nz) * vb, size_t(n_nz) * vb,
-                                    size_t(9 * plan->n_tiles), cudaMemcpyDeviceToDevice, s);
+  MSASM_CUDA(cudaMallocAsync(&padded, size_t(plan->n_tiles) * 9 * ld * vb, s));
+  cudaError_t e = cudaMemcpy2DAsync(padded, size_t(9) * ld * vb, d_nz, size_t(9) * n_nz * vb, size_t(9) * n_nz * vb,
+                                    size_t(plan->n_tiles), cudaMemcpyDeviceToDevice, s);
   msasm_status st = (e == cudaSuccess) ? scatter_dispatch(plan, prec, padded, 0, plan->n_tiles, d_values, s)
                                        : cuda_fail(e, "cudaMemcpy2DAsync(nz)");
   cudaFreeAsync(padded, s);

@@ -173,6 +173,7 @@ struct msasm_plan {
   std::vector<int> span_host[3];      // knot index of each element's span
   std::vector<int32_t> gmap_host;
   std::vector<int64_t> tile_vbase;    // host: first value index of the rows owned by tile t (n_tiles + 1)
+  std::vector<int64_t> tile_pbase;    // host: first global point id owned by tile t (n_tiles + 1)
   cudaStream_t copy_stream[2] = {nullptr, nullptr};   // device->host copies of msasm_assemble_host
   std::vector<cudaEvent_t> copy_events;
   // scratch

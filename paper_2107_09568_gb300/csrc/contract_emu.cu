@@ -53,7 +53,7 @@ struct EmuParams {
   int M, N, kblocks;
   const int* exp_m;        // sigma_m = 2^exp_m
   const int* exp_n;        // tau_n = 2^exp_n
-  double* out;             // nz[n][m], leading dimension ld
+  double* out;             // rows: out[n][m], leading dimension ld; blocks: out[n/9][m][n%9], m stride ld
   int ld;
   unsigned* err;
 };
@@ -110,7 +110,7 @@ __device__ __forceinline__ long long f32_to_i64_rn(float y) {
   return (b >> 31) ? -(long long)r : (long long)r;
 }
 
-template <bool ACCUMULATE>
+template <bool ACCUMULATE, bool BLOCKS>
 __global__ void __launch_bounds__(EMU_THREADS, 1)
     contract_emu_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, EmuParams p) {
   extern __shared__ uint8_t smem_raw[];
@@ -272,7 +272,9 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
         for (int j = 0; j < EMU_EPI_COLS; ++j) {
           const int n = n0 + j;
           if (n < p.N) {
-            double* o = p.out + size_t(n) * p.ld + m;
+            // rows: nz[n][m]; blocks: the tile block of eq. 58, nz[t][m][3a + b] for n = 9t + 3a + b
+            double* o = BLOCKS ? p.out + (size_t(n / 9) * size_t(p.ld) + size_t(m)) * 9 + (n % 9)
+                               : p.out + size_t(n) * p.ld + m;
             const double v = ldexp_i64_rn(X[j], em + p.exp_n[n]);
             if constexpr (ACCUMULATE) *o += v;
             else *o = v;
@@ -405,11 +407,15 @@ static msasm_status make_map_3d(CUtensorMap* map, const void* ptr, int64_t rows,
   return MSASM_OK;
 }
 
-// nz[n][m] (FP64, leading dimension ld) = sum_k A[m][k] B[n][k] from the slices of A (M rows) and B (N rows)
+// D[m][n] = sum_k A[m][k] B[n][k] (FP64) from the slices of A (M rows) and B (N rows), stored as
+// out[n][m] with leading dimension ld (blocks = false; accumulate adds to out), or as the tile
+// blocks of eq. 58, out[n/9][m][n%9] with m stride ld (blocks = true; N a multiple of 9).
 msasm_status contract_emu_gpu(const void* a_slices, const int* a_exp, int M, const void* b_slices,
-                              const int* b_exp, int64_t N, int K, double* out, int ld, bool accumulate,
+                              const int* b_exp, int64_t N, int K, double* out, int ld, bool accumulate, bool blocks,
                               unsigned* d_err, cudaStream_t s) {
   if (N > int64_t(2147483647) * EMU_BN) return fail(MSASM_EUNSUPPORTED, "too many rows for one launch");
+  if (blocks && (accumulate || N % 9 != 0))
+    return fail(MSASM_EINVAL, "the block layout takes whole tiles (N a multiple of 9) and no accumulation");
   CUtensorMap ma, mb;
   MSASM_TRY(make_map_3d(&ma, a_slices, M, K, EMU_BM));
   MSASM_TRY(make_map_3d(&mb, b_slices, N, K, EMU_BN));
@@ -422,7 +428,8 @@ msasm_status contract_emu_gpu(const void* a_slices, const int* a_exp, int M, con
   p.out = out;
   p.ld = ld;
   p.err = d_err;
-  auto kernel = accumulate ? contract_emu_kernel<true> : contract_emu_kernel<false>;
+  auto kernel = blocks ? contract_emu_kernel<false, true>
+                      : (accumulate ? contract_emu_kernel<true, false> : contract_emu_kernel<false, false>);
   MSASM_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, EMU_SMEM_BYTES));
   const long long tiles = ((N + EMU_BN - 1) / EMU_BN) * (long long)((M + EMU_BM - 1) / EMU_BM);
   if (tiles == 0) return MSASM_OK;

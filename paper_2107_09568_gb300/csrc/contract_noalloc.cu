@@ -12,17 +12,17 @@
 //  * The scratch is kNoAllocScratchBytes (32 MiB) in a static __device__ array.
 //    Every GPU on which this part of the library is loaded holds it until the
 //    process exits.
-//  * The scratch must hold 9 * n_tiles rows of the padded leading dimension
-//    (n_nz rounded up to 8) of FP64 values; larger requests fail with EINVAL and a
-//    message naming the limit.  No cudaMalloc, cudaFree or allocating library
+//  * The scratch must hold n_tiles padded tile runs of 9 * ld FP64 values (ld = n_nz
+//    rounded up to 8); larger requests fail with EINVAL and a message naming the
+//    limit.  No cudaMalloc, cudaFree or allocating library
 //    routine is called.
 //  * The device address of the array is looked up once per device with
 //    cudaGetSymbolAddress, during the first call made while that device is
 //    current; that first call should come before any stream capture is begun.
 //  * All calls share the one array and it keeps the last call's contents.  Every
 //    value a call reads from it was written earlier by the same call (the
-//    contraction kernel writes every element of the rows it uses and the copy
-//    reads only those), so nothing needs clearing.  Calls whose work overlaps on
+//    contraction kernel writes every value of the n_nz blocks of each tile and the
+//    copy reads only those), so nothing needs clearing.  Calls whose work overlaps on
 //    the GPU (different streams, or different host threads) race on the array and
 //    must be serialised by the caller.
 #include <mutex>
@@ -79,7 +79,7 @@ extern "C" msasm_status msasm_contract_noalloc(const msasm_tables* tab, const do
   MSASM_TRY(scratch_address(&scratch));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   MSASM_TRY(contract_simt_f64(d_coef, tab->d_T, n_tiles, n_nz, K, ld, scratch, s));
-  MSASM_CUDA(cudaMemcpy2DAsync(d_nz, size_t(n_nz) * sizeof(double), scratch, size_t(ld) * sizeof(double),
-                               size_t(n_nz) * sizeof(double), size_t(9 * n_tiles), cudaMemcpyDeviceToDevice, s));
+  MSASM_CUDA(cudaMemcpy2DAsync(d_nz, size_t(9) * n_nz * sizeof(double), scratch, size_t(9) * ld * sizeof(double),
+                               size_t(9) * n_nz * sizeof(double), size_t(n_tiles), cudaMemcpyDeviceToDevice, s));
   return MSASM_OK;
 }

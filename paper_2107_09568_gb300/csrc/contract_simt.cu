@@ -1,10 +1,11 @@
 // K3: the contraction of eq. 58 on the CUDA cores (FP64 DFMA or FP32 FFMA).
 //
-//   nz[n][m] = sum_k coef[n][k] * T[m][k],   n = 9t + 3a + b,  k = 9C + 3i + j,
+//   nz[t][m][3a + b] = sum_k coef[n][k] * T[m][k],   n = 9t + 3a + b,  k = 9C + 3i + j,
 //
-// i.e. nzdata^T = mat[<A>]^T mat[K]^T.  A 128 x 128 output tile per CTA, 256
-// threads with an 8 x 8 register tile each (two 4-wide groups per direction so
-// that the stores of a warp are contiguous), operands staged through shared
+// i.e. the tile blocks of nzdata = mat[K] mat[<A>] (the same GEMM serves the adjoint and the
+// surrogate with a plain row-major output C[n][m]).  A 128 x 128 output tile per CTA, 256
+// threads with an 8 x 8 register tile each (two 4-wide groups per direction, so
+// that in the row layout the stores of a warp are contiguous), operands staged through shared
 // memory k-major with a register prefetch of the next k-slab.  On GB300 the FP64
 // form is bound by the DFMA rate (about 1.2 TFLOP/s for the whole GPU), the FP32
 // form by the FFMA rate.
@@ -12,9 +13,10 @@
 
 namespace msasm {
 
-// C[n][m] = sum_k A[n][k] B[m][k] with row strides lda, ldb, ldc (the contraction uses A = coef,
-// B = table, C = nzdata; the adjoint uses A = G, B = the transposed table, C = W).
-template <typename T, int BK>
+// C[n][m] = sum_k A[n][k] B[m][k] with row strides lda, ldb, ldc (the adjoint uses A = G, B = the
+// transposed table, C = W); with BLOCKS the contraction's tile blocks C[n/9][m][n%9] with m stride
+// ld_nz (A = coef, B = table).
+template <typename T, int BK, bool BLOCKS>
 __global__ void __launch_bounds__(256) contract_simt_kernel(const T* __restrict__ coef, int64_t lda,
                                                             const T* __restrict__ tab, int64_t ldb, int64_t N, int M,
                                                             int K, int64_t ld_nz, T* __restrict__ nz) {
@@ -81,24 +83,39 @@ __global__ void __launch_bounds__(256) contract_simt_kernel(const T* __restrict_
   for (int i = 0; i < 8; ++i) {
     int64_t n = n0 + ((i < 4) ? ty * 4 + i : 64 + ty * 4 + (i - 4));
     if (n >= N) continue;
-    T* row = nz + n * ld_nz;
+    if constexpr (BLOCKS) {
+      T* blk = nz + (n / 9) * 9 * ld_nz + (n % 9);
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      int m = m0 + ((j < 4) ? tx * 4 + j : 64 + tx * 4 + (j - 4));
-      if (m < M) row[m] = acc[i][j];
+      for (int j = 0; j < 8; ++j) {
+        int m = m0 + ((j < 4) ? tx * 4 + j : 64 + tx * 4 + (j - 4));
+        if (m < M) blk[int64_t(m) * 9] = acc[i][j];
+      }
+    } else {
+      T* row = nz + n * ld_nz;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        int m = m0 + ((j < 4) ? tx * 4 + j : 64 + tx * 4 + (j - 4));
+        if (m < M) row[m] = acc[i][j];
+      }
     }
   }
+}
+
+template <typename T, bool BLOCKS>
+static msasm_status gemm_simt_any(const T* A, int64_t lda, const T* B, int64_t ldb, int64_t N, int M, int K, T* C,
+                                  int64_t ldc, cudaStream_t stream) {
+  dim3 grid(unsigned((M + 127) / 128), unsigned((N + 127) / 128));
+  if (grid.y > 65535) return fail(MSASM_EUNSUPPORTED, "too many rows for one CUDA-core contraction");
+  constexpr int BK = sizeof(T) == 8 ? 8 : 16;
+  contract_simt_kernel<T, BK, BLOCKS><<<grid, 256, 0, stream>>>(A, lda, B, ldb, N, M, K, ldc, C);
+  MSASM_CUDA(cudaGetLastError());
+  return MSASM_OK;
 }
 
 template <typename T>
 msasm_status gemm_simt(const T* A, int64_t lda, const T* B, int64_t ldb, int64_t N, int M, int K, T* C, int64_t ldc,
                        cudaStream_t stream) {
-  dim3 grid(unsigned((M + 127) / 128), unsigned((N + 127) / 128));
-  if (grid.y > 65535) return fail(MSASM_EUNSUPPORTED, "too many rows for one CUDA-core contraction");
-  constexpr int BK = sizeof(T) == 8 ? 8 : 16;
-  contract_simt_kernel<T, BK><<<grid, 256, 0, stream>>>(A, lda, B, ldb, N, M, K, ldc, C);
-  MSASM_CUDA(cudaGetLastError());
-  return MSASM_OK;
+  return gemm_simt_any<T, false>(A, lda, B, ldb, N, M, K, C, ldc, stream);
 }
 template msasm_status gemm_simt<double>(const double*, int64_t, const double*, int64_t, int64_t, int, int, double*,
                                         int64_t, cudaStream_t);
@@ -107,12 +124,12 @@ template msasm_status gemm_simt<float>(const float*, int64_t, const float*, int6
 
 msasm_status contract_simt_f64(const double* d_coef, const double* d_T, int64_t n_tiles, int n_nz, int K, int ld_nz,
                                double* d_nz, cudaStream_t stream) {
-  return gemm_simt<double>(d_coef, K, d_T, K, 9 * n_tiles, n_nz, K, d_nz, ld_nz, stream);
+  return gemm_simt_any<double, true>(d_coef, K, d_T, K, 9 * n_tiles, n_nz, K, d_nz, ld_nz, stream);
 }
 
 msasm_status contract_simt_f32(const float* d_coef, const float* d_T, int64_t n_tiles, int n_nz, int K, int ld_nz,
                                float* d_nz, cudaStream_t stream) {
-  return gemm_simt<float>(d_coef, K, d_T, K, 9 * n_tiles, n_nz, K, d_nz, ld_nz, stream);
+  return gemm_simt_any<float, true>(d_coef, K, d_T, K, 9 * n_tiles, n_nz, K, d_nz, ld_nz, stream);
 }
 
 // FP64 -> FP32 conversion of an operand (round to nearest).

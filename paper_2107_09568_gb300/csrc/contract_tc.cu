@@ -13,14 +13,21 @@
 // Keeping the small cross terms in their own accumulator keeps their FP32 accumulation error
 // relative to the small terms instead of to the whole sum.
 //
-// Persistent kernel, one CTA per SM looping over 128 (m) x 256 (n) output tiles; 10 warps: warp 0
-// issues TMA loads (128-byte swizzled K-major boxes) into a 2-stage shared-memory ring that runs
-// on across tiles, warp 1 owns the TMEM allocation and one elected lane issues tcgen05.mma
-// (M=128, N=256, K=16 for f16/bf16, K=8 for tf32), warps 2-9 (two per 32-lane TMEM quarter, 128
-// columns each) drain the accumulators into registers, release TMEM so that the next tile's MMAs
-// start, then scale and store nz with the rows of a warp contiguous in m.  Every mbarrier wait is
-// bounded; on a timeout (or another thread's) the CTA records the error flag, drains what it
-// issued and returns.
+// Persistent kernel, one CTA per SM looping over 128 (m) x BN (n) output tiles; 10 warps: warp 0
+// issues TMA loads (128-byte swizzled K-major boxes) into a shared-memory ring that runs on across
+// tiles, warp 1 owns the TMEM allocation and one elected lane issues tcgen05.mma (M=128, N=BN,
+// K=16 for f16/bf16, K=8 for tf32), warps 2-9 (two per 32-lane TMEM quarter, BN/2 columns each)
+// drain the accumulators into registers, release TMEM so that the next tile's MMAs start, then
+// scale and store.  Two output layouts:
+//   rows   (BN = 256, 2 stages): out[n][m], the rows of a warp contiguous in m (the MLP's output
+//          layer uses it);
+//   blocks (BN = 144 = lcm(16, 9), 3 stages): the tile blocks of eq. 58, out[t][m][3a + b] for
+//          n = 9t + 3a + b, which the scatter reads block by block.  Each epilogue warp holds whole
+//          tile blocks (72 columns = 8 tiles) for its 32 rows m; per tile it passes the 32 x 9 values
+//          through a small shared-memory buffer so that each store instruction writes 32
+//          consecutive floats of the tile's contiguous 32 x 9 run.
+// Every mbarrier wait is bounded; on a timeout (or another thread's) the CTA records the error
+// flag, drains what it issued and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -37,13 +44,22 @@ namespace msasm {
 enum SplitKind { kSplitF16 = 0, kSplitBF16 = 1, kTF32 = 2, kTF32x3 = 3 };
 
 constexpr int TC_BM = 128;          // rows of a CTA tile (TMEM lanes), table rows m
-constexpr int TC_BN = 256;          // columns of a CTA tile (TMEM columns), coefficient rows n
 constexpr int TC_ROW_BYTES = 128;   // one swizzle row: 64 x 16-bit or 32 x 32-bit elements of k
-constexpr int TC_STAGES = 2;
 constexpr int TC_A_BYTES = TC_BM * TC_ROW_BYTES;   // 16 KB
-constexpr int TC_B_BYTES = TC_BN * TC_ROW_BYTES;   // 32 KB
-constexpr int TC_STAGE_BYTES = 2 * TC_A_BYTES + 2 * TC_B_BYTES;
-constexpr int TC_SMEM_BYTES = TC_STAGES * TC_STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+
+// shape of the kernel for an n tile of BN columns (256: row layout; 144: block layout)
+template <int BN>
+struct TcShape {
+  static constexpr bool kBlocks = (BN % 9 == 0);
+  static constexpr int kStages = kBlocks ? 3 : 2;
+  static constexpr int kBBytes = BN * TC_ROW_BYTES;                          // 18 KB / 32 KB
+  static constexpr int kStageBytes = 2 * TC_A_BYTES + 2 * kBBytes;
+  static constexpr int kStagingFloats = 32 * 9;                              // one tile run of a warp
+  static constexpr int kStagingBytes = kBlocks ? 8 * kStagingFloats * 4 : 0;
+  static constexpr int kSmemBytes = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/ + kStagingBytes;
+  static_assert(BN % 16 == 0 && BN <= 256, "tcgen05 M=128 needs N a multiple of 16, at most 256");
+  static_assert(kSmemBytes <= 227 * 1024, "shared memory per CTA");
+};
 
 struct TcParams {
   int M, N, K;             // logical sizes: m rows, n rows, k
@@ -51,7 +67,7 @@ struct TcParams {
   int kind;                // SplitKind
   const float* scale_m;    // per-row 2^-e for split FP16 (else null)
   const float* scale_n;
-  float* out;              // nz[n][m], leading dimension ld
+  float* out;              // rows: out[n][m], leading dimension ld; blocks: out[n/9][m][n%9], m stride ld
   int ld;
   unsigned* err;           // set to 1 on a timed-out wait
 };
@@ -59,26 +75,31 @@ struct TcParams {
 // ------------------------------------------------------------------ the kernel
 constexpr int TC_EPI_WARPS = 8;                          // two per TMEM lane quarter
 constexpr int TC_THREADS = 64 + 32 * TC_EPI_WARPS;       // producer warp, MMA warp, epilogue warps
-constexpr int TC_EPI_COLS = TC_BN / 2;                   // columns of one epilogue warp
 
+template <int BN>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     contract_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
                        const __grid_constant__ CUtensorMap tmB_hi, const __grid_constant__ CUtensorMap tmB_lo,
                        TcParams p) {
+  using S = TcShape<BN>;
+  constexpr int STAGES = S::kStages, STAGE_BYTES = S::kStageBytes, B_BYTES = S::kBBytes;
+  constexpr int EPI_COLS = BN / 2;                             // columns of one epilogue warp
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;               // 1024-B alignment for the swizzle atoms
   uint8_t* gen_base = smem_raw + (base - raw);
-  const uint32_t bar0 = base + TC_STAGES * TC_STAGE_BYTES;     // barriers after the stages
+  const uint32_t bar0 = base + STAGES * STAGE_BYTES;          // barriers after the stages
   // barrier layout: full[S], empty[S], accum_full, tmem_empty, then the TMEM address slot
   auto full_bar = [&](int s) { return bar0 + 8u * s; };
-  auto empty_bar = [&](int s) { return bar0 + 8u * (TC_STAGES + s); };
-  const uint32_t accum_full = bar0 + 8u * (2 * TC_STAGES);
-  const uint32_t tmem_empty = bar0 + 8u * (2 * TC_STAGES + 1);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gen_base + TC_STAGES * TC_STAGE_BYTES + 8 * (2 * TC_STAGES + 2));
+  auto empty_bar = [&](int s) { return bar0 + 8u * (STAGES + s); };
+  const uint32_t accum_full = bar0 + 8u * (2 * STAGES);
+  const uint32_t tmem_empty = bar0 + 8u * (2 * STAGES + 1);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gen_base + STAGES * STAGE_BYTES + 8 * (2 * STAGES + 2));
+  // block layout: one 32 x 9 staging run per epilogue warp after the barrier area
+  float* staging = reinterpret_cast<float*>(gen_base + STAGES * STAGE_BYTES + 256);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n_mt = (p.M + TC_BM - 1) / TC_BM, n_nt = (p.N + TC_BN - 1) / TC_BN;
+  const int n_mt = (p.M + TC_BM - 1) / TC_BM, n_nt = (p.N + BN - 1) / BN;
   // tile t: m tile t % n_mt, n tile t / n_mt (CTAs running together share the coefficient tile and
   // sweep the table, the smaller operand, which stays in L2)
   const long long total = (long long)n_mt * n_nt;
@@ -86,10 +107,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const bool with_lo = (p.kind != kTF32);
   const float lo_weight = (p.kind == kSplitF16) ? 1.0f / 2048.0f : 1.0f;
   const uint32_t tmem_cols = two_acc ? 512u : 256u;
-  const uint32_t stage_tx = with_lo ? TC_STAGE_BYTES : (TC_A_BYTES + TC_B_BYTES);
+  const uint32_t stage_tx = with_lo ? STAGE_BYTES : (TC_A_BYTES + B_BYTES);
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < TC_STAGES; ++s) {
+    for (int s = 0; s < STAGES; ++s) {
       mbar_init(full_bar(s), 1);
       mbar_init(empty_bar(s), 1);
     }
@@ -115,32 +136,32 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     uint32_t g = 0;
     bool ok = true;
     for (long long t = blockIdx.x; t < total && ok; t += gridDim.x) {
-      const int m0 = int(t % n_mt) * TC_BM, n0 = int(t / n_mt) * TC_BN;
+      const int m0 = int(t % n_mt) * TC_BM, n0 = int(t / n_mt) * BN;
       for (int kb = 0; kb < p.kblocks; ++kb, ++g) {
-        const int s = int(g % TC_STAGES);
-        const uint32_t it = g / TC_STAGES;
+        const int s = int(g % STAGES);
+        const uint32_t it = g / STAGES;
         if (it > 0 && !mbar_wait_or_abort(empty_bar(s), (it - 1) & 1, p.err)) {
           ok = false;
           break;
         }
-        const uint32_t st = base + s * TC_STAGE_BYTES;
+        const uint32_t st = base + s * STAGE_BYTES;
         const int kx = kb * (p.kind >= kTF32 ? 32 : 64);       // element coordinate of the block
         mbar_expect_tx(full_bar(s), stage_tx);
         tma_load_2d(st, &tmA_hi, kx, m0, full_bar(s));
         tma_load_2d(st + 2 * TC_A_BYTES, &tmB_hi, kx, n0, full_bar(s));
         if (with_lo) {
           tma_load_2d(st + TC_A_BYTES, &tmA_lo, kx, m0, full_bar(s));
-          tma_load_2d(st + 2 * TC_A_BYTES + TC_B_BYTES, &tmB_lo, kx, n0, full_bar(s));
+          tma_load_2d(st + 2 * TC_A_BYTES + B_BYTES, &tmB_lo, kx, n0, full_bar(s));
         }
       }
     }
     // every issued copy has landed before the CTA can exit (bounded)
-    for (uint32_t q = (g > uint32_t(TC_STAGES) ? g - TC_STAGES : 0u); q < g; ++q)
-      mbar_wait(full_bar(int(q % TC_STAGES)), (q / TC_STAGES) & 1, p.err);
+    for (uint32_t q = (g > uint32_t(STAGES) ? g - STAGES : 0u); q < g; ++q)
+      mbar_wait(full_bar(int(q % STAGES)), (q / STAGES) & 1, p.err);
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
     const bool tf = p.kind >= kTF32;
-    const uint32_t idesc = instr_desc(p.kind == kSplitF16 ? 0u : (tf ? 2u : 1u), TC_BM, TC_BN);
+    const uint32_t idesc = instr_desc(p.kind == kSplitF16 ? 0u : (tf ? 2u : 1u), TC_BM, BN);
     const int ksteps = 4;                                       // 4 x 32 B of k per 128-B row
     const uint32_t acc0 = tmem, acc1 = tmem + (two_acc ? 256u : 0u);
     uint32_t g = 0, i_tile = 0;
@@ -151,16 +172,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         tc_fence_after();
       }
       for (int kb = 0; kb < p.kblocks; ++kb, ++g) {
-        const int s = int(g % TC_STAGES);
-        const uint32_t it = g / TC_STAGES;
+        const int s = int(g % STAGES);
+        const uint32_t it = g / STAGES;
         if (!mbar_wait_or_abort(full_bar(s), it & 1, p.err)) {
           ok = false;
           break;
         }
         tc_fence_after();
-        const uint32_t st = base + s * TC_STAGE_BYTES;
+        const uint32_t st = base + s * STAGE_BYTES;
         const uint64_t a_hi = sw128_desc(st), a_lo = sw128_desc(st + TC_A_BYTES);
-        const uint64_t b_hi = sw128_desc(st + 2 * TC_A_BYTES), b_lo = sw128_desc(st + 2 * TC_A_BYTES + TC_B_BYTES);
+        const uint64_t b_hi = sw128_desc(st + 2 * TC_A_BYTES), b_lo = sw128_desc(st + 2 * TC_A_BYTES + B_BYTES);
 #pragma unroll
         for (int j = 0; j < ksteps; ++j) {
           const uint64_t dk = uint64_t(2 * j);                    // +32 bytes of k, in 16-byte units
@@ -186,37 +207,60 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     if (i_tile > 0) mbar_wait(accum_full, (i_tile - 1) & 1, p.err);   // nothing in flight at exit
   } else if (warp >= 2) {
-    // ---------------- epilogue: drain TMEM into registers, release it, scale and store nz[n][m]
+    // ---------------- epilogue: drain TMEM into registers, release it, scale and store
     const int q = warp & 3;                                      // TMEM lane quarter of this warp
     const int h = (warp - 2) >> 2;                               // column half
     const uint32_t lane_off = uint32_t(32 * q) << 16;
+    float* stg = staging + (warp - 2) * S::kStagingFloats;
     uint32_t i_tile = 0;
     for (long long t = blockIdx.x; t < total; t += gridDim.x, ++i_tile) {
       if (!mbar_wait_or_abort(accum_full, i_tile & 1, p.err)) break;
       tc_fence_after();
-      const int m0 = int(t % n_mt) * TC_BM, n0 = int(t / n_mt) * TC_BN + h * TC_EPI_COLS;
-      float R[TC_EPI_COLS];
+      const int m0 = int(t % n_mt) * TC_BM, n0 = int(t / n_mt) * BN + h * EPI_COLS;
+      float R[EPI_COLS];
 #pragma unroll
-      for (int c = 0; c < TC_EPI_COLS / 16; ++c) {
-        float v[16];
-        tmem_ld16(tmem + lane_off + uint32_t(h * TC_EPI_COLS + 16 * c), v);
-        if (two_acc) {
-          float w[16];
-          tmem_ld16(tmem + 256u + lane_off + uint32_t(h * TC_EPI_COLS + 16 * c), w);
+      for (int c = 0; c < EPI_COLS / 8; ++c) {
+        uint32_t v[8], w[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+        tmem_ld8_nowait(tmem + lane_off + uint32_t(h * EPI_COLS + 8 * c), v);
+        if (two_acc) tmem_ld8_nowait(tmem + 256u + lane_off + uint32_t(h * EPI_COLS + 8 * c), w);
+        tmem_wait_ld();
 #pragma unroll
-          for (int j = 0; j < 16; ++j) v[j] = fmaf(w[j], lo_weight, v[j]);
+        for (int j = 0; j < 8; ++j) {
+          asm volatile("" : "+r"(v[j]), "+r"(w[j]));             // uses stay after the wait
+          R[8 * c + j] = two_acc ? fmaf(__uint_as_float(w[j]), lo_weight, __uint_as_float(v[j]))
+                                 : __uint_as_float(v[j]);
         }
-#pragma unroll
-        for (int j = 0; j < 16; ++j) R[16 * c + j] = v[j];
       }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(tmem_empty);                    // the MMAs of the next tile may start
       const int m = m0 + 32 * q + lane;
-      if (m < p.M) {
-        const float sm = p.scale_m ? p.scale_m[m] : 1.0f;
+      const float sm = (p.scale_m && m < p.M) ? p.scale_m[m] : 1.0f;
+      if constexpr (S::kBlocks) {
+        // n0 is a multiple of 9: the warp holds EPI_COLS / 9 whole tile blocks of its 32 rows
+        const int mr0 = m0 + 32 * q;
 #pragma unroll
-        for (int j = 0; j < TC_EPI_COLS; ++j) {
+        for (int b = 0; b < EPI_COLS / 9; ++b) {
+          const int nb = n0 + 9 * b;
+          if (nb >= p.N) break;                                  // N = 9 n_tiles: whole blocks only
+#pragma unroll
+          for (int k = 0; k < 9; ++k) {
+            float val = R[9 * b + k];
+            if (p.scale_m) val *= sm * p.scale_n[nb + k];
+            stg[lane * 9 + k] = val;                              // stride 9: no bank conflicts
+          }
+          __syncwarp();
+          float* dst = p.out + (size_t(nb / 9) * size_t(p.ld) + size_t(mr0)) * 9;
+#pragma unroll
+          for (int j = 0; j < 9; ++j) {
+            const int e = 32 * j + lane;                          // element of the 32 x 9 run
+            if (mr0 + e / 9 < p.M) dst[e] = stg[e];
+          }
+          __syncwarp();
+        }
+      } else if (m < p.M) {
+#pragma unroll
+        for (int j = 0; j < EPI_COLS; ++j) {
           const int n = n0 + j;
           if (n < p.N) {
             float val = R[j];
@@ -354,19 +398,39 @@ msasm_status tc_split_f32_gpu(const float* x, int64_t rows, int K, int kind, voi
   return tc_split_any<float>(x, rows, K, kind, hi, lo, row_scale, s);
 }
 
-// nz[n][m] (FP32, leading dimension ld) from sliced operands A (table, M rows) and B (coef, N rows).
+template <int BN>
+static msasm_status launch_tc(const CUtensorMap& ma_hi, const CUtensorMap& ma_lo, const CUtensorMap& mb_hi,
+                              const CUtensorMap& mb_lo, const TcParams& p, cudaStream_t s) {
+  constexpr int smem = TcShape<BN>::kSmemBytes;
+  MSASM_CUDA(cudaFuncSetAttribute(contract_tc_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  const long long tiles = ((p.M + TC_BM - 1) / TC_BM) * (long long)((p.N + BN - 1) / BN);
+  if (tiles == 0) return MSASM_OK;
+  int dev = 0, n_sm = 0;
+  MSASM_CUDA(cudaGetDevice(&dev));
+  MSASM_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+  const unsigned grid = unsigned(std::min<long long>(tiles, std::max(n_sm, 1)));   // one CTA per SM
+  contract_tc_kernel<BN><<<grid, TC_THREADS, smem, s>>>(ma_hi, ma_lo, mb_hi, mb_lo, p);
+  MSASM_CUDA(cudaGetLastError());
+  return MSASM_OK;
+}
+
+// D[m][n] = sum_k A[m][k] B[n][k] (FP32) from sliced operands A (table, M rows) and B (coef, N
+// rows), stored as out[n][m] with leading dimension ld (blocks = false), or as the tile blocks of
+// eq. 58, out[n/9][m][n%9] with m stride ld (blocks = true; N a multiple of 9).
 msasm_status contract_tc_gpu(int kind, const void* a_hi, const void* a_lo, const float* a_scale, int M,
                              const void* b_hi, const void* b_lo, const float* b_scale, int64_t N, int K, float* out,
-                             int ld, unsigned* d_err, cudaStream_t s) {
+                             int ld, bool blocks, unsigned* d_err, cudaStream_t s) {
   MSASM_TRY(get_encoder());
   if (N > int64_t(2147483647)) return fail(MSASM_EUNSUPPORTED, "too many coefficient rows for one launch");
+  if (blocks && N % 9 != 0) return fail(MSASM_EINVAL, "the block layout needs whole tiles (N a multiple of 9)");
   const int Kpad = tc_kpad(K, kind);
+  const int bn = blocks ? 144 : 256;
   CUtensorMap ma_hi, ma_lo, mb_hi, mb_lo;
   MSASM_TRY(make_map(&ma_hi, a_hi, kind, M, K, Kpad, TC_BM));
-  MSASM_TRY(make_map(&mb_hi, b_hi, kind, N, K, Kpad, TC_BN));
+  MSASM_TRY(make_map(&mb_hi, b_hi, kind, N, K, Kpad, bn));
   if (kind != kTF32) {
     MSASM_TRY(make_map(&ma_lo, a_lo, kind, M, K, Kpad, TC_BM));
-    MSASM_TRY(make_map(&mb_lo, b_lo, kind, N, K, Kpad, TC_BN));
+    MSASM_TRY(make_map(&mb_lo, b_lo, kind, N, K, Kpad, bn));
   } else {
     ma_lo = ma_hi;
     mb_lo = mb_hi;
@@ -382,16 +446,7 @@ msasm_status contract_tc_gpu(int kind, const void* a_hi, const void* a_lo, const
   p.out = out;
   p.ld = ld;
   p.err = d_err;
-  MSASM_CUDA(cudaFuncSetAttribute(contract_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BYTES));
-  const long long tiles = ((M + TC_BM - 1) / TC_BM) * ((N + TC_BN - 1) / TC_BN);
-  if (tiles == 0) return MSASM_OK;
-  int dev = 0, n_sm = 0;
-  MSASM_CUDA(cudaGetDevice(&dev));
-  MSASM_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
-  const unsigned grid = unsigned(std::min<long long>(tiles, std::max(n_sm, 1)));   // one CTA per SM
-  contract_tc_kernel<<<grid, TC_THREADS, TC_SMEM_BYTES, s>>>(ma_hi, ma_lo, mb_hi, mb_lo, p);
-  MSASM_CUDA(cudaGetLastError());
-  return MSASM_OK;
+  return blocks ? launch_tc<144>(ma_hi, ma_lo, mb_hi, mb_lo, p, s) : launch_tc<256>(ma_hi, ma_lo, mb_hi, mb_lo, p, s);
 }
 
 }  // namespace msasm

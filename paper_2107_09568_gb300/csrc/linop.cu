@@ -91,10 +91,10 @@ __global__ void linop_secondary_kernel(const T* __restrict__ nz, int ld_nz, int6
     const SecondaryEntry r = sec[i];
     const int m = int(r.m_flags & 0x3fffffffu);
     const int64_t t = r.tile;
-    const T* src = nz + 9 * (t - t0) * ld_nz + m;
+    const T* src = nz + 9 * ((t - t0) * ld_nz + m);     // the tile block of pair m (9 values)
     double v[9];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) v[k] = double(src[size_t(k) * ld_nz]);
+    for (int k = 0; k < 9; ++k) v[k] = double(src[k]);
     const int64_t gA = gmap[t * n_T + pairs[2 * m]], gB = gmap[t * n_T + pairs[2 * m + 1]];
     if (r.m_flags & (1u << 30)) {                  // rows of A: sum_b blk[a][b] u_B,b
       const double u0 = u[3 * gB], u1 = u[3 * gB + 1], u2 = u[3 * gB + 2];

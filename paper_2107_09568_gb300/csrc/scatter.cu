@@ -5,10 +5,13 @@
 // r_u | r_l << 16 of the plan the upper entry (a, b) lives at rowptr[3 g(A) + a] + 3 r_u + b and
 // the lower one at rowptr[3 g(B) + b] + 3 r_l + a.
 //
+// nzdata holds the tile blocks of eq. 58 block by block: nz[t][m][3a + b], so the nine values of
+// pair m of tile t are one contiguous 9-value run at 9 (t ld + m).
+//
 // Direct pass: the rows of the points a tile owns are one contiguous range of values, laid out
 // the same way for every tile of its type.  The type's value map (built once per plan from its
 // representative tile) holds for every value of the range its source in the tile's nzdata,
-// (3a + b) ld + m, or -1 where no block of the tile lands; each thread writes consecutive values
+// 9 m + 3a + b, or -1 where no block of the tile lands; each thread writes consecutive values
 // of the range (coalesced stores) from gathers that the tile's nzdata, read by the CTAs working
 // on the tile at the same time, serves mostly from L2.  Every CSR value is written exactly once.
 //
@@ -16,6 +19,11 @@
 // face) are added to the values the owner wrote; it runs after the direct pass on the same
 // stream and each position has at most one such contributor, so no atomics are needed and the
 // two-term sums are order independent.
+//
+// Both passes write into a window [v_lo, v_hi) of the global values (values[0] is value v_lo):
+// the whole array for a full assembly, or the rows owned by a range of tiles when one mesh is
+// split across GPUs (the direct pass then covers the range's tiles and the secondary pass also
+// the halo tiles above it, whose blocks land partly in the window).
 #include <algorithm>
 #include <cstdint>
 
@@ -31,14 +39,14 @@ __global__ void __launch_bounds__(kDirectThreads) scatter_direct_kernel(
     const T* __restrict__ nz, int ld_nz, int64_t t0, const int32_t* __restrict__ item_tile,
     const int32_t* __restrict__ item_start, const int64_t* __restrict__ tile_vbase,
     const int32_t* __restrict__ tile_type, const int64_t* __restrict__ type_map_off,
-    const int32_t* __restrict__ type_nvals, const int32_t* __restrict__ maps, T* __restrict__ values) {
+    const int32_t* __restrict__ type_nvals, const int32_t* __restrict__ maps, T* __restrict__ values, int64_t v_lo) {
   const int64_t t = item_tile[blockIdx.x];
   const int s0 = item_start[blockIdx.x];
   const int ty = tile_type[t];
   const int end = min(s0 + kScatterSegment, type_nvals[ty]);
   const int32_t* map = maps + type_map_off[ty];
   const T* nzt = nz + 9 * (t - t0) * ld_nz;
-  T* out = values + tile_vbase[t];
+  T* out = values + (tile_vbase[t] - v_lo);
   int k[kDirectPerThread];
 #pragma unroll
   for (int u = 0; u < kDirectPerThread; ++u) {
@@ -74,13 +82,13 @@ __global__ void type_maps_kernel(const int64_t* __restrict__ type_rep, int n_typ
       const int64_t L = rowptr[3 * gA + 1] - rowptr[3 * gA];
       const int64_t o = rA + 3 * int64_t(w & 0xffffu);
       for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b) map[o + a * L + b] = int32_t((3 * a + b) * ld_nz + m);
+        for (int b = 0; b < 3; ++b) map[o + a * L + b] = int32_t(9 * m + 3 * a + b);
     }
     if (A != B && rB >= 0 && rB < nv) {            // B owned: lower block in the rows of B
       const int64_t L = rowptr[3 * gB + 1] - rowptr[3 * gB];
       const int64_t o = rB + 3 * int64_t((w >> 16) & 0x7fffu);
       for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b) map[o + b * L + a] = int32_t((3 * a + b) * ld_nz + m);
+        for (int b = 0; b < 3; ++b) map[o + b * L + a] = int32_t(9 * m + 3 * a + b);
     }
   }
 }
@@ -161,27 +169,29 @@ msasm_status secondary_entries_gpu(msasm_plan* plan, cudaStream_t stream) {
 // owner of its rows wrote.
 template <typename T>
 __global__ void scatter_secondary_kernel(const T* __restrict__ nz, int ld_nz, int64_t t0, int64_t e0, int64_t e1,
-                                         const SecondaryEntry* __restrict__ sec, T* __restrict__ values) {
+                                         const SecondaryEntry* __restrict__ sec, T* __restrict__ values, int64_t v_lo,
+                                         int64_t v_hi) {
   for (int64_t i = e0 + int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < e1; i += int64_t(gridDim.x) * blockDim.x) {
     const SecondaryEntry r = sec[i];
     const int m = int(r.m_flags & 0x3fffffffu);
-    const T* src = nz + 9 * (int64_t(r.tile) - t0) * ld_nz + m;
+    const T* src = nz + 9 * ((int64_t(r.tile) - t0) * ld_nz + m);   // the block's contiguous run
     T v[9];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) v[k] = src[size_t(k) * ld_nz];
-    if (r.m_flags & (1u << 30)) {
+    for (int k = 0; k < 9; ++k) v[k] = src[k];
+    // the three rows of a point belong to one owner: the first row decides whether a block is in the window
+    if ((r.m_flags & (1u << 30)) && r.dst_u >= v_lo && r.dst_u < v_hi) {
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        T* d = values + r.dst_u + int64_t(a) * r.len_u;
+        T* d = values + (r.dst_u - v_lo) + int64_t(a) * r.len_u;
         d[0] += v[3 * a + 0];
         d[1] += v[3 * a + 1];
         d[2] += v[3 * a + 2];
       }
     }
-    if (r.m_flags & (1u << 31)) {
+    if ((r.m_flags & (1u << 31)) && r.dst_l >= v_lo && r.dst_l < v_hi) {
 #pragma unroll
       for (int b = 0; b < 3; ++b) {
-        T* d = values + r.dst_l + int64_t(b) * r.len_l;
+        T* d = values + (r.dst_l - v_lo) + int64_t(b) * r.len_l;
         d[0] += v[b];
         d[1] += v[3 + b];
         d[2] += v[6 + b];
@@ -190,29 +200,43 @@ __global__ void scatter_secondary_kernel(const T* __restrict__ nz, int ld_nz, in
   }
 }
 
-// steps 4 for tiles [t0, t0 + n_tiles) of the plan, nzdata of those tiles in d_nz
+// step 4 for tiles [t0, t0 + n_tiles) of the plan, nzdata of those tiles in d_nz: the direct pass
+// for the tiles below direct_end, the secondary pass for all of them, into the value window
+// [v_lo, v_hi) (d_values holds value v_lo first)
 template <typename T>
 msasm_status scatter_pass_gpu(const msasm_plan* plan, const T* d_nz, int ld_nz, int64_t t0, int64_t n_tiles,
-                              T* d_values, cudaStream_t stream) {
-  const int64_t i0 = plan->item_ptr[size_t(t0)], i1 = plan->item_ptr[size_t(t0 + n_tiles)];
+                              T* d_values, int64_t direct_end, int64_t v_lo, int64_t v_hi, cudaStream_t stream) {
+  const int64_t td = std::max(t0, std::min(t0 + n_tiles, direct_end));
+  const int64_t i0 = plan->item_ptr[size_t(t0)], i1 = plan->item_ptr[size_t(td)];
   if (i1 > i0) {
     scatter_direct_kernel<T><<<unsigned(i1 - i0), kDirectThreads, 0, stream>>>(
         d_nz, ld_nz, t0, plan->d_item_tile + i0, plan->d_item_start + i0, plan->d_tile_vbase, plan->d_tile_type,
-        plan->d_type_map_off, plan->d_type_nvals, plan->d_maps, d_values);
+        plan->d_type_map_off, plan->d_type_nvals, plan->d_maps, d_values, v_lo);
     MSASM_CUDA(cudaGetLastError());
   }
   const int64_t e0 = plan->sec_off_host[size_t(t0)], e1 = plan->sec_off_host[size_t(t0 + n_tiles)];
   if (e1 > e0) {
     const int64_t blocks = std::min<int64_t>((e1 - e0 + 255) / 256, 152 * 16);
-    scatter_secondary_kernel<T><<<unsigned(blocks), 256, 0, stream>>>(d_nz, ld_nz, t0, e0, e1, plan->d_sec, d_values);
+    scatter_secondary_kernel<T><<<unsigned(blocks), 256, 0, stream>>>(d_nz, ld_nz, t0, e0, e1, plan->d_sec, d_values,
+                                                                      v_lo, v_hi);
     MSASM_CUDA(cudaGetLastError());
   }
   return MSASM_OK;
+}
+
+template <typename T>
+msasm_status scatter_pass_gpu(const msasm_plan* plan, const T* d_nz, int ld_nz, int64_t t0, int64_t n_tiles,
+                              T* d_values, cudaStream_t stream) {
+  return scatter_pass_gpu<T>(plan, d_nz, ld_nz, t0, n_tiles, d_values, t0 + n_tiles, 0, plan->nnz, stream);
 }
 
 template msasm_status scatter_pass_gpu<double>(const msasm_plan*, const double*, int, int64_t, int64_t, double*,
                                                cudaStream_t);
 template msasm_status scatter_pass_gpu<float>(const msasm_plan*, const float*, int, int64_t, int64_t, float*,
                                               cudaStream_t);
+template msasm_status scatter_pass_gpu<double>(const msasm_plan*, const double*, int, int64_t, int64_t, double*,
+                                               int64_t, int64_t, int64_t, cudaStream_t);
+template msasm_status scatter_pass_gpu<float>(const msasm_plan*, const float*, int, int64_t, int64_t, float*, int64_t,
+                                              int64_t, int64_t, cudaStream_t);
 
 }  // namespace msasm

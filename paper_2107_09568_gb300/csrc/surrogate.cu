@@ -29,7 +29,7 @@ msasm_status tc_split_f32_gpu(const float* x, int64_t rows, int K, int kind, voi
                               cudaStream_t s);
 msasm_status contract_tc_gpu(int kind, const void* a_hi, const void* a_lo, const float* a_scale, int M,
                              const void* b_hi, const void* b_lo, const float* b_scale, int64_t N, int K, float* out,
-                             int ld, unsigned* d_err, cudaStream_t s);
+                             int ld, bool blocks, unsigned* d_err, cudaStream_t s);
 constexpr int kLowRankSplit = 0;   // split FP16 (hi + 2^-11 lo, three products): about 6e-7 relative
 template <typename T>
 msasm_status transpose_table_gpu(const double* d_T, int n_nz, int K, T* d_Tt, cudaStream_t s);
@@ -429,7 +429,7 @@ static msasm_status mlp_forward_tc(msasm_mlp* n, const float* d_x, int B, float*
   }
   MSASM_TRY(tc_split_f32_gpu(n->d_h2, B, L.H, kind, n->d_ahi, n->d_alo, n->d_ascale, s));
   MSASM_TRY(contract_tc_gpu(kind, n->d_w3hi, n->d_w3lo, n->d_w3scale, L.n_out, n->d_ahi, n->d_alo, n->d_ascale, B,
-                            L.H, d_y, L.n_out, n->d_tc_err, s));
+                            L.H, d_y, L.n_out, false, n->d_tc_err, s));
   const int64_t ny = int64_t(B) * L.n_out;
   add_bias_kernel<<<unsigned(std::min<int64_t>((ny + 255) / 256, 152 * 8)), 256, 0, s>>>(d_y, ny, L.n_out,
                                                                                          n->d_w16 + L.b3);
@@ -820,9 +820,9 @@ msasm_status msasm_surrogate_predict(msasm_surrogate* sur, const double* d_width
   return st;
 }
 
-// nzdata of n_tiles tiles from the low-rank factors: nz[9t + ab][m] = sum_r Z[9t + ab][r] U[m][r],
+// nzdata of n_tiles tiles from the low-rank factors: nz[t][m][ab] = sum_r Z[9t + ab][r] U[m][r],
 // Z[9t + ab][r] = sum_k Vt_t[r][k] coef[9t + ab][k] (FP32), the second product on the tensor cores
-// in split FP16 (U given as its slices; d_nz leading dimension ld).  d_work holds the slices of Z:
+// in split FP16 (U given as its slices; d_nz in the tile-block layout with m stride ld).  d_work holds the slices of Z:
 // lowrank_work_bytes(n_tiles, rank).
 static size_t lowrank_work_bytes(int64_t n_tiles, int rank) {
   return 2 * ((tc_slice_bytes(9 * n_tiles, rank, kLowRankSplit) + 255) & ~size_t(255)) + size_t(9 * n_tiles) * 4;
@@ -840,7 +840,7 @@ static msasm_status lowrank_contract_gpu(const void* U_hi, const void* U_lo, con
   float* z_scale = reinterpret_cast<float*>(w + 2 * sb);
   MSASM_TRY(tc_split_f32_gpu(d_Z, 9 * n_tiles, rank, kLowRankSplit, w, w + sb, z_scale, s));
   return contract_tc_gpu(kLowRankSplit, U_hi, U_lo, U_scale, n_nz, w, w + sb, z_scale, 9 * n_tiles, rank, d_nz, ld,
-                         d_err, s);
+                         true, d_err, s);
 }
 
 // split-FP16 slices of U, made once per surrogate

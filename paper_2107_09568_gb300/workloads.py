@@ -91,16 +91,16 @@ def surrogate(flush, nx=20, ny=10, nz=10, steps=(4000, 3000, 3000)):
     # per-width quadrature: one table per tile (error judge and the method without the network)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    nzd = torch.empty((9 * plan.n_tiles, base.n_nz), dtype=torch.float64, device="cuda")
+    nzd = torch.empty((plan.n_tiles, base.n_nz, 3, 3), dtype=torch.float64, device="cuda")
     for t in range(plan.n_tiles):
         tab_t = msasm.Tables(synth.micro_cross(3, float(widths[t])), 3)
-        nzd[9 * t:9 * t + 9] = tab_t.contract(coef[9 * t:9 * t + 9], "f64")
+        nzd[t] = tab_t.contract(coef[9 * t:9 * t + 9], "f64")[0]
     k_exact = plan.scatter(nzd, "f64")
     torch.cuda.synchronize()
     ms_exact = 1e3 * (time.perf_counter() - t0)
     nearest = np.abs(widths[:, None] - w_train[None, :]).argmin(1)
     for t in range(plan.n_tiles):
-        nzd[9 * t:9 * t + 9] = train_tabs[nearest[t]].contract(coef[9 * t:9 * t + 9], "f64")
+        nzd[t] = train_tabs[nearest[t]].contract(coef[9 * t:9 * t + 9], "f64")[0]
     k_near = plan.scatter(nzd, "f64")
     plan_mean = msasm.Plan(msasm.Tables(synth.micro_cross(3, 0.275), 3), m)
     k_mean = plan_mean.assemble(ctrl)

@@ -28,6 +28,12 @@ def oracle_table(n_e, q, width=0.3):
     return _TABLE_CACHE[key]
 
 
+
+def blocks_to_rows(nz):
+    """The library's tile blocks (n_tiles, n_nz, 3, 3) as the rows nz[9t + 3a + b][m] of coef @ T^T."""
+    t, m = nz.shape[:2]
+    return nz.reshape(t, m, 9).transpose(0, 2, 1).reshape(9 * t, m)
+
 def rel_fro(a, b):
     a = np.asarray(a, dtype=np.float64); b = np.asarray(b, dtype=np.float64)
     return np.linalg.norm(a - b) / np.linalg.norm(b)
@@ -134,7 +140,7 @@ def test_contract_parity(built, prec, n_e, q, n_tiles):
     tab = msasm.Tables(synth.micro_cross(n_e), q)
     rng = np.random.default_rng(7)
     coef = rng.normal(size=(9 * n_tiles, 9 * tab.n_pi))
-    nz = tab.contract(torch.tensor(coef, device="cuda"), prec).cpu().numpy()
+    nz = blocks_to_rows(tab.contract(torch.tensor(coef, device="cuda"), prec).cpu().numpy())
     ref = coef @ oracle_table(n_e, q).reshape(tab.n_nz, -1).T
     assert rel_fro(nz, ref) <= TOL[prec]
 
@@ -162,9 +168,8 @@ def test_assemble_in_passes(built, per_pass, prec, tol):
 def test_scatter_stage(built):
     """Step 4 alone from the oracle's own nzdata."""
     prob, tab, plan, ctrl = make_case("cube8")
-    nz = nzdata_lookup(prob.T, prob.mmap, prob.q, prob.lam, prob.mu)      # (t, m, a, b)
-    nz_t = nz.transpose(0, 2, 3, 1).reshape(9 * plan.n_tiles, tab.n_nz)
-    vals = plan.scatter(torch.tensor(np.ascontiguousarray(nz_t), device="cuda"), "f64").cpu().numpy()
+    nz = nzdata_lookup(prob.T, prob.mmap, prob.q, prob.lam, prob.mu)      # (t, m, a, b): the library's layout
+    vals = plan.scatter(torch.tensor(np.ascontiguousarray(nz), device="cuda"), "f64").cpu().numpy()
     assert rel_fro(vals, prob.assemble_lookup()) <= 1e-14
 
 

@@ -67,7 +67,7 @@ def test_lowrank_contract_matches_oracle():
     nz = msasm.lowrank_contract(torch.tensor(U, device="cuda"), torch.tensor(Vt, device="cuda"),
                                 torch.tensor(coef, device="cuda")).cpu().numpy()
     Z = np.einsum("trk,tak->tar", Vt.astype(np.float64), coef.reshape(n_tiles, 9, K))
-    ref = np.einsum("tar,mr->tam", Z, U.astype(np.float64)).reshape(9 * n_tiles, n_nz)
+    ref = np.einsum("tar,mr->tma", Z, U.astype(np.float64)).reshape(n_tiles, n_nz, 3, 3)
     assert np.linalg.norm(nz - ref) <= 1e-5 * np.linalg.norm(ref)
 
 
@@ -105,10 +105,10 @@ def test_surrogate_against_per_width_quadrature_and_gain():
     t_sur = (time.perf_counter() - t0) / 3
     # per-width quadrature: one table per tile (the error judge)
     t0 = time.perf_counter()
-    nz = torch.empty((9 * plan.n_tiles, base.n_nz), dtype=torch.float64, device="cuda")
+    nz = torch.empty((plan.n_tiles, base.n_nz, 3, 3), dtype=torch.float64, device="cuda")
     for t in range(plan.n_tiles):
         tab_t = msasm.Tables(synth.micro_cross(3, float(widths[t])), 3)
-        nz[9 * t:9 * t + 9] = tab_t.contract(coef[9 * t:9 * t + 9], "f64")
+        nz[t] = tab_t.contract(coef[9 * t:9 * t + 9], "f64")[0]
     k_exact = plan.scatter(nz, "f64")
     torch.cuda.synchronize()
     t_exact = time.perf_counter() - t0
@@ -116,7 +116,7 @@ def test_surrogate_against_per_width_quadrature_and_gain():
     k_mean = msasm.Plan(msasm.Tables(synth.micro_cross(3, 0.275), 3), m).assemble(ctrl)
     nearest = np.abs(widths[:, None] - w_train[None, :]).argmin(1)
     for t in range(plan.n_tiles):
-        nz[9 * t:9 * t + 9] = train_tabs[nearest[t]].contract(coef[9 * t:9 * t + 9], "f64")
+        nz[t] = train_tabs[nearest[t]].contract(coef[9 * t:9 * t + 9], "f64")[0]
     k_near = plan.scatter(nz, "f64")
     nrm = torch.linalg.vector_norm(k_exact)
     e_sur = (torch.linalg.vector_norm(k_sur.double() - k_exact) / nrm).item()

@@ -33,6 +33,12 @@ def oracle_table(n_e, q):
     return _T[(n_e, q)]
 
 
+
+def blocks_to_rows(nz):
+    """The library's tile blocks (n_tiles, n_nz, 3, 3) as the rows nz[9t + 3a + b][m] of coef @ T^T."""
+    t, m = nz.shape[:2]
+    return nz.reshape(t, m, 9).transpose(0, 2, 1).reshape(9 * t, m)
+
 def rel_fro(a, b):
     return np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b)
 
@@ -42,7 +48,7 @@ def test_tc_single_tile_small_table(prec):
     """One coefficient tile (N = 9), K = 72 (q = 1): two k-blocks, ragged m and n."""
     tab = msasm.Tables(synth.micro_cross(2), 1)
     coef = np.random.default_rng(1).normal(size=(9, 9 * tab.n_pi))
-    nz = tab.contract(torch.tensor(coef, device="cuda"), prec).cpu().numpy()
+    nz = blocks_to_rows(tab.contract(torch.tensor(coef, device="cuda"), prec).cpu().numpy())
     ref = coef @ oracle_table(2, 1).reshape(tab.n_nz, -1).T
     err = rel_fro(nz, ref)
     print(prec, err)
@@ -54,7 +60,7 @@ def test_tc_single_tile_small_table(prec):
 def test_tc_contract_parity(prec, n_e, q, n_tiles):
     tab = msasm.Tables(synth.micro_cross(n_e), q)
     coef = np.random.default_rng(2).normal(size=(9 * n_tiles, 9 * tab.n_pi))
-    nz = tab.contract(torch.tensor(coef, device="cuda"), prec).cpu().numpy()
+    nz = blocks_to_rows(tab.contract(torch.tensor(coef, device="cuda"), prec).cpu().numpy())
     ref = coef @ oracle_table(n_e, q).reshape(tab.n_nz, -1).T
     err = rel_fro(nz, ref)
     print(prec, n_e, q, n_tiles, err)
@@ -110,7 +116,7 @@ def test_f64_emu_contract_parity(n_e, q, n_tiles):
     tab = msasm.Tables(synth.micro_cross(n_e), q)
     coef = np.random.default_rng(4).normal(size=(9 * n_tiles, 9 * tab.n_pi))
     coef[:, ::7] *= 1e-3                            # a spread of magnitudes within rows
-    nz = tab.contract(torch.tensor(coef, device="cuda"), "f64_emu").cpu().numpy()
+    nz = blocks_to_rows(tab.contract(torch.tensor(coef, device="cuda"), "f64_emu").cpu().numpy())
     ref = coef @ oracle_table(n_e, q).reshape(tab.n_nz, -1).T
     err = rel_fro(nz, ref)
     print("f64_emu", n_e, q, n_tiles, err)

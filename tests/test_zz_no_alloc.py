@@ -25,7 +25,7 @@ TOL_F64 = 1e-12     # the FP64 tolerance of the parity tests
 
 def _noalloc(tab, coef, n_tiles):
     lib = msasm.load()
-    out = torch.full((9 * n_tiles, tab.n_nz), float("nan"), dtype=torch.float64, device="cuda")
+    out = torch.full((n_tiles, tab.n_nz, 3, 3), float("nan"), dtype=torch.float64, device="cuda")
     st = lib.msasm_contract_noalloc(tab.handle, C.c_void_p(coef.data_ptr()), n_tiles, C.c_void_p(out.data_ptr()),
                                     C.c_void_p(torch.cuda.current_stream().cuda_stream))
     return st, out
@@ -43,8 +43,8 @@ def test_contract_noalloc_matches_oracle_and_contract_on_consecutive_calls():
         st, out = _noalloc(tab, coef, n_tiles)
         assert st == _lib.OK, msasm.load().msasm_last_error()
         torch.cuda.synchronize()
-        got = out.cpu().numpy()
-        want = coef_h @ T.T                    # nz[9t + 3a + b][m] of eq. 58 on the host
+        got = out.cpu().numpy()                # tile blocks [t, m, a, b]
+        want = (coef_h @ T.T).reshape(n_tiles, 3, 3, tab.n_nz).transpose(0, 3, 1, 2)   # eq. 58 on the host
         err = np.linalg.norm(got - want) / np.linalg.norm(want)
         assert err <= TOL_F64, (call, err)
         ref = tab.contract(coef, "f64").cpu().numpy()   # the existing entry point (allocates its scratch)
