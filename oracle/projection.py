@@ -73,10 +73,18 @@ def projection_error(macro, q: int, E: float = 1.0, nu: float = 0.3, n_s: int = 
     return e, e.max()
 
 
+BAND = 1e-9      # errors within this relative band are equal (see select_degrees)
+
+
+def meets(err: float, tol: float) -> bool:
+    """E_proj <= tol, with an error within a relative BAND above tol counted as meeting it."""
+    return err <= tol * (1.0 + BAND)
+
+
 def select_degree(macro, tol: float, q0: int, q_max: int, **kw):
-    """Smallest q >= q0 with E_proj <= tol (eq. 65), or q_max."""
+    """Smallest q >= q0 with E_proj <= tol (eq. 65; within the relative BAND), or q_max."""
     for q in range(q0, q_max + 1):
-        if projection_error(macro, q, **kw)[1] <= tol:
+        if meets(projection_error(macro, q, **kw)[1], tol):
             return q
     return q_max
 
@@ -85,13 +93,13 @@ def select_degrees(macro, tol: float, q_init, q_max: int = 7, **kw):
     """A degree per direction (the anisotropic projection space of Sec. 3.3.4): from q_init (the
     macro map's degrees), enrich while E_proj > tol, each step raising the one direction whose
     increase lowers E_proj most; then coarsen while possible, each step lowering the direction whose
-    decrease keeps E_proj lowest, as long as it stays <= tol.  Errors within a relative 1e-9 of each
-    other are ties (rounding differences between implementations must not decide); ties go to the
-    lowest direction.
+    decrease keeps E_proj lowest, as long as it stays <= tol.  Errors within a relative 1e-9 (BAND) of
+    each other are ties, which go to the lowest direction, and an error within BAND above tol meets
+    it: rounding differences between implementations must not decide the path.
     Returns (degrees, E_proj)."""
     q = list(quadrature.degrees(q_init))
     err = projection_error(macro, tuple(q), **kw)[1]
-    while err > tol:
+    while not meets(err, tol):
         best = None
         for d in range(3):
             if q[d] >= q_max:
@@ -99,7 +107,7 @@ def select_degrees(macro, tol: float, q_init, q_max: int = 7, **kw):
             c = q.copy()
             c[d] += 1
             e = projection_error(macro, tuple(c), **kw)[1]
-            if best is None or e < best[0] * (1.0 - 1e-9):   # within 1e-9: a tie, the lower direction
+            if best is None or e < best[0] * (1.0 - BAND):   # within the band: a tie, the lower direction
                 best = (e, c)
         if best is None:
             break
@@ -112,7 +120,7 @@ def select_degrees(macro, tol: float, q_init, q_max: int = 7, **kw):
             c = q.copy()
             c[d] -= 1
             e = projection_error(macro, tuple(c), **kw)[1]
-            if e <= tol and (best is None or e < best[0] * (1.0 - 1e-9)):
+            if meets(e, tol) and (best is None or e < best[0] * (1.0 - BAND)):
                 best = (e, c)
         if best is None:
             break

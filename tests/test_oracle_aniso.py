@@ -70,9 +70,9 @@ def test_degree_selection_per_direction():
     beam = synth.macro_twisted_beam(4, 2, 2)
     tol = 1e-3
     q, err = projection.select_degrees(beam, tol, (3, 3, 3))
-    assert err <= tol and projection.projection_error(beam, q)[1] == err
+    assert projection.meets(err, tol) and projection.projection_error(beam, q)[1] == err
     for d in range(3):
         if q[d] > 0:
             c = list(q)
             c[d] -= 1
-            assert projection.projection_error(beam, tuple(c))[1] > tol
+            assert not projection.meets(projection.projection_error(beam, tuple(c))[1], tol)
