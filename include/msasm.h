@@ -394,6 +394,26 @@ msasm_status msasm_projection_error_l2(const msasm_plan* plan, const double* d_c
                                        int32_t n_samples, double E, double nu, double* d_err_tiles, double* d_err_max,
                                        void* stream);
 
+/* The degree of eq. 65 (Sec. 3.3.1): the smallest q in [q0, q_max] (0 <= q0 <= q_max <= 7) whose
+ * E_proj (msasm_projection_error with n_samples per direction) is at most tol, else q_max; into
+ * *q_out, and its E_proj into *err_out (may be NULL).  An error within a relative 1e-9 above tol
+ * counts as meeting it, so that rounding differences between implementations of E_proj cannot
+ * decide the degree.  Synchronises `stream`.  Errors: EINVAL, EUNSUPPORTED, ECUDA. */
+msasm_status msasm_select_degree(const msasm_plan* plan, const double* d_ctrl, double tol, int32_t q0, int32_t q_max,
+                                 int32_t n_samples, double E, double nu, int32_t* q_out, double* err_out,
+                                 void* stream);
+
+/* A projection degree per direction (the anisotropic space of Sec. 3.3.4), from q_init (host
+ * int32[3], e.g. the macro map's degrees; each in 0..q_max, q_max <= 7): while E_proj > tol, raise
+ * the one direction whose increase lowers E_proj most; then, while possible, lower the direction
+ * whose decrease keeps E_proj lowest and still within tol.  Errors within a relative 1e-9 of each
+ * other are ties, which go to the lowest direction, and within 1e-9 above tol meet it.  The
+ * degrees into q_out (host int32[3]), their E_proj into *err_out (may be NULL).  Synchronises
+ * `stream`.  Errors: EINVAL, EUNSUPPORTED, ECUDA. */
+msasm_status msasm_select_degrees(const msasm_plan* plan, const double* d_ctrl, double tol, const int32_t* q_init,
+                                  int32_t q_max, int32_t n_samples, double E, double nu, int32_t* q_out,
+                                  double* err_out, void* stream);
+
 /* ---------------------------------------------------------------- volume and loads */
 
 /* The load lookup table of eq. 54-55 (body term, F = 0): d_F[A][C] = int_{Omega_T} R_A N_C

@@ -14,13 +14,7 @@ import numpy as np
 from . import _lib
 from ._lib import MsasmError, PRECISIONS, FLAG_CHECK_DEGENERATE, check, load
 
-__all__ = ["Tables", "Plan", "MsasmError", "PRECISIONS", "load", "lame"]
-
-
-def lame(E: float, nu: float):
-    lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu))
-    mu = E / (2.0 * (1.0 + nu))
-    return lam, mu
+__all__ = ["Tables", "Plan", "MsasmError", "PRECISIONS", "load"]
 
 
 def _ptr(t):
@@ -340,50 +334,22 @@ def _plan_assemble_l2(self, ctrl, n_gauss, E=1.0, nu=0.3, precision="f64", strea
                                              stream=stream), precision, stream=stream)
 
 
-def select_projection_degree(plan, ctrl, tol, q0, q_max, **kw):
-    """Smallest q in [q0, q_max] with E_proj <= tol (eq. 65), else q_max."""
-    for q in range(q0, q_max + 1):
-        if plan.projection_error(ctrl, q, **kw)[1].item() <= tol:
-            return q
-    return q_max
+def select_projection_degree(plan, ctrl, tol, q0, q_max, n_samples=5, E=1.0, nu=0.3, stream=None):
+    """The degree of eq. 65 (msasm_select_degree): the smallest q in [q0, q_max] with E_proj <= tol, else q_max."""
+    q, e = C.c_int32(), C.c_double()
+    check(load().msasm_select_degree(plan.handle, _ptr(ctrl), float(tol), int(q0), int(q_max), int(n_samples),
+                                     float(E), float(nu), C.byref(q), C.byref(e), _stream(stream)))
+    return q.value
 
 
-def select_projection_degrees(plan, ctrl, tol, q_init, q_max=7, **kw):
-    """A degree per direction (the anisotropic space of Sec. 3.3.4; the projection errors on the
-    GPU): from q_init (the macro map's degrees), raise while E_proj > tol the one direction whose
-    increase lowers E_proj most, then lower while E_proj stays <= tol the direction whose decrease
-    keeps it lowest (errors within a relative 1e-9 are ties, which go to the lowest direction).  Returns
-    (degrees, E_proj)."""
-    err_of = lambda q: plan.projection_error(ctrl, tuple(q), **kw)[1].item()
-    q = [int(v) for v in q_init]
-    err = err_of(q)
-    while err > tol:
-        best = None
-        for d in range(3):
-            if q[d] >= q_max:
-                continue
-            c = q.copy()
-            c[d] += 1
-            e = err_of(c)
-            if best is None or e < best[0] * (1.0 - 1e-9):   # within 1e-9: a tie, the lower direction
-                best = (e, c)
-        if best is None:
-            break
-        err, q = best
-    while True:
-        best = None
-        for d in range(3):
-            if q[d] == 0:
-                continue
-            c = q.copy()
-            c[d] -= 1
-            e = err_of(c)
-            if e <= tol and (best is None or e < best[0] * (1.0 - 1e-9)):
-                best = (e, c)
-        if best is None:
-            break
-        err, q = best
-    return tuple(q), err
+def select_projection_degrees(plan, ctrl, tol, q_init, q_max=7, n_samples=5, E=1.0, nu=0.3, stream=None):
+    """A degree per direction (Sec. 3.3.4; msasm_select_degrees): (degrees, E_proj)."""
+    qi = (C.c_int32 * 3)(*[int(v) for v in q_init])
+    qo = (C.c_int32 * 3)()
+    e = C.c_double()
+    check(load().msasm_select_degrees(plan.handle, _ptr(ctrl), float(tol), qi, int(q_max), int(n_samples), float(E),
+                                      float(nu), qo, C.byref(e), _stream(stream)))
+    return tuple(int(v) for v in qo), e.value
 
 
 Plan.range = _plan_range

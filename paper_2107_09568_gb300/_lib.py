@@ -53,6 +53,9 @@ _SIGS = {
     "msasm_plan_destroy": (None, [c_vp]),
     "msasm_assemble": (c_i32, [c_vp, c_vp, c_dbl, c_dbl, c_i32, c_vp, c_u32, c_vp]),
     "msasm_assemble_host": (c_i32, [c_vp, c_vp, c_dbl, c_dbl, c_i32, c_vp, c_u32, c_vp]),
+    "msasm_select_degree": (c_i32, [c_vp, c_vp, c_dbl, c_i32, c_i32, c_i32, c_dbl, c_dbl, P(c_i32), P(c_dbl), c_vp]),
+    "msasm_select_degrees": (c_i32, [c_vp, c_vp, c_dbl, P(c_i32), c_i32, c_i32, c_dbl, c_dbl, P(c_i32), P(c_dbl),
+                                     c_vp]),
     "msasm_plan_range": (c_i32, [c_vp, c_i64, c_i64, P(c_i64), P(c_i64), P(c_i64), P(c_i64), P(c_i64)]),
     "msasm_assemble_range": (c_i32, [c_vp, c_vp, c_dbl, c_dbl, c_i32, c_i64, c_i64, c_vp, c_u32, c_vp]),
     "msasm_assemble_grad_range": (c_i32, [c_vp, c_vp, c_dbl, c_dbl, c_i32, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp]),

@@ -1,6 +1,7 @@
 // The C ABI of include/msasm.h: argument checking, handle lifetime, and the
 // sequencing of the kernels of one assembly (pullback -> contraction -> scatter).
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -125,6 +126,7 @@ msasm_plan::~msasm_plan() {
   cudaFree(d_type_nvals);
   cudaFree(d_type_map_off);
   cudaFree(d_maps);
+  cudaFree(d_maps3);
   cudaFree(d_tile_vbase);
   cudaFree(d_item_tile);
   cudaFree(d_item_start);
@@ -373,6 +375,7 @@ msasm_status msasm_plan_create(const msasm_tables* tab, const msasm_macro_desc* 
   if (err == cudaSuccess) err = dev((void**)&plan->d_type_nvals, sp.type_nvals.size() * sizeof(int32_t));
   if (err == cudaSuccess) err = dev((void**)&plan->d_type_map_off, sp.type_map_off.size() * sizeof(int64_t));
   if (err == cudaSuccess) err = dev((void**)&plan->d_maps, size_t(sp.type_map_off.back()) * sizeof(int32_t));
+  if (err == cudaSuccess) err = dev((void**)&plan->d_maps3, size_t(sp.type_map_off.back() / 3) * sizeof(int32_t));
   if (err == cudaSuccess) err = dev((void**)&plan->d_tile_vbase, plan->tile_vbase.size() * sizeof(int64_t));
   if (err == cudaSuccess) err = dev((void**)&plan->d_item_tile, sp.item_tile.size() * sizeof(int32_t));
   if (err == cudaSuccess) err = dev((void**)&plan->d_item_start, sp.item_start.size() * sizeof(int32_t));
@@ -930,6 +933,133 @@ msasm_status msasm_projection_error_l2(const msasm_plan* plan, const double* d_c
   const int q3[3] = {q, q, q};
   return projection_error_gpu(plan, d_ctrl, q3, n_samples, lam, mu, d_err_tiles, d_err_max,
                               static_cast<cudaStream_t>(stream), n_gauss);
+}
+
+// ---------------------------------------------------------------- degree selection (eq. 65, Sec. 3.3.4)
+// Errors within a relative kDegreeBand count as equal, both when two candidates are compared and
+// when an error is compared with the tolerance, so that rounding differences between
+// implementations of E_proj cannot change the selected degrees.
+constexpr double kDegreeBand = 1e-9;
+
+namespace {
+struct DegreeSearch {
+  const msasm_plan* plan;
+  const double* d_ctrl;
+  int n_s;
+  double lam, mu;
+  cudaStream_t s;
+  double* d_tmp = nullptr;
+  std::vector<std::pair<std::array<int, 3>, double>> cache;
+  // E_proj of eq. 59 (largest over the tiles) for the degrees q3, computed once per q3
+  msasm_status err(const std::array<int, 3>& q3, double* out) {
+    for (const auto& c : cache)
+      if (c.first == q3) {
+        *out = c.second;
+        return MSASM_OK;
+      }
+    const int q[3] = {q3[0], q3[1], q3[2]};
+    MSASM_TRY(projection_error_gpu(plan, d_ctrl, q, n_s, lam, mu, nullptr, d_tmp, s));
+    double h = 0.0;
+    MSASM_CUDA(cudaMemcpyAsync(&h, d_tmp, sizeof(double), cudaMemcpyDeviceToHost, s));
+    MSASM_CUDA(cudaStreamSynchronize(s));
+    cache.push_back({q3, h});
+    *out = h;
+    return MSASM_OK;
+  }
+};
+}  // namespace
+
+static bool meets(double e, double tol) { return e <= tol * (1.0 + kDegreeBand); }
+
+msasm_status msasm_select_degree(const msasm_plan* plan, const double* d_ctrl, double tol, int32_t q0, int32_t q_max,
+                                 int32_t n_samples, double E, double nu, int32_t* q_out, double* err_out,
+                                 void* stream) {
+  if (!plan || !d_ctrl || !q_out) return fail(MSASM_EINVAL, "plan, d_ctrl or q_out is NULL");
+  if (!(tol > 0.0) || !std::isfinite(tol)) return fail(MSASM_EINVAL, "tol must be positive and finite");
+  if (q0 < 0 || q_max > 7 || q0 > q_max) return fail(MSASM_EINVAL, "need 0 <= q0 <= q_max <= 7");
+  MSASM_TRY(check_material(E, nu));
+  DegreeSearch ds{plan, d_ctrl, n_samples, 0.0, 0.0, static_cast<cudaStream_t>(stream)};
+  lame(E, nu, ds.lam, ds.mu);
+  MSASM_CUDA(cudaMallocAsync(&ds.d_tmp, sizeof(double), ds.s));
+  msasm_status st = MSASM_OK;
+  int q = q_max;
+  double e = 0.0;
+  for (int c = q0; c <= q_max && st == MSASM_OK; ++c) {
+    st = ds.err({c, c, c}, &e);
+    if (st == MSASM_OK && meets(e, tol)) {
+      q = c;
+      break;
+    }
+  }
+  cudaFreeAsync(ds.d_tmp, ds.s);
+  if (st != MSASM_OK) return st;
+  *q_out = q;
+  if (err_out) *err_out = e;
+  return MSASM_OK;
+}
+
+msasm_status msasm_select_degrees(const msasm_plan* plan, const double* d_ctrl, double tol, const int32_t* q_init,
+                                  int32_t q_max, int32_t n_samples, double E, double nu, int32_t* q_out,
+                                  double* err_out, void* stream) {
+  if (!plan || !d_ctrl || !q_init || !q_out) return fail(MSASM_EINVAL, "plan, d_ctrl, q_init or q_out is NULL");
+  if (!(tol > 0.0) || !std::isfinite(tol)) return fail(MSASM_EINVAL, "tol must be positive and finite");
+  if (q_max < 0 || q_max > 7) return fail(MSASM_EINVAL, "q_max must be in 0..7");
+  for (int d = 0; d < 3; ++d)
+    if (q_init[d] < 0 || q_init[d] > q_max) return fail(MSASM_EINVAL, "q_init must be in 0..q_max");
+  MSASM_TRY(check_material(E, nu));
+  DegreeSearch ds{plan, d_ctrl, n_samples, 0.0, 0.0, static_cast<cudaStream_t>(stream)};
+  lame(E, nu, ds.lam, ds.mu);
+  MSASM_CUDA(cudaMallocAsync(&ds.d_tmp, sizeof(double), ds.s));
+  std::array<int, 3> q = {q_init[0], q_init[1], q_init[2]};
+  double err = 0.0;
+  msasm_status st = ds.err(q, &err);
+  // enrich: while the tolerance is not met, raise the direction whose increase lowers E_proj most
+  while (st == MSASM_OK && !meets(err, tol)) {
+    bool found = false;
+    double best_e = 0.0;
+    std::array<int, 3> best_q = q;
+    for (int d = 0; d < 3 && st == MSASM_OK; ++d) {
+      if (q[d] >= q_max) continue;
+      std::array<int, 3> c = q;
+      ++c[d];
+      double e = 0.0;
+      st = ds.err(c, &e);
+      if (st == MSASM_OK && (!found || e < best_e * (1.0 - kDegreeBand))) {   // a tie keeps the lower direction
+        found = true;
+        best_e = e;
+        best_q = c;
+      }
+    }
+    if (!found) break;
+    err = best_e;
+    q = best_q;
+  }
+  // coarsen: while possible, lower the direction whose decrease keeps E_proj lowest and within tol
+  while (st == MSASM_OK) {
+    bool found = false;
+    double best_e = 0.0;
+    std::array<int, 3> best_q = q;
+    for (int d = 0; d < 3 && st == MSASM_OK; ++d) {
+      if (q[d] == 0) continue;
+      std::array<int, 3> c = q;
+      --c[d];
+      double e = 0.0;
+      st = ds.err(c, &e);
+      if (st == MSASM_OK && meets(e, tol) && (!found || e < best_e * (1.0 - kDegreeBand))) {
+        found = true;
+        best_e = e;
+        best_q = c;
+      }
+    }
+    if (!found) break;
+    err = best_e;
+    q = best_q;
+  }
+  cudaFreeAsync(ds.d_tmp, ds.s);
+  if (st != MSASM_OK) return st;
+  for (int d = 0; d < 3; ++d) q_out[d] = q[d];
+  if (err_out) *err_out = err;
+  return MSASM_OK;
 }
 
 msasm_status msasm_pullback_l2(msasm_plan* plan, const double* d_ctrl, double E, double nu, int32_t n_gauss,

@@ -152,7 +152,8 @@ struct msasm_plan {
   int32_t* d_tile_type = nullptr;
   int32_t* d_type_nvals = nullptr;
   int64_t* d_type_map_off = nullptr;
-  int32_t* d_maps = nullptr;                 // value maps of all types: (3a + b) ld + m, or -1
+  int32_t* d_maps = nullptr;                 // value maps of all types: 9 m + 3a + b, or -1
+  int32_t* d_maps3 = nullptr;                // segment maps (one per 3 values): (source << 1) | lower, or -1
   int64_t* d_tile_vbase = nullptr;
   int32_t* d_item_tile = nullptr;
   int32_t* d_item_start = nullptr;

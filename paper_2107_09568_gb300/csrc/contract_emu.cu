@@ -25,7 +25,8 @@
 // in the collector buffer across its products) into 5 TMEM accumulators of 96 columns (480 of the
 // 512).  Eight epilogue warps (two per TMEM lane quarter, 48 columns each) drain the accumulators
 // into exact int64 sums in registers and release TMEM at once, so the MMAs of the next tile run
-// while they round and store the previous one.
+// while they round and store the previous one.  In the tile-block layout of nzdata a warp rounds
+// 24 columns at a time into shared memory and writes each tile block's 32 rows as one run.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -41,13 +42,25 @@ namespace msasm {
 constexpr int EMU_S = 7;                 // slices per operand
 constexpr int EMU_BM = 128, EMU_BN = 96, EMU_KB = 16;    // k block: 16 BF16 = one 32-byte swizzle row
 constexpr int EMU_ACC = 5;                               // accumulators: d = 0, 1, 2, 3 and d >= 4
-constexpr int EMU_STAGES = 4;
+constexpr int EMU_STAGES_ROWS = 4;                       // ring depth, row layout
+constexpr int EMU_STAGES_BLOCKS = 3;                     // ring depth, block layout (room for the staging)
 constexpr int EMU_A_SLICE = EMU_BM * 32;                 // one slice tile of A: 128 rows x 32 bytes
 constexpr int EMU_B_SLICE = EMU_BN * 32;                 // one slice tile of B: 96 rows x 32 bytes
 constexpr int EMU_A_BYTES = EMU_S * EMU_A_SLICE;         // 28 KB
 constexpr int EMU_B_BYTES = EMU_S * EMU_B_SLICE;         // 21 KB
 constexpr int EMU_STAGE_BYTES = EMU_A_BYTES + EMU_B_BYTES;
-constexpr int EMU_SMEM_BYTES = EMU_STAGES * EMU_STAGE_BYTES + 1024 + 256;
+// block layout: each epilogue warp rounds 24 columns of its 32 rows into a shared-memory buffer
+// (odd row stride: few bank conflicts either way) and writes them back tile block by tile block
+constexpr int EMU_STG_COLS = 24;
+constexpr int EMU_STG_LD = 25;
+constexpr int EMU_STG_DOUBLES = 32 * EMU_STG_LD;
+template <bool BLOCKS>
+__host__ __device__ constexpr int emu_stages() { return BLOCKS ? EMU_STAGES_BLOCKS : EMU_STAGES_ROWS; }
+template <bool BLOCKS>
+constexpr int emu_smem_bytes() {
+  return emu_stages<BLOCKS>() * EMU_STAGE_BYTES + 1024 + 256 + (BLOCKS ? 8 * EMU_STG_DOUBLES * 8 : 0);
+}
+static_assert(emu_smem_bytes<true>() <= 227 * 1024 && emu_smem_bytes<false>() <= 227 * 1024, "shared memory");
 
 struct EmuParams {
   int M, N, kblocks;
@@ -113,6 +126,7 @@ __device__ __forceinline__ long long f32_to_i64_rn(float y) {
 template <bool ACCUMULATE, bool BLOCKS>
 __global__ void __launch_bounds__(EMU_THREADS, 1)
     contract_emu_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, EmuParams p) {
+  constexpr int EMU_STAGES = emu_stages<BLOCKS>();
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -124,6 +138,7 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
   const uint32_t tmem_empty = bar0 + 8u * (2 * EMU_STAGES + 1);  // accumulators drained
   uint32_t* tmem_slot =
       reinterpret_cast<uint32_t*>(gen_base + EMU_STAGES * EMU_STAGE_BYTES + 8 * (2 * EMU_STAGES + 2));
+  double* staging = reinterpret_cast<double*>(gen_base + EMU_STAGES * EMU_STAGE_BYTES + 256);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n_nt = (p.N + EMU_BN - 1) / EMU_BN, n_mt = (p.M + EMU_BM - 1) / EMU_BM;
   const long long total = (long long)n_nt * n_mt;
@@ -266,15 +281,40 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(tmem_empty);                     // the MMAs of the next tile may start
       const int m = m0 + 32 * q + lane;
-      if (m < p.M) {
-        const int em = p.exp_m[m] - 49;                           // D = X 2^(e_m + e_n - 14 - 35)
+      const int em = (m < p.M) ? p.exp_m[m] - 49 : 0;            // D = X 2^(e_m + e_n - 14 - 35)
+      if constexpr (BLOCKS) {
+        // the tile blocks of eq. 58, nz[t][m][3a + b] for n = 9t + 3a + b: the 32 rows of a block
+        // are one run of 32 x 9 values, written with consecutive lanes on consecutive addresses
+        double* stg = staging + (warp - 2) * EMU_STG_DOUBLES;
+        const int mr0 = m0 + 32 * q;
+#pragma unroll
+        for (int half = 0; half < EMU_EPI_COLS / EMU_STG_COLS; ++half) {
+          const int c0 = n0 + half * EMU_STG_COLS;
+#pragma unroll
+          for (int j = 0; j < EMU_STG_COLS; ++j) {
+            const int n = c0 + j;
+            stg[lane * EMU_STG_LD + j] =
+                (m < p.M && n < p.N) ? ldexp_i64_rn(X[half * EMU_STG_COLS + j], em + p.exp_n[n]) : 0.0;
+          }
+          __syncwarp();
+          const int cend = min(c0 + EMU_STG_COLS, p.N);
+          for (int tb = c0 / 9; 9 * tb < cend; ++tb) {
+            const int ka = max(9 * tb, c0), kc = min(9 * tb + 9, cend) - ka;   // columns of block tb here
+            double* dst = p.out + (size_t(tb) * size_t(p.ld) + size_t(mr0)) * 9 + (ka - 9 * tb);
+            const double* src = stg + (ka - c0);
+            for (int e = lane; e < 32 * kc; e += 32) {
+              const int r = e / kc, kk = e - r * kc;
+              if (mr0 + r < p.M) dst[r * 9 + kk] = src[r * EMU_STG_LD + kk];
+            }
+          }
+          __syncwarp();
+        }
+      } else if (m < p.M) {
 #pragma unroll
         for (int j = 0; j < EMU_EPI_COLS; ++j) {
           const int n = n0 + j;
           if (n < p.N) {
-            // rows: nz[n][m]; blocks: the tile block of eq. 58, nz[t][m][3a + b] for n = 9t + 3a + b
-            double* o = BLOCKS ? p.out + (size_t(n / 9) * size_t(p.ld) + size_t(m)) * 9 + (n % 9)
-                               : p.out + size_t(n) * p.ld + m;
+            double* o = p.out + size_t(n) * p.ld + m;
             const double v = ldexp_i64_rn(X[j], em + p.exp_n[n]);
             if constexpr (ACCUMULATE) *o += v;
             else *o = v;
@@ -430,14 +470,15 @@ msasm_status contract_emu_gpu(const void* a_slices, const int* a_exp, int M, con
   p.err = d_err;
   auto kernel = blocks ? contract_emu_kernel<false, true>
                       : (accumulate ? contract_emu_kernel<true, false> : contract_emu_kernel<false, false>);
-  MSASM_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, EMU_SMEM_BYTES));
+  const int smem = blocks ? emu_smem_bytes<true>() : emu_smem_bytes<false>();
+  MSASM_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   const long long tiles = ((N + EMU_BN - 1) / EMU_BN) * (long long)((M + EMU_BM - 1) / EMU_BM);
   if (tiles == 0) return MSASM_OK;
   int dev = 0, n_sm = 0;
   MSASM_CUDA(cudaGetDevice(&dev));
   MSASM_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
   const unsigned grid = unsigned(std::min<long long>(tiles, std::max(n_sm, 1)));   // one CTA per SM
-  kernel<<<grid, EMU_THREADS, EMU_SMEM_BYTES, s>>>(ma, mb, p);
+  kernel<<<grid, EMU_THREADS, smem, s>>>(ma, mb, p);
   MSASM_CUDA(cudaGetLastError());
   return MSASM_OK;
 }

@@ -9,6 +9,7 @@ import pytest
 
 import synth
 from oracle import tables as otables
+from oracle import pullback as opullback
 from oracle.assembly import Problem, point_rows, coefficient_block, nzdata_lookup
 
 torch = pytest.importorskip("torch")
@@ -124,7 +125,7 @@ def test_pullback_cube_closed_form(built):
     tab = msasm.Tables(synth.micro_cross(2), 2)
     plan = msasm.Plan(tab, m)
     coef = plan.pullback(torch.tensor(m.ctrl, device="cuda"), 1.0, 0.3).cpu().numpy()
-    lam, mu = msasm.lame(1.0, 0.3)
+    lam, mu = opullback.lame(1.0, 0.3)
     A = coef.reshape(3, 3, tab.n_pi, 3, 3)                    # [a, b, C, i, j]
     a1, a2, a3 = (lam + 2 * mu) * L, mu * L, lam * L
     for C_ in range(tab.n_pi):

@@ -40,19 +40,3 @@ def test_cg_solve_block_spd_system_on_cpu():
     assert res < 1e-12 and iters < 2000
     assert np.abs(u.numpy() - ref).max() <= 1e-10 * np.abs(ref).max()
     assert np.all(u.numpy()[fixed] == 0.0)
-
-
-def test_per_direction_degree_selection_host_logic():
-    """The binding's per-direction selection (its projection errors replaced here by the oracle's,
-    on the CPU) takes the same steps as the oracle's selection."""
-    import synth
-    from oracle import projection as oproj
-    macro = synth.macro_twisted_beam(3, 2, 1)
-
-    class OraclePlan:
-        def projection_error(self, ctrl, q, **kw):
-            return None, torch.tensor(oproj.projection_error(macro, q)[1])
-
-    for tol in (1e-2, 1e-4):
-        q, err = msasm.select_projection_degrees(OraclePlan(), None, tol, (3, 3, 3))
-        assert (q, err) == tuple(oproj.select_degrees(macro, tol, (3, 3, 3)))
