@@ -248,8 +248,9 @@ def contraction_flops(n_nz, n_pi, n_tiles):
 
 
 # tensor-core products issued per algorithmic product, and the unit's peak relative to BF16 dense
-TC_PRODUCTS = {"split_f16": 3, "split_bf16": 3, "tf32": 1, "tf32x3": 3, "f64_emu": 28}
-TC_PEAK_RATIO = {"split_f16": 1.0, "split_bf16": 1.0, "tf32": 1.1 / 2.25, "tf32x3": 1.1 / 2.25, "f64_emu": 1.0}
+TC_PRODUCTS = {"split_f16": 3, "split_bf16": 3, "tf32": 1, "tf32x3": 3, "f64_emu": 28, "f32": 10}
+TC_PEAK_RATIO = {"split_f16": 1.0, "split_bf16": 1.0, "tf32": 1.1 / 2.25, "tf32x3": 1.1 / 2.25, "f64_emu": 1.0,
+                 "f32": 1.0}
 
 
 def oracle_problem(workload):
@@ -383,8 +384,8 @@ def roofline_of(stage_avg, prec, tab, n_tiles, nnz, pk, pk_kind, workload):
     nz_bytes = 9 * n_tiles * tab.n_nz * vbytes
     scatter_bytes = nz_bytes + nnz * vbytes                  # nzdata read, values written (once each)
     pull_bytes = 9 * n_tiles * K * 8
-    if names[dom] == "contraction" and prec in ("f64", "f32"):
-        alu_peak = FP64_ALU_PEAK_TFLOPS if prec == "f64" else FP32_ALU_PEAK_TFLOPS
+    if names[dom] == "contraction" and prec == "f64":
+        alu_peak = FP64_ALU_PEAK_TFLOPS
         ach = flops / (stage_avg[1] / 1e3) / 1e12
         roof = {"kernel": f"contract_simt_{prec}", "bound": "alu", "achieved": ach, "peak": alu_peak,
                 "unit": "TFLOP/s", "frac": ach / alu_peak, "traffic": None,
@@ -399,7 +400,7 @@ def roofline_of(stage_avg, prec, tab, n_tiles, nnz, pk, pk_kind, workload):
         peak = pk["bf16_tflops"] * ratio / n_prod
         peak_sus = pk["bf16_tflops_sustained"] * ratio / n_prod
         ach = flops / (stage_avg[1] / 1e3) / 1e12
-        roof = {"kernel": "contract_emu_kernel" if prec == "f64_emu" else "contract_tc_kernel", "bound": "tensor",
+        roof = {"kernel": "contract_emu_kernel" if prec in ("f64_emu", "f32") else "contract_tc_kernel", "bound": "tensor",
                 "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
                 "peak_source": f"{pk_kind} bf16 burst {pk['bf16_tflops']}"
                                + (" x 1.1/2.25 (tf32 nominal ratio)" if "tf32" in prec else "")
@@ -473,21 +474,37 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     msasm.load()
 
+    from paper_2107_09568_gb300 import slabs
     w = synth.workload(args.workload)
+    macro = w.macro
+    if world > 1:
+        # one mesh split across the GPUs, weak scaling: the same twisted beam with `world` times as many
+        # layers along z, rank r assembling the rows of one contiguous slab of tiles (plus the halo layer)
+        if not args.workload.startswith("beam"):
+            raise SystemExit("--gpus N > 1 splits a twisted-beam workload (beam125, beam1000, beam4000)")
+        nx, ny, nz = (int(v) for v in w.macro.n_elem)
+        macro = synth.macro_twisted_beam(nx, ny, nz * world)
+    n_elem = tuple(int(v) for v in macro.n_elem)
+    n_total = n_elem[0] * n_elem[1] * n_elem[2]
+    t0, t1 = slabs.slab_ranges(n_total, world)[rank]
+    t_halo = slabs.halo_end(t1, n_elem)
     micro = synth.micro_cross(w.n_e, w.width)
     tab = msasm.Tables(micro, w.q)
-    plan = msasm.Plan(tab, w.macro)
-    ctrl = torch.tensor(w.macro.ctrl, dtype=torch.float64, device="cuda")
+    plan = msasm.Plan(tab, macro, max_tiles_per_pass=(t_halo - t0) if world > 1 else 0)
+    r0, r1, v0, v1, _ = plan.range(t0, t1)
+    ctrl = torch.tensor(macro.ctrl, dtype=torch.float64, device="cuda")
     prec = args.precision
-    out = torch.empty(plan.nnz, dtype=msasm.Plan.value_dtype(prec), device="cuda")
+    out = torch.empty(v1 - v0, dtype=msasm.Plan.value_dtype(prec), device="cuda")     # this rank's rows
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 256 MB > L2
     stream = torch.cuda.current_stream()
+    step = lambda **kw: plan.assemble_range(ctrl, t0, t1, 1.0, 0.3, prec, out=out, **kw)
 
     # correctness of the timed configuration: degenerate check (and the tensor-core pipeline flag)
-    plan.assemble(ctrl, 1.0, 0.3, prec, out=out, check_degenerate=True)
+    if world == 1:
+        plan.assemble(ctrl, 1.0, 0.3, prec, out=out, check_degenerate=True)
     for _ in range(args.warmup):
         flush.zero_()
-        plan.assemble(ctrl, 1.0, 0.3, prec, out=out, stage_times=True)
+        step(stage_times=True)
     torch.cuda.synchronize()
 
     clocks = Clocks(local)
@@ -503,7 +520,7 @@ def main():
     for k in range(args.steps):
         flush.zero_()                                  # L2 flush between timed steps (not timed)
         ev[k][0].record(stream)
-        plan.assemble(ctrl, 1.0, 0.3, prec, out=out, stage_times=True)
+        step(stage_times=True)                         # the whole mesh at N = 1 (msasm_assemble's path)
         ev[k][1].record(stream)
         ms, ln = plan.stage_times()                    # events recorded inside the call, same stream
         stage_ms += np.array(ms)
@@ -516,31 +533,40 @@ def main():
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = max_over_ranks(sum(step_ms), dist, "cuda")
-    value = whole_job_rate(plan.n_tiles, world, args.steps, total_ms)
+    value = whole_job_rate(t1 - t0, world, args.steps, total_ms)      # balanced ranges: equal tiles per rank
     vbytes = 8 if prec in ("f64", "f64_emu") else 4
-    stiff_gbs = plan.nnz * vbytes * world * args.steps / (total_ms / 1e3) / 1e9
+    stiff_gbs = (v1 - v0) * vbytes * world * args.steps / (total_ms / 1e3) / 1e9
 
     # end to end through the public C ABI with host buffers (copies inside the timed region), on
     # every rank; the job's rate is set by the slowest rank
     e2e = None
     if not args.no_e2e:
-        h_ctrl = torch.tensor(w.macro.ctrl, dtype=torch.float64).pin_memory()
-        h_vals = torch.empty(plan.nnz, dtype=msasm.Plan.value_dtype(prec)).pin_memory()
-        plan.assemble_host(h_ctrl, h_vals, 1.0, 0.3, prec)
+        h_ctrl = torch.tensor(macro.ctrl, dtype=torch.float64).pin_memory()
+        h_vals = torch.empty(v1 - v0, dtype=msasm.Plan.value_dtype(prec)).pin_memory()
+        if world == 1:       # msasm_assemble_host: control net in, values out, copies overlapped with passes
+            e_step = lambda: plan.assemble_host(h_ctrl, h_vals, 1.0, 0.3, prec)
+            api = "msasm_assemble_host (pinned host buffers)"
+        else:                # msasm_assemble_range on this rank's slab, with the copies around it
+            def e_step():
+                ctrl.copy_(h_ctrl, non_blocking=True)
+                step()
+                h_vals.copy_(out, non_blocking=True)
+                torch.cuda.synchronize()
+            api = "H2D control net, msasm_assemble_range, D2H of the rank's values (pinned host buffers)"
+        e_step()
         e_steps = max(2, min(args.steps, 5))
         if dist is not None:
             dist.barrier()
         e_ms = []
         for _ in range(e_steps):
             flush.zero_(); torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            plan.assemble_host(h_ctrl, h_vals, 1.0, 0.3, prec)
-            e_ms.append(1e3 * (time.perf_counter() - t0))
+            ts = time.perf_counter()
+            e_step()
+            e_ms.append(1e3 * (time.perf_counter() - ts))
         em = max_over_ranks(sum(e_ms), dist, "cuda") / e_steps
-        e2e = {"value": whole_job_rate(plan.n_tiles, world, 1, em), "unit": "tiles/s", "ms_per_step": em,
+        e2e = {"value": whole_job_rate(t1 - t0, world, 1, em), "unit": "tiles/s", "ms_per_step": em,
                "h2d_bytes_per_step": int(h_ctrl.numel() * 8) * world,
-               "d2h_bytes_per_step": int(plan.nnz * vbytes) * world,
-               "api": "msasm_assemble_host (pinned host buffers)", "host_cpus": affinity}
+               "d2h_bytes_per_step": int((v1 - v0) * vbytes) * world, "api": api, "host_cpus": affinity}
         del h_vals, h_ctrl
 
     if rank != 0:
@@ -550,6 +576,23 @@ def main():
 
     pk, pk_kind = peaks()
     stage_avg = stage_ms / args.steps
+    if world > 1:
+        # rank 0's kernels: its slab plus the halo layer, writing its own rows
+        roof = roofline_of(stage_avg, prec, tab, t_halo - t0, v1 - v0, pk, pk_kind, args.workload)
+        line = {"metric": METRIC, "value": value, "unit": "tiles/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
+                "config": dict(workload_config(args.workload), mesh=list(n_elem), tiles=n_total,
+                               tiles_per_gpu=t1 - t0),
+                "execution": f"one mesh split into {world} contiguous tile slabs, one per GPU; each rank "
+                             "recomputes the layer of tiles above its slab (halo) and writes only its own rows",
+                "sizes": {"rank0_rows": r1 - r0, "rank0_values": v1 - v0, "rank0_tiles_with_halo": t_halo - t0},
+                "stiffness_gbs": stiff_gbs, "roofline": roof, "cpu_baseline": None, "e2e": e2e,
+                "gpu_launches": int(launches), "clocks": clk, "forms": "reported at N = 1",
+                "wall_s_timed_region": wall}
+        print(json.dumps(line), flush=True)
+        dist.destroy_process_group()
+        return 0
     roof = roofline_of(stage_avg, prec, tab, plan.n_tiles, plan.nnz, pk, pk_kind, args.workload)
 
     # every precision form on the same workload: throughput and relative Frobenius error against the
@@ -622,7 +665,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
             "config": workload_config(args.workload),
-            "execution": f"{world} independent replica(s), one per GPU",
+            "execution": "one GPU: the whole mesh (msasm_assemble_range over all tiles, the path of msasm_assemble)",
             "sizes": sizes, "stiffness_gbs": stiff_gbs, "rel_fro_vs_f64_gpu": main_err, "roofline": roof,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "forms": forms,
             "workloads": extra, "wall_s_timed_region": wall}

@@ -63,7 +63,9 @@ typedef enum {
 
 typedef enum {
   MSASM_F64 = 0,            /* FP64 contraction (CUDA-core DFMA) */
-  MSASM_F32 = 1,            /* FP32 contraction (CUDA-core FFMA), FP32 values */
+  MSASM_F32 = 1,            /* tensor cores, FP32 values: each operand row cut into 4 exact BF16 slices (28
+                               bits), the 10 slice products with i+j <= 3 summed exactly, one rounding to
+                               FP32 (CUDA-core FFMA for tables with 9 n_pi > 576) */
   MSASM_SPLIT_F16 = 2,      /* tensor cores, FP16 hi/lo operands, FP32 accumulation, FP32 values */
   MSASM_SPLIT_BF16 = 3,     /* tensor cores, BF16 hi/lo operands, FP32 accumulation, FP32 values */
   MSASM_TF32 = 4,           /* tensor cores, TF32 operands, FP32 accumulation, FP32 values */

@@ -76,12 +76,12 @@ msasm_status traction_load_gpu(const msasm_plan* plan, const double* d_ctrl, int
                                cudaStream_t s);
 int tc_kind_of(msasm_precision prec);
 int emu_kpad(int K);
-size_t emu_slice_bytes(int64_t rows, int K);
+size_t emu_slice_bytes(int64_t rows, int K, int n_slices = 7);
 msasm_status emu_slice_gpu(const double* x, int64_t rows, int64_t ldx, int K, void* slices, int* scale_exp,
-                           cudaStream_t s);
+                           cudaStream_t s, int n_slices = 7);
 msasm_status contract_emu_gpu(const void* a_slices, const int* a_exp, int M, const void* b_slices, const int* b_exp,
-                              int64_t N, int K, double* out, int ld, bool accumulate, bool blocks, unsigned* d_err,
-                              cudaStream_t s);
+                              int64_t N, int K, void* out, int ld, bool accumulate, bool blocks, unsigned* d_err,
+                              cudaStream_t s, int n_slices = 7);
 int tc_kpad(int K, int kind);
 size_t tc_slice_bytes(int64_t rows, int K, int kind);
 msasm_status tc_split_gpu(const double* x, int64_t rows, int K, int kind, void* hi, void* lo, float* row_scale,
@@ -111,6 +111,8 @@ msasm_tables::~msasm_tables() {
   cudaFree(d_Tt32);
   cudaFree(d_Tslices);
   cudaFree(d_Tslice_scale);
+  cudaFree(d_Tslices4);
+  cudaFree(d_Tslice_scale4);
 }
 
 msasm_plan::~msasm_plan() {
@@ -126,10 +128,8 @@ msasm_plan::~msasm_plan() {
   cudaFree(d_type_nvals);
   cudaFree(d_type_map_off);
   cudaFree(d_maps);
-  cudaFree(d_maps3);
   cudaFree(d_tile_vbase);
-  cudaFree(d_item_tile);
-  cudaFree(d_item_start);
+  cudaFree(d_items);
   cudaFree(d_tmpl);
   cudaFree(d_tmpl_ptr);
   cudaFree(d_sec_off);
@@ -375,10 +375,8 @@ msasm_status msasm_plan_create(const msasm_tables* tab, const msasm_macro_desc* 
   if (err == cudaSuccess) err = dev((void**)&plan->d_type_nvals, sp.type_nvals.size() * sizeof(int32_t));
   if (err == cudaSuccess) err = dev((void**)&plan->d_type_map_off, sp.type_map_off.size() * sizeof(int64_t));
   if (err == cudaSuccess) err = dev((void**)&plan->d_maps, size_t(sp.type_map_off.back()) * sizeof(int32_t));
-  if (err == cudaSuccess) err = dev((void**)&plan->d_maps3, size_t(sp.type_map_off.back() / 3) * sizeof(int32_t));
   if (err == cudaSuccess) err = dev((void**)&plan->d_tile_vbase, plan->tile_vbase.size() * sizeof(int64_t));
-  if (err == cudaSuccess) err = dev((void**)&plan->d_item_tile, sp.item_tile.size() * sizeof(int32_t));
-  if (err == cudaSuccess) err = dev((void**)&plan->d_item_start, sp.item_start.size() * sizeof(int32_t));
+  if (err == cudaSuccess) err = dev((void**)&plan->d_items, sp.items.size() * sizeof(ScatterItem));
   if (err == cudaSuccess) err = dev((void**)&plan->d_tmpl, sp.tmpl.size() * sizeof(uint32_t));
   if (err == cudaSuccess) err = dev((void**)&plan->d_tmpl_ptr, sp.tmpl_ptr.size() * sizeof(int64_t));
   if (err == cudaSuccess) err = dev((void**)&d_type_rep, sp.type_rep.size() * sizeof(int64_t));
@@ -419,8 +417,7 @@ msasm_status msasm_plan_create(const msasm_tables* tab, const msasm_macro_desc* 
     err = cudaMemsetAsync(plan->d_maps, 0xff, size_t(sp.type_map_off.back()) * sizeof(int32_t), s);   // -1
   if (err == cudaSuccess)
     err = h2d(plan->d_tile_vbase, plan->tile_vbase.data(), plan->tile_vbase.size() * sizeof(int64_t));
-  if (err == cudaSuccess) err = h2d(plan->d_item_tile, sp.item_tile.data(), sp.item_tile.size() * sizeof(int32_t));
-  if (err == cudaSuccess) err = h2d(plan->d_item_start, sp.item_start.data(), sp.item_start.size() * sizeof(int32_t));
+  if (err == cudaSuccess) err = h2d(plan->d_items, sp.items.data(), sp.items.size() * sizeof(ScatterItem));
   if (err == cudaSuccess) err = h2d(plan->d_tmpl, sp.tmpl.data(), sp.tmpl.size() * sizeof(uint32_t));
   if (err == cudaSuccess) err = h2d(plan->d_tmpl_ptr, sp.tmpl_ptr.data(), sp.tmpl_ptr.size() * sizeof(int64_t));
   if (err == cudaSuccess) err = h2d(d_type_rep, sp.type_rep.data(), sp.type_rep.size() * sizeof(int64_t));
@@ -531,6 +528,19 @@ static size_t coef_lp_bytes_for(int64_t n_tiles, int n_pi) {
   return std::max(split, emu) + 512;
 }
 
+// FP32 on the CUDA cores (FFMA): for tables wider than the exact slice accumulation allows (9 n_pi > 576)
+static msasm_status contract_f32_simt(msasm_tables* tab, const double* d_coef, int64_t n_tiles, void* d_nz,
+                                      void* scratch_lp, cudaStream_t s) {
+  const int K = 9 * tab->n_pi, n_nz = tab->n_nz, ld = ld_nz_of(n_nz);
+  if (!tab->d_T32) {
+    MSASM_CUDA(cudaMalloc(&tab->d_T32, size_t(n_nz) * K * sizeof(float)));
+    MSASM_TRY(to_f32_gpu(tab->d_T, int64_t(n_nz) * K, tab->d_T32, s));
+  }
+  float* c32 = static_cast<float*>(scratch_lp);
+  MSASM_TRY(to_f32_gpu(d_coef, 9 * n_tiles * K, c32, s));
+  return contract_simt_f32(c32, tab->d_T32, n_tiles, n_nz, K, ld, static_cast<float*>(d_nz), s);
+}
+
 static msasm_status contract_dispatch(const msasm_tables* ctab, msasm_precision prec, const double* d_coef,
                                       int64_t n_tiles, void* d_nz, void* scratch_lp, cudaStream_t s,
                                       unsigned* d_err) {
@@ -540,13 +550,19 @@ static msasm_status contract_dispatch(const msasm_tables* ctab, msasm_precision 
     case MSASM_F64:
       return contract_simt_f64(d_coef, tab->d_T, n_tiles, n_nz, K, ld, static_cast<double*>(d_nz), s);
     case MSASM_F32: {
-      if (!tab->d_T32) {
-        MSASM_CUDA(cudaMalloc(&tab->d_T32, size_t(n_nz) * K * sizeof(float)));
-        MSASM_TRY(to_f32_gpu(tab->d_T, int64_t(n_nz) * K, tab->d_T32, s));
+      // FP32 values from the tensor cores: 4 exact BF16 slices (28 bits) of each operand row, the 10
+      // slice products with i + j <= 3 accumulated exactly, the result rounded once to FP32
+      if (K > 576) return contract_f32_simt(tab, d_coef, n_tiles, d_nz, scratch_lp, s);   // beyond exactness
+      if (!tab->d_Tslices4) {
+        MSASM_CUDA(cudaMalloc(&tab->d_Tslices4, emu_slice_bytes(n_nz, K, 4)));
+        MSASM_CUDA(cudaMalloc(&tab->d_Tslice_scale4, size_t(n_nz) * sizeof(int)));
+        MSASM_TRY(emu_slice_gpu(tab->d_T, n_nz, K, K, tab->d_Tslices4, tab->d_Tslice_scale4, s, 4));
       }
-      float* c32 = static_cast<float*>(scratch_lp);
-      MSASM_TRY(to_f32_gpu(d_coef, 9 * n_tiles * K, c32, s));
-      return contract_simt_f32(c32, tab->d_T32, n_tiles, n_nz, K, ld, static_cast<float*>(d_nz), s);
+      uint8_t* sl = static_cast<uint8_t*>(scratch_lp);
+      int* sc = reinterpret_cast<int*>(sl + ((emu_slice_bytes(9 * n_tiles, K, 4) + 255) & ~size_t(255)));
+      MSASM_TRY(emu_slice_gpu(d_coef, 9 * n_tiles, K, K, sl, sc, s, 4));
+      return contract_emu_gpu(tab->d_Tslices4, tab->d_Tslice_scale4, n_nz, sl, sc, 9 * n_tiles, K, d_nz, ld, false,
+                              true, d_err, s, 4);
     }
     case MSASM_SPLIT_F16:
     case MSASM_SPLIT_BF16:
@@ -580,7 +596,7 @@ static msasm_status contract_dispatch(const msasm_tables* ctab, msasm_precision 
   }
 }
 
-static int contract_launches(msasm_precision prec) { return prec == MSASM_F64 ? 1 : 2; }
+static int contract_launches(msasm_precision prec) { return prec == MSASM_F64 ? 1 : 2; }   // slicing + product
 
 static msasm_status ensure_lp_scratch(msasm_plan* plan, msasm_precision prec) {
   if (prec == MSASM_F64) return MSASM_OK;

@@ -1,32 +1,36 @@
-// K4 (FP64 form): the contraction of eq. 58 to FP64 accuracy on the BF16 tensor cores.
+// K4 (FP64 and FP32 forms): the contraction of eq. 58 to FP64 (or FP32) accuracy on the BF16
+// tensor cores.
 //
 // GB300 executes FP64 at about 1.2 TFLOP/s, so the exact-accumulation slicing scheme of Ozaki,
 // Ogita, Oishi and Rump (2012) is used instead: every row x of either operand is scaled by a
-// power of two sigma >= max|x| and cut into S = 7 slices of 7 bits,
+// power of two sigma >= max|x| and cut into S slices of 7 bits (S = 7 for FP64, S = 4 for FP32),
 //
-//   x / sigma = sum_{i=0..6} a_i 2^-7(i+1),  a_0 in [-128, 128], a_i in [-64, 64] (i > 0),
+//   x / sigma = sum_{i=0..S-1} a_i 2^-7(i+1),  a_0 in [-128, 128], a_i in [-64, 64] (i > 0),
 //
 // each stored exactly in BF16 as s_i = a_i 2^-7i.  Then
-//   D[m][n] = sigma_m tau_n 2^-14 sum_{i+j <= 6} sum_k s_i[m][k] t_j[n][k]
-// (the terms with i + j > 6 are below 2^-49 of the result).  Grouping the products by d = i + j,
-// acc_d for d = 0..3 holds a sum of integer multiples of 2^-7d whose magnitude stays below 2^24
-// for K <= 576 (per k: |a_0 b_0| <= 2^14, 2 * 2^13, 2 * 2^13 + 2^12, 2 * 2^13 + 2 * 2^12 in units
-// of the diagonal), so the tensor cores' FP32 accumulation is exact in them whatever its
-// internal rounding; acc4 collects d = 4..6, at most 2^-28 of acc0, where that rounding is
-// harmless.  (Merging d = 3 into the last accumulator, with its mixed scales, measurably loses
+//   D[m][n] = sigma_m tau_n 2^-14 sum_{i+j <= S-1} sum_k s_i[m][k] t_j[n][k]
+// (the terms with i + j > S - 1 are below 2^-7S of the result).  Grouping the products by
+// d = i + j, acc_d for d = 0..3 holds a sum of integer multiples of 2^-7d whose magnitude stays
+// below 2^24 for K <= 576 (per k: |a_0 b_0| <= 2^14, 2 * 2^13, 2 * 2^13 + 2^12, 2 * 2^13 + 2 * 2^12
+// in units of the diagonal), so the tensor cores' FP32 accumulation is exact in them whatever its
+// internal rounding; for S = 7, acc4 collects d = 4..6, at most 2^-28 of acc0, where that rounding
+// is harmless.  (Merging d = 3 into the last accumulator, with its mixed scales, measurably loses
 // accuracy: the accumulation truncates relative to the largest term.)  The epilogue forms the
-// exact fixed-point sum X = sum_d acc_d 2^35 in int64 (acc4 rounded at 2^-35) and writes
-// X 2^(e_m + e_n - 49) as an FP64 bit pattern rounded to nearest even, with integer instructions
-// only: the FP64 pipe, about 1/64 of the FP32 rate per SM on GB300, is not used at all.
+// exact fixed-point sum X = sum_d acc_d 2^(7 n_acc) in int64 (acc4 rounded at 2^-35) and writes
+// X 2^(e_m + e_n - 14 - 7 n_acc) as an FP64 (or FP32) bit pattern rounded to nearest even, with
+// integer instructions only: the FP64 pipe, about 1/64 of the FP32 rate per SM on GB300, is not
+// used at all.  The FP32 form keeps 28 bits of each operand row (10 products, 4 accumulators, all
+// exact): its error is the truncation of the operands, the same whatever the accumulation order.
 //
 // Persistent kernel, one CTA per SM looping over 128 (m) x 96 (n) output tiles.  Per 16-element
-// k block, one 3-D TMA box brings all 7 slices of each operand (32-byte swizzle) into a 4-stage
-// ring that runs on across tiles; one lane issues the 28 MMAs (M=128, N=96, K=16, the A slice kept
-// in the collector buffer across its products) into 5 TMEM accumulators of 96 columns (480 of the
-// 512).  Eight epilogue warps (two per TMEM lane quarter, 48 columns each) drain the accumulators
-// into exact int64 sums in registers and release TMEM at once, so the MMAs of the next tile run
-// while they round and store the previous one.  In the tile-block layout of nzdata a warp rounds
-// 24 columns at a time into shared memory and writes each tile block's 32 rows as one run.
+// k block, one 3-D TMA box brings all S slices of each operand (32-byte swizzle) into a ring that
+// runs on across tiles; one lane issues the S(S+1)/2 MMAs (M=128, N=96, K=16, the A slice kept in
+// the collector buffer across its products) into min(S, 5) TMEM accumulators of 96 columns (at
+// most 480 of the 512).  Eight epilogue warps (two per TMEM lane quarter, 48 columns each) drain
+// the accumulators into exact int64 sums in registers and release TMEM at once, so the MMAs of
+// the next tile run while they round and store the previous one.  In the tile-block layout of
+// nzdata a warp rounds 24 columns at a time into shared memory and writes each tile block's 32
+// rows as one run.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -39,34 +43,34 @@
 
 namespace msasm {
 
-constexpr int EMU_S = 7;                 // slices per operand
 constexpr int EMU_BM = 128, EMU_BN = 96, EMU_KB = 16;    // k block: 16 BF16 = one 32-byte swizzle row
-constexpr int EMU_ACC = 5;                               // accumulators: d = 0, 1, 2, 3 and d >= 4
-constexpr int EMU_STAGES_ROWS = 4;                       // ring depth, row layout
-constexpr int EMU_STAGES_BLOCKS = 3;                     // ring depth, block layout (room for the staging)
 constexpr int EMU_A_SLICE = EMU_BM * 32;                 // one slice tile of A: 128 rows x 32 bytes
 constexpr int EMU_B_SLICE = EMU_BN * 32;                 // one slice tile of B: 96 rows x 32 bytes
-constexpr int EMU_A_BYTES = EMU_S * EMU_A_SLICE;         // 28 KB
-constexpr int EMU_B_BYTES = EMU_S * EMU_B_SLICE;         // 21 KB
-constexpr int EMU_STAGE_BYTES = EMU_A_BYTES + EMU_B_BYTES;
 // block layout: each epilogue warp rounds 24 columns of its 32 rows into a shared-memory buffer
 // (odd row stride: few bank conflicts either way) and writes them back tile block by tile block
 constexpr int EMU_STG_COLS = 24;
 constexpr int EMU_STG_LD = 25;
-constexpr int EMU_STG_DOUBLES = 32 * EMU_STG_LD;
-template <bool BLOCKS>
-__host__ __device__ constexpr int emu_stages() { return BLOCKS ? EMU_STAGES_BLOCKS : EMU_STAGES_ROWS; }
-template <bool BLOCKS>
-constexpr int emu_smem_bytes() {
-  return emu_stages<BLOCKS>() * EMU_STAGE_BYTES + 1024 + 256 + (BLOCKS ? 8 * EMU_STG_DOUBLES * 8 : 0);
-}
-static_assert(emu_smem_bytes<true>() <= 227 * 1024 && emu_smem_bytes<false>() <= 227 * 1024, "shared memory");
+constexpr int EMU_STG_ELEMS = 32 * EMU_STG_LD;
+
+// the kernel's shape for S slices per operand (OutT the output type, BLOCKS the nzdata layout)
+template <int S, typename OutT, bool BLOCKS>
+struct EmuShape {
+  static constexpr int kAcc = S < 5 ? S : 5;             // accumulators: d = 0..3 alone, d >= 4 together
+  static constexpr int kABytes = S * EMU_A_SLICE;        // 28 KB (S = 7)
+  static constexpr int kBBytes = S * EMU_B_SLICE;        // 21 KB (S = 7)
+  static constexpr int kStageBytes = kABytes + kBBytes;
+  static constexpr int kStages = S == 7 ? (BLOCKS ? 3 : 4) : 6;   // ring depth (room for the staging)
+  static constexpr int kStagingBytes = BLOCKS ? 8 * EMU_STG_ELEMS * int(sizeof(OutT)) : 0;
+  static constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 256 + kStagingBytes;
+  static_assert(kSmemBytes <= 227 * 1024, "shared memory per CTA");
+  static_assert(S >= 1 && S <= 7 && 5 * EMU_BN <= 512, "slices and TMEM columns");
+};
 
 struct EmuParams {
   int M, N, kblocks;
   const int* exp_m;        // sigma_m = 2^exp_m
   const int* exp_n;        // tau_n = 2^exp_n
-  double* out;             // rows: out[n][m], leading dimension ld; blocks: out[n/9][m][n%9], m stride ld
+  void* out;               // rows: out[n][m], leading dimension ld; blocks: out[n/9][m][n%9], m stride ld
   int ld;
   unsigned* err;
 };
@@ -99,6 +103,37 @@ __device__ __forceinline__ double ldexp_i64_rn(long long x, int e) {
   return __longlong_as_double((long long)(sign | ((unsigned long long)biased << 52) | (mant & ((1ull << 52) - 1))));
 }
 
+// x 2^e as the nearest FP32 (ties to even), by integer operations on the bit pattern.
+__device__ __forceinline__ float ldexp_i64_rn_f32(long long x, int e) {
+  if (x == 0) return 0.0f;
+  const uint32_t sign = x < 0 ? 0x80000000u : 0u;
+  unsigned long long u = x < 0 ? 0ull - (unsigned long long)x : (unsigned long long)x;
+  const int nbits = 64 - __clzll(u);
+  int exp = nbits - 1 + e;                                     // unbiased exponent of the result
+  unsigned long long mant;
+  if (nbits <= 24) {
+    mant = u << (24 - nbits);
+  } else {
+    const int sh = nbits - 24;
+    mant = u >> sh;
+    const unsigned long long rem = u & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (mant & 1ull))) {
+      ++mant;
+      if (mant == (1ull << 24)) {
+        mant >>= 1;
+        ++exp;
+      }
+    }
+  }
+  const int biased = exp + 127;
+  if (biased <= 0) return __uint_as_float(sign);                      // below the normal range
+  if (biased >= 255) return __uint_as_float(sign | 0x7F800000u);
+  return __uint_as_float(sign | (uint32_t(biased) << 23) | uint32_t(mant & 0x7FFFFFull));
+}
+
+__device__ __forceinline__ double round_out(long long x, int e, double*) { return ldexp_i64_rn(x, e); }
+__device__ __forceinline__ float round_out(long long x, int e, float*) { return ldexp_i64_rn_f32(x, e); }
+
 constexpr int EMU_BAND = 32;                              // m tiles per band of the tile order
 constexpr int EMU_EPI_WARPS = 8;                          // two per TMEM lane quarter
 constexpr int EMU_THREADS = 64 + 32 * EMU_EPI_WARPS;      // producer warp, MMA warp, epilogue warps
@@ -123,10 +158,13 @@ __device__ __forceinline__ long long f32_to_i64_rn(float y) {
   return (b >> 31) ? -(long long)r : (long long)r;
 }
 
-template <bool ACCUMULATE, bool BLOCKS>
+template <int S, typename OutT, bool ACCUMULATE, bool BLOCKS>
 __global__ void __launch_bounds__(EMU_THREADS, 1)
     contract_emu_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, EmuParams p) {
-  constexpr int EMU_STAGES = emu_stages<BLOCKS>();
+  using Sh = EmuShape<S, OutT, BLOCKS>;
+  constexpr int EMU_STAGES = Sh::kStages, EMU_STAGE_BYTES = Sh::kStageBytes, EMU_A_BYTES = Sh::kABytes;
+  constexpr int EMU_ACC = Sh::kAcc;
+  OutT* const out = static_cast<OutT*>(p.out);
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -138,7 +176,7 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
   const uint32_t tmem_empty = bar0 + 8u * (2 * EMU_STAGES + 1);  // accumulators drained
   uint32_t* tmem_slot =
       reinterpret_cast<uint32_t*>(gen_base + EMU_STAGES * EMU_STAGE_BYTES + 8 * (2 * EMU_STAGES + 2));
-  double* staging = reinterpret_cast<double*>(gen_base + EMU_STAGES * EMU_STAGE_BYTES + 256);
+  OutT* staging = reinterpret_cast<OutT*>(gen_base + EMU_STAGES * EMU_STAGE_BYTES + 256);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n_nt = (p.N + EMU_BN - 1) / EMU_BN, n_mt = (p.M + EMU_BM - 1) / EMU_BM;
   const long long total = (long long)n_nt * n_mt;
@@ -175,7 +213,7 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0 && lane == 0) {
-    // ---------------- TMA producer: both operands' 7 slices per k block, ring across tiles
+    // ---------------- TMA producer: both operands' S slices per k block, ring across tiles
     uint32_t g = 0;
     bool ok = true;
     for (long long t = blockIdx.x; t < total && ok; t += gridDim.x) {
@@ -198,7 +236,7 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
     for (uint32_t q = (g > uint32_t(EMU_STAGES) ? g - EMU_STAGES : 0u); q < g; ++q)
       mbar_wait(full_bar(int(q % EMU_STAGES)), (q / EMU_STAGES) & 1, p.err);
   } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer: 28 products per k block, grouped by i + j
+    // ---------------- MMA issuer: S(S+1)/2 products per k block, grouped by i + j
     const uint32_t idesc = instr_desc(1u, EMU_BM, EMU_BN);        // BF16 x BF16 -> F32
     uint32_t g = 0, i_tile = 0;
     bool ok = true;
@@ -218,20 +256,20 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
         tc_fence_after();
         const uint32_t st = base + s * EMU_STAGE_BYTES;
 #pragma unroll
-        for (int i = 0; i < EMU_S; ++i) {
-          // slice i of A stays in the collector buffer for its 7 - i products
+        for (int i = 0; i < S; ++i) {
+          // slice i of A stays in the collector buffer for its S - i products
           const uint64_t a = sw32_desc(st + i * EMU_A_SLICE);
 #pragma unroll
-          for (int j = 0; j + i < EMU_S; ++j) {
+          for (int j = 0; j + i < S; ++j) {
             const int acc = (i + j < EMU_ACC - 1) ? i + j : EMU_ACC - 1;
             const uint64_t b = sw32_desc(st + EMU_A_BYTES + j * EMU_B_SLICE);
             const uint32_t accumulate = (started >> acc) & 1u;
             const uint32_t d = tmem + uint32_t(acc * EMU_BN);
-            if (i + j == EMU_S - 1 && j == 0)
+            if (i + j == S - 1 && j == 0)
               mma_f16(d, a, b, idesc, accumulate);                                   // a single product
             else if (j == 0)
               mma_f16_collect<CollectorA::FILL>(d, a, b, idesc, accumulate);
-            else if (i + j == EMU_S - 1)
+            else if (i + j == S - 1)
               mma_f16_collect<CollectorA::LASTUSE>(d, a, b, idesc, accumulate);
             else
               mma_f16_collect<CollectorA::USE>(d, a, b, idesc, accumulate);
@@ -244,7 +282,7 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
     }
     if (i_tile > 0) mbar_wait(accum_full, (i_tile - 1) & 1, p.err);   // nothing in flight at exit
   } else if (warp >= 2) {
-    // ---------------- epilogue: drain five accumulators into exact int64 sums, release, round, store
+    // ---------------- epilogue: drain the accumulators into exact int64 sums, release, round, store
     const int q = warp & 3;                                       // TMEM lane quarter of this warp
     const int h = (warp - 2) >> 2;                                // column half
     const uint32_t lane_off = uint32_t(32 * q) << 16;
@@ -269,23 +307,26 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
           for (int j = 0; j < 8; ++j) asm volatile("" : "+r"(v[a][j]));   // uses stay after the wait
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-          // exact integers: acc0, acc1 2^7, acc2 2^14, acc3 2^21 (all below 2^24 in magnitude)
-          X[8 * c + j] = ((long long)__float2int_rn(__uint_as_float(v[0][j])) << 35) +
-                         ((long long)__float2int_rn(__uint_as_float(v[1][j]) * 128.0f) << 28) +
-                         ((long long)__float2int_rn(__uint_as_float(v[2][j]) * 16384.0f) << 21) +
-                         ((long long)__float2int_rn(__uint_as_float(v[3][j]) * 2097152.0f) << 14) +
-                         f32_to_i64_rn(__uint_as_float(v[4][j]) * 34359738368.0f);
+          // exact integers acc_d 2^7d for d <= 3 (all below 2^24 in magnitude) at weight 2^7(n_acc - d);
+          // for S = 7, acc4 (d >= 4) rounded at 2^-35
+          long long x = 0;
+#pragma unroll
+          for (int a = 0; a < (EMU_ACC < 4 ? EMU_ACC : 4); ++a)
+            x += (long long)__float2int_rn(__uint_as_float(v[a][j]) * __int_as_float((127 + 7 * a) << 23))
+                 << (7 * (EMU_ACC - a));
+          if constexpr (EMU_ACC == 5) x += f32_to_i64_rn(__uint_as_float(v[4][j]) * 34359738368.0f);
+          X[8 * c + j] = x;
         }
       }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(tmem_empty);                     // the MMAs of the next tile may start
       const int m = m0 + 32 * q + lane;
-      const int em = (m < p.M) ? p.exp_m[m] - 49 : 0;            // D = X 2^(e_m + e_n - 14 - 35)
+      const int em = (m < p.M) ? p.exp_m[m] - 14 - 7 * EMU_ACC : 0;   // D = X 2^(e_m + e_n - 14 - 7 n_acc)
       if constexpr (BLOCKS) {
         // the tile blocks of eq. 58, nz[t][m][3a + b] for n = 9t + 3a + b: the 32 rows of a block
         // are one run of 32 x 9 values, written with consecutive lanes on consecutive addresses
-        double* stg = staging + (warp - 2) * EMU_STG_DOUBLES;
+        OutT* stg = staging + (warp - 2) * EMU_STG_ELEMS;
         const int mr0 = m0 + 32 * q;
 #pragma unroll
         for (int half = 0; half < EMU_EPI_COLS / EMU_STG_COLS; ++half) {
@@ -294,14 +335,14 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
           for (int j = 0; j < EMU_STG_COLS; ++j) {
             const int n = c0 + j;
             stg[lane * EMU_STG_LD + j] =
-                (m < p.M && n < p.N) ? ldexp_i64_rn(X[half * EMU_STG_COLS + j], em + p.exp_n[n]) : 0.0;
+                (m < p.M && n < p.N) ? round_out(X[half * EMU_STG_COLS + j], em + p.exp_n[n], stg) : OutT(0);
           }
           __syncwarp();
           const int cend = min(c0 + EMU_STG_COLS, p.N);
           for (int tb = c0 / 9; 9 * tb < cend; ++tb) {
             const int ka = max(9 * tb, c0), kc = min(9 * tb + 9, cend) - ka;   // columns of block tb here
-            double* dst = p.out + (size_t(tb) * size_t(p.ld) + size_t(mr0)) * 9 + (ka - 9 * tb);
-            const double* src = stg + (ka - c0);
+            OutT* dst = out + (size_t(tb) * size_t(p.ld) + size_t(mr0)) * 9 + (ka - 9 * tb);
+            const OutT* src = stg + (ka - c0);
             for (int e = lane; e < 32 * kc; e += 32) {
               const int r = e / kc, kk = e - r * kc;
               if (mr0 + r < p.M) dst[r * 9 + kk] = src[r * EMU_STG_LD + kk];
@@ -314,8 +355,8 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
         for (int j = 0; j < EMU_EPI_COLS; ++j) {
           const int n = n0 + j;
           if (n < p.N) {
-            double* o = p.out + size_t(n) * p.ld + m;
-            const double v = ldexp_i64_rn(X[j], em + p.exp_n[n]);
+            OutT* o = out + size_t(n) * p.ld + m;
+            const OutT v = round_out(X[j], em + p.exp_n[n], o);
             if constexpr (ACCUMULATE) *o += v;
             else *o = v;
           }
@@ -331,9 +372,9 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
   }
 }
 
-// x 2^(49 - e) rounded to the nearest integer (ties to even), for |x| < 2^e, from the FP64 bit
+// x 2^(bits - e) rounded to the nearest integer (ties to even), for |x| < 2^e, from the FP64 bit
 // pattern by integer shifts: the fixed-point value whose base-128 digits are the slices.
-__device__ __forceinline__ long long fixed_point_49(double x, int e) {
+__device__ __forceinline__ long long fixed_point(double x, int e, int bits) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const int E = int((b >> 52) & 0x7ffu);
   unsigned long long M = b & ((1ull << 52) - 1);
@@ -343,8 +384,9 @@ __device__ __forceinline__ long long fixed_point_49(double x, int e) {
     M |= 1ull << 52;
     Eeff = E;
   }
-  // |x| = M 2^(Eeff - 1075), so X = M 2^-s with s = 1026 + e - Eeff (s >= 4 for a normal x < 2^e)
-  const int sh = 1026 + e - Eeff;
+  // |x| = M 2^(Eeff - 1075), so X = M 2^-s with s = 1075 - bits + e - Eeff (s >= 4 for a normal x < 2^e
+  // and bits <= 49)
+  const int sh = 1075 - bits + e - Eeff;
   unsigned long long X;
   if (sh <= 0) {
     X = M << (-sh);
@@ -358,9 +400,10 @@ __device__ __forceinline__ long long fixed_point_49(double x, int e) {
   return (b >> 63) ? -(long long)X : (long long)X;
 }
 
-// One warp per row: sigma = 2^e >= max|x| and the 7 BF16 slices s_i = a_i 2^-7i, [i][row][Kpad],
-// where X = x 2^(49-e) = sum_i a_i 128^(6-i) with balanced digits a_i in [-64, 63] (i > 0) and
+// One warp per row: sigma = 2^e >= max|x| and the S BF16 slices s_i = a_i 2^-7i, [i][row][Kpad],
+// where X = x 2^(7S-e) = sum_i a_i 128^(S-1-i) with balanced digits a_i in [-64, 63] (i > 0) and
 // |a_0| <= 128.  Integer instructions only (the FP64 pipe runs at 1/64 of the FP32 rate).
+template <int S>
 __global__ void emu_slice_kernel(const double* __restrict__ x, int64_t rows, int64_t ldx, int K, int Kpad,
                                  __nv_bfloat16* __restrict__ slices, int* __restrict__ scale_exp) {
   const int lane = threadIdx.x & 31;
@@ -381,13 +424,13 @@ __global__ void emu_slice_kernel(const double* __restrict__ x, int64_t rows, int
     if (lane == 0) scale_exp[r] = e;
     for (int k = 2 * lane; k < Kpad; k += 64) {
       long long X[2];
-      X[0] = (k < K) ? fixed_point_49(xr[k], e) : 0;
-      X[1] = (k + 1 < K) ? fixed_point_49(xr[k + 1], e) : 0;
-      int a[2][EMU_S];
+      X[0] = (k < K) ? fixed_point(xr[k], e, 7 * S) : 0;
+      X[1] = (k + 1 < K) ? fixed_point(xr[k + 1], e, 7 * S) : 0;
+      int a[2][S];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
 #pragma unroll
-        for (int i = EMU_S - 1; i >= 1; --i) {
+        for (int i = S - 1; i >= 1; --i) {
           const long long d = ((X[h] + 64) & 127) - 64;
           a[h][i] = int(d);
           X[h] = (X[h] - d) / 128;             // exact
@@ -395,7 +438,7 @@ __global__ void emu_slice_kernel(const double* __restrict__ x, int64_t rows, int
         a[h][0] = int(X[h]);
       }
 #pragma unroll
-      for (int i = 0; i < EMU_S; ++i) {
+      for (int i = 0; i < S; ++i) {
         const float p = __int_as_float((127 - 7 * i) << 23);      // 2^-7i
         __nv_bfloat162 v;
         v.x = __float2bfloat16_rn(float(a[0][i]) * p);            // exact: |a| <= 128
@@ -408,15 +451,22 @@ __global__ void emu_slice_kernel(const double* __restrict__ x, int64_t rows, int
 
 int emu_kpad(int K) { return (K + EMU_KB - 1) / EMU_KB * EMU_KB; }
 
-size_t emu_slice_bytes(int64_t rows, int K) { return size_t(EMU_S) * rows * emu_kpad(K) * sizeof(__nv_bfloat16); }
+size_t emu_slice_bytes(int64_t rows, int K, int n_slices) {
+  return size_t(n_slices) * rows * emu_kpad(K) * sizeof(__nv_bfloat16);
+}
 
-// rows of x with leading dimension ldx (elements), K of them each
+// rows of x with leading dimension ldx (elements), K of them each, into n_slices (7 or 4) slices
 msasm_status emu_slice_gpu(const double* x, int64_t rows, int64_t ldx, int K, void* slices, int* scale_exp,
-                           cudaStream_t s) {
+                           cudaStream_t s, int n_slices) {
   if (K > 576 + 15) return fail(MSASM_EUNSUPPORTED, "FP64 emulation is exact for K <= 576 (q <= 3)");
+  if (n_slices != 7 && n_slices != 4) return fail(MSASM_EINVAL, "emulation slices must be 7 (FP64) or 4 (FP32)");
   int64_t blocks = std::min<int64_t>((rows * 32 + 255) / 256, 152 * 16);
-  emu_slice_kernel<<<unsigned(blocks), 256, 0, s>>>(x, rows, ldx, K, emu_kpad(K), static_cast<__nv_bfloat16*>(slices),
-                                                    scale_exp);
+  if (n_slices == 7)
+    emu_slice_kernel<7><<<unsigned(blocks), 256, 0, s>>>(x, rows, ldx, K, emu_kpad(K),
+                                                         static_cast<__nv_bfloat16*>(slices), scale_exp);
+  else
+    emu_slice_kernel<4><<<unsigned(blocks), 256, 0, s>>>(x, rows, ldx, K, emu_kpad(K),
+                                                         static_cast<__nv_bfloat16*>(slices), scale_exp);
   MSASM_CUDA(cudaGetLastError());
   return MSASM_OK;
 }
@@ -424,7 +474,7 @@ msasm_status emu_slice_gpu(const double* x, int64_t rows, int64_t ldx, int K, vo
 static PFN_cuTensorMapEncodeTiled_v12000 g_encode3 = nullptr;
 static std::mutex g_encode3_mutex;
 
-static msasm_status make_map_3d(CUtensorMap* map, const void* ptr, int64_t rows, int K, int box_rows) {
+static msasm_status make_map_3d(CUtensorMap* map, const void* ptr, int64_t rows, int K, int box_rows, int n_slices) {
   {
     std::lock_guard<std::mutex> lock(g_encode3_mutex);
     if (!g_encode3) {
@@ -436,9 +486,9 @@ static msasm_status make_map_3d(CUtensorMap* map, const void* ptr, int64_t rows,
     }
   }
   const int Kpad = emu_kpad(K);
-  cuuint64_t dims[3] = {cuuint64_t(K), cuuint64_t(rows), cuuint64_t(EMU_S)};
+  cuuint64_t dims[3] = {cuuint64_t(K), cuuint64_t(rows), cuuint64_t(n_slices)};
   cuuint64_t strides[2] = {cuuint64_t(Kpad) * 2, cuuint64_t(rows) * Kpad * 2};
-  cuuint32_t box[3] = {cuuint32_t(EMU_KB), cuuint32_t(box_rows), cuuint32_t(EMU_S)};
+  cuuint32_t box[3] = {cuuint32_t(EMU_KB), cuuint32_t(box_rows), cuuint32_t(n_slices)};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = g_encode3(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(ptr), dims, strides, box, estr,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -447,18 +497,37 @@ static msasm_status make_map_3d(CUtensorMap* map, const void* ptr, int64_t rows,
   return MSASM_OK;
 }
 
-// D[m][n] = sum_k A[m][k] B[n][k] (FP64) from the slices of A (M rows) and B (N rows), stored as
-// out[n][m] with leading dimension ld (blocks = false; accumulate adds to out), or as the tile
-// blocks of eq. 58, out[n/9][m][n%9] with m stride ld (blocks = true; N a multiple of 9).
+template <int S, typename OutT, bool ACCUMULATE, bool BLOCKS>
+static msasm_status launch_emu(const CUtensorMap& ma, const CUtensorMap& mb, const EmuParams& p, cudaStream_t s) {
+  constexpr int smem = EmuShape<S, OutT, BLOCKS>::kSmemBytes;
+  auto kernel = contract_emu_kernel<S, OutT, ACCUMULATE, BLOCKS>;
+  MSASM_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  const long long tiles = ((p.N + EMU_BN - 1) / EMU_BN) * (long long)((p.M + EMU_BM - 1) / EMU_BM);
+  if (tiles == 0) return MSASM_OK;
+  int dev = 0, n_sm = 0;
+  MSASM_CUDA(cudaGetDevice(&dev));
+  MSASM_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+  const unsigned grid = unsigned(std::min<long long>(tiles, std::max(n_sm, 1)));   // one CTA per SM
+  kernel<<<grid, EMU_THREADS, smem, s>>>(ma, mb, p);
+  MSASM_CUDA(cudaGetLastError());
+  return MSASM_OK;
+}
+
+// D[m][n] = sum_k A[m][k] B[n][k] from the slices of A (M rows) and B (N rows), n_slices of each:
+// 7 slices give FP64 results (out double*), 4 give FP32 results (out float*, block layout only).
+// Stored as out[n][m] with leading dimension ld (blocks = false; accumulate adds to out), or as the
+// tile blocks of eq. 58, out[n/9][m][n%9] with m stride ld (blocks = true; N a multiple of 9).
 msasm_status contract_emu_gpu(const void* a_slices, const int* a_exp, int M, const void* b_slices,
-                              const int* b_exp, int64_t N, int K, double* out, int ld, bool accumulate, bool blocks,
-                              unsigned* d_err, cudaStream_t s) {
+                              const int* b_exp, int64_t N, int K, void* out, int ld, bool accumulate, bool blocks,
+                              unsigned* d_err, cudaStream_t s, int n_slices) {
   if (N > int64_t(2147483647) * EMU_BN) return fail(MSASM_EUNSUPPORTED, "too many rows for one launch");
   if (blocks && (accumulate || N % 9 != 0))
     return fail(MSASM_EINVAL, "the block layout takes whole tiles (N a multiple of 9) and no accumulation");
+  if (n_slices != 7 && !(n_slices == 4 && blocks))
+    return fail(MSASM_EINVAL, "the 4-slice (FP32) contraction writes the block layout only");
   CUtensorMap ma, mb;
-  MSASM_TRY(make_map_3d(&ma, a_slices, M, K, EMU_BM));
-  MSASM_TRY(make_map_3d(&mb, b_slices, N, K, EMU_BN));
+  MSASM_TRY(make_map_3d(&ma, a_slices, M, K, EMU_BM, n_slices));
+  MSASM_TRY(make_map_3d(&mb, b_slices, N, K, EMU_BN, n_slices));
   EmuParams p;
   p.M = M;
   p.N = int(N);
@@ -468,19 +537,9 @@ msasm_status contract_emu_gpu(const void* a_slices, const int* a_exp, int M, con
   p.out = out;
   p.ld = ld;
   p.err = d_err;
-  auto kernel = blocks ? contract_emu_kernel<false, true>
-                      : (accumulate ? contract_emu_kernel<true, false> : contract_emu_kernel<false, false>);
-  const int smem = blocks ? emu_smem_bytes<true>() : emu_smem_bytes<false>();
-  MSASM_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  const long long tiles = ((N + EMU_BN - 1) / EMU_BN) * (long long)((M + EMU_BM - 1) / EMU_BM);
-  if (tiles == 0) return MSASM_OK;
-  int dev = 0, n_sm = 0;
-  MSASM_CUDA(cudaGetDevice(&dev));
-  MSASM_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
-  const unsigned grid = unsigned(std::min<long long>(tiles, std::max(n_sm, 1)));   // one CTA per SM
-  kernel<<<grid, EMU_THREADS, smem, s>>>(ma, mb, p);
-  MSASM_CUDA(cudaGetLastError());
-  return MSASM_OK;
+  if (n_slices == 4) return launch_emu<4, float, false, true>(ma, mb, p, s);
+  if (blocks) return launch_emu<7, double, false, true>(ma, mb, p, s);
+  return accumulate ? launch_emu<7, double, true, false>(ma, mb, p, s) : launch_emu<7, double, false, false>(ma, mb, p, s);
 }
 
 }  // namespace msasm

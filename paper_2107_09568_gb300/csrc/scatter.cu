@@ -11,10 +11,7 @@
 // Direct pass: the rows of the points a tile owns are one contiguous range of values, laid out
 // the same way for every tile of its type.  The type's value map (built once per plan from its
 // representative tile) holds for every value of the range its source in the tile's nzdata,
-// 9 m + 3a + b, or -1 where no block of the tile lands.  Every row is a sequence of 3-value
-// segments, one per column point, each from one block: (a, b = 0..2) of an upper block, sources
-// 9 m + 3a + b (stride 1), or (a = 0..2, b) of a lower one, 9 m + 3a + b (stride 3); the direct
-// pass reads the compact segment map, (first source << 1) | lower, or -1; each thread writes consecutive values
+// 9 m + 3a + b, or -1 where no block of the tile lands; each thread writes consecutive values
 // of the range (coalesced stores) from gathers that the tile's nzdata, read by the CTAs working
 // on the tile at the same time, serves mostly from L2.  Every CSR value is written exactly once.
 //
@@ -37,37 +34,36 @@ namespace msasm {
 constexpr int kDirectThreads = 256;
 constexpr int kDirectPerThread = kScatterSegment / kDirectThreads;   // 16
 
+// One work item per CTA, in tile order: the CTAs the hardware keeps resident work on a few
+// consecutive tiles, whose nzdata stays in L2 for the gathers of both the upper and the lower
+// blocks.  The item's descriptor is one load, so the dependent chain before the gathers is
+// descriptor -> value map.  Each thread owns values i = u * 256 + threadIdx.x of the item (a
+// warp's loads and stores cover 32 consecutive values); every gather is issued before the first
+// store.
 template <typename T>
-__global__ void __launch_bounds__(kDirectThreads) scatter_direct_kernel(
-    const T* __restrict__ nz, int ld_nz, int64_t t0, const int32_t* __restrict__ item_tile,
-    const int32_t* __restrict__ item_start, const int64_t* __restrict__ tile_vbase,
-    const int32_t* __restrict__ tile_type, const int64_t* __restrict__ type_map_off,
-    const int32_t* __restrict__ type_nvals, const int32_t* __restrict__ maps3, T* __restrict__ values, int64_t v_lo) {
-  const int64_t t = item_tile[blockIdx.x];
-  const int s0 = item_start[blockIdx.x];
-  const int ty = tile_type[t];
-  const int end = min(s0 + kScatterSegment, type_nvals[ty]);
-  const int32_t* map3 = maps3 + type_map_off[ty] / 3;           // ranges and offsets are multiples of 9
-  const T* nzt = nz + 9 * (t - t0) * ld_nz;
-  T* out = values + (tile_vbase[t] - v_lo);
+__global__ void __launch_bounds__(kDirectThreads, sizeof(T) == 8 ? 5 : 8) scatter_direct_kernel(
+    const T* __restrict__ nz, int ld_nz, int64_t t0, const ScatterItem* __restrict__ items,
+    const int32_t* __restrict__ maps, T* __restrict__ values, int64_t v_lo) {
+  const int tid = int(threadIdx.x);
+  const ScatterItem it = items[blockIdx.x];
+  const int32_t* map = maps + it.map_off;
   int k[kDirectPerThread];
 #pragma unroll
   for (int u = 0; u < kDirectPerThread; ++u) {
-    const int i = s0 + u * kDirectThreads + int(threadIdx.x);
-    if (i < end) {
-      const int e = map3[i / 3], c = i % 3;
-      k[u] = (e < 0) ? -1 : (e >> 1) + c * (1 + 2 * (e & 1));
-    } else {
-      k[u] = -2;
-    }
+    const int i = u * kDirectThreads + tid;
+    k[u] = (i < it.count) ? __ldg(map + i) : -1;
   }
+  const T* nzt = nz + 9 * (int64_t(it.tile) - t0) * ld_nz;
   T v[kDirectPerThread];
 #pragma unroll
   for (int u = 0; u < kDirectPerThread; ++u) v[u] = (k[u] >= 0) ? __ldg(nzt + k[u]) : T(0);
   asm volatile("" ::: "memory");                  // every gather is issued before the first store
+  T* out = values + (it.out_off - v_lo);
 #pragma unroll
-  for (int u = 0; u < kDirectPerThread; ++u)
-    if (k[u] != -2) out[s0 + u * kDirectThreads + int(threadIdx.x)] = v[u];
+  for (int u = 0; u < kDirectPerThread; ++u) {
+    const int i = u * kDirectThreads + tid;
+    if (i < it.count) out[i] = v[u];
+  }
 }
 
 // Value maps of all types from their representative tiles (maps preset to -1).
@@ -101,23 +97,6 @@ __global__ void type_maps_kernel(const int64_t* __restrict__ type_rep, int n_typ
   }
 }
 
-// Segment maps from the value maps: one entry per 3 values, (first source << 1) | lower, or -1.
-__global__ void segment_maps_kernel(const int32_t* __restrict__ maps, int64_t n_seg, int32_t* __restrict__ maps3,
-                                    unsigned long long* __restrict__ bad) {
-  for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < n_seg; s += int64_t(gridDim.x) * blockDim.x) {
-    const int32_t a = maps[3 * s], b = maps[3 * s + 1], c = maps[3 * s + 2];
-    int32_t e = -1;
-    if (a >= 0) {
-      const int32_t d = b - a;
-      e = (a << 1) | (d == 3 ? 1 : 0);
-      if ((d != 1 && d != 3) || c - b != d) atomicAdd(bad, 1ull);   // not one block's row segment
-    } else if (b >= 0 || c >= 0) {
-      atomicAdd(bad, 1ull);
-    }
-    maps3[s] = e;
-  }
-}
-
 // Every tile of a type places its blocks where the representative does (same column ranks).
 __global__ void rank_invariance_kernel(const int32_t* __restrict__ tile_type, const int64_t* __restrict__ type_rep,
                                        int64_t n_tiles, int n_nz, const uint32_t* __restrict__ rank,
@@ -143,11 +122,6 @@ msasm_status scatter_maps_gpu(msasm_plan* plan, const int64_t* d_type_rep, int n
   rank_invariance_kernel<<<152 * 8, 256, 0, stream>>>(plan->d_tile_type, d_type_rep, plan->n_tiles, tab->n_nz,
                                                       plan->d_rank, d_bad);
   MSASM_CUDA(cudaGetLastError());
-  const int64_t n_seg = plan->type_map_off_host.back() / 3;
-  if (n_seg > 0) {
-    segment_maps_kernel<<<152 * 4, 256, 0, stream>>>(plan->d_maps, n_seg, plan->d_maps3, d_bad);
-    MSASM_CUDA(cudaGetLastError());
-  }
   return MSASM_OK;
 }
 
@@ -239,9 +213,9 @@ msasm_status scatter_pass_gpu(const msasm_plan* plan, const T* d_nz, int ld_nz, 
   const int64_t td = std::max(t0, std::min(t0 + n_tiles, direct_end));
   const int64_t i0 = plan->item_ptr[size_t(t0)], i1 = plan->item_ptr[size_t(td)];
   if (i1 > i0) {
-    scatter_direct_kernel<T><<<unsigned(i1 - i0), kDirectThreads, 0, stream>>>(
-        d_nz, ld_nz, t0, plan->d_item_tile + i0, plan->d_item_start + i0, plan->d_tile_vbase, plan->d_tile_type,
-        plan->d_type_map_off, plan->d_type_nvals, plan->d_maps3, d_values, v_lo);
+    if (i1 - i0 > 2147483647LL) return fail(MSASM_EUNSUPPORTED, "too many scatter work items for one launch");
+    scatter_direct_kernel<T><<<unsigned(i1 - i0), kDirectThreads, 0, stream>>>(d_nz, ld_nz, t0, plan->d_items + i0,
+                                                                               plan->d_maps, d_values, v_lo);
     MSASM_CUDA(cudaGetLastError());
   }
   const int64_t e0 = plan->sec_off_host[size_t(t0)], e1 = plan->sec_off_host[size_t(t0 + n_tiles)];

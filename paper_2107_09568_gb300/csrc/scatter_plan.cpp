@@ -5,7 +5,8 @@
 // owned points of a tile have consecutive global ids (tile-major numbering), so their CSR rows
 // form one contiguous range of values, laid out the same way for every tile of the type: one
 // value map per type (built on the GPU from the type's representative tile) gives the source
-// of every value of the range.  The range is cut into work items of kScatterSegment values.
+// of every value of the range.  The range is cut into work items of kScatterSegment values, each
+// described by one ScatterItem (its map offset, output offset, tile and count).
 // Blocks landing in rows owned by a lower tile form the type's secondary template, added after
 // the owner has written its rows; per tile, its entries are numbered from sec_off[t].
 #include <algorithm>
@@ -94,8 +95,7 @@ msasm_status build_scatter_plan(msasm_plan* plan, const std::vector<int32_t>& gm
   }
   // every tile has its type's layout: owned points with consecutive ids in local order and the
   // same row lengths; work items of kScatterSegment values
-  out.item_tile.clear();
-  out.item_start.clear();
+  out.items.clear();
   out.item_ptr.assign(size_t(plan->n_tiles) + 1, 0);
   out.sec_off.assign(size_t(plan->n_tiles) + 1, 0);
   for (int64_t t = 0; t < plan->n_tiles; ++t) {
@@ -111,11 +111,16 @@ msasm_status build_scatter_plan(msasm_plan* plan, const std::vector<int32_t>& gm
       if (pptr[size_t(g[A]) + 1] - pptr[size_t(g[A])] != deg_of[size_t(ty)][size_t(A)])
         return fail(MSASM_EUNSUPPORTED, "tile numbering is not translation invariant within a tile type");
     }
-    for (int s0 = 0; s0 < out.type_nvals[size_t(ty)]; s0 += kScatterSegment) {
-      out.item_tile.push_back(int32_t(t));
-      out.item_start.push_back(s0);
+    const int32_t nv = out.type_nvals[size_t(ty)];
+    for (int32_t s0 = 0; s0 < nv; s0 += kScatterSegment) {
+      ScatterItem it;
+      it.map_off = out.type_map_off[size_t(ty)] + s0;
+      it.out_off = plan->tile_vbase[size_t(t)] + s0;
+      it.tile = int32_t(t);
+      it.count = std::min(kScatterSegment, nv - s0);
+      out.items.push_back(it);
     }
-    out.item_ptr[size_t(t) + 1] = int64_t(out.item_tile.size());
+    out.item_ptr[size_t(t) + 1] = int64_t(out.items.size());
     out.sec_off[size_t(t) + 1] = out.sec_off[size_t(t)] + (out.tmpl_ptr[size_t(ty) + 1] - out.tmpl_ptr[size_t(ty)]);
   }
   return MSASM_OK;
