@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(kDirectThreads, sizeof(T) == 8 ? 5 : 8) scatte
 #pragma unroll
   for (int u = 0; u < kDirectPerThread; ++u) {
     const int i = u * kDirectThreads + tid;
-    k[u] = (i < it.count) ? __ldg(map + i) : -1;
+    k[u] = (i < it.count) ? map[i] : -2;          // -1: no block of the tile lands here (value 0)
   }
   const T* nzt = nz + 9 * (int64_t(it.tile) - t0) * ld_nz;
   T v[kDirectPerThread];
@@ -60,10 +60,8 @@ __global__ void __launch_bounds__(kDirectThreads, sizeof(T) == 8 ? 5 : 8) scatte
   asm volatile("" ::: "memory");                  // every gather is issued before the first store
   T* out = values + (it.out_off - v_lo);
 #pragma unroll
-  for (int u = 0; u < kDirectPerThread; ++u) {
-    const int i = u * kDirectThreads + tid;
-    if (i < it.count) out[i] = v[u];
-  }
+  for (int u = 0; u < kDirectPerThread; ++u)
+    if (k[u] != -2) out[u * kDirectThreads + tid] = v[u];
 }
 
 // Value maps of all types from their representative tiles (maps preset to -1).
