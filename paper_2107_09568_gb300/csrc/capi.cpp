@@ -82,6 +82,10 @@ msasm_status emu_slice_gpu(const double* x, int64_t rows, int64_t ldx, int K, vo
 msasm_status contract_emu_gpu(const void* a_slices, const int* a_exp, int M, const void* b_slices, const int* b_exp,
                               int64_t N, int K, void* out, int ld, bool accumulate, bool blocks, unsigned* d_err,
                               cudaStream_t s, int n_slices = 7);
+msasm_status contract_tc_linop_gpu(int kind, const void* a_hi, const void* a_lo, const float* a_scale, int M,
+                                   const void* b_hi, const void* b_lo, const float* b_scale, int64_t N, int K,
+                                   const double* u, double* y, const int32_t* gmap, const int32_t* pairs, int n_T,
+                                   int64_t t0, unsigned* d_err, cudaStream_t s);
 int tc_kpad(int K, int kind);
 size_t tc_slice_bytes(int64_t rows, int K, int kind);
 msasm_status tc_split_gpu(const double* x, int64_t rows, int K, int kind, void* hi, void* lo, float* row_scale,
@@ -899,10 +903,29 @@ msasm_status msasm_linop_apply(msasm_plan* plan, const double* d_coef, msasm_pre
   if (!plan || !d_coef || !d_u || !d_y) return fail(MSASM_EINVAL, "plan, d_coef, d_u or d_y is NULL");
   if (prec < MSASM_F64 || prec > MSASM_F64_EMU) return fail(MSASM_EINVAL, "unknown precision");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  MSASM_TRY(linop_prepare_gpu(plan, s));
   MSASM_TRY(ensure_lp_scratch(plan, prec));
   const int K = 9 * plan->tab->n_pi, ld = ld_nz_of(plan->tab->n_nz);
   const int64_t P = plan->tiles_per_pass;
+  const int kind = tc_kind_of(prec);
+  if (kind >= 0) {
+    // split tensor-core forms: the contraction's epilogue applies every tile block to u and adds it
+    // into y (Sec. 4.2: the local matrices are never stored; no nzdata scratch)
+    msasm_tables* tab = const_cast<msasm_tables*>(plan->tab);
+    MSASM_TRY(ensure_table_slices(tab, kind, s));
+    MSASM_CUDA(cudaMemsetAsync(d_y, 0, size_t(plan->n_rows) * sizeof(double), s));
+    for (int64_t t0 = 0; t0 < plan->n_tiles; t0 += P) {
+      const int64_t nt = std::min(P, plan->n_tiles - t0);
+      const size_t sb = tc_slice_bytes(9 * nt, K, kind);
+      uint8_t* hi = static_cast<uint8_t*>(plan->d_coef_lp);
+      uint8_t* lo = hi + sb;
+      float* sc = reinterpret_cast<float*>(lo + sb);
+      MSASM_TRY(tc_split_gpu(d_coef + size_t(9 * t0) * K, 9 * nt, K, kind, hi, lo, sc, s));
+      MSASM_TRY(contract_tc_linop_gpu(kind, tab->d_Thi, tab->d_Tlo, tab->d_Tscale, tab->n_nz, hi, lo, sc, 9 * nt, K,
+                                      d_u, d_y, plan->d_gmap, tab->d_pairs, tab->topo.n_T, t0, plan->d_tc_err, s));
+    }
+    return MSASM_OK;
+  }
+  MSASM_TRY(linop_prepare_gpu(plan, s));
   for (int64_t t0 = 0; t0 < plan->n_tiles; t0 += P) {
     const int64_t nt = std::min(P, plan->n_tiles - t0);
     MSASM_TRY(contract_dispatch(plan->tab, prec, d_coef + size_t(9 * t0) * K, nt, plan->d_nz, plan->d_coef_lp, s,

@@ -70,13 +70,20 @@ struct TcParams {
   float* out;              // rows: out[n][m], leading dimension ld; blocks: out[n/9][m][n%9], m stride ld
   int ld;
   unsigned* err;           // set to 1 on a timed-out wait
+  // matrix-free mode (y += K u, nothing stored): tile t0 + n/9 of the mesh, pair m = (A, B)
+  const double* u;
+  double* y;
+  const int32_t* gmap;     // [t][A] global point ids
+  const int32_t* pairs;    // [m][2] local (A, B), sorted by A
+  int n_T;
+  int64_t t0;
 };
 
 // ------------------------------------------------------------------ the kernel
 constexpr int TC_EPI_WARPS = 8;                          // two per TMEM lane quarter
 constexpr int TC_THREADS = 64 + 32 * TC_EPI_WARPS;       // producer warp, MMA warp, epilogue warps
 
-template <int BN>
+template <int BN, bool LINOP>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     contract_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
                        const __grid_constant__ CUtensorMap tmB_hi, const __grid_constant__ CUtensorMap tmB_lo,
@@ -236,7 +243,62 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (lane == 0) mbar_arrive(tmem_empty);                    // the MMAs of the next tile may start
       const int m = m0 + 32 * q + lane;
       const float sm = (p.scale_m && m < p.M) ? p.scale_m[m] : 1.0f;
-      if constexpr (S::kBlocks) {
+      if constexpr (LINOP) {
+        // y += K_t u block by block (Sec. 4.2: the tile matrices are applied, never stored): lane m
+        // holds K_t[m] = block (A, B); rows of A get K u_B, summed over the run of lanes that share A
+        // (the pairs are sorted by A) before one atomic add per run, rows of B get K^T u_A
+        static_assert(S::kBlocks, "the matrix-free mode takes whole tile blocks");
+        const bool mv = m < p.M;
+        const int A = mv ? p.pairs[2 * m] : 0, B = mv ? p.pairs[2 * m + 1] : 0;
+#pragma unroll
+        for (int b = 0; b < EPI_COLS / 9; ++b) {
+          const int nb = n0 + 9 * b;
+          if (nb >= p.N) break;
+          const int64_t tt = p.t0 + nb / 9;
+          int gA = -1;
+          float rA[3] = {0.f, 0.f, 0.f}, rB[3] = {0.f, 0.f, 0.f};
+          int gB = -1;
+          if (mv) {
+            const int32_t* gt = p.gmap + tt * p.n_T;
+            gA = gt[A];
+            gB = gt[B];
+            float kv[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) kv[k] = p.scale_m ? R[9 * b + k] * sm * p.scale_n[nb + k] : R[9 * b + k];
+            const double* ua = p.u + 3 * int64_t(gA);
+            const double* ub = p.u + 3 * int64_t(gB);
+            const float a0 = float(ua[0]), a1 = float(ua[1]), a2 = float(ua[2]);
+            const float b0 = float(ub[0]), b1 = float(ub[1]), b2 = float(ub[2]);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) rA[a] = fmaf(kv[3 * a], b0, fmaf(kv[3 * a + 1], b1, kv[3 * a + 2] * b2));
+            if (A != B) {
+#pragma unroll
+              for (int c = 0; c < 3; ++c) rB[c] = fmaf(kv[c], a0, fmaf(kv[3 + c], a1, kv[6 + c] * a2));
+            }
+          }
+          const int prev = __shfl_up_sync(0xffffffffu, gA, 1);
+          const bool head = (lane == 0) || (prev != gA);
+          const unsigned heads = __ballot_sync(0xffffffffu, head);
+          const int seg = __popc(heads & ((2u << lane) - 1u));   // runs of equal gA, numbered from 1
+#pragma unroll
+          for (int d = 1; d < 32; d *= 2) {                       // segmented suffix sums: the head gets its run's
+            const int so = __shfl_down_sync(0xffffffffu, seg, d);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+              const float o = __shfl_down_sync(0xffffffffu, rA[a], d);
+              if (lane + d < 32 && so == seg) rA[a] += o;
+            }
+          }
+          if (mv && head) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) atomicAdd(p.y + 3 * int64_t(gA) + a, double(rA[a]));
+          }
+          if (mv && A != B) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) atomicAdd(p.y + 3 * int64_t(gB) + c, double(rB[c]));
+          }
+        }
+      } else if constexpr (S::kBlocks) {
         // n0 is a multiple of 9: the warp holds EPI_COLS / 9 whole tile blocks of its 32 rows
         const int mr0 = m0 + 32 * q;
 #pragma unroll
@@ -398,18 +460,18 @@ msasm_status tc_split_f32_gpu(const float* x, int64_t rows, int K, int kind, voi
   return tc_split_any<float>(x, rows, K, kind, hi, lo, row_scale, s);
 }
 
-template <int BN>
+template <int BN, bool LINOP = false>
 static msasm_status launch_tc(const CUtensorMap& ma_hi, const CUtensorMap& ma_lo, const CUtensorMap& mb_hi,
                               const CUtensorMap& mb_lo, const TcParams& p, cudaStream_t s) {
   constexpr int smem = TcShape<BN>::kSmemBytes;
-  MSASM_CUDA(cudaFuncSetAttribute(contract_tc_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  MSASM_CUDA(cudaFuncSetAttribute(contract_tc_kernel<BN, LINOP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   const long long tiles = ((p.M + TC_BM - 1) / TC_BM) * (long long)((p.N + BN - 1) / BN);
   if (tiles == 0) return MSASM_OK;
   int dev = 0, n_sm = 0;
   MSASM_CUDA(cudaGetDevice(&dev));
   MSASM_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
   const unsigned grid = unsigned(std::min<long long>(tiles, std::max(n_sm, 1)));   // one CTA per SM
-  contract_tc_kernel<BN><<<grid, TC_THREADS, smem, s>>>(ma_hi, ma_lo, mb_hi, mb_lo, p);
+  contract_tc_kernel<BN, LINOP><<<grid, TC_THREADS, smem, s>>>(ma_hi, ma_lo, mb_hi, mb_lo, p);
   MSASM_CUDA(cudaGetLastError());
   return MSASM_OK;
 }
@@ -417,9 +479,19 @@ static msasm_status launch_tc(const CUtensorMap& ma_hi, const CUtensorMap& ma_lo
 // D[m][n] = sum_k A[m][k] B[n][k] (FP32) from sliced operands A (table, M rows) and B (coef, N
 // rows), stored as out[n][m] with leading dimension ld (blocks = false), or as the tile blocks of
 // eq. 58, out[n/9][m][n%9] with m stride ld (blocks = true; N a multiple of 9).
-msasm_status contract_tc_gpu(int kind, const void* a_hi, const void* a_lo, const float* a_scale, int M,
-                             const void* b_hi, const void* b_lo, const float* b_scale, int64_t N, int K, float* out,
-                             int ld, bool blocks, unsigned* d_err, cudaStream_t s) {
+struct TcLinop {                // the matrix-free mode's arguments (null y: store the product)
+  const double* u = nullptr;
+  double* y = nullptr;
+  const int32_t* gmap = nullptr;
+  const int32_t* pairs = nullptr;
+  int n_T = 0;
+  int64_t t0 = 0;
+};
+
+static msasm_status contract_tc_any(int kind, const void* a_hi, const void* a_lo, const float* a_scale, int M,
+                                    const void* b_hi, const void* b_lo, const float* b_scale, int64_t N, int K,
+                                    float* out, int ld, bool blocks, const TcLinop& lin, unsigned* d_err,
+                                    cudaStream_t s) {
   MSASM_TRY(get_encoder());
   if (N > int64_t(2147483647)) return fail(MSASM_EUNSUPPORTED, "too many coefficient rows for one launch");
   if (blocks && N % 9 != 0) return fail(MSASM_EINVAL, "the block layout needs whole tiles (N a multiple of 9)");
@@ -446,7 +518,38 @@ msasm_status contract_tc_gpu(int kind, const void* a_hi, const void* a_lo, const
   p.out = out;
   p.ld = ld;
   p.err = d_err;
+  p.u = lin.u;
+  p.y = lin.y;
+  p.gmap = lin.gmap;
+  p.pairs = lin.pairs;
+  p.n_T = lin.n_T;
+  p.t0 = lin.t0;
+  if (lin.y) return launch_tc<144, true>(ma_hi, ma_lo, mb_hi, mb_lo, p, s);
   return blocks ? launch_tc<144>(ma_hi, ma_lo, mb_hi, mb_lo, p, s) : launch_tc<256>(ma_hi, ma_lo, mb_hi, mb_lo, p, s);
+}
+
+msasm_status contract_tc_gpu(int kind, const void* a_hi, const void* a_lo, const float* a_scale, int M,
+                             const void* b_hi, const void* b_lo, const float* b_scale, int64_t N, int K, float* out,
+                             int ld, bool blocks, unsigned* d_err, cudaStream_t s) {
+  return contract_tc_any(kind, a_hi, a_lo, a_scale, M, b_hi, b_lo, b_scale, N, K, out, ld, blocks, TcLinop(), d_err, s);
+}
+
+// y += K u for the N / 9 tiles t0 .. of the coefficient slices B, without storing the tile matrices:
+// the split-form contraction whose epilogue applies each block to u (FP32 products of the FP32
+// block values and u, FP64 atomic additions into y; y must hold the sum so far)
+msasm_status contract_tc_linop_gpu(int kind, const void* a_hi, const void* a_lo, const float* a_scale, int M,
+                                   const void* b_hi, const void* b_lo, const float* b_scale, int64_t N, int K,
+                                   const double* u, double* y, const int32_t* gmap, const int32_t* pairs, int n_T,
+                                   int64_t t0, unsigned* d_err, cudaStream_t s) {
+  if (N % 9 != 0) return fail(MSASM_EINVAL, "the matrix-free contraction takes whole tiles");
+  TcLinop lin;
+  lin.u = u;
+  lin.y = y;
+  lin.gmap = gmap;
+  lin.pairs = pairs;
+  lin.n_T = n_T;
+  lin.t0 = t0;
+  return contract_tc_any(kind, a_hi, a_lo, a_scale, M, b_hi, b_lo, b_scale, N, K, nullptr, 0, true, lin, d_err, s);
 }
 
 }  // namespace msasm

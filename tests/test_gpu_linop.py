@@ -23,21 +23,49 @@ def _rel(a, b):
     return (torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b)).item()
 
 
+# matrix-free against the CSR product of the same form: FP64 forms to the order of the sums; the
+# FP32 form (blocks in scratch, FP64 products) up to the FP32 rounding of the two-term values on glued
+# faces, which the assembly stores and the matrix-free product never forms (about 1e-8); the split
+# forms, applied in the contraction's epilogue with FP32 products of u (rounded to FP32) and the block
+# values, up to that FP32 arithmetic (about 1e-7)
+LINOP_TOL = {"f64": 1e-13, "f64_emu": 1e-13, "f32": 1e-7, "split_f16": 5e-7, "split_bf16": 5e-7, "tf32x3": 5e-7}
+
+
 @pytest.mark.parametrize("per_pass", [0, 2])
-@pytest.mark.parametrize("prec", ["f64", "f64_emu", "split_f16", "f32"])
+@pytest.mark.parametrize("prec", ["f64", "f64_emu", "split_f16", "f32", "split_bf16", "tf32x3"])
 @pytest.mark.parametrize("name", list(CASES))
 def test_linop_equals_assembled_product(name, prec, per_pass):
     """Same contraction, same values: the matrix-free product equals the CSR product of the assembled
-    matrix in the same precision up to the order of the sums -- and, for the FP32 forms, up to the
-    FP32 rounding of the two-term values on glued faces, which the assembly stores and the
-    matrix-free product never forms (about 1e-8 relative)."""
+    matrix in the same precision, to the tolerance of the form's arithmetic (LINOP_TOL)."""
     n_e, q, macro = CASES[name]()
     plan = msasm.Plan(msasm.Tables(synth.micro_cross(n_e), q), macro, max_tiles_per_pass=per_pass)
     ctrl = torch.tensor(macro.ctrl, device="cuda")
     u = torch.tensor(np.random.default_rng(1).normal(size=plan.n_rows), device="cuda")
     K = msasm.csr_matrix(plan, plan.assemble(ctrl, 1.0, 0.3, prec).double())
     y = plan.linop(plan.pullback(ctrl), u, prec)
-    assert _rel(y, K @ u) <= (1e-13 if prec.startswith("f64") else 1e-7)
+    err = _rel(y, K @ u)
+    print(name, prec, per_pass, err)
+    assert err <= LINOP_TOL[prec], err
+
+
+@pytest.mark.parametrize("prec,tol", [("split_f16", 2e-6), ("tf32x3", 3e-6)])
+def test_linop_split_forms_against_oracle(prec, tol):
+    """The epilogue-applied product (no tile matrix stored) against the oracle's assembled matrix:
+    the split form's own error level."""
+    n_e, q, macro = CASES["beam3x2x2_q3"]()
+    micro = synth.micro_cross(n_e)
+    prob = Problem(micro, macro, q, table=otables.build_table(ReferenceTile(micro), q))
+    plan = msasm.Plan(msasm.Tables(micro, q), macro)
+    u = np.random.default_rng(4).normal(size=plan.n_rows)
+    vals = prob.assemble_lookup()
+    rows = np.repeat(np.arange(plan.n_rows), np.diff(prob.rowptr))
+    ref = np.zeros(plan.n_rows)
+    np.add.at(ref, rows, vals * u[prob.col])
+    y = plan.linop(plan.pullback(torch.tensor(macro.ctrl, device="cuda")), torch.tensor(u, device="cuda"),
+                   prec).cpu().numpy()
+    err = np.linalg.norm(y - ref) / np.linalg.norm(ref)
+    print(prec, err)
+    assert err <= tol, err
 
 
 def test_linop_against_oracle():
@@ -60,4 +88,9 @@ def test_linop_beam1000_full_size():
     ctrl = torch.tensor(w.macro.ctrl, device="cuda")
     u = torch.tensor(np.random.default_rng(3).normal(size=plan.n_rows), device="cuda")
     K = msasm.csr_matrix(plan, plan.assemble(ctrl, 1.0, 0.3, "f64_emu"))
-    assert _rel(plan.linop(plan.pullback(ctrl), u, "f64_emu"), K @ u) <= 1e-13
+    coef = plan.pullback(ctrl)
+    assert _rel(plan.linop(coef, u, "f64_emu"), K @ u) <= 1e-13
+    # the epilogue-applied split-FP16 product at full size, against the CSR product of the split-FP16
+    # matrix (values in FP32, the product in FP64)
+    K16 = msasm.csr_matrix(plan, plan.assemble(ctrl, 1.0, 0.3, "split_f16").double())
+    assert _rel(plan.linop(coef, u, "split_f16"), K16 @ u) <= 5e-7
