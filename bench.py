@@ -226,7 +226,10 @@ FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # command.  Keyed by (kernel, workload, precision); the last field is the digest of the kernel's
 # source files when the counters were taken: when the source has changed since, the figure no
 # longer describes the kernel and the line reports traffic as null.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    ("contract_emu_kernel", "beam4000", "f64_emu"): (4335646464 + 6687818752, "profiles/contract_emu_beam4000.md",
+                                                     "dffcfc1e922fd8d7"),
+}
 KERNEL_SOURCES = {
     "contract_emu_kernel": ("contract_emu.cu", "tc_ptx.cuh"),
     "contract_tc_kernel": ("contract_tc.cu", "tc_ptx.cuh"),

@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
             const OutT* src = stg + (ka - c0);
             for (int e = lane; e < 32 * kc; e += 32) {
               const int r = e / kc, kk = e - r * kc;
-              if (mr0 + r < p.M) dst[r * 9 + kk] = src[r * EMU_STG_LD + kk];
+              if (mr0 + r < p.M) __stcs(dst + r * 9 + kk, src[r * EMU_STG_LD + kk]);   // evict-first: read by the next kernel
             }
           }
           __syncwarp();

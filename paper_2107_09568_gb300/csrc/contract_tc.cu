@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
           for (int j = 0; j < 9; ++j) {
             const int e = 32 * j + lane;                          // element of the 32 x 9 run
-            if (mr0 + e / 9 < p.M) dst[e] = stg[e];
+            if (mr0 + e / 9 < p.M) __stcs(dst + e, stg[e]);     // evict-first: read by the next kernel
           }
           __syncwarp();
         }

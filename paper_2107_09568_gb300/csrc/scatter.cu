@@ -59,9 +59,11 @@ __global__ void __launch_bounds__(kDirectThreads, sizeof(T) == 8 ? 5 : 8) scatte
   for (int u = 0; u < kDirectPerThread; ++u) v[u] = (k[u] >= 0) ? __ldg(nzt + k[u]) : T(0);
   asm volatile("" ::: "memory");                  // every gather is issued before the first store
   T* out = values + (it.out_off - v_lo);
+  // streaming stores: the values are not read again here, so they should not push the tile's
+  // nzdata (gathered twice) and the type maps out of L2
 #pragma unroll
   for (int u = 0; u < kDirectPerThread; ++u)
-    if (k[u] != -2) out[u * kDirectThreads + tid] = v[u];
+    if (k[u] != -2) __stcs(out + u * kDirectThreads + tid, v[u]);
 }
 
 // Value maps of all types from their representative tiles (maps preset to -1).
@@ -168,7 +170,9 @@ msasm_status secondary_entries_gpu(msasm_plan* plan, cudaStream_t stream) {
 }
 
 // Secondary pass over the entries of tiles [t0, t0 + n_tiles): add each block to the values the
-// owner of its rows wrote.
+// owner of its rows wrote.  The (up to) 18 destinations of an entry are distinct values (three rows
+// of A and three of B), and no other entry adds to them, so all their loads are issued before the
+// first store: one round trip for the read-modify-write instead of one per value.
 template <typename T>
 __global__ void scatter_secondary_kernel(const T* __restrict__ nz, int ld_nz, int64_t t0, int64_t e0, int64_t e1,
                                          const SecondaryEntry* __restrict__ sec, T* __restrict__ values, int64_t v_lo,
@@ -177,27 +181,33 @@ __global__ void scatter_secondary_kernel(const T* __restrict__ nz, int ld_nz, in
     const SecondaryEntry r = sec[i];
     const int m = int(r.m_flags & 0x3fffffffu);
     const T* src = nz + 9 * ((int64_t(r.tile) - t0) * ld_nz + m);   // the block's contiguous run
-    T v[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) v[k] = src[k];
     // the three rows of a point belong to one owner: the first row decides whether a block is in the window
-    if ((r.m_flags & (1u << 30)) && r.dst_u >= v_lo && r.dst_u < v_hi) {
+    const bool up = (r.m_flags & (1u << 30)) && r.dst_u >= v_lo && r.dst_u < v_hi;
+    const bool lo = (r.m_flags & (1u << 31)) && r.dst_l >= v_lo && r.dst_l < v_hi;
+    T* du = values + (r.dst_u - v_lo);
+    T* dl = values + (r.dst_l - v_lo);
+    T v[9], wu[9], wl[9];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        T* d = values + (r.dst_u - v_lo) + int64_t(a) * r.len_u;
-        d[0] += v[3 * a + 0];
-        d[1] += v[3 * a + 1];
-        d[2] += v[3 * a + 2];
+    for (int k = 0; k < 9; ++k) v[k] = __ldg(src + k);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        wu[3 * a + c] = up ? du[int64_t(a) * r.len_u + c] : T(0);
+        wl[3 * a + c] = lo ? dl[int64_t(a) * r.len_l + c] : T(0);
       }
+    asm volatile("" ::: "memory");                // every load is issued before the first store
+    if (up) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) du[int64_t(a) * r.len_u + c] = wu[3 * a + c] + v[3 * a + c];   // block (a, c)
     }
-    if ((r.m_flags & (1u << 31)) && r.dst_l >= v_lo && r.dst_l < v_hi) {
+    if (lo) {
 #pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        T* d = values + (r.dst_l - v_lo) + int64_t(b) * r.len_l;
-        d[0] += v[b];
-        d[1] += v[3 + b];
-        d[2] += v[6 + b];
-      }
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) dl[int64_t(b) * r.len_l + c] = wl[3 * b + c] + v[3 * c + b];   // transpose
     }
   }
 }
