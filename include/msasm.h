@@ -135,8 +135,10 @@ void msasm_tables_destroy(msasm_tables* tab);
 
 /* ---------------------------------------------------------------- plan (integer work, once per mesh) */
 
-/* Number the global control points of the tiled structure, build the CSR
- * pattern and the per-(tile, pair) index map, and allocate scratch for
+/* Number the global control points of the tiled structure and build the CSR pattern of the
+ * stiffness: the union over tiles of the pairs of eq. 56 (two control points interact when they
+ * share a micro element of a tile; the pattern is the sparse structure of K that Sec. 3.2.4's
+ * step 4 fills), the per-(tile, pair) index map of each tile block into it, and allocate scratch for
  * `max_tiles_per_pass` tiles (<= 0: all tiles in one pass).  The plan keeps a
  * reference to `tab`, which must outlive it.  Writes n_rows = 3 * n_points and
  * nnz (host).  Synchronises `stream`.  Errors: EINVAL, ENOMEM, ECUDA. */
@@ -148,7 +150,8 @@ msasm_status msasm_plan_create(const msasm_tables* tab, const msasm_macro_desc* 
 msasm_status msasm_plan_info(const msasm_plan* plan, int64_t* n_tiles, int64_t* n_points,
                              int64_t* n_rows, int64_t* nnz, int64_t* n_ctrl);
 
-/* Copy the CSR pattern: d_rowptr (n_rows+1 int64) and d_col (nnz int32). */
+/* Copy the CSR pattern of eq. 56 (every (A, B) pair of every tile, in global numbering, with full
+ * symmetric storage): d_rowptr (n_rows+1 int64) and d_col (nnz int32, ascending within a row). */
 msasm_status msasm_plan_csr(const msasm_plan* plan, int64_t* d_rowptr, int32_t* d_col, void* stream);
 
 /* Copy the global numbering gmap[t][A] (n_tiles * n_T int32) to d_gmap. */
