@@ -268,5 +268,11 @@ def linop(flush, workload="beam1000"):
     out["csr_spmv_ms_f64"] = ms_csr
     out["rel_linop_vs_csr_f64_emu"] = (torch.linalg.vector_norm(plan.linop(coef, u, "f64_emu") - yk)
                                        / torch.linalg.vector_norm(yk)).item()
+    del K
+    K16 = msasm.csr_matrix(plan, plan.assemble(ctrl, 1.0, 0.3, "split_f16").double())
+    y16 = K16 @ u
+    out["rel_linop_vs_csr_split_f16"] = (torch.linalg.vector_norm(plan.linop(coef, u, "split_f16") - y16)
+                                         / torch.linalg.vector_norm(y16)).item()
+    out["speedup_split_f16_vs_csr_product"] = ms_csr / out["linop_ms_split_f16"]
     return out
 
