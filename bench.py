@@ -50,6 +50,25 @@ L2_POLICY = "256 MB buffer written between timed steps (L2 is 129 MB); each step
 FORMS = "f64,f32,split_f16,split_bf16,tf32,tf32x3,f64_emu"
 
 
+def slab_setup(workload, world, rank):
+    """The mesh and this rank's tiles: the workload itself at one GPU; with N > 1 GPUs (weak scaling)
+    the same twisted beam with N times as many layers along z, rank r taking one contiguous slab of the
+    tiles and recomputing the layer above it.  Returns (macro, mesh, tiles, t0, t1, halo end)."""
+    import synth
+    from paper_2107_09568_gb300 import slabs
+    w = synth.workload(workload)
+    macro = w.macro
+    if world > 1:
+        if not workload.startswith("beam"):
+            raise SystemExit("--gpus N > 1 splits a twisted-beam workload (beam125, beam1000, beam4000)")
+        nx, ny, nz = (int(v) for v in w.macro.n_elem)
+        macro = synth.macro_twisted_beam(nx, ny, nz * world)
+    n_elem = tuple(int(v) for v in macro.n_elem)
+    n_total = n_elem[0] * n_elem[1] * n_elem[2]
+    t0, t1 = slabs.slab_ranges(n_total, world)[rank]
+    return macro, n_elem, n_total, t0, t1, slabs.halo_end(t1, n_elem)
+
+
 def workload_config(name):
     """The `config` object of the JSON line: the workload alone, identical in both arms."""
     import synth
@@ -477,20 +496,8 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     msasm.load()
 
-    from paper_2107_09568_gb300 import slabs
     w = synth.workload(args.workload)
-    macro = w.macro
-    if world > 1:
-        # one mesh split across the GPUs, weak scaling: the same twisted beam with `world` times as many
-        # layers along z, rank r assembling the rows of one contiguous slab of tiles (plus the halo layer)
-        if not args.workload.startswith("beam"):
-            raise SystemExit("--gpus N > 1 splits a twisted-beam workload (beam125, beam1000, beam4000)")
-        nx, ny, nz = (int(v) for v in w.macro.n_elem)
-        macro = synth.macro_twisted_beam(nx, ny, nz * world)
-    n_elem = tuple(int(v) for v in macro.n_elem)
-    n_total = n_elem[0] * n_elem[1] * n_elem[2]
-    t0, t1 = slabs.slab_ranges(n_total, world)[rank]
-    t_halo = slabs.halo_end(t1, n_elem)
+    macro, n_elem, n_total, t0, t1, t_halo = slab_setup(args.workload, world, rank)
     micro = synth.micro_cross(w.n_e, w.width)
     tab = msasm.Tables(micro, w.q)
     plan = msasm.Plan(tab, macro, max_tiles_per_pass=(t_halo - t0) if world > 1 else 0)

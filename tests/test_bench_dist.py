@@ -92,3 +92,21 @@ def test_cpulist_parsing_and_binding_fallback():
     before = os.sched_getaffinity(0)
     r = bench.bind_to_gpu_local_cpus(0)           # no GPU here: nothing is changed
     assert r["bound"] is False and os.sched_getaffinity(0) == before
+
+
+@pytest.mark.parametrize("world", [1, 2, 4, 8])
+def test_slab_setup_of_the_multi_gpu_bench(world):
+    """bench.py --gpus N: every rank gets the same per-GPU work (the 4000 tiles of the 40x10x10 beam,
+    weak scaling along z), the ranks' slabs tile the grown mesh, and each recomputes at most one layer."""
+    ranges = [bench.slab_setup("beam4000", world, r) for r in range(world)]
+    macro, n_elem, n_total, _, _, _ = ranges[0]
+    assert n_elem == (40, 10, 10 * world) and n_total == 4000 * world
+    assert macro.ctrl.shape[0] == 43 * 13 * (10 * world + 3)      # degree-3 net of the grown beam
+    assert ranges[0][3] == 0 and ranges[-1][4] == n_total
+    for r, (_, _, _, t0, t1, he) in enumerate(ranges):
+        assert t1 - t0 == 4000                                     # the same work on every GPU
+        if r + 1 < world:
+            assert ranges[r + 1][3] == t1                          # consecutive slabs
+            assert he == t1 + 400                                  # one 40 x 10 layer of halo
+        else:
+            assert he == n_total
