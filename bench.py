@@ -383,7 +383,7 @@ def run_report(args):
         elif item == "volume":
             out[item] = wl.volume(flush)
         elif item == "linop":
-            out[item] = wl.linop(flush)
+            out[item] = wl.linop(flush, args.workload if args.workload != "beam4000" else "beam1000")
         elif item == "projection":
             out[item] = wl.projection(flush)
         elif item == "cpu_forms":

@@ -21,7 +21,7 @@ pytestmark = pytest.mark.gpu
 
 import paper_2107_09568_gb300 as msasm  # noqa: E402
 
-TOL = {"split_f16": 1e-6, "tf32x3": 2e-6, "split_bf16": 3e-5, "tf32": 2e-3}
+TOL = {"split_f16": 1e-6, "tf32x3": 2e-6, "split_bf16": 3e-5, "tf32": 2e-3, "f32": 1e-6}
 TOL_RANDOM = {"split_f16": 2e-6, "tf32x3": 2e-6, "split_bf16": 3e-5, "tf32": 2e-3}
 _T = {}
 
@@ -80,7 +80,7 @@ def test_tc_assemble_parity(prec):
     assert err <= TOL[prec], err
 
 
-@pytest.mark.parametrize("prec", ["split_f16", "tf32x3", "split_bf16", "tf32"])
+@pytest.mark.parametrize("prec", ["split_f16", "tf32x3", "split_bf16", "tf32", "f32"])
 def test_beam4000_full_size_sampled(prec):
     """The 40x10x10 twisted beam (precision-form workload, 4000 tiles in one pass): sampled rows
     against the oracle, and the translation null space of the whole matrix."""
