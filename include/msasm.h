@@ -370,11 +370,12 @@ msasm_status msasm_scatter(msasm_plan* plan, msasm_precision prec, const void* d
  * fly from the lookup table and the projection coefficients d_coef (9 n_tiles x 9 n_pi FP64, as
  * written by msasm_pullback) by the contraction of eq. 58 in precision `prec`, and applied to u.
  * d_u, d_y: n_rows FP64 (y overwritten).
- *  - Split tensor-core forms (MSASM_SPLIT_F16, _SPLIT_BF16, _TF32, _TF32X3): the contraction's
- *    epilogue applies each tile block to u as it leaves the accumulators (FP32 products, FP64
- *    atomic additions into y): no tile matrix is ever stored, no nzdata scratch is used, and the
- *    last bits of every row may vary between calls (the order of the atomic additions).
- *  - Other forms: pass by pass in the plan's nzdata scratch; every row is written by the tile that
+ *  - Tensor-core forms MSASM_F64_EMU (FP64 products) and MSASM_SPLIT_F16, _SPLIT_BF16, _TF32,
+ *    _TF32X3 (FP32 products): the contraction's epilogue applies each tile block to u as it leaves
+ *    the accumulators, with FP64 atomic additions into y: no tile matrix is ever stored, no nzdata
+ *    scratch is used, and the last bits of every row may vary between calls (the order of the
+ *    atomic additions).
+ *  - MSASM_F64 and MSASM_F32: pass by pass in the plan's nzdata scratch; every row is written by the tile that
  *    owns it, then the glued-face blocks are added with atomics (so the last bits of those rows may
  *    vary between calls); the first such call builds per-type column maps and synchronises `stream`.
  * Errors: EINVAL, EUNSUPPORTED, ECUDA. */

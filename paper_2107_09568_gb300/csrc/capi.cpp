@@ -86,6 +86,10 @@ msasm_status contract_tc_linop_gpu(int kind, const void* a_hi, const void* a_lo,
                                    const void* b_hi, const void* b_lo, const float* b_scale, int64_t N, int K,
                                    const double* u, double* y, const int32_t* gmap, const int32_t* pairs, int n_T,
                                    int64_t t0, unsigned* d_err, cudaStream_t s);
+msasm_status contract_emu_linop_gpu(const void* a_slices, const int* a_exp, int M, const void* b_slices,
+                                    const int* b_exp, int64_t N, int K, const double* u, double* y,
+                                    const int32_t* gmap, const int32_t* pairs, int n_T, int64_t t0, unsigned* d_err,
+                                    cudaStream_t s);
 int tc_kpad(int K, int kind);
 size_t tc_slice_bytes(int64_t rows, int K, int kind);
 msasm_status tc_split_gpu(const double* x, int64_t rows, int K, int kind, void* hi, void* lo, float* row_scale,
@@ -922,6 +926,27 @@ msasm_status msasm_linop_apply(msasm_plan* plan, const double* d_coef, msasm_pre
       MSASM_TRY(tc_split_gpu(d_coef + size_t(9 * t0) * K, 9 * nt, K, kind, hi, lo, sc, s));
       MSASM_TRY(contract_tc_linop_gpu(kind, tab->d_Thi, tab->d_Tlo, tab->d_Tscale, tab->n_nz, hi, lo, sc, 9 * nt, K,
                                       d_u, d_y, plan->d_gmap, tab->d_pairs, tab->topo.n_T, t0, plan->d_tc_err, s));
+    }
+    return MSASM_OK;
+  }
+  if (prec == MSASM_F64_EMU && K <= 576) {
+    // FP64-accurate form: the same in the 7-slice contraction's epilogue (FP64 products)
+    msasm_tables* tab = const_cast<msasm_tables*>(plan->tab);
+    const int n_nz = tab->n_nz;
+    if (!tab->d_Tslices) {
+      MSASM_CUDA(cudaMalloc(&tab->d_Tslices, emu_slice_bytes(n_nz, K)));
+      MSASM_CUDA(cudaMalloc(&tab->d_Tslice_scale, size_t(n_nz) * sizeof(int)));
+      MSASM_TRY(emu_slice_gpu(tab->d_T, n_nz, K, K, tab->d_Tslices, tab->d_Tslice_scale, s));
+      tab->n_slices = 7;
+    }
+    MSASM_CUDA(cudaMemsetAsync(d_y, 0, size_t(plan->n_rows) * sizeof(double), s));
+    for (int64_t t0 = 0; t0 < plan->n_tiles; t0 += P) {
+      const int64_t nt = std::min(P, plan->n_tiles - t0);
+      uint8_t* sl = static_cast<uint8_t*>(plan->d_coef_lp);
+      int* sc = reinterpret_cast<int*>(sl + ((emu_slice_bytes(9 * nt, K) + 255) & ~size_t(255)));
+      MSASM_TRY(emu_slice_gpu(d_coef + size_t(9 * t0) * K, 9 * nt, K, K, sl, sc, s));
+      MSASM_TRY(contract_emu_linop_gpu(tab->d_Tslices, tab->d_Tslice_scale, n_nz, sl, sc, 9 * nt, K, d_u, d_y,
+                                       plan->d_gmap, tab->d_pairs, tab->topo.n_T, t0, plan->d_tc_err, s));
     }
     return MSASM_OK;
   }

@@ -73,6 +73,13 @@ struct EmuParams {
   void* out;               // rows: out[n][m], leading dimension ld; blocks: out[n/9][m][n%9], m stride ld
   int ld;
   unsigned* err;
+  // matrix-free mode (y += K u, nothing stored): tile t0 + n/9 of the mesh, pair m = (A, B)
+  const double* u;
+  double* y;
+  const int32_t* gmap;     // [t][A] global point ids
+  const int32_t* pairs;    // [m][2] local (A, B), sorted by A
+  int n_T;
+  int64_t t0;
 };
 
 // x 2^e as the nearest FP64 (ties to even), by integer operations on the bit pattern.
@@ -158,7 +165,7 @@ __device__ __forceinline__ long long f32_to_i64_rn(float y) {
   return (b >> 31) ? -(long long)r : (long long)r;
 }
 
-template <int S, typename OutT, bool ACCUMULATE, bool BLOCKS>
+template <int S, typename OutT, bool ACCUMULATE, bool BLOCKS, bool LINOP = false>
 __global__ void __launch_bounds__(EMU_THREADS, 1)
     contract_emu_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, EmuParams p) {
   using Sh = EmuShape<S, OutT, BLOCKS>;
@@ -339,13 +346,64 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
           }
           __syncwarp();
           const int cend = min(c0 + EMU_STG_COLS, p.N);
-          for (int tb = c0 / 9; 9 * tb < cend; ++tb) {
-            const int ka = max(9 * tb, c0), kc = min(9 * tb + 9, cend) - ka;   // columns of block tb here
-            OutT* dst = out + (size_t(tb) * size_t(p.ld) + size_t(mr0)) * 9 + (ka - 9 * tb);
-            const OutT* src = stg + (ka - c0);
-            for (int e = lane; e < 32 * kc; e += 32) {
-              const int r = e / kc, kk = e - r * kc;
-              if (mr0 + r < p.M) __stcs(dst + r * 9 + kk, src[r * EMU_STG_LD + kk]);   // evict-first: read by the next kernel
+          if constexpr (LINOP) {
+            // y += K_t u (Sec. 4.2: applied, never stored): lane m's columns of block tb in this chunk
+            // (a block split across chunks or n tiles contributes in parts), the rows of A summed over
+            // the run of lanes sharing A before one atomic add per run, the rows of B per lane
+            const bool mv = m < p.M;
+            const int A = mv ? p.pairs[2 * m] : 0, B = mv ? p.pairs[2 * m + 1] : 0;
+            for (int tb = c0 / 9; 9 * tb < cend; ++tb) {
+              const int ka = max(9 * tb, c0), kb = min(9 * tb + 9, cend);
+              int gA = -1, gB = -1;
+              double rA[3] = {0.0, 0.0, 0.0}, rB[3] = {0.0, 0.0, 0.0};
+              if (mv) {
+                const int32_t* gt = p.gmap + (p.t0 + tb) * p.n_T;
+                gA = gt[A];
+                gB = gt[B];
+                const double* ua = p.u + 3 * int64_t(gA);
+                const double* ub = p.u + 3 * int64_t(gB);
+                const double a3[3] = {ua[0], ua[1], ua[2]}, b3[3] = {ub[0], ub[1], ub[2]};
+#pragma unroll
+                for (int ab = 0; ab < 9; ++ab) {
+                  const int k = 9 * tb + ab;
+                  if (k >= ka && k < kb) {
+                    const double v = double(stg[lane * EMU_STG_LD + (k - c0)]);
+                    rA[ab / 3] = fma(v, b3[ab % 3], rA[ab / 3]);
+                    if (A != B) rB[ab % 3] = fma(v, a3[ab / 3], rB[ab % 3]);
+                  }
+                }
+              }
+              const int prev = __shfl_up_sync(0xffffffffu, gA, 1);
+              const bool head = (lane == 0) || (prev != gA);
+              const unsigned heads = __ballot_sync(0xffffffffu, head);
+              const int seg = __popc(heads & ((2u << lane) - 1u));
+#pragma unroll
+              for (int d = 1; d < 32; d *= 2) {
+                const int so = __shfl_down_sync(0xffffffffu, seg, d);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                  const double o = __shfl_down_sync(0xffffffffu, rA[a], d);
+                  if (lane + d < 32 && so == seg) rA[a] += o;
+                }
+              }
+              if (mv && head) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) atomicAdd(p.y + 3 * int64_t(gA) + a, rA[a]);
+              }
+              if (mv && A != B) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) atomicAdd(p.y + 3 * int64_t(gB) + c, rB[c]);
+              }
+            }
+          } else {
+            for (int tb = c0 / 9; 9 * tb < cend; ++tb) {
+              const int ka = max(9 * tb, c0), kc = min(9 * tb + 9, cend) - ka;   // columns of block tb here
+              OutT* dst = out + (size_t(tb) * size_t(p.ld) + size_t(mr0)) * 9 + (ka - 9 * tb);
+              const OutT* src = stg + (ka - c0);
+              for (int e = lane; e < 32 * kc; e += 32) {
+                const int r = e / kc, kk = e - r * kc;
+                if (mr0 + r < p.M) __stcs(dst + r * 9 + kk, src[r * EMU_STG_LD + kk]);   // evict-first: read by the next kernel
+              }
             }
           }
           __syncwarp();
@@ -497,10 +555,10 @@ static msasm_status make_map_3d(CUtensorMap* map, const void* ptr, int64_t rows,
   return MSASM_OK;
 }
 
-template <int S, typename OutT, bool ACCUMULATE, bool BLOCKS>
+template <int S, typename OutT, bool ACCUMULATE, bool BLOCKS, bool LINOP = false>
 static msasm_status launch_emu(const CUtensorMap& ma, const CUtensorMap& mb, const EmuParams& p, cudaStream_t s) {
   constexpr int smem = EmuShape<S, OutT, BLOCKS>::kSmemBytes;
-  auto kernel = contract_emu_kernel<S, OutT, ACCUMULATE, BLOCKS>;
+  auto kernel = contract_emu_kernel<S, OutT, ACCUMULATE, BLOCKS, LINOP>;
   MSASM_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   const long long tiles = ((p.N + EMU_BN - 1) / EMU_BN) * (long long)((p.M + EMU_BM - 1) / EMU_BM);
   if (tiles == 0) return MSASM_OK;
@@ -537,9 +595,45 @@ msasm_status contract_emu_gpu(const void* a_slices, const int* a_exp, int M, con
   p.out = out;
   p.ld = ld;
   p.err = d_err;
+  p.u = nullptr;
+  p.y = nullptr;
+  p.gmap = nullptr;
+  p.pairs = nullptr;
+  p.n_T = 0;
+  p.t0 = 0;
   if (n_slices == 4) return launch_emu<4, float, false, true>(ma, mb, p, s);
   if (blocks) return launch_emu<7, double, false, true>(ma, mb, p, s);
   return accumulate ? launch_emu<7, double, true, false>(ma, mb, p, s) : launch_emu<7, double, false, false>(ma, mb, p, s);
+}
+
+// y += K u for the N / 9 tiles t0 .. of the coefficient slices B (FP64-accurate, 7 slices), without
+// storing the tile matrices: the epilogue applies each rounded block value to u (FP64 products, FP64
+// atomic additions into y; y must hold the sum so far)
+msasm_status contract_emu_linop_gpu(const void* a_slices, const int* a_exp, int M, const void* b_slices,
+                                    const int* b_exp, int64_t N, int K, const double* u, double* y,
+                                    const int32_t* gmap, const int32_t* pairs, int n_T, int64_t t0, unsigned* d_err,
+                                    cudaStream_t s) {
+  if (N > int64_t(2147483647) * EMU_BN) return fail(MSASM_EUNSUPPORTED, "too many rows for one launch");
+  if (N % 9 != 0) return fail(MSASM_EINVAL, "the matrix-free contraction takes whole tiles");
+  CUtensorMap ma, mb;
+  MSASM_TRY(make_map_3d(&ma, a_slices, M, K, EMU_BM, 7));
+  MSASM_TRY(make_map_3d(&mb, b_slices, N, K, EMU_BN, 7));
+  EmuParams p;
+  p.M = M;
+  p.N = int(N);
+  p.kblocks = emu_kpad(K) / EMU_KB;
+  p.exp_m = a_exp;
+  p.exp_n = b_exp;
+  p.out = nullptr;
+  p.ld = 0;
+  p.err = d_err;
+  p.u = u;
+  p.y = y;
+  p.gmap = gmap;
+  p.pairs = pairs;
+  p.n_T = n_T;
+  p.t0 = t0;
+  return launch_emu<7, double, false, true, true>(ma, mb, p, s);
 }
 
 }  // namespace msasm

@@ -256,9 +256,8 @@ def linop(flush, workload="beam1000"):
     u = torch.randn(plan.n_rows, dtype=torch.float64, device="cuda")
     out = {"tiles": plan.n_tiles, "nnz": plan.nnz,
            "csr_bytes_f64": plan.nnz * (8 + 4) + (plan.n_rows + 1) * 8,
-           "linop_scratch_bytes_f64_emu": 9 * plan.n_tiles * ((plan.tables.n_nz + 7) // 8 * 8) * 8,
-           "linop_scratch_bytes_split": 0, "coef_bytes": coef.numel() * 8,
-           "split_forms": "tile blocks applied to u in the contraction's epilogue, never stored"}
+           "linop_nzdata_scratch_bytes": 0, "coef_bytes": coef.numel() * 8,
+           "tensor_core_forms": "tile blocks applied to u in the contraction's epilogue, never stored"}
     y = torch.empty_like(u)
     for prec in ("f64_emu", "split_f16", "split_bf16", "tf32x3"):
         _, ms = _timed(lambda: plan.linop(coef, u, prec, out=y), reps=5, flush=flush)

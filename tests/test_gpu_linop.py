@@ -68,7 +68,10 @@ def test_linop_split_forms_against_oracle(prec, tol):
     assert err <= tol, err
 
 
-def test_linop_against_oracle():
+@pytest.mark.parametrize("prec", ["f64", "f64_emu"])
+def test_linop_against_oracle(prec):
+    """FP64 forms: the CUDA-core product through the blocks in scratch, and the FP64-accurate one applied
+    in the contraction's epilogue (no tile matrix stored), both to 1e-12 of the oracle."""
     n_e, q, macro = CASES["beam3x2x2_q3"]()
     micro = synth.micro_cross(n_e)
     prob = Problem(micro, macro, q, table=otables.build_table(ReferenceTile(micro), q))
@@ -78,7 +81,8 @@ def test_linop_against_oracle():
     rows = np.repeat(np.arange(plan.n_rows), np.diff(prob.rowptr))
     ref = np.zeros(plan.n_rows)
     np.add.at(ref, rows, vals * u[prob.col])
-    y = plan.linop(plan.pullback(torch.tensor(macro.ctrl, device="cuda")), torch.tensor(u, device="cuda")).cpu().numpy()
+    y = plan.linop(plan.pullback(torch.tensor(macro.ctrl, device="cuda")), torch.tensor(u, device="cuda"),
+                   prec).cpu().numpy()
     assert np.linalg.norm(y - ref) <= 1e-12 * np.linalg.norm(ref)
 
 
