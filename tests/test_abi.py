@@ -79,3 +79,19 @@ def test_edge_and_corner_points_are_rejected_before_any_cuda_call():
     assert lib.msasm_build_tables(C.byref(d), 2, 0, None, C.byref(out)) == _lib.EUNSUPPORTED
     assert b"edge or corner" in lib.msasm_last_error()
     assert out.value is None
+
+
+def test_host_side_validation_of_the_range_and_degree_calls():
+    """The tile-range and degree-selection entry points refuse NULL handles and bad arguments before
+    any CUDA call."""
+    lib = msasm.load()
+    i64 = [C.c_int64() for _ in range(5)]
+    assert lib.msasm_plan_range(None, 0, 1, *[C.byref(v) for v in i64]) == _lib.EINVAL
+    assert lib.msasm_assemble_range(None, None, 1.0, 0.3, 0, 0, 1, None, 0, None) == _lib.EINVAL
+    assert lib.msasm_assemble_grad_range(None, None, 1.0, 0.3, 0, 0, 1, None, None, None, None) == _lib.EINVAL
+    q = C.c_int32()
+    e = C.c_double()
+    assert lib.msasm_select_degree(None, None, 1e-3, 0, 7, 5, 1.0, 0.3, C.byref(q), C.byref(e), None) == _lib.EINVAL
+    q3 = (C.c_int32 * 3)(3, 3, 3)
+    out3 = (C.c_int32 * 3)()
+    assert lib.msasm_select_degrees(None, None, 1e-3, q3, 7, 5, 1.0, 0.3, out3, C.byref(e), None) == _lib.EINVAL
