@@ -58,7 +58,8 @@ typedef enum {
   MSASM_ECUDA = -2,         /* a CUDA runtime/driver call failed */
   MSASM_ENOMEM = -3,        /* device or host allocation failed */
   MSASM_EDEGENERATE = -4,   /* |det J| <= tol at some node: degenerate macro element (Sec. 3.3.4) */
-  MSASM_EUNSUPPORTED = -5   /* precision/feature not available for this shape */
+  MSASM_EUNSUPPORTED = -5,  /* precision/feature not available for this shape */
+  MSASM_EIO = -6            /* a file cannot be opened, read or written, or is not a valid file of its kind */
 } msasm_status;
 
 typedef enum {
@@ -132,6 +133,19 @@ msasm_status msasm_tables_info(const msasm_tables* tab, int32_t* n_T, int32_t* n
 msasm_status msasm_tables_copy(const msasm_tables* tab, double* d_table, int32_t* h_pairs, void* stream);
 
 void msasm_tables_destroy(msasm_tables* tab);
+
+/* Store the tables of a reference tile in a file and read them back (Sec. 3.1.1, 3.2.3: the
+ * lookup tables of a microstructure are computed once and kept, and an assembly only reads
+ * them).  The file holds the micro descriptor, the projection degrees and every FP64 table
+ * (stiffness eq. 57, load eq. 55, volume eq. 18, faces eq. 55 with F >= 1), followed by a 64-bit
+ * FNV-1a checksum; numbers are little-endian.  msasm_tables_load rebuilds the tile topology
+ * from the stored descriptor, checks that it gives the stored sizes, and uploads the tables
+ * without recomputing them: every call then behaves bit for bit as with the saved object.
+ * Both synchronise `stream`.  Errors: EINVAL (NULL argument), EIO (the file cannot be opened,
+ * read or written, has another kind tag, format version or byte order, is truncated, fails its
+ * checksum, or describes a tile whose topology does not match its sizes), ENOMEM, ECUDA. */
+msasm_status msasm_tables_save(const msasm_tables* tab, const char* path, void* stream);
+msasm_status msasm_tables_load(const char* path, void* stream, msasm_tables** out);
 
 /* ---------------------------------------------------------------- plan (integer work, once per mesh) */
 
@@ -306,6 +320,14 @@ msasm_status msasm_lowrank_contract(const float* d_U, int32_t n_nz, int32_t rank
 msasm_status msasm_surrogate_assemble(msasm_plan* plan, msasm_surrogate* sur, const double* d_ctrl, double E,
                                       double nu, const double* d_widths, float* d_values, void* stream);
 void msasm_surrogate_destroy(msasm_surrogate* sur);
+
+/* Store a fitted (and possibly trained) surrogate in a file and read it back: the basis U, the
+ * width normalisation, the normalised training targets, and the MLP with its Adam state, so that
+ * a loaded surrogate predicts and assembles bit for bit as the saved one and continues training
+ * from the same step.  File format and errors as msasm_tables_save / msasm_tables_load (EIO also
+ * for sizes outside the limits of msasm_surrogate_create).  Both synchronise `stream`. */
+msasm_status msasm_surrogate_save(const msasm_surrogate* sur, const char* path, void* stream);
+msasm_status msasm_surrogate_load(const char* path, void* stream, msasm_surrogate** out);
 
 /* Number of interpolation nodes with |det J| <= tol found by the last assemble
  * on this plan (reads back from the device; synchronises `stream`). */

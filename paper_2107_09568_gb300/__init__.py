@@ -8,6 +8,7 @@ implementation of any step here.
 from __future__ import annotations
 
 import ctypes as C
+import os
 
 import numpy as np
 
@@ -47,6 +48,24 @@ class Tables:
         else:                                     # one projection degree per direction
             q3 = (C.c_int32 * 3)(*[int(v) for v in q])
             check(lib.msasm_build_tables_q3(C.byref(d), q3, int(n_gauss), _stream(stream), C.byref(h)))
+        self._adopt(h)
+
+    @classmethod
+    def load_file(cls, path, stream=None):
+        """Tables stored by `save` (msasm_tables_load: read back, not recomputed)."""
+        h = C.c_void_p()
+        check(load().msasm_tables_load(os.fsencode(path), _stream(stream), C.byref(h)))
+        obj = cls.__new__(cls)
+        obj._keep = []
+        obj._adopt(h)
+        return obj
+
+    def save(self, path, stream=None):
+        """Store the tables in a file (msasm_tables_save)."""
+        check(load().msasm_tables_save(self.handle, os.fsencode(path), _stream(stream)))
+
+    def _adopt(self, h):
+        lib = load()
         self.handle = h
         n_T, n_nz, n_pi = C.c_int32(), C.c_int32(), C.c_int32()
         check(lib.msasm_tables_info(h, C.byref(n_T), C.byref(n_nz), C.byref(n_pi)))
@@ -559,6 +578,24 @@ class Surrogate:
         check(lib.msasm_surrogate_create(arr, w.ctypes.data_as(C.c_void_p), len(tables), _ptr(coef_samples),
                                          coef_samples.shape[0], int(rank), int(hidden), int(power_iters),
                                          C.c_uint64(seed), _stream(stream), C.byref(h)))
+        self._adopt(h)
+
+    @classmethod
+    def load_file(cls, path, stream=None):
+        """A surrogate stored by `save` (msasm_surrogate_load), MLP and Adam state included."""
+        h = C.c_void_p()
+        check(load().msasm_surrogate_load(os.fsencode(path), _stream(stream), C.byref(h)))
+        obj = cls.__new__(cls)
+        obj._tables = []
+        obj._adopt(h)
+        return obj
+
+    def save(self, path, stream=None):
+        """Store the surrogate in a file (msasm_surrogate_save)."""
+        check(load().msasm_surrogate_save(self.handle, os.fsencode(path), _stream(stream)))
+
+    def _adopt(self, h):
+        lib = load()
         self.handle = h
         r, K, n = C.c_int32(), C.c_int32(), C.c_int32()
         check(lib.msasm_surrogate_info(h, C.byref(r), C.byref(K), C.byref(n)))

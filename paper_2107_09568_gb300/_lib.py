@@ -13,8 +13,9 @@ from . import build as _build
 c_i32, c_i64, c_u32, c_dbl, c_vp = C.c_int32, C.c_int64, C.c_uint32, C.c_double, C.c_void_p
 P = C.POINTER
 
-OK, EINVAL, ECUDA, ENOMEM, EDEGENERATE, EUNSUPPORTED = 0, -1, -2, -3, -4, -5
-STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ECUDA", -3: "ENOMEM", -4: "EDEGENERATE", -5: "EUNSUPPORTED"}
+OK, EINVAL, ECUDA, ENOMEM, EDEGENERATE, EUNSUPPORTED, EIO = 0, -1, -2, -3, -4, -5, -6
+STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ECUDA", -3: "ENOMEM", -4: "EDEGENERATE", -5: "EUNSUPPORTED",
+                -6: "EIO"}
 PRECISIONS = {"f64": 0, "f32": 1, "split_f16": 2, "split_bf16": 3, "tf32": 4, "tf32x3": 5, "f64_emu": 6}
 FLAG_CHECK_DEGENERATE = 1
 FLAG_STAGE_TIMES = 2
@@ -46,6 +47,8 @@ _SIGS = {
     "msasm_projection_error_q3": (c_i32, [c_vp, c_vp, P(c_i32), c_i32, c_dbl, c_dbl, c_vp, c_vp, c_vp]),
     "msasm_tables_copy": (c_i32, [c_vp, c_vp, c_vp, c_vp]),
     "msasm_tables_destroy": (None, [c_vp]),
+    "msasm_tables_save": (c_i32, [c_vp, C.c_char_p, c_vp]),
+    "msasm_tables_load": (c_i32, [C.c_char_p, c_vp, P(c_vp)]),
     "msasm_plan_create": (c_i32, [c_vp, P(MacroDescC), c_i32, c_vp, P(c_vp), P(c_i64), P(c_i64)]),
     "msasm_plan_info": (c_i32, [c_vp, P(c_i64), P(c_i64), P(c_i64), P(c_i64), P(c_i64)]),
     "msasm_plan_csr": (c_i32, [c_vp, c_vp, c_vp, c_vp]),
@@ -97,6 +100,8 @@ _SIGS = {
     "msasm_lowrank_contract": (c_i32, [c_vp, c_i32, c_i32, c_i32, c_vp, c_vp, c_i64, c_vp, c_vp]),
     "msasm_surrogate_assemble": (c_i32, [c_vp, c_vp, c_vp, c_dbl, c_dbl, c_vp, c_vp, c_vp]),
     "msasm_surrogate_destroy": (None, [c_vp]),
+    "msasm_surrogate_save": (c_i32, [c_vp, C.c_char_p, c_vp]),
+    "msasm_surrogate_load": (c_i32, [C.c_char_p, c_vp, P(c_vp)]),
     "msasm_last_error": (C.c_char_p, []),
     "msasm_version": (C.c_char_p, []),
 }

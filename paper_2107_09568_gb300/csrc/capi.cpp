@@ -159,6 +159,48 @@ msasm_plan::~msasm_plan() {
     if (copy_stream[k]) cudaStreamDestroy(copy_stream[k]);
 }
 
+namespace msasm {
+
+// Everything of a table object but the tables themselves: the tile topology, degrees and sizes,
+// the device table d_T (allocated, not filled) and the pair list (filled).  Synchronises `s`.
+msasm_status tables_init(const msasm_micro_desc* micro, const int32_t q3[3], int n_gauss, cudaStream_t s,
+                         msasm_tables* tab) {
+  for (int d = 0; d < 3; ++d)
+    if (q3[d] < 0 || q3[d] > 5) return fail(MSASM_EINVAL, "interpolation degrees must be in 0..5");
+  MSASM_TRY(build_topology(micro, tab->topo));
+  for (int d = 0; d < 3; ++d) tab->qd[d] = q3[d];
+  tab->q = std::max({q3[0], q3[1], q3[2]});
+  tab->n_pi = (q3[0] + 1) * (q3[1] + 1) * (q3[2] + 1);
+  tab->face_off[0] = 0;
+  for (int f = 0; f < 6; ++f) {
+    const int d = f / 2, ia = d == 0 ? 1 : 0, ib = d == 2 ? 1 : 2;
+    tab->face_off[f + 1] = tab->face_off[f] + int64_t(tab->topo.n_T) * (q3[ia] + 1) * (q3[ib] + 1);
+  }
+  double best = 1e300;
+  for (int A = 0; A < tab->topo.n_T; ++A) {
+    double d2 = 0.0;
+    for (int k = 0; k < 3; ++k) d2 += (tab->topo.pos[3 * A + k] - 0.5) * (tab->topo.pos[3 * A + k] - 0.5);
+    if (d2 < best) {
+      best = d2;
+      tab->ref_point = A;
+    }
+  }
+  tab->n_nz = int(tab->topo.pair_A.size());
+  tab->n_gauss = n_gauss;
+  MSASM_CUDA(cudaMalloc(&tab->d_T, size_t(tab->n_nz) * 9 * tab->n_pi * sizeof(double)));
+  MSASM_CUDA(cudaMalloc(&tab->d_pairs, size_t(tab->n_nz) * 2 * sizeof(int32_t)));
+  std::vector<int32_t> pairs(size_t(tab->n_nz) * 2);
+  for (int m = 0; m < tab->n_nz; ++m) {
+    pairs[2 * m] = tab->topo.pair_A[m];
+    pairs[2 * m + 1] = tab->topo.pair_B[m];
+  }
+  MSASM_CUDA(cudaMemcpyAsync(tab->d_pairs, pairs.data(), pairs.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  MSASM_CUDA(cudaStreamSynchronize(s));   // `pairs` (host) must outlive the copy
+  return MSASM_OK;
+}
+
+}  // namespace msasm
+
 extern "C" {
 
 const char* msasm_last_error(void) { return g_error.c_str(); }
@@ -180,56 +222,11 @@ msasm_status msasm_build_tables_q3(const msasm_micro_desc* micro, const int32_t*
                                    msasm_tables** out) {
   if (!out || !q3) return fail(MSASM_EINVAL, "out or q3 is NULL");
   *out = nullptr;
-  for (int d = 0; d < 3; ++d)
-    if (q3[d] < 0 || q3[d] > 5) return fail(MSASM_EINVAL, "interpolation degrees must be in 0..5");
   if (n_gauss > 16) return fail(MSASM_EINVAL, "n_gauss must be <= 16");
   msasm_tables* tab = new msasm_tables();
-  msasm_status st = build_topology(micro, tab->topo);
-  if (st != MSASM_OK) {
-    delete tab;
-    return st;
-  }
-  for (int d = 0; d < 3; ++d) tab->qd[d] = q3[d];
-  tab->q = std::max({q3[0], q3[1], q3[2]});
-  tab->n_pi = (q3[0] + 1) * (q3[1] + 1) * (q3[2] + 1);
-  tab->face_off[0] = 0;
-  for (int f = 0; f < 6; ++f) {
-    const int d = f / 2, ia = d == 0 ? 1 : 0, ib = d == 2 ? 1 : 2;
-    tab->face_off[f + 1] = tab->face_off[f] + int64_t(tab->topo.n_T) * (q3[ia] + 1) * (q3[ib] + 1);
-  }
-  {
-    double best = 1e300;
-    for (int A = 0; A < tab->topo.n_T; ++A) {
-      double d2 = 0.0;
-      for (int k = 0; k < 3; ++k) d2 += (tab->topo.pos[3 * A + k] - 0.5) * (tab->topo.pos[3 * A + k] - 0.5);
-      if (d2 < best) {
-        best = d2;
-        tab->ref_point = A;
-      }
-    }
-  }
-  tab->n_nz = int(tab->topo.pair_A.size());
-  tab->n_gauss = n_gauss;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  size_t tbytes = size_t(tab->n_nz) * 9 * tab->n_pi * sizeof(double);
-  cudaError_t e1 = cudaMalloc(&tab->d_T, tbytes);
-  cudaError_t e2 = cudaMalloc(&tab->d_pairs, size_t(tab->n_nz) * 2 * sizeof(int32_t));
-  if (e1 != cudaSuccess || e2 != cudaSuccess) {
-    delete tab;
-    return cuda_fail(e1 != cudaSuccess ? e1 : e2, "cudaMalloc(table)");
-  }
-  std::vector<int32_t> pairs(size_t(tab->n_nz) * 2);
-  for (int m = 0; m < tab->n_nz; ++m) {
-    pairs[2 * m] = tab->topo.pair_A[m];
-    pairs[2 * m + 1] = tab->topo.pair_B[m];
-  }
-  cudaError_t e3 = cudaMemcpyAsync(tab->d_pairs, pairs.data(), pairs.size() * sizeof(int32_t),
-                                   cudaMemcpyHostToDevice, s);
-  if (e3 != cudaSuccess) {
-    delete tab;
-    return cuda_fail(e3, "cudaMemcpyAsync(pairs)");
-  }
-  st = build_table_gpu(tab, s);   // synchronises `s`
+  msasm_status st = tables_init(micro, q3, n_gauss, s, tab);
+  if (st == MSASM_OK) st = build_table_gpu(tab, s);   // synchronises `s`
   if (st != MSASM_OK) {
     delete tab;
     return st;

@@ -140,6 +140,11 @@ struct msasm_tables {
   ~msasm_tables();
 };
 
+namespace msasm {
+msasm_status tables_init(const msasm_micro_desc* micro, const int32_t q3[3], int n_gauss, cudaStream_t s,
+                         msasm_tables* tab);
+}  // namespace msasm
+
 struct msasm_mlp;
 struct msasm_surrogate;
 
@@ -189,8 +194,8 @@ struct msasm_plan {
   // scratch
   double* d_coef = nullptr;         // 9 tiles_per_pass x 9 n_pi, FP64
   void* d_nz = nullptr;             // 9 tiles_per_pass x n_nz, FP64-sized
-  void* d_coef_lp = nullptr;
-  void* d_adj_lp = nullptr;        // slices of one chunk of the transposed table (emulated FP64 adjoint)        // reduced-precision coefficient operands
+  void* d_coef_lp = nullptr;        // reduced-precision coefficient operands
+  void* d_adj_lp = nullptr;         // slices of one chunk of the transposed table (emulated FP64 adjoint)
   size_t coef_lp_bytes = 0;
   unsigned long long* d_degenerate = nullptr;
   unsigned* d_tc_err = nullptr;     // set by a tensor-core kernel whose pipeline wait timed out

@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "common.h"
+#include "store.h"
 
 namespace msasm {
 
@@ -924,5 +925,118 @@ msasm_status msasm_surrogate_assemble(msasm_plan* plan, msasm_surrogate* sur, co
 }
 
 void msasm_surrogate_destroy(msasm_surrogate* sur) { delete sur; }
+
+// Surrogate file payload (kind tag "MSASMSUR"): rank, K, n_nz, n_train, q3 (int32), the width
+// normalisation w0, ws (double) and target scale (float), the MLP shape H, n_out (int32), its
+// parameter count (int64) and Adam step (int32); then the FP32 arrays U (n_nz x rank), target mean
+// (n_out), training inputs (n_train), normalised targets (n_train x n_out), and the MLP's master
+// weights, Adam first and second moments (each n_params).  A loaded surrogate predicts, assembles
+// and continues training exactly as the saved one.
+static const char kSurrogateTag[8] = {'M', 'S', 'A', 'S', 'M', 'S', 'U', 'R'};
+
+msasm_status msasm_surrogate_save(const msasm_surrogate* sur, const char* path, void* stream) {
+  if (!sur || !path || !sur->mlp) return fail(MSASM_EINVAL, "surrogate or path is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const msasm_mlp* n = sur->mlp;
+  const int32_t head[7] = {sur->rank, sur->K, sur->n_nz, sur->n_train, sur->qd[0], sur->qd[1], sur->qd[2]};
+  StoreWriter w;
+  w.put_array(head, 7);
+  w.put(sur->w0);
+  w.put(sur->ws);
+  w.put(sur->scale);
+  const int32_t shape[2] = {n->lay.H, n->lay.n_out};
+  w.put_array(shape, 2);
+  const int64_t P = int64_t(n->lay.total);
+  w.put(P);
+  int32_t* step = w.reserve_array<int32_t>(1);
+  const size_t n_out = size_t(n->lay.n_out);
+  const size_t nU = size_t(sur->n_nz) * sur->rank, nX = size_t(sur->n_train), nTg = nX * n_out;
+  const size_t step_off = reinterpret_cast<unsigned char*>(step) - w.at(0);
+  const size_t arr_off = w.size();
+  w.reserve_array<float>(nU + n_out + nX + nTg + 3 * size_t(P));
+  // pointers into the buffer only after its last growth
+  int32_t* hstep = reinterpret_cast<int32_t*>(w.at(step_off));
+  float* h = reinterpret_cast<float*>(w.at(arr_off));
+  MSASM_CUDA(cudaMemcpyAsync(hstep, n->d_step, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  MSASM_CUDA(cudaMemcpyAsync(h, sur->d_U, nU * 4, cudaMemcpyDeviceToHost, s));
+  MSASM_CUDA(cudaMemcpyAsync(h + nU, sur->d_mean, n_out * 4, cudaMemcpyDeviceToHost, s));
+  MSASM_CUDA(cudaMemcpyAsync(h + nU + n_out, sur->d_x, nX * 4, cudaMemcpyDeviceToHost, s));
+  MSASM_CUDA(cudaMemcpyAsync(h + nU + n_out + nX, sur->d_targets, nTg * 4, cudaMemcpyDeviceToHost, s));
+  float* hw = h + nU + n_out + nX + nTg;
+  MSASM_CUDA(cudaMemcpyAsync(hw, n->d_w, size_t(P) * 4, cudaMemcpyDeviceToHost, s));
+  MSASM_CUDA(cudaMemcpyAsync(hw + P, n->d_m, size_t(P) * 4, cudaMemcpyDeviceToHost, s));
+  MSASM_CUDA(cudaMemcpyAsync(hw + 2 * P, n->d_v, size_t(P) * 4, cudaMemcpyDeviceToHost, s));
+  MSASM_CUDA(cudaStreamSynchronize(s));
+  return w.write(path, kSurrogateTag);
+}
+
+msasm_status msasm_surrogate_load(const char* path, void* stream, msasm_surrogate** out) {
+  if (!out || !path) return fail(MSASM_EINVAL, "out or path is NULL");
+  *out = nullptr;
+  StoreReader r;
+  MSASM_TRY(r.open(path, kSurrogateTag));
+  auto bad = [&](const char* what) { return fail(MSASM_EIO, std::string("surrogate file: ") + what + ": " + path); };
+  int32_t head[7], shape[2], step = 0;
+  double w0 = 0.0, ws = 0.0;
+  float scale = 0.0f;
+  int64_t P = 0;
+  bool ok = true;
+  for (int i = 0; i < 7; ++i) ok = ok && r.get(head[i]);
+  ok = ok && r.get(w0) && r.get(ws) && r.get(scale) && r.get(shape[0]) && r.get(shape[1]) && r.get(P) && r.get(step);
+  if (!ok) return bad("header");
+  const int rank = head[0], K = head[1], n_nz = head[2], n_train = head[3];
+  if (rank < 1 || rank > 64 || K < 1 || n_nz < 1 || n_train < 2 || shape[1] != rank * K) return bad("sizes");
+  for (int d = 0; d < 3; ++d)
+    if (head[4 + d] < 0 || head[4 + d] > 5) return bad("degrees");
+  if (shape[0] <= 0 || shape[0] > 1024 || (shape[0] % 2) || int64_t(MlpLayout(shape[0], shape[1]).total) != P)
+    return bad("MLP shape");
+  const size_t n_out = size_t(shape[1]);
+  const size_t nU = size_t(n_nz) * rank, nX = size_t(n_train), nTg = nX * n_out;
+  const unsigned char* src = r.get_array<float>(nU + n_out + nX + nTg + 3 * size_t(P));
+  if (!src || !r.at_end()) return bad("arrays");
+  msasm_surrogate* sur = new msasm_surrogate();
+  auto bail = [&](msasm_status st) {
+    delete sur;
+    return st;
+  };
+  sur->rank = rank;
+  sur->K = K;
+  sur->n_nz = n_nz;
+  sur->n_train = n_train;
+  for (int d = 0; d < 3; ++d) sur->qd[d] = head[4 + d];
+  sur->w0 = w0;
+  sur->ws = ws;
+  sur->scale = scale;
+  msasm_status st = msasm_mlp_create(int32_t(n_out), shape[0], 0, &sur->mlp);
+  if (st != MSASM_OK) return bail(st);
+  msasm_mlp* n = sur->mlp;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMalloc(&sur->d_U, nU * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&sur->d_mean, n_out * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&sur->d_x, nX * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&sur->d_targets, nTg * 4);
+  size_t off = 0;
+  auto up = [&](void* dst, size_t count) {
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dst, src + off, count * 4, cudaMemcpyHostToDevice, s);
+    off += count * 4;
+  };
+  up(sur->d_U, nU);
+  up(sur->d_mean, n_out);
+  up(sur->d_x, nX);
+  up(sur->d_targets, nTg);
+  up(n->d_w, size_t(P));
+  up(n->d_m, size_t(P));
+  up(n->d_v, size_t(P));
+  if (e == cudaSuccess) e = cudaMemcpyAsync(n->d_step, &step, sizeof(int32_t), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    to_half_kernel<<<152 * 4, 256, 0, s>>>(n->d_w, n->lay.total, n->d_w16);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the reader's buffer and `step` must outlive the copies
+  if (e != cudaSuccess) return bail(cuda_fail(e, "msasm_surrogate_load"));
+  n->w3_split_ok = false;
+  *out = sur;
+  return MSASM_OK;
+}
 
 }  // extern "C"

@@ -95,3 +95,65 @@ def test_host_side_validation_of_the_range_and_degree_calls():
     q3 = (C.c_int32 * 3)(3, 3, 3)
     out3 = (C.c_int32 * 3)()
     assert lib.msasm_select_degrees(None, None, 1e-3, q3, 7, 5, 1.0, 0.3, out3, C.byref(e), None) == _lib.EINVAL
+
+
+def _fnv1a64(data: bytes) -> int:
+    """64-bit FNV-1a (offset basis 14695981039346656037, prime 1099511628211)."""
+    h = 14695981039346656037
+    for b in data:
+        h = ((h ^ b) * 1099511628211) & 0xFFFFFFFFFFFFFFFF
+    return h
+
+
+def _store_file(path, tag: bytes, payload: bytes, checksum=None, version=1):
+    import struct
+    h = _fnv1a64(payload) if checksum is None else checksum
+    path.write_bytes(tag + struct.pack("<IIQ", version, 0x01020304, len(payload)) + payload + struct.pack("<Q", h))
+
+
+def test_stored_files_are_checked_before_any_cuda_call(tmp_path):
+    """msasm_tables_load / msasm_surrogate_load refuse a missing file, another kind of file, another
+    format version, a truncated file, a checksum mismatch and a payload whose sizes do not fit the
+    tile its descriptor builds, all with EIO and before anything is allocated on a device."""
+    import struct
+    lib = msasm.load()
+    h = C.c_void_p()
+
+    def status(path, fn=lib.msasm_tables_load):
+        h.value = None
+        st = fn(os.fsencode(path), None, C.byref(h))
+        assert h.value is None
+        return st
+
+    assert status(tmp_path / "missing") == _lib.EIO
+    assert lib.msasm_tables_load(None, None, C.byref(h)) == _lib.EINVAL
+    # a payload with a valid micro descriptor: one quadratic patch on the box [0.25, 0.75]^3 (no
+    # point on the tile's faces), 27 control points and 378 pairs
+    deg, ne = np.array([2, 2, 2], np.int32), np.array([1, 1, 1], np.int32)
+    lo, hi = np.full(3, 0.25), np.full(3, 0.75)
+    desc = struct.pack("<i", 1) + deg.tobytes() + ne.tobytes() + lo.tobytes() + hi.tobytes()
+    sizes = struct.pack("<7i", 1, 1, 1, 0, 27, 378, 8) + struct.pack("<7q", *range(7))
+    good = tmp_path / "t.msasm"
+    _store_file(good, b"MSASMTAB", desc + sizes + b"\0" * 64)
+    assert status(good) == _lib.EIO                        # 27 points, 378 pairs: the arrays are missing
+    assert b"table arrays" in lib.msasm_last_error()
+    wrong = struct.pack("<7i", 1, 1, 1, 0, 28, 378, 8) + struct.pack("<7q", *range(7))
+    _store_file(good, b"MSASMTAB", desc + wrong + b"\0" * 64)
+    assert status(good) == _lib.EIO and b"do not match" in lib.msasm_last_error()
+    _store_file(good, b"MSASMSUR", desc + sizes)
+    assert status(good) == _lib.EIO and b"kind" in lib.msasm_last_error()
+    _store_file(good, b"MSASMTAB", desc + sizes, version=2)
+    assert status(good) == _lib.EIO and b"version" in lib.msasm_last_error()
+    _store_file(good, b"MSASMTAB", desc + sizes, checksum=12345)
+    assert status(good) == _lib.EIO and b"checksum" in lib.msasm_last_error()
+    raw = good.read_bytes()
+    good.write_bytes(raw[:-20])
+    assert status(good) == _lib.EIO and b"truncated" in lib.msasm_last_error()
+    _store_file(good, b"MSASMTAB", struct.pack("<i", 40))
+    assert status(good) == _lib.EIO and b"patch count" in lib.msasm_last_error()
+    # surrogate files
+    assert status(tmp_path / "missing", lib.msasm_surrogate_load) == _lib.EIO
+    _store_file(good, b"MSASMSUR", struct.pack("<7i", 0, 576, 100, 8, 3, 3, 3))
+    assert status(good, lib.msasm_surrogate_load) == _lib.EIO
+    assert lib.msasm_tables_save(None, b"x", None) == _lib.EINVAL
+    assert lib.msasm_surrogate_save(None, b"x", None) == _lib.EINVAL
