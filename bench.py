@@ -22,6 +22,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import math
 import os
@@ -246,8 +247,8 @@ FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # source files when the counters were taken: when the source has changed since, the figure no
 # longer describes the kernel and the line reports traffic as null.
 NCU_TRAFFIC = {
-    ("contract_emu_kernel", "beam4000", "f64_emu"): (4335646464 + 6687818752, "profiles/contract_emu_beam4000.md",
-                                                     "dffcfc1e922fd8d7"),
+    ("contract_emu_kernel", "beam4000", "f64_emu"): (4653725440 + 6782921472, "profiles/contract_emu_beam4000.md",
+                                                     "165dbd63a2a790a0"),
 }
 KERNEL_SOURCES = {
     "contract_emu_kernel": ("contract_emu.cu", "tc_ptx.cuh"),
@@ -256,12 +257,20 @@ KERNEL_SOURCES = {
 }
 
 
+def _code_only(text):
+    """C/C++/CUDA source without comments, blank lines or trailing blanks (a comment edit does not
+    change the compiled kernel, so it does not make counters taken before it stale)."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(ln.rstrip() for ln in text.splitlines() if ln.strip())
+
+
 def kernel_source_digest(kernel):
-    """sha256 (first 16 hex digits) of the source files a kernel is compiled from."""
+    """sha256 (first 16 hex digits) of the code (comments stripped) of the files a kernel is compiled from."""
     h = hashlib.sha256()
     for f in KERNEL_SOURCES.get(kernel, ()):
-        with open(os.path.join(ROOT, "paper_2107_09568_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2107_09568_gb300", "csrc", f), encoding="utf-8") as fh:
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -27,10 +27,10 @@
 // runs on across tiles; one lane issues the S(S+1)/2 MMAs (M=128, N=96, K=16, the A slice kept in
 // the collector buffer across its products) into min(S, 5) TMEM accumulators of 96 columns (at
 // most 480 of the 512).  Eight epilogue warps (two per TMEM lane quarter, 48 columns each) drain
-// the accumulators into exact int64 sums in registers and release TMEM at once, so the MMAs of
-// the next tile run while they round and store the previous one.  In the tile-block layout of
-// nzdata a warp rounds 24 columns at a time into shared memory and writes each tile block's 32
-// rows as one run.
+// the accumulators into exact int64 sums in registers (the last accumulator as raw values, folded
+// in afterwards) and release TMEM at once, so the MMAs of the next tile run while they round and
+// store the previous one.  In the tile-block layout of nzdata a warp rounds 12 (FP64-accurate
+// form) or 24 columns at a time into shared memory and writes each tile block's 32 rows as one run.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -46,21 +46,25 @@ namespace msasm {
 constexpr int EMU_BM = 128, EMU_BN = 96, EMU_KB = 16;    // k block: 16 BF16 = one 32-byte swizzle row
 constexpr int EMU_A_SLICE = EMU_BM * 32;                 // one slice tile of A: 128 rows x 32 bytes
 constexpr int EMU_B_SLICE = EMU_BN * 32;                 // one slice tile of B: 96 rows x 32 bytes
-// block layout: each epilogue warp rounds 24 columns of its 32 rows into a shared-memory buffer
-// (odd row stride: few bank conflicts either way) and writes them back tile block by tile block
-constexpr int EMU_STG_COLS = 24;
-constexpr int EMU_STG_LD = 25;
-constexpr int EMU_STG_ELEMS = 32 * EMU_STG_LD;
+// block layout: each epilogue warp rounds 24 columns of its 32 rows into a shared-memory buffer (odd
+// row stride: few bank conflicts either way) and writes them back tile block by tile block; the
+// FP64-accurate form stages 12 columns at a time, which leaves room for a fourth pipeline stage (its
+// matrix-free mode keeps 24 columns and 3 stages: it applies whole blocks per round)
 
-// the kernel's shape for S slices per operand (OutT the output type, BLOCKS the nzdata layout)
-template <int S, typename OutT, bool BLOCKS>
+// the kernel's shape for S slices per operand (OutT the output type, BLOCKS the nzdata layout,
+// LINOP the matrix-free mode)
+template <int S, typename OutT, bool BLOCKS, bool LINOP>
 struct EmuShape {
   static constexpr int kAcc = S < 5 ? S : 5;             // accumulators: d = 0..3 alone, d >= 4 together
   static constexpr int kABytes = S * EMU_A_SLICE;        // 28 KB (S = 7)
   static constexpr int kBBytes = S * EMU_B_SLICE;        // 21 KB (S = 7)
   static constexpr int kStageBytes = kABytes + kBBytes;
-  static constexpr int kStages = S == 7 ? (BLOCKS ? 3 : 4) : 6;   // ring depth (room for the staging)
-  static constexpr int kStagingBytes = BLOCKS ? 8 * EMU_STG_ELEMS * int(sizeof(OutT)) : 0;
+  static constexpr bool kNarrow = S == 7 && !LINOP;             // 12 staged columns, 4 stages
+  static constexpr int kStages = S == 7 ? (kNarrow ? 4 : 3) : 6; // ring depth
+  static constexpr int kStgCols = kNarrow ? 12 : 24;             // staged columns per round
+  static constexpr int kStgLd = kStgCols + 1;
+  static constexpr int kStgElems = 32 * kStgLd;
+  static constexpr int kStagingBytes = BLOCKS ? 8 * kStgElems * int(sizeof(OutT)) : 0;
   static constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 256 + kStagingBytes;
   static_assert(kSmemBytes <= 227 * 1024, "shared memory per CTA");
   static_assert(S >= 1 && S <= 7 && 5 * EMU_BN <= 512, "slices and TMEM columns");
@@ -168,9 +172,10 @@ __device__ __forceinline__ long long f32_to_i64_rn(float y) {
 template <int S, typename OutT, bool ACCUMULATE, bool BLOCKS, bool LINOP = false>
 __global__ void __launch_bounds__(EMU_THREADS, 1)
     contract_emu_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, EmuParams p) {
-  using Sh = EmuShape<S, OutT, BLOCKS>;
+  using Sh = EmuShape<S, OutT, BLOCKS, LINOP>;
   constexpr int EMU_STAGES = Sh::kStages, EMU_STAGE_BYTES = Sh::kStageBytes, EMU_A_BYTES = Sh::kABytes;
   constexpr int EMU_ACC = Sh::kAcc;
+  constexpr int EMU_STG_COLS = Sh::kStgCols, EMU_STG_LD = Sh::kStgLd, EMU_STG_ELEMS = Sh::kStgElems;
   OutT* const out = static_cast<OutT*>(p.out);
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -301,6 +306,7 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
       tile_mn(t, m0, n0);
       n0 += h * EMU_EPI_COLS;
       long long X[EMU_EPI_COLS];
+      uint32_t R4[EMU_ACC == 5 ? EMU_EPI_COLS : 1];               // acc4 raw: converted after the release
 #pragma unroll
       for (int c = 0; c < EMU_EPI_COLS / 8; ++c) {
         uint32_t v[EMU_ACC][8];
@@ -321,13 +327,17 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
           for (int a = 0; a < (EMU_ACC < 4 ? EMU_ACC : 4); ++a)
             x += (long long)__float2int_rn(__uint_as_float(v[a][j]) * __int_as_float((127 + 7 * a) << 23))
                  << (7 * (EMU_ACC - a));
-          if constexpr (EMU_ACC == 5) x += f32_to_i64_rn(__uint_as_float(v[4][j]) * 34359738368.0f);
+          if constexpr (EMU_ACC == 5) R4[8 * c + j] = v[4][j];
           X[8 * c + j] = x;
         }
       }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(tmem_empty);                     // the MMAs of the next tile may start
+      if constexpr (EMU_ACC == 5) {
+#pragma unroll
+        for (int j = 0; j < EMU_EPI_COLS; ++j) X[j] += f32_to_i64_rn(__uint_as_float(R4[j]) * 34359738368.0f);
+      }
       const int m = m0 + 32 * q + lane;
       const int em = (m < p.M) ? p.exp_m[m] - 14 - 7 * EMU_ACC : 0;   // D = X 2^(e_m + e_n - 14 - 7 n_acc)
       if constexpr (BLOCKS) {
@@ -557,7 +567,7 @@ static msasm_status make_map_3d(CUtensorMap* map, const void* ptr, int64_t rows,
 
 template <int S, typename OutT, bool ACCUMULATE, bool BLOCKS, bool LINOP = false>
 static msasm_status launch_emu(const CUtensorMap& ma, const CUtensorMap& mb, const EmuParams& p, cudaStream_t s) {
-  constexpr int smem = EmuShape<S, OutT, BLOCKS>::kSmemBytes;
+  constexpr int smem = EmuShape<S, OutT, BLOCKS, LINOP>::kSmemBytes;
   auto kernel = contract_emu_kernel<S, OutT, ACCUMULATE, BLOCKS, LINOP>;
   MSASM_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   const long long tiles = ((p.N + EMU_BN - 1) / EMU_BN) * (long long)((p.M + EMU_BM - 1) / EMU_BM);

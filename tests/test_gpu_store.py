@@ -72,9 +72,11 @@ def test_surrogate_round_trip_predicts_assembles_and_trains_alike(tmp_path):
     dw = torch.tensor(synth.width_field(m.n_elem, seed=1), device="cuda")
     assert torch.equal(back.predict(dw), sur.predict(dw))
     assert torch.equal(back.assemble(plan, ctrl, dw), sur.assemble(plan, ctrl, dw))
-    # Adam moments and step were stored: training continues identically
+    # Adam moments and step were stored: training continues identically.  The weights' updates are
+    # deterministic; the reported loss is a sum of per-warp partials added atomically, so its last
+    # bits depend on the order of those additions.
     h0, h1 = sur.train(50, 1e-3), back.train(50, 1e-3)
-    assert np.allclose(h0, h1, rtol=1e-6, atol=0.0)
+    assert np.allclose(h0, h1, rtol=1e-5, atol=0.0)
     assert torch.equal(back.predict(dw), sur.predict(dw))
     # a table file is not a surrogate file
     tpath = tmp_path / "tab.msasm"
