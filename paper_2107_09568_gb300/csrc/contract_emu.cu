@@ -410,8 +410,10 @@ __global__ void __launch_bounds__(EMU_THREADS, 1)
               const int ka = max(9 * tb, c0), kc = min(9 * tb + 9, cend) - ka;   // columns of block tb here
               OutT* dst = out + (size_t(tb) * size_t(p.ld) + size_t(mr0)) * 9 + (ka - 9 * tb);
               const OutT* src = stg + (ka - c0);
+              // e / kc as (e inv) >> 32 with inv = ceil(2^32 / kc): exact for e < 2^16, one division per block
+              const unsigned long long inv = (unsigned long long)(0xFFFFFFFFu / unsigned(kc)) + 1ull;
               for (int e = lane; e < 32 * kc; e += 32) {
-                const int r = e / kc, kk = e - r * kc;
+                const int r = int(((unsigned long long)e * inv) >> 32), kk = e - r * kc;
                 if (mr0 + r < p.M) __stcs(dst + r * 9 + kk, src[r * EMU_STG_LD + kk]);   // evict-first: read by the next kernel
               }
             }
