@@ -137,7 +137,6 @@ msasm_plan::~msasm_plan() {
   cudaFree(d_type_map_off);
   cudaFree(d_maps);
   cudaFree(d_tile_vbase);
-  cudaFree(d_items);
   cudaFree(d_tmpl);
   cudaFree(d_tmpl_ptr);
   cudaFree(d_sec_off);
@@ -347,7 +346,6 @@ msasm_status msasm_plan_create(const msasm_tables* tab, const msasm_macro_desc* 
     msasm_status st0 = build_scatter_plan(plan, gmap, pptr, sp);
     if (st0 != MSASM_OK) return bail(st0);
   }
-  plan->item_ptr = sp.item_ptr;
   plan->sec_off_host = sp.sec_off;
   plan->type_rep_host = sp.type_rep;
   plan->type_map_off_host = sp.type_map_off;
@@ -381,7 +379,6 @@ msasm_status msasm_plan_create(const msasm_tables* tab, const msasm_macro_desc* 
   if (err == cudaSuccess) err = dev((void**)&plan->d_type_map_off, sp.type_map_off.size() * sizeof(int64_t));
   if (err == cudaSuccess) err = dev((void**)&plan->d_maps, size_t(sp.type_map_off.back()) * sizeof(int32_t));
   if (err == cudaSuccess) err = dev((void**)&plan->d_tile_vbase, plan->tile_vbase.size() * sizeof(int64_t));
-  if (err == cudaSuccess) err = dev((void**)&plan->d_items, sp.items.size() * sizeof(ScatterItem));
   if (err == cudaSuccess) err = dev((void**)&plan->d_tmpl, sp.tmpl.size() * sizeof(uint32_t));
   if (err == cudaSuccess) err = dev((void**)&plan->d_tmpl_ptr, sp.tmpl_ptr.size() * sizeof(int64_t));
   if (err == cudaSuccess) err = dev((void**)&d_type_rep, sp.type_rep.size() * sizeof(int64_t));
@@ -422,7 +419,6 @@ msasm_status msasm_plan_create(const msasm_tables* tab, const msasm_macro_desc* 
     err = cudaMemsetAsync(plan->d_maps, 0xff, size_t(sp.type_map_off.back()) * sizeof(int32_t), s);   // -1
   if (err == cudaSuccess)
     err = h2d(plan->d_tile_vbase, plan->tile_vbase.data(), plan->tile_vbase.size() * sizeof(int64_t));
-  if (err == cudaSuccess) err = h2d(plan->d_items, sp.items.data(), sp.items.size() * sizeof(ScatterItem));
   if (err == cudaSuccess) err = h2d(plan->d_tmpl, sp.tmpl.data(), sp.tmpl.size() * sizeof(uint32_t));
   if (err == cudaSuccess) err = h2d(plan->d_tmpl_ptr, sp.tmpl_ptr.data(), sp.tmpl_ptr.size() * sizeof(int64_t));
   if (err == cudaSuccess) err = h2d(d_type_rep, sp.type_rep.data(), sp.type_rep.size() * sizeof(int64_t));

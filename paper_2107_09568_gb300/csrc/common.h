@@ -79,28 +79,16 @@ struct SecondaryEntry {
 };
 static_assert(sizeof(SecondaryEntry) == 32, "SecondaryEntry is 32 bytes");
 
-// one work item of the direct scatter pass: up to kScatterSegment consecutive values of a tile's
-// owned range, with everything the kernel needs to start on it in one load
-struct ScatterItem {
-  int64_t map_off;           // its first entry in the value maps (type map offset + first value)
-  int64_t out_off;           // global index of its first value
-  int32_t tile;              // the tile whose nzdata it reads
-  int32_t count;             // values (<= kScatterSegment)
-};
-static_assert(sizeof(ScatterItem) == 24, "ScatterItem is 24 bytes");
-
 // scatter plan (scatter_plan.cpp): a tile's owned rows are one contiguous range of values whose
 // layout depends only on the tile's type (which faces are glued), so one value map per type
 // tells, for every value of the range, where it comes from in the tile's nzdata
-constexpr int kScatterSegment = 4096;     // values of one work item (one CTA)
+constexpr int kScatterSegment = 4096;     // values of one chunk of a tile's owned range (one CTA)
 inline int ld_nz_of(int n_nz) { return (n_nz + 7) & ~7; }   // leading dimension of nzdata rows
 struct ScatterPlanHost {
   std::vector<int32_t> tile_type;          // per tile
   std::vector<int64_t> type_rep;           // per type: representative tile
   std::vector<int32_t> type_nvals;         // per type: values in the owned rows of a tile
   std::vector<int64_t> type_map_off;       // per type: offset of its value map (n_types + 1)
-  std::vector<ScatterItem> items;          // work items of the direct pass, in tile order
-  std::vector<int64_t> item_ptr;           // per tile: its work items [item_ptr[t], item_ptr[t+1])
   std::vector<uint32_t> tmpl;              // secondary template per type: m | upper << 30 | lower << 31
   std::vector<int64_t> tmpl_ptr;
   std::vector<int64_t> sec_off;            // per tile: first secondary entry (n_tiles + 1)
@@ -170,8 +158,6 @@ struct msasm_plan {
   int64_t* d_type_map_off = nullptr;
   int32_t* d_maps = nullptr;                 // value maps of all types: 9 m + 3a + b, or -1
   int64_t* d_tile_vbase = nullptr;
-  msasm::ScatterItem* d_items = nullptr;
-  std::vector<int64_t> item_ptr;             // host copy
   uint32_t* d_tmpl = nullptr;
   int64_t* d_tmpl_ptr = nullptr;
   int64_t* d_sec_off = nullptr;              // secondary entries of tile t: [sec_off[t], sec_off[t+1])

@@ -33,37 +33,55 @@ namespace msasm {
 
 constexpr int kDirectThreads = 256;
 constexpr int kDirectPerThread = kScatterSegment / kDirectThreads;   // 16
+constexpr int kDirectRun64 = 2, kDirectRun32 = 4;                    // tiles per CTA (FP64, FP32 values)
 
-// One work item per CTA, in tile order: the CTAs the hardware keeps resident work on a few
-// consecutive tiles, whose nzdata stays in L2 for the gathers of both the upper and the lower
-// blocks.  The item's descriptor is one load, so the dependent chain before the gathers is
-// descriptor -> value map.  Each thread owns values i = u * 256 + threadIdx.x of the item (a
-// warp's loads and stores cover 32 consecutive values); every gather is issued before the first
-// store.
-template <typename T>
-__global__ void __launch_bounds__(kDirectThreads, sizeof(T) == 8 ? 5 : 8) scatter_direct_kernel(
-    const T* __restrict__ nz, int ld_nz, int64_t t0, const ScatterItem* __restrict__ items,
+// A CTA takes chunk s (values [4096 s, 4096 s + 4096) of a tile's owned range) of R consecutive
+// tiles, tile order first: the CTAs the hardware keeps resident work on a few consecutive tiles,
+// whose nzdata stays in L2 for the gathers of both the upper and the lower blocks.  Tiles of one
+// type share the chunk's value map, so the map entries stay in registers from one tile to the
+// next (reloaded only where the type changes): the map loads, one per value for one tile, are
+// one per R values.  Each thread owns values i = u * 256 + threadIdx.x of the chunk (a warp's
+// loads and stores cover 32 consecutive values); every gather of a tile is issued before its
+// first store.
+template <typename T, int R>
+__global__ void __launch_bounds__(kDirectThreads, sizeof(T) == 8 ? (R > 1 ? 4 : 5) : 8) scatter_direct_kernel(
+    const T* __restrict__ nz, int ld_nz, int64_t t0, int64_t ta, int64_t tb, int n_chunks,
+    const int32_t* __restrict__ tile_type, const int64_t* __restrict__ tile_vbase,
+    const int64_t* __restrict__ type_map_off, const int32_t* __restrict__ type_nvals,
     const int32_t* __restrict__ maps, T* __restrict__ values, int64_t v_lo) {
   const int tid = int(threadIdx.x);
-  const ScatterItem it = items[blockIdx.x];
-  const int32_t* map = maps + it.map_off;
+  const int64_t t_first = ta + int64_t(blockIdx.x / unsigned(n_chunks)) * R;
+  const int s0 = int(blockIdx.x % unsigned(n_chunks)) * kScatterSegment;
   int k[kDirectPerThread];
+  int loaded = -1;                                // the type whose map chunk k holds (CTA-uniform)
+#pragma unroll 1
+  for (int r = 0; r < R; ++r) {
+    const int64_t t = t_first + r;
+    if (t >= tb) break;
+    const int ty = tile_type[t];
+    const int count = type_nvals[ty] - s0;        // values of this chunk (<= 0: none for this type)
+    if (count <= 0) continue;
+    if (ty != loaded) {
+      const int32_t* map = maps + type_map_off[ty] + s0;
 #pragma unroll
-  for (int u = 0; u < kDirectPerThread; ++u) {
-    const int i = u * kDirectThreads + tid;
-    k[u] = (i < it.count) ? map[i] : -2;          // -1: no block of the tile lands here (value 0)
+      for (int u = 0; u < kDirectPerThread; ++u) {
+        const int i = u * kDirectThreads + tid;
+        k[u] = (i < count) ? map[i] : -2;         // -1: no block of the tile lands here (value 0)
+      }
+      loaded = ty;
+    }
+    const T* nzt = nz + 9 * (t - t0) * ld_nz;
+    T v[kDirectPerThread];
+#pragma unroll
+    for (int u = 0; u < kDirectPerThread; ++u) v[u] = (k[u] >= 0) ? __ldg(nzt + k[u]) : T(0);
+    asm volatile("" ::: "memory");                // every gather is issued before the first store
+    T* out = values + (tile_vbase[t] + s0 - v_lo);
+    // streaming stores: the values are not read again here, so they should not push the tile's
+    // nzdata (gathered twice) and the type maps out of L2
+#pragma unroll
+    for (int u = 0; u < kDirectPerThread; ++u)
+      if (k[u] != -2) __stcs(out + u * kDirectThreads + tid, v[u]);
   }
-  const T* nzt = nz + 9 * (int64_t(it.tile) - t0) * ld_nz;
-  T v[kDirectPerThread];
-#pragma unroll
-  for (int u = 0; u < kDirectPerThread; ++u) v[u] = (k[u] >= 0) ? __ldg(nzt + k[u]) : T(0);
-  asm volatile("" ::: "memory");                  // every gather is issued before the first store
-  T* out = values + (it.out_off - v_lo);
-  // streaming stores: the values are not read again here, so they should not push the tile's
-  // nzdata (gathered twice) and the type maps out of L2
-#pragma unroll
-  for (int u = 0; u < kDirectPerThread; ++u)
-    if (k[u] != -2) __stcs(out + u * kDirectThreads + tid, v[u]);
 }
 
 // Value maps of all types from their representative tiles (maps preset to -1).
@@ -219,11 +237,19 @@ template <typename T>
 msasm_status scatter_pass_gpu(const msasm_plan* plan, const T* d_nz, int ld_nz, int64_t t0, int64_t n_tiles,
                               T* d_values, int64_t direct_end, int64_t v_lo, int64_t v_hi, cudaStream_t stream) {
   const int64_t td = std::max(t0, std::min(t0 + n_tiles, direct_end));
-  const int64_t i0 = plan->item_ptr[size_t(t0)], i1 = plan->item_ptr[size_t(td)];
-  if (i1 > i0) {
-    if (i1 - i0 > 2147483647LL) return fail(MSASM_EUNSUPPORTED, "too many scatter work items for one launch");
-    scatter_direct_kernel<T><<<unsigned(i1 - i0), kDirectThreads, 0, stream>>>(d_nz, ld_nz, t0, plan->d_items + i0,
-                                                                               plan->d_maps, d_values, v_lo);
+  if (td > t0) {
+    // chunks of the largest type: CTAs of chunks a tile's type does not have return at once
+    int n_chunks = 1;
+    for (size_t ty = 0; ty + 1 < plan->type_map_off_host.size(); ++ty) {
+      const int64_t nv = plan->type_map_off_host[ty + 1] - plan->type_map_off_host[ty];
+      n_chunks = std::max<int>(n_chunks, int((nv + kScatterSegment - 1) / kScatterSegment));
+    }
+    constexpr int R = sizeof(T) == 8 ? kDirectRun64 : kDirectRun32;
+    const int64_t grid = (td - t0 + R - 1) / R * n_chunks;
+    if (grid > 2147483647LL) return fail(MSASM_EUNSUPPORTED, "too many scatter work items for one launch");
+    scatter_direct_kernel<T, R><<<unsigned(grid), kDirectThreads, 0, stream>>>(
+        d_nz, ld_nz, t0, t0, td, n_chunks, plan->d_tile_type, plan->d_tile_vbase, plan->d_type_map_off,
+        plan->d_type_nvals, plan->d_maps, d_values, v_lo);
     MSASM_CUDA(cudaGetLastError());
   }
   const int64_t e0 = plan->sec_off_host[size_t(t0)], e1 = plan->sec_off_host[size_t(t0 + n_tiles)];

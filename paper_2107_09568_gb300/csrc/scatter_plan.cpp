@@ -5,8 +5,8 @@
 // owned points of a tile have consecutive global ids (tile-major numbering), so their CSR rows
 // form one contiguous range of values, laid out the same way for every tile of the type: one
 // value map per type (built on the GPU from the type's representative tile) gives the source
-// of every value of the range.  The range is cut into work items of kScatterSegment values, each
-// described by one ScatterItem (its map offset, output offset, tile and count).
+// of every value of the range.  The direct pass cuts the range into chunks of kScatterSegment
+// values; a chunk's map serves every tile of the type.
 // Blocks landing in rows owned by a lower tile form the type's secondary template, added after
 // the owner has written its rows; per tile, its entries are numbered from sec_off[t].
 #include <algorithm>
@@ -94,9 +94,7 @@ msasm_status build_scatter_plan(msasm_plan* plan, const std::vector<int32_t>& gm
     out.tmpl_ptr[size_t(ty) + 1] = int64_t(out.tmpl.size());
   }
   // every tile has its type's layout: owned points with consecutive ids in local order and the
-  // same row lengths; work items of kScatterSegment values
-  out.items.clear();
-  out.item_ptr.assign(size_t(plan->n_tiles) + 1, 0);
+  // same row lengths
   out.sec_off.assign(size_t(plan->n_tiles) + 1, 0);
   for (int64_t t = 0; t < plan->n_tiles; ++t) {
     const int ty = out.tile_type[size_t(t)];
@@ -111,16 +109,6 @@ msasm_status build_scatter_plan(msasm_plan* plan, const std::vector<int32_t>& gm
       if (pptr[size_t(g[A]) + 1] - pptr[size_t(g[A])] != deg_of[size_t(ty)][size_t(A)])
         return fail(MSASM_EUNSUPPORTED, "tile numbering is not translation invariant within a tile type");
     }
-    const int32_t nv = out.type_nvals[size_t(ty)];
-    for (int32_t s0 = 0; s0 < nv; s0 += kScatterSegment) {
-      ScatterItem it;
-      it.map_off = out.type_map_off[size_t(ty)] + s0;
-      it.out_off = plan->tile_vbase[size_t(t)] + s0;
-      it.tile = int32_t(t);
-      it.count = std::min(kScatterSegment, nv - s0);
-      out.items.push_back(it);
-    }
-    out.item_ptr[size_t(t) + 1] = int64_t(out.items.size());
     out.sec_off[size_t(t) + 1] = out.sec_off[size_t(t)] + (out.tmpl_ptr[size_t(ty) + 1] - out.tmpl_ptr[size_t(ty)]);
   }
   return MSASM_OK;
