@@ -16,11 +16,13 @@
 // internal rounding; for S = 7, acc4 collects d = 4..6, at most 2^-28 of acc0, where that rounding
 // is harmless.  (Merging d = 3 into the last accumulator, with its mixed scales, measurably loses
 // accuracy: the accumulation truncates relative to the largest term.)  The epilogue forms the
-// exact fixed-point sum X = sum_d acc_d 2^(7 n_acc) in int64 (acc4 rounded at 2^-35) and writes
-// X 2^(e_m + e_n - 14 - 7 n_acc) as an FP64 (or FP32) bit pattern rounded to nearest even, with
-// integer instructions only: the FP64 pipe, about 1/64 of the FP32 rate per SM on GB300, is not
-// used at all.  The FP32 form keeps 28 bits of each operand row (10 products, 4 accumulators, all
-// exact): its error is the truncation of the operands, the same whatever the accumulation order.
+// exact fixed-point sum X = sum_d acc_d 2^(7 n_acc) in int64 (acc4 rounded at 2^-35, by integer
+// operations) and writes X 2^(e_m + e_n - 14 - 7 n_acc) rounded to nearest even: one conversion of X
+// to FP64 (or FP32), then the exponent field moved by integer addition.  No FP64 arithmetic (about
+// 1/64 of the FP32 rate per SM on GB300) is used; float-to-int64 conversions, which measured slow
+// on this chip (20.9 against 16.1 ms for the kernel), are not used either.  The FP32 form keeps 28
+// bits of each operand row (10 products, 4 accumulators, all exact): its error is the truncation of
+// the operands, the same whatever the accumulation order.
 //
 // Persistent kernel, one CTA per SM looping over 128 (m) x 96 (n) output tiles.  Per 16-element
 // k block, one 3-D TMA box brings all S slices of each operand (32-byte swizzle) into a ring that
@@ -86,64 +88,31 @@ struct EmuParams {
   int64_t t0;
 };
 
-// x 2^e as the nearest FP64 (ties to even), by integer operations on the bit pattern.
-__device__ __forceinline__ double ldexp_i64_rn(long long x, int e) {
-  if (x == 0) return 0.0;
-  const unsigned long long sign = x < 0 ? (1ull << 63) : 0ull;
-  unsigned long long u = x < 0 ? 0ull - (unsigned long long)x : (unsigned long long)x;
-  const int nbits = 64 - __clzll(u);
-  long long exp = (long long)nbits - 1 + e;             // unbiased exponent of the result
-  unsigned long long mant;
-  if (nbits <= 53) {
-    mant = u << (53 - nbits);
-  } else {
-    const int sh = nbits - 53;
-    mant = u >> sh;
-    const unsigned long long rem = u & ((1ull << sh) - 1), half = 1ull << (sh - 1);
-    if (rem > half || (rem == half && (mant & 1ull))) {
-      ++mant;
-      if (mant == (1ull << 53)) {
-        mant >>= 1;
-        ++exp;
-      }
-    }
-  }
-  const long long biased = exp + 1023;
-  if (biased <= 0) return __longlong_as_double((long long)sign);                 // below the normal range
-  if (biased >= 2047) return __longlong_as_double((long long)(sign | 0x7FF0000000000000ull));
-  return __longlong_as_double((long long)(sign | ((unsigned long long)biased << 52) | (mant & ((1ull << 52) - 1))));
+// x 2^e as the nearest FP64 (ties to even): the conversion of x rounds to nearest (even), and
+// scaling by 2^e is exact, so it only moves the exponent field; results below the normal range
+// give a signed zero and above it a signed infinity.
+__device__ __forceinline__ double round_out(long long x, int e, double*) {
+  const double d = __ll2double_rn(x);
+  const long long b = __double_as_longlong(d);
+  const int be = int((b >> 52) & 0x7ff);
+  if (be == 0) return d;                                          // x == 0
+  const int nb = be + e;
+  const long long sign = b & (long long)0x8000000000000000ull;
+  if (nb <= 0) return __longlong_as_double(sign);
+  if (nb >= 2047) return __longlong_as_double(sign | 0x7FF0000000000000ll);
+  return __longlong_as_double((long long)((unsigned long long)b + ((unsigned long long)(long long)e << 52)));
 }
-
-// x 2^e as the nearest FP32 (ties to even), by integer operations on the bit pattern.
-__device__ __forceinline__ float ldexp_i64_rn_f32(long long x, int e) {
-  if (x == 0) return 0.0f;
-  const uint32_t sign = x < 0 ? 0x80000000u : 0u;
-  unsigned long long u = x < 0 ? 0ull - (unsigned long long)x : (unsigned long long)x;
-  const int nbits = 64 - __clzll(u);
-  int exp = nbits - 1 + e;                                     // unbiased exponent of the result
-  unsigned long long mant;
-  if (nbits <= 24) {
-    mant = u << (24 - nbits);
-  } else {
-    const int sh = nbits - 24;
-    mant = u >> sh;
-    const unsigned long long rem = u & ((1ull << sh) - 1), half = 1ull << (sh - 1);
-    if (rem > half || (rem == half && (mant & 1ull))) {
-      ++mant;
-      if (mant == (1ull << 24)) {
-        mant >>= 1;
-        ++exp;
-      }
-    }
-  }
-  const int biased = exp + 127;
-  if (biased <= 0) return __uint_as_float(sign);                      // below the normal range
-  if (biased >= 255) return __uint_as_float(sign | 0x7F800000u);
-  return __uint_as_float(sign | (uint32_t(biased) << 23) | uint32_t(mant & 0x7FFFFFull));
+// the same to FP32
+__device__ __forceinline__ float round_out(long long x, int e, float*) {
+  const float f = __ll2float_rn(x);
+  const uint32_t b = __float_as_uint(f);
+  const int be = int((b >> 23) & 0xff);
+  if (be == 0) return f;
+  const int nb = be + e;
+  if (nb <= 0) return __uint_as_float(b & 0x80000000u);
+  if (nb >= 255) return __uint_as_float((b & 0x80000000u) | 0x7F800000u);
+  return __uint_as_float(b + (uint32_t(e) << 23));
 }
-
-__device__ __forceinline__ double round_out(long long x, int e, double*) { return ldexp_i64_rn(x, e); }
-__device__ __forceinline__ float round_out(long long x, int e, float*) { return ldexp_i64_rn_f32(x, e); }
 
 constexpr int EMU_BAND = 32;                              // m tiles per band of the tile order
 constexpr int EMU_EPI_WARPS = 8;                          // two per TMEM lane quarter
