@@ -340,7 +340,7 @@ msasm_status msasm_plan_create(const msasm_tables* tab, const msasm_macro_desc* 
     }
   }
 
-  // scatter plan: tile types, value maps, work items, secondary templates
+  // scatter plan: tile types, value maps, secondary templates
   ScatterPlanHost sp;
   {
     msasm_status st0 = build_scatter_plan(plan, gmap, pptr, sp);

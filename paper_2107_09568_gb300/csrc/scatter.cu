@@ -246,7 +246,7 @@ msasm_status scatter_pass_gpu(const msasm_plan* plan, const T* d_nz, int ld_nz, 
     }
     constexpr int R = sizeof(T) == 8 ? kDirectRun64 : kDirectRun32;
     const int64_t grid = (td - t0 + R - 1) / R * n_chunks;
-    if (grid > 2147483647LL) return fail(MSASM_EUNSUPPORTED, "too many scatter work items for one launch");
+    if (grid > 2147483647LL) return fail(MSASM_EUNSUPPORTED, "too many scatter chunks for one launch");
     scatter_direct_kernel<T, R><<<unsigned(grid), kDirectThreads, 0, stream>>>(
         d_nz, ld_nz, t0, t0, td, n_chunks, plan->d_tile_type, plan->d_tile_vbase, plan->d_type_map_off,
         plan->d_type_nvals, plan->d_maps, d_values, v_lo);
