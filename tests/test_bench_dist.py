@@ -110,3 +110,14 @@ def test_slab_setup_of_the_multi_gpu_bench(world):
             assert he == t1 + 400                                  # one 40 x 10 layer of halo
         else:
             assert he == n_total
+
+
+def test_traffic_figure_follows_the_kernel_code_not_its_comments():
+    """The DRAM traffic in the bench line is tied to a digest of the contraction's code: a comment
+    edit keeps it, a code edit makes the line report traffic as null."""
+    base = "int a = 1;  // one\n/* block\n comment */\nint b = a;\n"
+    assert bench._code_only(base) == bench._code_only(base.replace("// one", "// two").replace("block", "x"))
+    assert bench._code_only(base) != bench._code_only(base.replace("int b = a;", "int b = a + 1;"))
+    d = bench.kernel_source_digest("contract_emu_kernel")
+    assert (("contract_emu_kernel", "beam4000", "f64_emu") in bench.NCU_TRAFFIC
+            and bench.NCU_TRAFFIC[("contract_emu_kernel", "beam4000", "f64_emu")][2] == d)
