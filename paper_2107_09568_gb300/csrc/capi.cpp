@@ -1035,7 +1035,7 @@ msasm_status msasm_select_degree(const msasm_plan* plan, const double* d_ctrl, d
   if (!(tol > 0.0) || !std::isfinite(tol)) return fail(MSASM_EINVAL, "tol must be positive and finite");
   if (q0 < 0 || q_max > 7 || q0 > q_max) return fail(MSASM_EINVAL, "need 0 <= q0 <= q_max <= 7");
   MSASM_TRY(check_material(E, nu));
-  DegreeSearch ds{plan, d_ctrl, n_samples, 0.0, 0.0, static_cast<cudaStream_t>(stream)};
+  DegreeSearch ds{plan, d_ctrl, n_samples, 0.0, 0.0, static_cast<cudaStream_t>(stream), nullptr, {}};
   lame(E, nu, ds.lam, ds.mu);
   MSASM_CUDA(cudaMallocAsync(&ds.d_tmp, sizeof(double), ds.s));
   msasm_status st = MSASM_OK;
@@ -1064,7 +1064,7 @@ msasm_status msasm_select_degrees(const msasm_plan* plan, const double* d_ctrl, 
   for (int d = 0; d < 3; ++d)
     if (q_init[d] < 0 || q_init[d] > q_max) return fail(MSASM_EINVAL, "q_init must be in 0..q_max");
   MSASM_TRY(check_material(E, nu));
-  DegreeSearch ds{plan, d_ctrl, n_samples, 0.0, 0.0, static_cast<cudaStream_t>(stream)};
+  DegreeSearch ds{plan, d_ctrl, n_samples, 0.0, 0.0, static_cast<cudaStream_t>(stream), nullptr, {}};
   lame(E, nu, ds.lam, ds.mu);
   MSASM_CUDA(cudaMallocAsync(&ds.d_tmp, sizeof(double), ds.s));
   std::array<int, 3> q = {q_init[0], q_init[1], q_init[2]};
