@@ -16,10 +16,7 @@ using namespace msasm;
 
 static const char kTableTag[8] = {'M', 'S', 'A', 'S', 'M', 'T', 'A', 'B'};
 
-extern "C" {
-
-msasm_status msasm_tables_save(const msasm_tables* tab, const char* path, void* stream) {
-  if (!tab || !path) return fail(MSASM_EINVAL, "tables or path is NULL");
+static msasm_status tables_save_impl(const msasm_tables* tab, const char* path, void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   StoreWriter w;
   const int32_t n_patches = int32_t(tab->topo.patches.size());
@@ -42,6 +39,17 @@ msasm_status msasm_tables_save(const msasm_tables* tab, const char* path, void* 
   if (nFf) MSASM_CUDA(cudaMemcpyAsync(hT + nT + nF + nV, tab->d_Fface, nFf * 8, cudaMemcpyDeviceToHost, s));
   MSASM_CUDA(cudaStreamSynchronize(s));
   return w.write(path, kTableTag);
+}
+
+extern "C" {
+
+msasm_status msasm_tables_save(const msasm_tables* tab, const char* path, void* stream) {
+  if (!tab || !path) return fail(MSASM_EINVAL, "tables or path is NULL");
+  try {
+    return tables_save_impl(tab, path, stream);
+  } catch (const std::bad_alloc&) {
+    return fail(MSASM_ENOMEM, "no host memory to stage the tables");
+  }
 }
 
 msasm_status msasm_tables_load(const char* path, void* stream, msasm_tables** out) {

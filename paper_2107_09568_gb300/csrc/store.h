@@ -10,6 +10,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -97,7 +98,12 @@ class StoreReader {
     long end = ok ? std::ftell(f) : -1;
     ok = ok && end >= here && uint64_t(end - here) == n + 8 && std::fseek(f, here, SEEK_SET) == 0;
     if (ok) {
-      buf_.resize(n);
+      try {
+        buf_.resize(n);
+      } catch (const std::bad_alloc&) {
+        std::fclose(f);
+        return fail(MSASM_ENOMEM, std::string("no host memory for the file: ") + path);
+      }
       ok = (n == 0 || std::fread(buf_.data(), 1, n, f) == n) && std::fread(&h, 8, 1, f) == 1;
     }
     std::fclose(f);

@@ -934,8 +934,7 @@ void msasm_surrogate_destroy(msasm_surrogate* sur) { delete sur; }
 // and continues training exactly as the saved one.
 static const char kSurrogateTag[8] = {'M', 'S', 'A', 'S', 'M', 'S', 'U', 'R'};
 
-msasm_status msasm_surrogate_save(const msasm_surrogate* sur, const char* path, void* stream) {
-  if (!sur || !path || !sur->mlp) return fail(MSASM_EINVAL, "surrogate or path is NULL");
+static msasm_status surrogate_save_impl(const msasm_surrogate* sur, const char* path, void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const msasm_mlp* n = sur->mlp;
   const int32_t head[7] = {sur->rank, sur->K, sur->n_nz, sur->n_train, sur->qd[0], sur->qd[1], sur->qd[2]};
@@ -968,6 +967,15 @@ msasm_status msasm_surrogate_save(const msasm_surrogate* sur, const char* path, 
   MSASM_CUDA(cudaMemcpyAsync(hw + 2 * P, n->d_v, size_t(P) * 4, cudaMemcpyDeviceToHost, s));
   MSASM_CUDA(cudaStreamSynchronize(s));
   return w.write(path, kSurrogateTag);
+}
+
+msasm_status msasm_surrogate_save(const msasm_surrogate* sur, const char* path, void* stream) {
+  if (!sur || !path || !sur->mlp) return fail(MSASM_EINVAL, "surrogate or path is NULL");
+  try {
+    return surrogate_save_impl(sur, path, stream);
+  } catch (const std::bad_alloc&) {
+    return fail(MSASM_ENOMEM, "no host memory to stage the surrogate");
+  }
 }
 
 msasm_status msasm_surrogate_load(const char* path, void* stream, msasm_surrogate** out) {
