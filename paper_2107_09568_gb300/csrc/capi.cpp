@@ -4,6 +4,7 @@
 #include <array>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -222,16 +223,16 @@ msasm_status msasm_build_tables_q3(const msasm_micro_desc* micro, const int32_t*
   if (!out || !q3) return fail(MSASM_EINVAL, "out or q3 is NULL");
   *out = nullptr;
   if (n_gauss > 16) return fail(MSASM_EINVAL, "n_gauss must be <= 16");
-  msasm_tables* tab = new msasm_tables();
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  msasm_status st = tables_init(micro, q3, n_gauss, s, tab);
-  if (st == MSASM_OK) st = build_table_gpu(tab, s);   // synchronises `s`
-  if (st != MSASM_OK) {
-    delete tab;
-    return st;
+  try {
+    std::unique_ptr<msasm_tables> tab(new msasm_tables());   // freed on an error or an exception
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    MSASM_TRY(tables_init(micro, q3, n_gauss, s, tab.get()));
+    MSASM_TRY(build_table_gpu(tab.get(), s));                // synchronises `s`
+    *out = tab.release();
+    return MSASM_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(MSASM_ENOMEM, "host allocation failed while building the tables");
   }
-  *out = tab;
-  return MSASM_OK;
 }
 
 msasm_status msasm_tables_info(const msasm_tables* tab, int32_t* n_T, int32_t* n_nz, int32_t* n_pi) {
@@ -258,18 +259,14 @@ msasm_status msasm_tables_copy(const msasm_tables* tab, double* d_table, int32_t
 
 void msasm_tables_destroy(msasm_tables* tab) { delete tab; }
 
-msasm_status msasm_plan_create(const msasm_tables* tab, const msasm_macro_desc* macro, int32_t max_tiles_per_pass,
-                               void* stream, msasm_plan** out, int64_t* n_rows, int64_t* nnz) {
-  if (!out) return fail(MSASM_EINVAL, "out is NULL");
-  *out = nullptr;
-  if (!tab || !macro) return fail(MSASM_EINVAL, "tables or macro descriptor is NULL");
+static msasm_status plan_create_impl(const msasm_tables* tab, const msasm_macro_desc* macro,
+                                     int32_t max_tiles_per_pass, void* stream, msasm_plan** out, int64_t* n_rows,
+                                     int64_t* nnz) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  msasm_plan* plan = new msasm_plan();
+  std::unique_ptr<msasm_plan> guard(new msasm_plan());   // freed on every early return or exception
+  msasm_plan* plan = guard.get();
   plan->tab = tab;
-  auto bail = [&](msasm_status st) {
-    delete plan;
-    return st;
-  };
+  auto bail = [&](msasm_status st) { return st; };
   std::vector<double> basis[3];
   std::vector<int32_t> first[3];
   for (int d = 0; d < 3; ++d) {
@@ -456,8 +453,20 @@ msasm_status msasm_plan_create(const msasm_tables* tab, const msasm_macro_desc* 
   plan->gmap_host = std::move(gmap);
   if (n_rows) *n_rows = plan->n_rows;
   if (nnz) *nnz = plan->nnz;
-  *out = plan;
+  *out = guard.release();
   return MSASM_OK;
+}
+
+msasm_status msasm_plan_create(const msasm_tables* tab, const msasm_macro_desc* macro, int32_t max_tiles_per_pass,
+                               void* stream, msasm_plan** out, int64_t* n_rows, int64_t* nnz) {
+  if (!out) return fail(MSASM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!tab || !macro) return fail(MSASM_EINVAL, "tables or macro descriptor is NULL");
+  try {
+    return plan_create_impl(tab, macro, max_tiles_per_pass, stream, out, n_rows, nnz);
+  } catch (const std::bad_alloc&) {
+    return fail(MSASM_ENOMEM, "host allocation failed while building the plan");
+  }
 }
 
 msasm_status msasm_plan_info(const msasm_plan* plan, int64_t* n_tiles, int64_t* n_points, int64_t* n_rows,
