@@ -13,6 +13,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <memory>
 #include <random>
 #include <vector>
 
@@ -615,11 +616,10 @@ msasm_status msasm_mlp_train(msasm_mlp* n, const float* d_x, const float* d_t, i
 void msasm_mlp_destroy(msasm_mlp* n) { delete n; }
 
 // ------------------------------------------------------------------ surrogate
-msasm_status msasm_surrogate_create(const msasm_tables* const* tables, const double* widths, int32_t n_tables,
-                                    const double* d_coef_samples, int64_t n_sample_rows, int32_t rank, int32_t hidden,
-                                    int32_t power_iters, uint64_t seed, void* stream, msasm_surrogate** out) {
-  if (!out) return fail(MSASM_EINVAL, "out is NULL");
-  *out = nullptr;
+static msasm_status surrogate_create_impl(const msasm_tables* const* tables, const double* widths,
+                                          int32_t n_tables, const double* d_coef_samples, int64_t n_sample_rows,
+                                          int32_t rank, int32_t hidden, int32_t power_iters, uint64_t seed,
+                                          void* stream, msasm_surrogate** out) {
   if (!tables || !widths || n_tables < 2 || !d_coef_samples || n_sample_rows <= 0 || rank <= 0 || rank > 64)
     return fail(MSASM_EINVAL, "surrogate: need >= 2 tables, coefficient samples and 1 <= rank <= 64");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -630,16 +630,14 @@ msasm_status msasm_surrogate_create(const msasm_tables* const* tables, const dou
       return fail(MSASM_EINVAL, "surrogate: all tables must share topology and q");
   const int over = 8, r_s = rank + over;                  // sketch width
   const int64_t J = int64_t(n_tables) * n_sample_rows;     // columns of M = [T_k C^T]
-  msasm_surrogate* sur = new msasm_surrogate();
+  std::unique_ptr<msasm_surrogate> guard(new msasm_surrogate());   // freed on an error or an exception
+  msasm_surrogate* sur = guard.get();
   sur->rank = rank;
   for (int d = 0; d < 3; ++d) sur->qd[d] = tables[0]->qd[d];
   sur->K = K;
   sur->n_nz = n_nz;
   sur->n_train = n_tables;
-  auto bail = [&](msasm_status st) {
-    delete sur;
-    return st;
-  };
+  auto bail = [&](msasm_status st) { return st; };
   double *Mt = nullptr, *M = nullptr, *Om = nullptr, *Yt = nullptr, *Qt = nullptr, *Zt = nullptr, *Gd = nullptr,
          *Sd = nullptr, *Ud = nullptr, *Tt = nullptr, *Vk = nullptr;
   auto release = [&]() {
@@ -773,8 +771,21 @@ msasm_status msasm_surrogate_create(const msasm_tables* const* tables, const dou
   if (st != MSASM_OK) return bail(st);
   st = msasm_mlp_create(n_out, hidden, seed, &sur->mlp);
   if (st != MSASM_OK) return bail(st);
-  *out = sur;
+  *out = guard.release();
   return MSASM_OK;
+}
+
+msasm_status msasm_surrogate_create(const msasm_tables* const* tables, const double* widths, int32_t n_tables,
+                                    const double* d_coef_samples, int64_t n_sample_rows, int32_t rank, int32_t hidden,
+                                    int32_t power_iters, uint64_t seed, void* stream, msasm_surrogate** out) {
+  if (!out) return fail(MSASM_EINVAL, "out is NULL");
+  *out = nullptr;
+  try {
+    return surrogate_create_impl(tables, widths, n_tables, d_coef_samples, n_sample_rows, rank, hidden, power_iters,
+                                 seed, stream, out);
+  } catch (const std::bad_alloc&) {
+    return fail(MSASM_ENOMEM, "host allocation failed while fitting the surrogate");
+  }
 }
 
 msasm_status msasm_surrogate_train(msasm_surrogate* sur, int32_t steps, float lr, float* h_loss, void* stream) {
