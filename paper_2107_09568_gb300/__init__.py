@@ -485,7 +485,7 @@ def cg_solve(K, f, fixed_dofs, tol=1e-12, max_iter=20000, x0=None, replace_every
             if rn < tol:
                 break
             # the true residual has reached its rounding floor (about eps |K| |u| / |f|); the
-            # CG residual is not monotone, so this is only judged once it is small
+            # CG residual is not monotone, so this is only checked once it is small
             best, stall = (rn, 0) if rn < 0.5 * best else (best, stall + 1)
             if stall >= 8 and rn < 1e-8:
                 break

@@ -88,7 +88,7 @@ def surrogate(flush, nx=20, ny=10, nz=10, steps=(4000, 3000, 3000)):
     t_train = time.perf_counter() - t0
     dw = torch.tensor(widths, device="cuda")
     k_sur, ms_sur = _timed(lambda: sur.assemble(plan, ctrl, dw), reps=5, flush=flush)
-    # per-width quadrature: one table per tile (error judge and the method without the network)
+    # per-width quadrature: one table per tile (the error reference and the method without the network)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     nzd = torch.empty((plan.n_tiles, base.n_nz, 3, 3), dtype=torch.float64, device="cuda")

@@ -81,7 +81,7 @@ def _graded_setup(nx=6, ny=3, nz=3):
 def test_surrogate_against_per_width_quadrature_and_gain():
     """A quarter arc of 6x3x3 tiles with strut widths from the sinusoidal field in [0.15, 0.40]:
     the surrogate (trained on 64 quadrature tables) against the per-width quadrature assembly (the
-    method with one table per tile, the error judge), and what it gains over the method without it:
+    method with one table per tile, the error reference), and what it gains over the method without it:
     one table at the mean width for every tile, or the nearest of the 64 training tables."""
     m, widths, w_train = _graded_setup()
     ctrl = torch.tensor(m.ctrl, device="cuda")
@@ -103,7 +103,7 @@ def test_surrogate_against_per_width_quadrature_and_gain():
         sur.assemble(plan, ctrl, dw, out=k_sur)
     torch.cuda.synchronize()
     t_sur = (time.perf_counter() - t0) / 3
-    # per-width quadrature: one table per tile (the error judge)
+    # per-width quadrature: one table per tile (the error reference)
     t0 = time.perf_counter()
     nz = torch.empty((plan.n_tiles, base.n_nz, 3, 3), dtype=torch.float64, device="cuda")
     for t in range(plan.n_tiles):
@@ -132,7 +132,7 @@ def test_surrogate_against_per_width_quadrature_and_gain():
 
 
 def _per_width_assembly(plan, macro_ctrl, coef, widths, base_n_nz):
-    """The method without the network: one quadrature table per tile (the error judge)."""
+    """The method without the network: one quadrature table per tile (the error reference)."""
     nz = torch.empty((plan.n_tiles, base_n_nz, 3, 3), dtype=torch.float64, device="cuda")
     for t in range(plan.n_tiles):
         tab_t = msasm.Tables(synth.micro_cross(3, float(widths[t])), 3)
