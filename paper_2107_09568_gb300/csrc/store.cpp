@@ -76,6 +76,8 @@ msasm_status msasm_tables_load(const char* path, void* stream, msasm_tables** ou
     if (!r.get(sizes[i])) return bad("sizes");
   for (int i = 0; i < 7; ++i)
     if (!r.get(face_off[i])) return bad("face offsets");
+  for (int d = 0; d < 3; ++d)
+    if (sizes[d] < 0 || sizes[d] > 5) return bad("projection degrees outside 0..5");
   msasm_micro_desc micro;
   micro.n_patches = n_patches;
   micro.degree = degree.data();

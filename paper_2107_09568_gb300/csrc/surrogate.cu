@@ -1004,7 +1004,8 @@ msasm_status msasm_surrogate_load(const char* path, void* stream, msasm_surrogat
   ok = ok && r.get(w0) && r.get(ws) && r.get(scale) && r.get(shape[0]) && r.get(shape[1]) && r.get(P) && r.get(step);
   if (!ok) return bad("header");
   const int rank = head[0], K = head[1], n_nz = head[2], n_train = head[3];
-  if (rank < 1 || rank > 64 || K < 1 || n_nz < 1 || n_train < 2 || shape[1] != rank * K) return bad("sizes");
+  if (rank < 1 || rank > 64 || K < 1 || K > 9 * 216 || n_nz < 1 || n_train < 2 || shape[1] != rank * K)
+    return bad("sizes");
   for (int d = 0; d < 3; ++d)
     if (head[4 + d] < 0 || head[4 + d] > 5) return bad("degrees");
   if (shape[0] <= 0 || shape[0] > 1024 || (shape[0] % 2) || int64_t(MlpLayout(shape[0], shape[1]).total) != P)
