@@ -151,6 +151,9 @@ def test_stored_files_are_checked_before_any_cuda_call(tmp_path):
     assert status(good) == _lib.EIO and b"truncated" in lib.msasm_last_error()
     _store_file(good, b"MSASMTAB", struct.pack("<i", 40))
     assert status(good) == _lib.EIO and b"patch count" in lib.msasm_last_error()
+    bad_q = struct.pack("<7i", 9, 1, 1, 0, 27, 378, 8) + struct.pack("<7q", *range(7))
+    _store_file(good, b"MSASMTAB", desc + bad_q + b"\0" * 64)
+    assert status(good) == _lib.EIO and b"degrees" in lib.msasm_last_error()
     # surrogate files
     assert status(tmp_path / "missing", lib.msasm_surrogate_load) == _lib.EIO
     _store_file(good, b"MSASMSUR", struct.pack("<7i", 0, 576, 100, 8, 3, 3, 3))
