@@ -155,6 +155,9 @@ msasm_plan::~msasm_plan() {
   cudaFree(d_values_stage);
   for (cudaEvent_t e : events) cudaEventDestroy(e);
   for (cudaEvent_t e : copy_events) cudaEventDestroy(e);
+  for (cudaEvent_t e : scatter_ev)
+    if (e) cudaEventDestroy(e);
+  if (scatter_side) cudaStreamDestroy(scatter_side);
   for (int k = 0; k < 2; ++k)
     if (copy_stream[k]) cudaStreamDestroy(copy_stream[k]);
 }
@@ -450,6 +453,8 @@ static msasm_status plan_create_impl(const msasm_tables* tab, const msasm_macro_
   if (bad)
     return bail(fail(MSASM_ECUDA, "index map: a tile pair is missing from the CSR pattern, or a tile places its "
                                   "blocks differently from its type"));
+  MSASM_CUDA(cudaStreamCreateWithFlags(&plan->scatter_side, cudaStreamNonBlocking));
+  for (cudaEvent_t& e : plan->scatter_ev) MSASM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   plan->gmap_host = std::move(gmap);
   if (n_rows) *n_rows = plan->n_rows;
   if (nnz) *nnz = plan->nnz;

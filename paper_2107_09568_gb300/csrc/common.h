@@ -83,6 +83,7 @@ static_assert(sizeof(SecondaryEntry) == 32, "SecondaryEntry is 32 bytes");
 // layout depends only on the tile's type (which faces are glued), so one value map per type
 // tells, for every value of the range, where it comes from in the tile's nzdata
 constexpr int kScatterSegment = 4096;     // values of one chunk of a tile's owned range (one CTA)
+constexpr int kScatterPieces = 8;         // direct-pass pieces whose secondary pass runs on a second stream
 inline int ld_nz_of(int n_nz) { return (n_nz + 7) & ~7; }   // leading dimension of nzdata rows
 struct ScatterPlanHost {
   std::vector<int32_t> tile_type;          // per tile
@@ -176,6 +177,9 @@ struct msasm_plan {
   std::vector<int64_t> tile_vbase;    // host: first value index of the rows owned by tile t (n_tiles + 1)
   std::vector<int64_t> tile_pbase;    // host: first global point id owned by tile t (n_tiles + 1)
   cudaStream_t copy_stream[2] = {nullptr, nullptr};   // device->host copies of msasm_assemble_host
+  // second stream of the scatter: the secondary pass of each finished piece of the direct pass
+  cudaStream_t scatter_side = nullptr;
+  cudaEvent_t scatter_ev[msasm::kScatterPieces + 1] = {};
   std::vector<cudaEvent_t> copy_events;
   // scratch
   double* d_coef = nullptr;         // 9 tiles_per_pass x 9 n_pi, FP64

@@ -237,28 +237,55 @@ template <typename T>
 msasm_status scatter_pass_gpu(const msasm_plan* plan, const T* d_nz, int ld_nz, int64_t t0, int64_t n_tiles,
                               T* d_values, int64_t direct_end, int64_t v_lo, int64_t v_hi, cudaStream_t stream) {
   const int64_t td = std::max(t0, std::min(t0 + n_tiles, direct_end));
-  if (td > t0) {
-    // chunks of the largest type: CTAs of chunks a tile's type does not have return at once
-    int n_chunks = 1;
-    for (size_t ty = 0; ty + 1 < plan->type_map_off_host.size(); ++ty) {
-      const int64_t nv = plan->type_map_off_host[ty + 1] - plan->type_map_off_host[ty];
-      n_chunks = std::max<int>(n_chunks, int((nv + kScatterSegment - 1) / kScatterSegment));
-    }
+  // chunks of the largest type: CTAs of chunks a tile's type does not have return at once
+  int n_chunks = 1;
+  for (size_t ty = 0; ty + 1 < plan->type_map_off_host.size(); ++ty) {
+    const int64_t nv = plan->type_map_off_host[ty + 1] - plan->type_map_off_host[ty];
+    n_chunks = std::max<int>(n_chunks, int((nv + kScatterSegment - 1) / kScatterSegment));
+  }
+  auto direct = [&](int64_t ta, int64_t tb) -> msasm_status {
+    if (tb <= ta) return MSASM_OK;
     constexpr int R = sizeof(T) == 8 ? kDirectRun64 : kDirectRun32;
-    const int64_t grid = (td - t0 + R - 1) / R * n_chunks;
+    const int64_t grid = (tb - ta + R - 1) / R * n_chunks;
     if (grid > 2147483647LL) return fail(MSASM_EUNSUPPORTED, "too many scatter chunks for one launch");
     scatter_direct_kernel<T, R><<<unsigned(grid), kDirectThreads, 0, stream>>>(
-        d_nz, ld_nz, t0, t0, td, n_chunks, plan->d_tile_type, plan->d_tile_vbase, plan->d_type_map_off,
+        d_nz, ld_nz, t0, ta, tb, n_chunks, plan->d_tile_type, plan->d_tile_vbase, plan->d_type_map_off,
         plan->d_type_nvals, plan->d_maps, d_values, v_lo);
     MSASM_CUDA(cudaGetLastError());
-  }
-  const int64_t e0 = plan->sec_off_host[size_t(t0)], e1 = plan->sec_off_host[size_t(t0 + n_tiles)];
-  if (e1 > e0) {
+    return MSASM_OK;
+  };
+  auto secondary = [&](int64_t ta, int64_t tb, cudaStream_t s) -> msasm_status {
+    const int64_t e0 = plan->sec_off_host[size_t(ta)], e1 = plan->sec_off_host[size_t(tb)];
+    if (e1 <= e0) return MSASM_OK;
     const int64_t blocks = std::min<int64_t>((e1 - e0 + 255) / 256, 152 * 16);
-    scatter_secondary_kernel<T><<<unsigned(blocks), 256, 0, stream>>>(d_nz, ld_nz, t0, e0, e1, plan->d_sec, d_values,
-                                                                      v_lo, v_hi);
+    scatter_secondary_kernel<T><<<unsigned(blocks), 256, 0, s>>>(d_nz, ld_nz, t0, e0, e1, plan->d_sec, d_values, v_lo,
+                                                                 v_hi);
     MSASM_CUDA(cudaGetLastError());
+    return MSASM_OK;
+  };
+  const bool overlap = plan->scatter_side != nullptr && td - t0 >= int64_t(kScatterPieces) * 64 &&
+                       plan->sec_off_host[size_t(t0 + n_tiles)] > plan->sec_off_host[size_t(t0)];
+  if (!overlap) {
+    MSASM_TRY(direct(t0, td));
+    return secondary(t0, t0 + n_tiles, stream);
   }
+  // The direct pass in pieces of consecutive tiles on the caller's stream; the secondary entries of a
+  // piece's tiles add to rows of those or lower tiles, all written once the piece is done, while the
+  // next pieces write rows of higher tiles only: so each piece's secondary pass runs on a second
+  // stream beside the next piece's direct pass (each value has at most one secondary contribution,
+  // so the secondary launches never touch the same value).
+  int64_t prev = t0;
+  for (int k = 0; k < kScatterPieces; ++k) {
+    const int64_t b = t0 + (td - t0) * (k + 1) / kScatterPieces;
+    MSASM_TRY(direct(prev, b));
+    MSASM_CUDA(cudaEventRecord(plan->scatter_ev[k], stream));
+    MSASM_CUDA(cudaStreamWaitEvent(plan->scatter_side, plan->scatter_ev[k], 0));
+    MSASM_TRY(secondary(prev, b, plan->scatter_side));
+    prev = b;
+  }
+  MSASM_TRY(secondary(td, t0 + n_tiles, plan->scatter_side));   // halo tiles above a range
+  MSASM_CUDA(cudaEventRecord(plan->scatter_ev[kScatterPieces], plan->scatter_side));
+  MSASM_CUDA(cudaStreamWaitEvent(stream, plan->scatter_ev[kScatterPieces], 0));   // joined before return
   return MSASM_OK;
 }
 
