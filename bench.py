@@ -449,6 +449,8 @@ def roofline_of(stage_avg, prec, tab, n_tiles, nnz, pk, pk_kind, workload):
         roof = {"kernel": names[dom], "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / pk["hbm_gbs"], "traffic": None, "peak_source": pk_kind}
     tr = NCU_TRAFFIC.get((roof["kernel"], workload, prec))
+    if tr is not None and n_tiles != workload_config(workload)["tiles"]:
+        tr = None          # captured on one launch over the whole workload, not this rank's slab and halo
     if tr is not None:
         if tr[2] == kernel_source_digest(roof["kernel"]):
             roof["traffic"] = tr[0]
