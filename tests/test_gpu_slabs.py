@@ -42,6 +42,21 @@ def test_beam1000_two_slabs_bit_identical(prec):
     _check_slabs(plan, ctrl, prec, 2, m.n_elem)
 
 
+@pytest.mark.parametrize("prec", ["f64_emu", "f32"])
+def test_long_range_with_overlapped_secondary_pass(prec):
+    """A range of 640 tiles with its halo and a value window: the scatter's direct pass runs in pieces
+    with the secondary pass on a second stream (512 tiles and more), as in the whole-mesh assembly
+    of the 1000 tiles, and both give the same values bit for bit."""
+    m = synth.macro_twisted_beam(10, 10, 10)
+    tab, plan = _plan(m, 3, 3)
+    ctrl = torch.tensor(m.ctrl, device="cuda")
+    whole = plan.assemble(ctrl, 1.0, 0.3, prec)
+    for t0, t1 in ((0, 640), (640, 1000), (100, 900)):
+        r0, r1, v0, v1, he = plan.range(t0, t1)
+        part = plan.assemble_range(ctrl, t0, t1, 1.0, 0.3, prec)
+        assert torch.equal(part, whole[v0:v1]), (prec, t0, t1)
+
+
 @pytest.mark.parametrize("prec,per_pass,world", [("f64", 0, 3), ("f32", 2, 4), ("f64_emu", 1, 5), ("tf32x3", 3, 2)])
 def test_ragged_mesh_uneven_ranges_in_passes(prec, per_pass, world):
     """Ranges that end mid-layer, scratch for fewer tiles than a range plus its halo."""
